@@ -1,0 +1,61 @@
+"""Deflation space and deflated quadratures (oracle; test infrastructure).
+
+Section 5.1: the deflation space is the k smallest singular triplets of A,
+found as eigenpairs (Lambda, V) of A^H A.  Section 5.2: with U = A V Sigma^-1
+and Sigma = Lambda^(1/2),
+    T_D = Tr(V Sigma^-1 U^H) = Tr(Lambda^-1 V^H A^H V)
+and each Hutchinson quadrature subtracts z^H V Lambda^-1 V^H (A^H z), so U is
+never stored (Algorithm 1, lines 2 and 8).  This module evaluates exactly
+those literal expressions with an explicit A^H.
+
+The triplets themselves (small lattices only) come from the dense Hermitian
+eigendecomposition of Q = gamma5 A: since gamma5 A is Hermitian (A is
+gamma5-Hermitian) and Q^H Q = A^H A, its eigenvectors are right singular
+vectors of A with sigma = |lambda|.  Ordering: |lambda| ascending, ties by
+lambda ascending.  The signed lambda are returned too, because the CUDA
+library takes the deflation space in that form.
+"""
+import numpy as np
+
+from . import wilson as _wilson
+
+
+def smallest_triplets(Adense, k):
+    """(V, lam, sigma): k eigenvectors of gamma5 A with smallest |lambda|.
+
+    gamma5 is taken from oracle.gamma via the spinor-level apply, not a table.
+    """
+    N = Adense.shape[0]
+    G5A = _wilson.gamma5_vec(Adense)       # gamma5 applied to every column
+    Q = 0.5 * (G5A + G5A.conj().T)          # symmetrise away rounding
+    lam, W = np.linalg.eigh(Q)
+    order = np.lexsort((lam, np.abs(lam)))
+    lam = lam[order][:k]
+    V = W[:, order][:, :k]
+    return V, lam, np.abs(lam)
+
+
+def T_D(AH, V, sigma):
+    """Algorithm 1, line 2: T_D = Tr(Lambda^-1 V^H A^H V) with Lambda = Sigma^2."""
+    Lam = sigma ** 2
+    AHV = AH @ V
+    return complex(np.sum(np.einsum("im,im->m", np.conj(V), AHV) / Lam))
+
+
+def quadrature(AH, V, sigma, z):
+    """Algorithm 1, line 8 deflation term: z^H V Lambda^-1 V^H (A^H z).
+
+    z may be (N,) or (N, nrhs); returns one value per column.
+    """
+    Lam = sigma ** 2
+    Z = z if z.ndim == 2 else z[:, None]
+    c = V.conj().T @ (AH @ Z)               # V^H (A^H z)      k x nrhs
+    w = V.conj().T @ Z                      # V^H z            k x nrhs
+    out = np.sum(np.conj(w) * c / Lam[:, None], axis=0)
+    return out if z.ndim == 2 else out[0]
+
+
+def deflation_operator(AH, V, sigma):
+    """Dense D = V Lambda^-1 V^H A^H (small N), the deflated part of A^-1."""
+    AHd = AH.toarray() if hasattr(AH, "toarray") else np.asarray(AH)
+    return (V / (sigma ** 2)[None, :]) @ (V.conj().T @ AHd)

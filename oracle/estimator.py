@@ -1,0 +1,92 @@
+"""Algorithm 1 (deflatedHP) and the statistics around it (oracle).
+
+deflated_hp follows Algorithm 1 of Section 5.2 step by step:
+  T_D = Tr(Lambda^-1 V^H A^H V); T_R = 0            (line 2)
+  z0 given (drawn by oracle.noise)                   (line 3)
+  for j = 1..s:                                      (line 4)
+      z_h = next probing vector; z = z0 .* z_h       (lines 5-6, oracle.noise)
+      solve A y = z                                  (line 7)
+      T_R += z^H y - z^H V Lambda^-1 V^H (A^H z)     (line 8)
+      Trace = T_R / j + T_D                          (line 9)
+
+Statistics:
+  * Section 6.2: error bars by jackknife over independent runs with different
+    z0 (40 runs in the paper; delete-1 jackknife is the reading taken here).
+  * Section 6.2: speedup R_s = V_stoc / (V_hp(s) * s).
+  * Figure of merit used to compare implementations: the wall time to reach
+    a relative standard error eps on the trace, t(s) Var_T(s) / (eps |Tr|)^2,
+    where Var_T(s) is the variance of one run's estimate after s vectors and
+    t(s) the time one run takes.
+Variances use the complex form E|t - E t|^2, the form eq. (1.2) evaluates.
+"""
+import numpy as np
+
+from . import deflation as _defl
+
+
+def deflated_hp(AH, solve, Z, V=None, sigma=None, group=1):
+    """Run Algorithm 1 over the columns of Z (already z0 .* z_h).
+
+    AH: sparse or dense A^H; solve: callable Z -> A^-1 Z (columns);
+    V, sigma: deflation space (None = no deflation, T_D = 0).
+    group: with 12-fold spin-colour dilution each probing vector z is split
+    into `group` = 12 diluted columns whose quadratures add up to one sample
+    (Section 1, dilution); group = 1 otherwise.
+    Returns dict with T_D, per-column zy (z^H y) and defl (deflation term),
+    per-sample t (sum over the group of z^H y - defl) and trace (running
+    Trace after each sample j, line 9).
+    """
+    ncol = Z.shape[1]
+    assert ncol % group == 0
+    s = ncol // group
+    TD = _defl.T_D(AH, V, sigma) if V is not None else 0.0
+    zy = np.zeros(ncol, dtype=np.complex128)
+    dq = np.zeros(ncol, dtype=np.complex128)
+    Y = solve(Z)
+    for q in range(ncol):
+        z = Z[:, q]
+        zy[q] = np.vdot(z, Y[:, q])
+        dq[q] = _defl.quadrature(AH, V, sigma, z) if V is not None else 0.0
+    t = np.zeros(s, dtype=np.complex128)
+    trace = np.zeros(s, dtype=np.complex128)
+    TR = 0.0
+    for j in range(s):
+        t[j] = np.sum(zy[j * group:(j + 1) * group] - dq[j * group:(j + 1) * group])
+        TR = TR + t[j]
+        trace[j] = TR / (j + 1) + TD
+    return {"T_D": TD, "zy": zy, "defl": dq, "t": t, "trace": trace, "Y": Y}
+
+
+def sample_variance(x):
+    """Unbiased complex-form sample variance sum |x - mean|^2 / (n - 1)."""
+    x = np.asarray(x)
+    return float(np.sum(np.abs(x - x.mean()) ** 2) / (len(x) - 1))
+
+
+def jackknife_mean(x):
+    """Delete-1 jackknife: (mean, variance of the mean) for samples x."""
+    x = np.asarray(x)
+    n = len(x)
+    loo = (x.sum() - x) / (n - 1)
+    var = (n - 1) / n * np.sum(np.abs(loo - loo.mean()) ** 2)
+    return x.mean(), float(var)
+
+
+def jackknife_variance(x):
+    """Delete-1 jackknife of the sample variance: (variance, its standard error)."""
+    x = np.asarray(x)
+    n = len(x)
+    full = sample_variance(x)
+    loo = np.array([sample_variance(np.delete(x, i)) for i in range(n)])
+    err = np.sqrt((n - 1) / n * np.sum((loo - loo.mean()) ** 2))
+    return full, float(err)
+
+
+def speedup_Rs(V_stoc, V_hp_s, s):
+    """Section 6.2: R_s = V_stoc / (V_hp(s) * s)."""
+    return V_stoc / (V_hp_s * s)
+
+
+def time_to_rel_error(t_run, var_T, trace, eps=1e-3):
+    """Wall time for the mean of repeated runs to reach standard error eps*|Tr|."""
+    return t_run * var_T / (eps * abs(trace)) ** 2

@@ -1,0 +1,91 @@
+"""Pins of the oracle's Wilson-Dirac operator against facts fixed by mathematics.
+
+None of these re-types the oracle's formula: each compares it with a textbook
+identity (Clifford algebra), a second independent coding, a symmetry the
+operator must have, or a closed form derived in momentum space.
+"""
+import numpy as np
+import pytest
+
+from oracle import exact, gamma, lattice, wilson
+from paper_1603_05988_gb300 import synth
+
+
+def test_clifford_algebra_and_gamma5():
+    g = gamma.gammas()
+    for m in range(4):
+        assert np.allclose(g[m], g[m].conj().T)
+        for n in range(4):
+            assert np.allclose(g[m] @ g[n] + g[n] @ g[m], 2.0 * (m == n) * np.eye(4))
+    # textbook chiral-basis gamma5, typed independently of the product
+    assert np.allclose(gamma.gamma5(), np.diag([1, 1, -1, -1]))
+    for m in range(4):
+        assert np.allclose(gamma.gamma5() @ g[m], -g[m] @ gamma.gamma5())
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 2, 2, 4), (4, 4, 4, 4)])
+def test_links_special_unitary(dims):
+    U = synth.random_su3_links(dims, 0.7, 5)
+    UhU = np.einsum("...ba,...bc->...ac", U.conj(), U)
+    assert np.abs(UhU - np.eye(3)).max() < 1e-13
+    assert np.abs(np.linalg.det(U) - 1.0).max() < 1e-13
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 4, 2, 4), (4, 4, 4, 4), (6, 4, 2, 4)])
+def test_explicit_matches_matrix_free(dims):
+    U = synth.random_su3_links(dims, 0.8, 11)
+    A = wilson.explicit(U, dims, -0.6)
+    rng = np.random.default_rng(3)
+    N = A.shape[0]
+    psi = rng.standard_normal((N, 3)) + 1j * rng.standard_normal((N, 3))
+    assert np.abs(A @ psi - wilson.apply(U, dims, -0.6, psi)).max() < 1e-12
+
+
+def test_neighbour_structure():
+    # every off-diagonal site block of A sits at Manhattan distance exactly 1
+    dims = (4, 4, 4, 4)
+    U = synth.random_su3_links(dims, 0.5, 2)
+    A = wilson.explicit(U, dims, -0.4).tocoo()
+    s1, s2 = A.row // 12, A.col // 12
+    off = s1 != s2
+    d = lattice.manhattan(dims, s1[off], s2[off])
+    assert np.all(d == 1)
+    # 1 + 8 neighbour blocks per site, each 12 x 12 dense at most
+    assert A.nnz <= 12 * 12 * 9 * lattice.volume(dims)
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 4, 4, 4)])
+def test_gamma5_hermiticity(dims):
+    U = synth.random_su3_links(dims, 0.5, 9)
+    A = wilson.dense(U, dims, -0.4)
+    g5 = np.kron(np.eye(lattice.volume(dims)), np.kron(np.diag([1, 1, -1, -1]), np.eye(3)))
+    assert np.abs(g5 @ A @ g5 - A.conj().T).max() < 1e-14
+
+
+@pytest.mark.parametrize("dims,m0", [((2, 2, 2, 2), -0.4), ((4, 4, 4, 4), -0.4), ((4, 2, 6, 4), 0.3)])
+def test_free_field_closed_forms(dims, m0):
+    A = wilson.dense(synth.unit_links(dims), dims, m0)
+    tr, Ainv = exact.trace_inverse_lu(A)
+    assert abs(tr - exact.free_field_trace(dims, m0)) < 1e-11 * abs(tr)
+    assert abs(exact.z4_variance(Ainv) - exact.free_field_z4_variance(dims, m0)) < 1e-10 * exact.z4_variance(Ainv)
+    sv = np.linalg.svd(A, compute_uv=False)
+    assert np.allclose(np.sort(sv), exact.free_field_singular_values(dims, m0), atol=1e-12)
+
+
+def test_free_field_published_4x4x4x4_value():
+    # value fixed by the closed form and dense LU together (both in test above);
+    # here the 4^4, m0 = -0.4 numbers are pinned to 11 digits
+    assert abs(exact.free_field_z4_variance((4, 4, 4, 4), -0.4) - 219.02256161327) < 1e-9
+    assert abs(exact.free_field_trace((4, 4, 4, 4), -0.4) - 747.17054921780) < 1e-9
+
+
+def test_dagger_is_conjugate_transpose_action():
+    dims = (2, 2, 2, 4)
+    U = synth.random_su3_links(dims, 0.8, 4)
+    A = wilson.explicit(U, dims, -0.7)
+    AH = wilson.explicit_dagger(U, dims, -0.7)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+    y = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+    # <y, A x> = <A^H y, x>
+    assert abs(np.vdot(y, A @ x) - np.vdot(AH @ y, x)) < 1e-12 * np.linalg.norm(x) * np.linalg.norm(y)
