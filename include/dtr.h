@@ -1,0 +1,242 @@
+/*
+ * dtr.h -- C ABI of libdtr: the deflated Hutchinson estimator of Tr(A^-1) for
+ * the 4D Wilson-Dirac matrix A on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Gambhir, Stathopoulos & Orginos, "Deflation as a method of variance
+ * reduction for estimating the trace of a matrix inverse" (arXiv:1603.05988),
+ * Algorithm 1 (deflatedHP), Section 5.2.  Each entry point below names the
+ * passage that defines the operation it performs.
+ *
+ * ---------------------------------------------------------------- conventions
+ * Lattice      periodic, dims = {Lx, Ly, Lz, Lt}, every extent even;
+ *              site = x + Lx*(y + Ly*(z + Lz*t)); V = Lx*Ly*Lz*Lt.
+ * Spinor field complex128 stored as interleaved (re, im) doubles; N = 12 V
+ *              degrees of freedom, dof i = 12*site + 3*spin + colour
+ *              (4 spins x 3 colours per site, Section 1).  A block of nrhs
+ *              fields is column-major N x nrhs: complex element (i, j) at
+ *              complex offset j*N + i.
+ * Links        complex128, U[site][mu][a][b] (row a, column b of the SU(3)
+ *              matrix U_mu(site)), mu = 0..3 <-> x, y, z, t: 4*V*9 complex.
+ * Operator     (A psi)(x) = (4 + m0) psi(x)
+ *                  - 1/2 sum_mu [ (1 - gamma_mu) U_mu(x) psi(x + mu)
+ *                               + (1 + gamma_mu) U_mu(x - mu)^H psi(x - mu) ]
+ *              with the chiral basis gamma_k = [[0, -i s_k], [i s_k, 0]]
+ *              (k = x, y, z; s_k Pauli), gamma_t = [[0, 1], [1, 0]],
+ *              gamma_5 = diag(1, 1, -1, -1).  A is gamma_5-Hermitian:
+ *              A^H = gamma_5 A gamma_5.
+ *
+ * Ownership    Vectors passed to an entry point are caller-owned memory; the
+ *              library never frees them.  Pointers documented as "device"
+ *              must be device memory (or managed) of the current device;
+ *              "host" pointers are ordinary host memory.  Handles
+ *              (dtr_lattice, dtr_gauge, dtr_defl) are opaque, own their
+ *              device memory and are released with the matching
+ *              dtr_destroy_* call.  Workspace is caller-owned device memory
+ *              of at least the size the matching *_workspace_bytes call
+ *              returns; its contents are scratch between calls.
+ * Streams      `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *              default stream).  Work is stream-ordered; calls that return
+ *              host values synchronise that stream before returning.
+ * Errors       every int-returning call returns DTR_OK (0) or one of the
+ *              DTR_E* codes; dtr_last_error() returns a message for the most
+ *              recent failure on the calling thread.  No call aborts, traps
+ *              or throws across the ABI.
+ * Threads      handles may be shared between threads only for read-only use
+ *              (concurrent calls that use one workspace race).
+ */
+#ifndef DTR_H
+#define DTR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DTR_OK 0
+#define DTR_EINVAL 1     /* bad argument (null pointer, size, unsupported combination) */
+#define DTR_ENOMEM 2     /* device allocation by a handle failed, or workspace too small */
+#define DTR_ECUDA 3      /* a CUDA runtime call failed; message has the CUDA error */
+#define DTR_ENOTCONV 4   /* solver hit maxiter; results and per-RHS stats still written */
+#define DTR_ENAN 5       /* NaN/Inf met in a residual norm; per-RHS stats still written */
+
+typedef struct dtr_lattice_s *dtr_lattice;
+typedef struct dtr_gauge_s *dtr_gauge;
+typedef struct dtr_defl_s *dtr_defl;
+
+/* Storage precision of a field or of the deflation space. */
+typedef enum { DTR_F64 = 0, DTR_F32 = 1, DTR_BF16 = 2, DTR_F16 = 3 } dtr_prec;
+
+/* Krylov solver for A y = z (Algorithm 1, line 7; the paper does not name one). */
+typedef enum {
+  DTR_SOLVER_BICGSTAB_F64 = 0,   /* plain FP64 BiCGStab */
+  DTR_SOLVER_MIXED_F32 = 1       /* FP32 BiCGStab inner solves inside FP64 defect correction */
+} dtr_solver;
+
+/* Message of the last failure on this thread ("" if none).  Never NULL. */
+const char *dtr_last_error(void);
+
+/* Library version string. */
+const char *dtr_version(void);
+
+/* ------------------------------------------------------------------ lattice */
+/* Describe a periodic 4D lattice (Section 6: 4D lattice, 12 dof per site).
+ * dims: host array of 4 positive even extents.  *out receives the handle.
+ * DTR_EINVAL if any extent is odd or < 2, or V * 12 overflows int32 ranges
+ * the kernels index with (V <= 2^26). */
+int dtr_make_lattice(const int dims[4], dtr_lattice *out);
+void dtr_destroy_lattice(dtr_lattice lat);
+/* Query: dims (4 ints), volume V and N = 12 V (any output may be NULL). */
+int dtr_lattice_info(dtr_lattice lat, int dims[4], int64_t *volume, int64_t *ndof);
+
+/* -------------------------------------------------------------------- gauge */
+/* Upload SU(3) links (host pointer, canonical layout above, 4*V*9 complex128)
+ * and build the library's internal copies (FP64 and FP32).  The gauge field
+ * is the coefficient field of the Dirac matrix of Section 6.  Synchronous. */
+int dtr_make_gauge(dtr_lattice lat, const double *links_host, dtr_gauge *out);
+/* Copy the FP64 links back to a host buffer in the canonical layout. */
+int dtr_gauge_to_host(dtr_gauge g, double *links_host);
+void dtr_destroy_gauge(dtr_gauge g);
+
+/* ------------------------------------------------------------------- dslash */
+/* out = A in (dagger = 0) or out = A^H in (dagger = 1), for nrhs fields.
+ * Operator definition above (the matrix of Algorithm 1; A^H is the product
+ * of Algorithm 1, lines 2 and 8).  in, out: device, canonical N x nrhs
+ * complex128, must not overlap.  prec selects the arithmetic: DTR_F64, or
+ * DTR_F32 (fields rounded to FP32, FP32 math, result widened to FP64).
+ * work: device workspace of dtr_dslash_workspace_bytes(lat, nrhs) bytes. */
+size_t dtr_dslash_workspace_bytes(dtr_lattice lat, int nrhs);
+int dtr_dslash(dtr_gauge g, double m0, const double *in, double *out, int nrhs, int dagger,
+               dtr_prec prec, void *work, size_t work_bytes, void *stream);
+
+/* -------------------------------------------------------------------- noise */
+/* Probing vectors z = z0 .* z_h (Algorithm 1, lines 3-6; Section 5.2).
+ *   z0(i)  = i^q(i), q(i) in {0,1,2,3} the 2-bit code of dof i taken from
+ *            Philox4x64-10 (Salmon et al., SC'11) with key {seed, 0} and
+ *            counter {i / 128, z0_index, 0, 0}: output word (i % 128) / 32,
+ *            bits 2*(i % 32) .. 2*(i % 32) + 1.
+ *   z_h    = Sylvester Hadamard column j over the hierarchical-probing colour
+ *            of the dof's site: H[c, j] = (-1)^popcount(c & j).  Colours:
+ *            bit 0 = parity of x+y+z+t; then for l = 0, 1, ...: 3 bits
+ *            ((y>>l)&1, (z>>l)&1, (t>>l)&1), then 1 bit parity of
+ *            sum_mu (x_mu >> (l+1)).  ncolors in {1, 2, 16, 32, 256, 512, ...}
+ *            (1 = plain Z4 noise); every extent must be a multiple of the
+ *            colouring period (2, 2, 4, 4, 8, 8, ... for those counts).
+ *   dilute12 != 0: column q = 12*j + a keeps only dofs with i % 12 == a.
+ * Writes columns q0 .. q0+nrhs-1 to out (device, canonical N x nrhs
+ * complex128).  Bit-exact: every entry is exactly 0, +-1 or +-i. */
+int dtr_gen_noise(dtr_lattice lat, uint64_t seed, int64_t z0_index, int ncolors, int dilute12,
+                  int64_t q0, int nrhs, double *out, void *stream);
+
+/* ------------------------------------------------------------------- solver */
+typedef struct {
+  double tol;          /* stop when ||z - A y|| / ||z|| <= tol (true residual, FP64) */
+  int maxiter;         /* cap on inner iterations per RHS (summed over restarts) */
+  int solver;          /* dtr_solver */
+  int check_every;     /* iterations between host convergence checks (>= 1) */
+  double inner_tol;    /* mixed solver: relative residual reduction per inner solve */
+} dtr_solve_params;
+
+typedef struct {
+  int iterations;      /* inner Krylov iterations this RHS was active */
+  int restarts;        /* true-residual restarts / defect-correction cycles */
+  int converged;       /* 1 if the true residual met tol */
+  int pad_;
+  double true_residual;/* ||z - A y|| / ||z|| recomputed in FP64 at exit */
+} dtr_solve_stat;
+
+/* Fill *p with defaults: tol 1e-10, maxiter 5000, FP64 BiCGStab, check 8,
+ * inner_tol 1e-5. */
+void dtr_solve_params_default(dtr_solve_params *p);
+
+/* Solve A y = z for nrhs right-hand sides at once (Algorithm 1, line 7).
+ * z: device, canonical N x nrhs; y: device, canonical N x nrhs, used as the
+ * initial guess on entry (zero it for none), solution on exit.  stats: host
+ * array of nrhs entries, or NULL.  Returns DTR_ENOTCONV if any RHS missed
+ * tol within maxiter (y and stats still written). */
+size_t dtr_solve_workspace_bytes(dtr_lattice lat, int nrhs, const dtr_solve_params *p);
+int dtr_solve_batch(dtr_gauge g, double m0, const double *z, double *y, int nrhs,
+                    const dtr_solve_params *p, void *work, size_t work_bytes,
+                    dtr_solve_stat *stats, void *stream);
+
+/* --------------------------------------------------------------- deflation */
+/* Deflation space (Section 5.2): k right singular vectors of A given as
+ * eigenvectors v_m of the Hermitian matrix Q = gamma_5 A, with signed
+ * eigenvalues lambda_m (sigma_m = |lambda_m|).  Then U = A V Sigma^-1 is
+ * never formed: U = gamma_5 V sign(Lambda), and
+ *   T_D = Tr(Lambda_{A^HA}^-1 V^H A^H V) = sum_m v_m^H gamma_5 v_m / lambda_m
+ *   z^H V Lambda_{A^HA}^-1 V^H A^H z  = z^H V diag(1/lambda) V^H gamma_5 z.
+ * V: HOST, canonical N x k complex128 column-major; lambda: host, k doubles
+ * (non-zero).  The library copies V to device memory in precision prec
+ * (DTR_F64 or DTR_F32) and computes T_D in FP64 from the stored copy, so
+ * the estimator stays unbiased for the rounded V. */
+int dtr_defl_create(dtr_lattice lat, int k, dtr_prec prec, const double *V_host,
+                    const double *lambda_host, dtr_defl *out);
+/* T_D (Algorithm 1, line 2) as (re, im) in td[2] (host). */
+int dtr_defl_trace(dtr_defl d, double td[2]);
+void dtr_destroy_defl(dtr_defl d);
+
+/* Deflation projection of a block of probing vectors (Algorithm 1, line 8,
+ * second term; Section 5.2):
+ *   C = V^H [Z, gamma_5 Z]                       (k x 2 nrhs, FP64)
+ *   d_j = sum_m conj(C[m, j]) C[m, nrhs + j] / lambda_m
+ * z: device, canonical N x nrhs.  d_out: device, nrhs complex128.
+ * coeff_out: device k x 2 nrhs complex128 column-major, or NULL.
+ * x0_out: device canonical N x nrhs, or NULL: receives the deflated solution
+ *   V diag(1/lambda) V^H gamma_5 z = A_D^-1 z.
+ * work: device workspace of dtr_deflate_workspace_bytes(d, nrhs) bytes. */
+size_t dtr_deflate_workspace_bytes(dtr_defl d, int nrhs);
+int dtr_deflate_project(dtr_defl d, const double *z, int nrhs, double *d_out, double *coeff_out,
+                        double *x0_out, void *work, size_t work_bytes, void *stream);
+
+/* ---------------------------------------------------------------- estimator */
+typedef struct {
+  uint64_t seed;       /* noise seed (Philox key) */
+  int64_t z0_first;    /* first z0 run index */
+  int n_z0;            /* R: independent runs of Algorithm 1, one z0 each */
+  int ncolors;         /* hierarchical-probing colours (1 = plain Z4 noise) */
+  int nvec;            /* s: probing vectors per run (<= ncolors, or 1 if ncolors = 1) */
+  int dilute12;        /* 12-fold spin-colour dilution of each probing vector */
+  int block;           /* right-hand sides solved per launch */
+  int use_x0;          /* start each solve from the deflated solution A_D^-1 z */
+  dtr_solve_params solve;
+} dtr_trace_params;
+
+typedef struct {
+  double trace[2];      /* mean over runs of Trace_r (Algorithm 1, line 9), (re, im) */
+  double T_D[2];        /* deflated part (Algorithm 1, line 2) */
+  double var_runs;      /* sample variance over runs of Trace_r (complex form) */
+  double jk_err;        /* delete-1 jackknife standard error of trace (complex form) */
+  double var_samples;   /* sample variance of the individual samples t_j */
+  int64_t n_solves;     /* right-hand sides solved */
+  int64_t iterations;   /* inner Krylov iterations summed over right-hand sides */
+  double max_true_residual;
+  int all_converged;
+  int pad_;
+  /* optional caller-owned HOST outputs (NULL to skip):
+   *   samples     2 * n_z0 * nvec doubles: t_j = sum over dilution of
+   *               z^H y - z^H V Lambda^-1 V^H A^H z, run-major
+   *   trace_runs  2 * n_z0 doubles: Trace_r after nvec vectors
+   *   replay      2 * n_z0 * nvec * k doubles: per-vector, per-m deflation
+   *               terms conj(C[m,j]) C[m,b+j] / lambda_m, so the estimate
+   *               can be replayed for any k' <= k (Section 6.3) */
+  double *samples;
+  double *trace_runs;
+  double *replay;
+} dtr_trace_result;
+
+/* Algorithm 1 (deflatedHP) for R = n_z0 runs: for each run r and each block
+ * of probing vectors: generate z = z0_r .* z_h, project onto the deflation
+ * space, solve A y = z, reduce t_j = z^H y - d_j in FP64; Trace_r = T_D +
+ * mean_j t_j.  defl may be NULL (no deflation, T_D = 0).  work: device
+ * workspace of dtr_trace_workspace_bytes bytes.  Synchronises `stream`. */
+size_t dtr_trace_workspace_bytes(dtr_gauge g, dtr_defl d, const dtr_trace_params *p);
+int dtr_trace_estimate(dtr_gauge g, double m0, dtr_defl d, const dtr_trace_params *p,
+                       void *work, size_t work_bytes, dtr_trace_result *res, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DTR_H */

@@ -55,6 +55,27 @@ def quadrature(AH, V, sigma, z):
     return out if z.ndim == 2 else out[0]
 
 
+def quadrature_gamma5(V, lam, z):
+    """The same deflation term with the left singular vectors taken from the
+    right ones through gamma5 (U = gamma5 V sign(lambda), valid because
+    gamma5 A is Hermitian): z^H V diag(1/lambda) V^H gamma5 z.
+
+    For eigenvectors of gamma5 A this equals `quadrature` (pinned by a test);
+    for any other (V, lambda) it is still an unbiased deflation of the
+    estimator, whose deflated trace is `T_D_gamma5`.
+    """
+    Z = z if z.ndim == 2 else z[:, None]
+    c = V.conj().T @ _wilson.gamma5_vec(Z)      # V^H gamma5 z
+    w = V.conj().T @ Z                          # V^H z
+    out = np.sum(np.conj(w) * c / lam[:, None], axis=0)
+    return out if z.ndim == 2 else out[0]
+
+
+def T_D_gamma5(V, lam):
+    """Tr(V diag(1/lambda) V^H gamma5) = sum_m v_m^H gamma5 v_m / lambda_m."""
+    return complex(np.sum(np.einsum("im,im->m", np.conj(V), _wilson.gamma5_vec(V)) / lam))
+
+
 def deflation_operator(AH, V, sigma):
     """Dense D = V Lambda^-1 V^H A^H (small N), the deflated part of A^-1."""
     AHd = AH.toarray() if hasattr(AH, "toarray") else np.asarray(AH)

@@ -1,0 +1,408 @@
+// C-ABI entry points of libdtr (declared in include/dtr.h): argument checks,
+// handle management, layout conversion at the boundary and dispatch to the
+// kernels.  No exception or trap crosses the boundary; failures return a
+// status code and leave a message for dtr_last_error().
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "deflate.cuh"
+#include "dtr_internal.cuh"
+#include "solver.cuh"
+
+namespace dtr {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char *what) {
+  g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return DTR_ECUDA;
+}
+
+size_t trace_workspace_bytes(const dtr_gauge_s *g, const dtr_defl_s *D, const dtr_trace_params *p);
+int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, const dtr_trace_params *p, void *work,
+                   size_t work_bytes, dtr_trace_result *res, cudaStream_t st);
+
+__global__ void k_to_f32(const double2 *__restrict__ a, float2 *__restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
+static unsigned grid1d(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > 65535LL * 8) g = 65535LL * 8;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+static int valid_ncolors(int nc) {
+  if (nc == 1 || nc == 2) return 1;
+  int n = 2;
+  while (n < nc) {
+    n *= 8;
+    if (n == nc) return 1;
+    if (n > nc) return 0;
+    n *= 2;
+    if (n == nc) return 1;
+  }
+  return 0;
+}
+
+static int colour_period(int nc) {
+  if (nc == 1) return 1;
+  int n = 2, period = 2, level = 0;
+  while (n < nc) {
+    n *= 8;
+    if ((1 << (level + 1)) > period) period = 1 << (level + 1);
+    if (n >= nc) break;
+    n *= 2;
+    period = 1 << (level + 2);
+    ++level;
+  }
+  return period;
+}
+
+static int check_colouring(const dtr_lattice_s &l, int ncolors) {
+  if (!valid_ncolors(ncolors)) return fail(DTR_EINVAL, "ncolors must be 1, 2, 16, 32, 256, 512, ...");
+  const int per = colour_period(ncolors);
+  for (int i = 0; i < 4; ++i)
+    if (l.dims[i] % per) return fail(DTR_EINVAL, "lattice extents must be multiples of the colouring period");
+  return DTR_OK;
+}
+
+}  // namespace dtr
+
+using namespace dtr;
+
+extern "C" {
+
+const char *dtr_last_error(void) { return g_err.c_str(); }
+const char *dtr_version(void) { return "dtr 0.1 (sm_103a)"; }
+
+int dtr_make_lattice(const int dims[4], dtr_lattice *out) {
+  if (!dims || !out) return fail(DTR_EINVAL, "null argument");
+  int64_t V = 1;
+  for (int i = 0; i < 4; ++i) {
+    if (dims[i] < 2 || (dims[i] & 1)) return fail(DTR_EINVAL, "lattice extents must be even and >= 2");
+    V *= dims[i];
+  }
+  if (V > (1LL << 26)) return fail(DTR_EINVAL, "lattice volume above 2^26 sites");
+  dtr_lattice_s *l = new (std::nothrow) dtr_lattice_s;
+  if (!l) return fail(DTR_ENOMEM, "host allocation failed");
+  for (int i = 0; i < 4; ++i) l->dims[i] = dims[i];
+  l->V = V;
+  l->N = 12 * V;
+  *out = l;
+  return DTR_OK;
+}
+
+void dtr_destroy_lattice(dtr_lattice lat) { delete lat; }
+
+int dtr_lattice_info(dtr_lattice lat, int dims[4], int64_t *volume, int64_t *ndof) {
+  if (!lat) return fail(DTR_EINVAL, "null lattice");
+  if (dims)
+    for (int i = 0; i < 4; ++i) dims[i] = lat->dims[i];
+  if (volume) *volume = lat->V;
+  if (ndof) *ndof = lat->N;
+  return DTR_OK;
+}
+
+int dtr_make_gauge(dtr_lattice lat, const double *links_host, dtr_gauge *out) {
+  if (!lat || !links_host || !out) return fail(DTR_EINVAL, "null argument");
+  dtr_gauge_s *g = new (std::nothrow) dtr_gauge_s;
+  if (!g) return fail(DTR_ENOMEM, "host allocation failed");
+  g->lat = *lat;
+  g->U64 = nullptr;
+  g->U32 = nullptr;
+  const int64_t n = lat->V * 4 * 9;
+  cudaError_t e = cudaMalloc((void **)&g->U64, n * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&g->U32, n * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMemcpy(g->U64, links_host, n * sizeof(double2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_to_f32<<<grid1d(n), 256>>>(g->U64, g->U32, n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(g->U64);
+    cudaFree(g->U32);
+    delete g;
+    return cuda_fail(e, "gauge upload");
+  }
+  *out = g;
+  return DTR_OK;
+}
+
+int dtr_gauge_to_host(dtr_gauge g, double *links_host) {
+  if (!g || !links_host) return fail(DTR_EINVAL, "null argument");
+  DTR_CUDA(cudaMemcpy(links_host, g->U64, g->lat.V * 4 * 9 * sizeof(double2), cudaMemcpyDeviceToHost));
+  return DTR_OK;
+}
+
+void dtr_destroy_gauge(dtr_gauge g) {
+  if (!g) return;
+  cudaFree(g->U64);
+  cudaFree(g->U32);
+  delete g;
+}
+
+size_t dtr_dslash_workspace_bytes(dtr_lattice lat, int nrhs) {
+  if (!lat || nrhs < 1 || nrhs > 64) return 0;
+  const int b = pad_rhs(nrhs);
+  return 2 * (((size_t)lat->V * 12 * b * sizeof(double2) + 255) / 256 * 256) + 256;
+}
+
+int dtr_dslash(dtr_gauge g, double m0, const double *in, double *out, int nrhs, int dagger, dtr_prec prec,
+               void *work, size_t work_bytes, void *stream) {
+  if (!g || !in || !out || !work) return fail(DTR_EINVAL, "null argument");
+  if (nrhs < 1 || nrhs > 64) return fail(DTR_EINVAL, "nrhs must be in [1, 64]");
+  if (prec != DTR_F64 && prec != DTR_F32) return fail(DTR_EINVAL, "dslash precision must be DTR_F64 or DTR_F32");
+  if (work_bytes < dtr_dslash_workspace_bytes(&g->lat, nrhs)) return fail(DTR_ENOMEM, "dslash workspace too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int b = pad_rhs(nrhs);
+  const Geom geo = geom_of(g->lat);
+  const size_t vb = ((size_t)g->lat.V * 12 * b * sizeof(double2) + 255) / 256 * 256;
+  char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+  if (prec == DTR_F64) {
+    double2 *a = (double2 *)w, *o = (double2 *)(w + vb);
+    launch_pack<double>((const double2 *)in, a, g->lat.V, nrhs, b, st);
+    launch_dslash<double>(g->U64, a, o, geo, b, m0, dagger, st);
+    launch_unpack<double>(o, (double2 *)out, g->lat.V, nrhs, b, st);
+  } else {
+    float2 *a = (float2 *)w, *o = (float2 *)(w + vb);
+    launch_pack<float>((const double2 *)in, a, g->lat.V, nrhs, b, st);
+    launch_dslash<float>(g->U32, a, o, geo, b, m0, dagger, st);
+    launch_unpack<float>(o, (double2 *)out, g->lat.V, nrhs, b, st);
+  }
+  DTR_LAUNCH_CHECK("dslash");
+  return DTR_OK;
+}
+
+int dtr_gen_noise(dtr_lattice lat, uint64_t seed, int64_t z0_index, int ncolors, int dilute12, int64_t q0, int nrhs,
+                  double *out, void *stream) {
+  if (!lat || !out) return fail(DTR_EINVAL, "null argument");
+  if (nrhs < 1 || q0 < 0 || z0_index < 0) return fail(DTR_EINVAL, "bad column range");
+  int rc = check_colouring(*lat, ncolors);
+  if (rc) return rc;
+  launch_noise_canon((double2 *)out, geom_of(*lat), seed, z0_index, ncolors, dilute12, q0, nrhs,
+                     (cudaStream_t)stream);
+  DTR_LAUNCH_CHECK("noise");
+  return DTR_OK;
+}
+
+void dtr_solve_params_default(dtr_solve_params *p) {
+  if (!p) return;
+  p->tol = 1e-10;
+  p->maxiter = 5000;
+  p->solver = DTR_SOLVER_BICGSTAB_F64;
+  p->check_every = 8;
+  p->inner_tol = 1e-5;
+}
+
+static int check_solve_params(const dtr_solve_params *p) {
+  if (!p) return fail(DTR_EINVAL, "null solve params");
+  if (!(p->tol > 0.0) || p->maxiter < 1) return fail(DTR_EINVAL, "tol must be > 0 and maxiter >= 1");
+  if (p->solver != DTR_SOLVER_BICGSTAB_F64 && p->solver != DTR_SOLVER_MIXED_F32)
+    return fail(DTR_EINVAL, "unknown solver");
+  return DTR_OK;
+}
+
+size_t dtr_solve_workspace_bytes(dtr_lattice lat, int nrhs, const dtr_solve_params *p) {
+  if (!lat || !p || nrhs < 1 || nrhs > 64) return 0;
+  const int b = pad_rhs(nrhs);
+  const size_t vb = ((size_t)lat->V * 12 * b * sizeof(double2) + 255) / 256 * 256;
+  return 256 + 2 * vb + solver_scratch_bytes(lat->V, b, p->solver);
+}
+
+int dtr_solve_batch(dtr_gauge g, double m0, const double *z, double *y, int nrhs, const dtr_solve_params *p,
+                    void *work, size_t work_bytes, dtr_solve_stat *stats, void *stream) {
+  if (!g || !z || !y || !work) return fail(DTR_EINVAL, "null argument");
+  if (nrhs < 1 || nrhs > 64) return fail(DTR_EINVAL, "nrhs must be in [1, 64]");
+  int rc = check_solve_params(p);
+  if (rc) return rc;
+  const size_t need = dtr_solve_workspace_bytes(&g->lat, nrhs, p);
+  if (work_bytes < need) return fail(DTR_ENOMEM, "solver workspace too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int b = pad_rhs(nrhs);
+  const size_t vb = ((size_t)g->lat.V * 12 * b * sizeof(double2) + 255) / 256 * 256;
+  char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+  double2 *X = (double2 *)w, *Z = (double2 *)(w + vb);
+  launch_pack<double>((const double2 *)z, Z, g->lat.V, nrhs, b, st);
+  launch_pack<double>((const double2 *)y, X, g->lat.V, nrhs, b, st);
+  DTR_LAUNCH_CHECK("pack");
+  Scal *sc = nullptr;
+  rc = solve_internal(g, m0, X, Z, b, p, w + 2 * vb, work_bytes - (size_t)(w + 2 * vb - (char *)work), st, &sc);
+  if (rc) return rc;
+  launch_unpack<double>(X, (double2 *)y, g->lat.V, nrhs, b, st);
+  DTR_LAUNCH_CHECK("unpack");
+  Scal h;
+  DTR_CUDA(cudaMemcpyAsync(&h, sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
+  DTR_CUDA(cudaStreamSynchronize(st));
+  int all = 1, nan = 0;
+  for (int j = 0; j < nrhs; ++j) {
+    if (!h.conv[j]) all = 0;
+    if (h.flags[j] & kFlagNaN) nan = 1;
+    if (stats) {
+      stats[j].iterations = h.iters[j];
+      stats[j].restarts = h.restarts[j];
+      stats[j].converged = h.conv[j];
+      stats[j].pad_ = h.flags[j];
+      stats[j].true_residual = h.bnorm2[j] > 0 ? std::sqrt(h.rtrue2[j] / h.bnorm2[j]) : 0.0;
+    }
+  }
+  if (nan) return fail(DTR_ENAN, "NaN or Inf in a residual norm");
+  if (!all) return fail(DTR_ENOTCONV, "some right-hand sides did not reach tol within maxiter");
+  return DTR_OK;
+}
+
+int dtr_defl_create(dtr_lattice lat, int k, dtr_prec prec, const double *V_host, const double *lambda_host,
+                    dtr_defl *out) {
+  if (!lat || !V_host || !lambda_host || !out) return fail(DTR_EINVAL, "null argument");
+  if (k < 1) return fail(DTR_EINVAL, "k must be >= 1");
+  if (prec != DTR_F64 && prec != DTR_F32) return fail(DTR_EINVAL, "deflation storage must be DTR_F64 or DTR_F32");
+  for (int m = 0; m < k; ++m)
+    if (!(lambda_host[m] != 0.0) || !std::isfinite(lambda_host[m]))
+      return fail(DTR_EINVAL, "lambda must be finite and non-zero");
+  const int64_t N = lat->N;
+  // canonical column-major N x k -> row-major [dof][k]
+  std::vector<double2> rowmajor;
+  try {
+    rowmajor.resize((size_t)N * k);
+  } catch (...) {
+    return fail(DTR_ENOMEM, "host allocation failed");
+  }
+  const double2 *src = (const double2 *)V_host;
+  for (int m = 0; m < k; ++m)
+    for (int64_t i = 0; i < N; ++i) rowmajor[(size_t)i * k + m] = src[(size_t)m * N + i];
+  dtr_defl_s *D = new (std::nothrow) dtr_defl_s;
+  if (!D) return fail(DTR_ENOMEM, "host allocation failed");
+  D->lat = *lat;
+  D->k = k;
+  D->prec = prec;
+  D->V = nullptr;
+  D->inv_lambda = nullptr;
+  std::vector<double> inv(k);
+  for (int m = 0; m < k; ++m) inv[m] = 1.0 / lambda_host[m];
+  cudaError_t e = cudaMalloc(&D->inv_lambda, k * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(D->inv_lambda, inv.data(), k * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    if (prec == DTR_F64) {
+      e = cudaMalloc(&D->V, (size_t)N * k * sizeof(double2));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(D->V, rowmajor.data(), (size_t)N * k * sizeof(double2), cudaMemcpyHostToDevice);
+    } else {
+      double2 *tmp = nullptr;
+      e = cudaMalloc(&D->V, (size_t)N * k * sizeof(float2));
+      if (e == cudaSuccess) e = cudaMalloc(&tmp, (size_t)N * k * sizeof(double2));
+      if (e == cudaSuccess) e = cudaMemcpy(tmp, rowmajor.data(), (size_t)N * k * sizeof(double2), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) {
+        k_to_f32<<<grid1d((int64_t)N * k), 256>>>(tmp, (float2 *)D->V, (int64_t)N * k);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaDeviceSynchronize();
+      cudaFree(tmp);
+    }
+  }
+  if (e != cudaSuccess) {
+    cudaFree(D->V);
+    cudaFree(D->inv_lambda);
+    delete D;
+    return cuda_fail(e, "deflation space upload");
+  }
+  int rc = defl_trace_TD(D, 0);
+  if (rc) {
+    cudaFree(D->V);
+    cudaFree(D->inv_lambda);
+    delete D;
+    return rc;
+  }
+  *out = D;
+  return DTR_OK;
+}
+
+int dtr_defl_trace(dtr_defl d, double td[2]) {
+  if (!d || !td) return fail(DTR_EINVAL, "null argument");
+  td[0] = d->td[0];
+  td[1] = d->td[1];
+  return DTR_OK;
+}
+
+void dtr_destroy_defl(dtr_defl d) {
+  if (!d) return;
+  cudaFree(d->V);
+  cudaFree(d->inv_lambda);
+  delete d;
+}
+
+size_t dtr_deflate_workspace_bytes(dtr_defl d, int nrhs) {
+  if (!d || nrhs < 1 || nrhs > 64) return 0;
+  const int b = pad_rhs(nrhs);
+  const size_t vb = ((size_t)d->lat.V * 12 * b * sizeof(double2) + 255) / 256 * 256;
+  return 256 + 2 * vb + 256 * 3 + 64 * sizeof(double2) + defl_scratch_bytes(d->lat.V, d->k, b, device_sms());
+}
+
+int dtr_deflate_project(dtr_defl d, const double *z, int nrhs, double *d_out, double *coeff_out, double *x0_out,
+                        void *work, size_t work_bytes, void *stream) {
+  if (!d || !z || !d_out || !work) return fail(DTR_EINVAL, "null argument");
+  if (nrhs < 1 || nrhs > 64) return fail(DTR_EINVAL, "nrhs must be in [1, 64]");
+  if (work_bytes < dtr_deflate_workspace_bytes(d, nrhs)) return fail(DTR_ENOMEM, "deflation workspace too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int b = pad_rhs(nrhs);
+  const size_t vb = ((size_t)d->lat.V * 12 * b * sizeof(double2) + 255) / 256 * 256;
+  char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+  double2 *Z = (double2 *)w;
+  double2 *X0 = (double2 *)(w + vb);
+  double2 *dd = (double2 *)(w + 2 * vb);
+  char *scratch = w + 2 * vb + 256 + 64 * sizeof(double2);
+  const size_t scratch_bytes = work_bytes - (size_t)(scratch - (char *)work);
+  launch_pack<double>((const double2 *)z, Z, d->lat.V, nrhs, b, st);
+  double2 *C = nullptr;
+  int rc = defl_project_internal(d, Z, b, dd, nullptr, x0_out ? X0 : nullptr, &C, scratch, scratch_bytes,
+                                 device_sms(), st);
+  if (rc) return rc;
+  DTR_CUDA(cudaMemcpyAsync(d_out, dd, sizeof(double2) * nrhs, cudaMemcpyDeviceToDevice, st));
+  if (coeff_out) {
+    const size_t colbytes = sizeof(double2) * d->k;
+    DTR_CUDA(cudaMemcpyAsync(coeff_out, C, colbytes * nrhs, cudaMemcpyDeviceToDevice, st));
+    DTR_CUDA(cudaMemcpyAsync((char *)coeff_out + colbytes * nrhs, C + (size_t)b * d->k, colbytes * nrhs,
+                             cudaMemcpyDeviceToDevice, st));
+  }
+  if (x0_out) launch_unpack<double>(X0, (double2 *)x0_out, d->lat.V, nrhs, b, st);
+  DTR_LAUNCH_CHECK("deflate project");
+  return DTR_OK;
+}
+
+static int check_trace_params(const dtr_gauge_s *g, const dtr_defl_s *D, const dtr_trace_params *p) {
+  if (!p) return fail(DTR_EINVAL, "null trace params");
+  int rc = check_solve_params(&p->solve);
+  if (rc) return rc;
+  if (p->block < 1 || p->block > 64) return fail(DTR_EINVAL, "block must be in [1, 64]");
+  if (p->n_z0 < 1 || p->nvec < 1 || p->z0_first < 0) return fail(DTR_EINVAL, "n_z0 and nvec must be >= 1");
+  rc = check_colouring(g->lat, p->ncolors);
+  if (rc) return rc;
+  if (p->ncolors > 1 && p->nvec > p->ncolors) return fail(DTR_EINVAL, "nvec must be <= ncolors");
+  if (p->ncolors == 1 && p->nvec != 1) return fail(DTR_EINVAL, "plain Z4 noise (ncolors = 1) has nvec = 1");
+  if (D && (D->lat.V != g->lat.V)) return fail(DTR_EINVAL, "deflation space built for another lattice");
+  return DTR_OK;
+}
+
+size_t dtr_trace_workspace_bytes(dtr_gauge g, dtr_defl d, const dtr_trace_params *p) {
+  if (!g || !p || p->block < 1 || p->block > 64) return 0;
+  return trace_workspace_bytes(g, d, p);
+}
+
+int dtr_trace_estimate(dtr_gauge g, double m0, dtr_defl d, const dtr_trace_params *p, void *work, size_t work_bytes,
+                       dtr_trace_result *res, void *stream) {
+  if (!g || !res || !work) return fail(DTR_EINVAL, "null argument");
+  int rc = check_trace_params(g, d, p);
+  if (rc) return rc;
+  return trace_estimate(g, m0, d, p, work, work_bytes, res, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,239 @@
+// Deflation projection (Section 5.2; Algorithm 1, lines 2 and 8).
+//
+// With V the right singular vectors stored as eigenvectors of Q = g5 A
+// (signed eigenvalues lambda), the paper's quadrature z^H V L^-1 V^H (A^H z),
+// L = Sigma^2, equals z^H V diag(1/lambda) V^H g5 z because V^H A^H =
+// diag(lambda) V^H g5.  The tall-skinny contraction C = V^H [Z, g5 Z] is
+// computed as two accumulators per (m, j): the upper-spin part P and the
+// lower-spin part Q of V^H Z, so that V^H Z = P + Q and V^H g5 Z = P - Q.
+//
+// Layouts: V row-major [dof][k] (FP64 or FP32); Z internal [site][12][b] FP64.
+// Partial sums per site chunk go to scratch and are reduced over chunks in a
+// fixed order, so results are bit-reproducible.
+#include "dtr_internal.cuh"
+#include "deflate.cuh"
+
+namespace dtr {
+
+constexpr int kDeflBlock = 256;
+constexpr int kMPT = 4;  // vectors m per thread per tile
+
+template <typename VC>
+__global__ void __launch_bounds__(kDeflBlock)
+    k_defl_partial(const VC *__restrict__ Vd, const double2 *__restrict__ Z, int k, int b, int logb, int nsites,
+                   int nchunks, double2 *__restrict__ partial) {
+  const int G = kDeflBlock >> logb;  // m-groups per block
+  const int tile = G * kMPT;
+  const int chunk = blockIdx.x % nchunks;
+  const int mt = blockIdx.x / nchunks;
+  const int j = threadIdx.x & (b - 1);
+  const int grp = threadIdx.x >> logb;
+  const int s0 = (int)(((int64_t)nsites * chunk) / nchunks);
+  const int s1 = (int)(((int64_t)nsites * (chunk + 1)) / nchunks);
+  int m[kMPT];
+  bool ok[kMPT];
+#pragma unroll
+  for (int q = 0; q < kMPT; ++q) {
+    m[q] = mt * tile + grp + q * G;
+    ok[q] = m[q] < k;
+  }
+  double2 P[kMPT], Q[kMPT];
+#pragma unroll
+  for (int q = 0; q < kMPT; ++q) P[q] = Q[q] = make_double2(0.0, 0.0);
+  for (int s = s0; s < s1; ++s) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      const int64_t i = (int64_t)s * 12 + c;
+      const double2 z = Z[i * b + j];
+#pragma unroll
+      for (int q = 0; q < kMPT; ++q) {
+        if (!ok[q]) continue;
+        const VC vv = Vd[i * k + m[q]];
+        const double vx = vv.x, vy = vv.y;
+        // conj(v) * z
+        const double re = vx * z.x + vy * z.y, im = vx * z.y - vy * z.x;
+        if (c < 6) {
+          P[q].x += re;
+          P[q].y += im;
+        } else {
+          Q[q].x += re;
+          Q[q].y += im;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kMPT; ++q) {
+    if (!ok[q]) continue;
+    const int64_t base = (((int64_t)chunk * k + m[q]) * 2) * b + j;
+    partial[base] = P[q];
+    partial[base + b] = Q[q];
+  }
+}
+
+// C (column-major k x 2b): C[m + k*j] = P + Q, C[m + k*(b+j)] = P - Q
+__global__ void k_defl_reduce(const double2 *__restrict__ partial, int k, int b, int nchunks, double2 *__restrict__ C) {
+  const int64_t n = (int64_t)k * b;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e % b);
+    const int m = (int)(e / b);
+    double2 P = make_double2(0.0, 0.0), Q = make_double2(0.0, 0.0);
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int64_t base = (((int64_t)ch * k + m) * 2) * b + j;
+      P = cadd(P, partial[base]);
+      Q = cadd(Q, partial[base + b]);
+    }
+    C[(int64_t)j * k + m] = cadd(P, Q);
+    C[(int64_t)(b + j) * k + m] = csub(P, Q);
+  }
+}
+
+// d_j = sum_m conj(C[m, j]) C[m, b+j] / lambda_m ; optional per-m terms
+__global__ void k_defl_d(const double2 *__restrict__ C, const double *__restrict__ inv_lambda, int k, int b,
+                         double2 *__restrict__ d, double2 *__restrict__ terms) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= b) return;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int m = 0; m < k; ++m) {
+    const double2 a = C[(int64_t)j * k + m], g = C[(int64_t)(b + j) * k + m];
+    const double2 t = cscale(cjmul(a, g), inv_lambda[m]);
+    if (terms) terms[(int64_t)j * k + m] = t;
+    acc = cadd(acc, t);
+  }
+  d[j] = acc;
+}
+
+// x0 (internal [site][12][b]) = V diag(1/lambda) C[:, b:2b]
+template <typename VC>
+__global__ void k_defl_expand(const VC *__restrict__ Vd, const double2 *__restrict__ C,
+                              const double *__restrict__ inv_lambda, int k, int b, int64_t N, double2 *__restrict__ x) {
+  const int64_t n = N * b;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e % b);
+    const int64_t i = e / b;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int m = 0; m < k; ++m) {
+      const VC vv = Vd[i * k + m];
+      const double2 w = cscale(C[(int64_t)(b + j) * k + m], inv_lambda[m]);
+      acc = caxpy(make_double2(vv.x, vv.y), w, acc);
+    }
+    x[e] = acc;
+  }
+}
+
+// T_D partials: sum_i sign(i) |V[i][m]|^2 over a chunk of dofs
+template <typename VC>
+__global__ void k_defl_td_partial(const VC *__restrict__ Vd, int k, int64_t N, int nchunks, double *__restrict__ part) {
+  const int chunk = blockIdx.x;
+  const int64_t i0 = (N * chunk) / nchunks, i1 = (N * (chunk + 1)) / nchunks;
+  for (int m = threadIdx.x; m < k; m += blockDim.x) {
+    double acc = 0.0;
+    for (int64_t i = i0; i < i1; ++i) {
+      const VC vv = Vd[i * k + m];
+      const double a2 = (double)vv.x * vv.x + (double)vv.y * vv.y;
+      acc += ((i % 12) < 6) ? a2 : -a2;
+    }
+    part[(int64_t)chunk * k + m] = acc;
+  }
+}
+
+__global__ void k_defl_td_reduce(const double *__restrict__ part, const double *__restrict__ inv_lambda, int k,
+                                 int nchunks, double *__restrict__ td) {
+  // single thread, fixed order: deterministic
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double t = 0.0;
+  for (int m = 0; m < k; ++m) {
+    double s = 0.0;
+    for (int ch = 0; ch < nchunks; ++ch) s += part[(int64_t)ch * k + m];
+    t += s * inv_lambda[m];
+  }
+  *td = t;
+}
+
+static int log2i(int b) {
+  int l = 0;
+  while ((1 << l) < b) ++l;
+  return l;
+}
+
+static int defl_chunks(int64_t V, int k, int b, int sms) {
+  const int G = kDeflBlock / b;
+  const int tiles = (k + G * kMPT - 1) / (G * kMPT);
+  int64_t want = (2LL * sms + tiles - 1) / tiles;
+  if (want > V) want = V;
+  if (want < 1) want = 1;
+  return (int)want;
+}
+
+size_t defl_scratch_bytes(int64_t V, int k, int b, int sms) {
+  const int nch = defl_chunks(V, k, b, sms);
+  size_t part = (size_t)nch * k * 2 * b * sizeof(double2);
+  const size_t C = (size_t)k * 2 * b * sizeof(double2);
+  const size_t d = 64 * sizeof(double2);
+  return ((part + 255) / 256 + (C + 255) / 256 + (d + 255) / 256 + 2) * 256;
+}
+
+int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 *d_dev, double2 *terms_dev,
+                          double2 *x0_internal, double2 **C_out, void *work, size_t work_bytes, int sms,
+                          cudaStream_t st) {
+  const int64_t V = D->lat.V;
+  const int k = D->k;
+  if (work_bytes < defl_scratch_bytes(V, k, b, sms)) return fail(DTR_ENOMEM, "deflation workspace too small");
+  const int nch = defl_chunks(V, k, b, sms);
+  const int G = kDeflBlock / b;
+  const int tiles = (k + G * kMPT - 1) / (G * kMPT);
+  char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+  double2 *partial = (double2 *)w;
+  w += (((size_t)nch * k * 2 * b * sizeof(double2) + 255) / 256) * 256;
+  double2 *C = (double2 *)w;
+  w += (((size_t)k * 2 * b * sizeof(double2) + 255) / 256) * 256;
+  const int logb = log2i(b);
+  if (D->prec == DTR_F64)
+    k_defl_partial<double2><<<nch * tiles, kDeflBlock, 0, st>>>((const double2 *)D->V, Z, k, b, logb, (int)V, nch,
+                                                                partial);
+  else
+    k_defl_partial<float2><<<nch * tiles, kDeflBlock, 0, st>>>((const float2 *)D->V, Z, k, b, logb, (int)V, nch,
+                                                               partial);
+  const int64_t nkb = (int64_t)k * b;
+  k_defl_reduce<<<(unsigned)((nkb + 255) / 256), 256, 0, st>>>(partial, k, b, nch, C);
+  k_defl_d<<<1, 64, 0, st>>>(C, D->inv_lambda, k, b, d_dev, terms_dev);
+  if (x0_internal) {
+    const int64_t n = V * 12 * b;
+    unsigned grid = (unsigned)((n + 255) / 256);
+    if (grid > 65535u * 8) grid = 65535u * 8;
+    if (D->prec == DTR_F64)
+      k_defl_expand<double2><<<grid, 256, 0, st>>>((const double2 *)D->V, C, D->inv_lambda, k, b, V * 12,
+                                                   x0_internal);
+    else
+      k_defl_expand<float2><<<grid, 256, 0, st>>>((const float2 *)D->V, C, D->inv_lambda, k, b, V * 12, x0_internal);
+  }
+  DTR_LAUNCH_CHECK("deflation projection");
+  if (C_out) *C_out = C;
+  return DTR_OK;
+}
+
+int defl_trace_TD(dtr_defl_s *D, cudaStream_t st) {
+  const int64_t N = D->lat.N;
+  const int k = D->k;
+  int nch = 256;
+  if (nch > N) nch = (int)N;
+  double *part = nullptr, *td = nullptr;
+  DTR_CUDA(cudaMalloc((void **)&part, (size_t)nch * k * sizeof(double) + 256));
+  td = (double *)((char *)part + (((size_t)nch * k * sizeof(double) + 127) / 128) * 128);
+  if (D->prec == DTR_F64)
+    k_defl_td_partial<double2><<<nch, 256, 0, st>>>((const double2 *)D->V, k, N, nch, part);
+  else
+    k_defl_td_partial<float2><<<nch, 256, 0, st>>>((const float2 *)D->V, k, N, nch, part);
+  k_defl_td_reduce<<<1, 1, 0, st>>>(part, D->inv_lambda, k, nch, td);
+  cudaError_t e = cudaGetLastError();
+  double h = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, td, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(part);
+  if (e != cudaSuccess) return cuda_fail(e, "T_D reduction");
+  D->td[0] = h;
+  D->td[1] = 0.0;
+  return DTR_OK;
+}
+
+}  // namespace dtr

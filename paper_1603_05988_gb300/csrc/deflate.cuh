@@ -1,0 +1,23 @@
+// Deflation-space kernels shared by the C-ABI entry points and the estimator.
+#pragma once
+
+#include "dtr_internal.cuh"
+
+namespace dtr {
+
+// Scratch for one projection of a width-b block.
+size_t defl_scratch_bytes(int64_t V, int k, int b, int sms);
+
+// C = V^H [Z, g5 Z] (k x 2b, kept in scratch; *C_out points at it),
+// d_dev[j] = sum_m conj(C[m,j]) C[m,b+j] / lambda_m, terms_dev (k x b, or
+// NULL) the per-m terms, x0_internal (or NULL) = V diag(1/lambda) C[:, b:].
+int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 *d_dev, double2 *terms_dev,
+                          double2 *x0_internal, double2 **C_out, void *work, size_t work_bytes, int sms,
+                          cudaStream_t st);
+
+// T_D = sum_m v_m^H g5 v_m / lambda_m from the stored V (FP64 accumulation).
+int defl_trace_TD(dtr_defl_s *D, cudaStream_t st);
+
+int device_sms();
+
+}  // namespace dtr

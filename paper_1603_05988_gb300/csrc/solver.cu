@@ -1,0 +1,513 @@
+// Batched BiCGStab for A y = z (Algorithm 1, line 7), one column per probing
+// vector, all columns of a block advanced together with per-column scalars
+// kept on the device.  Two drivers:
+//   * plain FP64 BiCGStab with true-residual restarts;
+//   * mixed precision: FP64 defect correction (r = z - A y in FP64, y
+//     accumulated in FP64) around FP32 BiCGStab inner solves.
+// Every iteration is five kernels: fused dslash + dot (alpha), s = r - alpha v,
+// fused dslash + two dots (omega), fused x/r update + two dots (beta and the
+// convergence test), p update.  The scalar algebra of each step runs in the
+// last block of the reducing kernel, so the host only polls a device-side
+// active-column count every `check_every` iterations.
+#include <cstring>
+#include <vector>
+
+#include "dslash_core.cuh"
+#include "reduce.cuh"
+#include "solver.cuh"
+
+namespace dtr {
+
+int device_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+// ------------------------------------------------------------- finalizers
+// All run in the last block, thread j < b, with the block totals of column j.
+
+__device__ __forceinline__ void count_active(Scal *sc, int b) {
+  // called by thread 0 after a __syncthreads in the caller
+  int n = 0;
+  for (int j = 0; j < b; ++j) n += sc->active[j];
+  sc->n_active = n;
+}
+
+// true residual r = z - A x: tot = (||r||^2, ||z||^2)
+__device__ __forceinline__ void fin_resid(Scal *sc, int j, double2 t0, int restart) {
+  const double r2 = t0.x, z2 = t0.y;
+  sc->bnorm2[j] = z2;
+  sc->rtrue2[j] = r2;
+  const bool nan = !(r2 == r2) || !(z2 == z2) || isinf(r2);
+  const bool conv = (z2 == 0.0) || (r2 <= sc->tol2 * z2);
+  sc->conv[j] = conv ? 1 : 0;
+  if (nan) sc->flags[j] |= kFlagNaN;
+  if (!conv && !nan && sc->iters[j] < sc->maxiter && restart) {
+    sc->active[j] = 1;
+    sc->restarts[j] += 1;
+    sc->rho[j] = make_double2(r2, 0.0);
+    sc->rnorm2[j] = r2;
+    sc->scale[j] = 1.0 / sqrt(r2);
+  } else {
+    sc->active[j] = 0;
+  }
+}
+
+__device__ __forceinline__ void fin_alpha(Scal *sc, int j, double2 sigma) {
+  if (!sc->active[j]) {
+    sc->alpha[j] = make_double2(0.0, 0.0);
+    return;
+  }
+  if (sigma.x == 0.0 && sigma.y == 0.0) {
+    sc->flags[j] |= kFlagBreakdown;
+    sc->active[j] = 0;
+    sc->alpha[j] = make_double2(0.0, 0.0);
+    return;
+  }
+  sc->alpha[j] = cdiv(sc->rho[j], sigma);
+}
+
+__device__ __forceinline__ void fin_omega(Scal *sc, int j, double2 ts, double2 tt) {
+  if (!sc->active[j] || tt.x == 0.0) {
+    sc->omega[j] = make_double2(0.0, 0.0);
+    return;
+  }
+  sc->omega[j] = make_double2(ts.x / tt.x, ts.y / tt.x);
+}
+
+__device__ __forceinline__ void fin_beta(Scal *sc, int j, double2 rr0, double2 rr) {
+  if (!sc->active[j]) {
+    sc->beta[j] = make_double2(0.0, 0.0);
+    return;
+  }
+  sc->iters[j] += 1;
+  const double rn2 = rr.x;
+  sc->rnorm2[j] = rn2;
+  if (!(rn2 == rn2) || isinf(rn2)) {
+    sc->flags[j] |= kFlagNaN;
+    sc->active[j] = 0;
+    return;
+  }
+  if (rn2 <= sc->tol2 * sc->bnorm2[j]) {  // converged on the recursive residual
+    sc->active[j] = 0;
+    sc->beta[j] = make_double2(0.0, 0.0);
+    return;
+  }
+  if (sc->iters[j] >= sc->maxiter) {
+    sc->active[j] = 0;
+    return;
+  }
+  const double2 om = sc->omega[j];
+  const double2 rho = sc->rho[j];
+  if ((om.x == 0.0 && om.y == 0.0) || (rho.x == 0.0 && rho.y == 0.0)) {
+    sc->flags[j] |= kFlagBreakdown;
+    sc->active[j] = 0;
+    return;
+  }
+  sc->beta[j] = cmul(cdiv(rr0, rho), cdiv(sc->alpha[j], om));
+  sc->rho[j] = rr0;
+}
+
+// ------------------------------------------------------------------ kernels
+template <typename R> struct Vec { typedef typename cplx_t<R>::type C; };
+
+template <typename C> __device__ __forceinline__ C scal_as(double2 v) { return mk<C>(v.x, v.y); }
+
+template <typename C> __device__ __forceinline__ double2 dot_acc(double2 acc, C a, C b) {
+  // acc += conj(a) * b in double
+  const double ax = a.x, ay = a.y, bx = b.x, by = b.y;
+  return make_double2(acc.x + ax * bx + ay * by, acc.y + ax * by - ay * bx);
+}
+
+// r = z - A x; optionally rhat = p = r.  tot = (||r||^2, ||z||^2).
+template <typename R, int KRYLOV>
+__global__ void __launch_bounds__(kBlock) k_resid(const typename cplx_t<R>::type *__restrict__ U,
+                                                  const typename cplx_t<R>::type *__restrict__ x,
+                                                  const typename cplx_t<R>::type *__restrict__ z,
+                                                  typename cplx_t<R>::type *__restrict__ r,
+                                                  typename cplx_t<R>::type *__restrict__ rhat,
+                                                  typename cplx_t<R>::type *__restrict__ p, Geom g, int b, int logb,
+                                                  R diag, Scal *sc, Reduce red, int restart) {
+  typedef typename cplx_t<R>::type C;
+  __shared__ double2 tot[64];
+  double2 acc[1] = {make_double2(0.0, 0.0)};
+  const int64_t n = (int64_t)g.V << logb;
+  const int j = threadIdx.x & (b - 1);
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n; it += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(it >> logb);
+    C o[12], self[12];
+    dslash_site<1, R>(U, x, g, b, s, j, diag, o, self);
+    const int64_t base = (int64_t)s * 12 * b + j;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      const C zz = z[base + c * b];
+      const C rr = csub(zz, o[c]);
+      r[base + c * b] = rr;
+      if (KRYLOV) {
+        rhat[base + c * b] = rr;
+        p[base + c * b] = rr;
+      }
+      acc[0].x += (double)rr.x * rr.x + (double)rr.y * rr.y;
+      acc[0].y += (double)zz.x * zz.x + (double)zz.y * zz.y;
+    }
+  }
+  if (block_reduce<1>(acc, b, red.partial, red.counter, tot)) {
+    if (threadIdx.x < b) fin_resid(sc, threadIdx.x, tot[threadIdx.x], restart);
+    __syncthreads();
+    if (threadIdx.x == 0) count_active(sc, b);
+  }
+}
+
+// v = A p; sigma = rhat^H v -> alpha
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_dslash_alpha(const typename cplx_t<R>::type *__restrict__ U,
+                                                         const typename cplx_t<R>::type *__restrict__ p,
+                                                         const typename cplx_t<R>::type *__restrict__ rhat,
+                                                         typename cplx_t<R>::type *__restrict__ v, Geom g, int b,
+                                                         int logb, R diag, Scal *sc, Reduce red) {
+  typedef typename cplx_t<R>::type C;
+  __shared__ double2 tot[64];
+  double2 acc[1] = {make_double2(0.0, 0.0)};
+  const int64_t n = (int64_t)g.V << logb;
+  const int j = threadIdx.x & (b - 1);
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n; it += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(it >> logb);
+    C o[12], self[12];
+    dslash_site<1, R>(U, p, g, b, s, j, diag, o, self);
+    const int64_t base = (int64_t)s * 12 * b + j;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      v[base + c * b] = o[c];
+      acc[0] = dot_acc(acc[0], rhat[base + c * b], o[c]);
+    }
+  }
+  if (block_reduce<1>(acc, b, red.partial, red.counter, tot)) {
+    if (threadIdx.x < b) fin_alpha(sc, threadIdx.x, tot[threadIdx.x]);
+  }
+}
+
+// s = r - alpha v (in place in r)
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_supdate(typename cplx_t<R>::type *__restrict__ r,
+                                                    const typename cplx_t<R>::type *__restrict__ v, int64_t n, int b,
+                                                    const Scal *__restrict__ sc) {
+  typedef typename cplx_t<R>::type C;
+  const int j = threadIdx.x & (b - 1);
+  const C a = scal_as<C>(sc->alpha[j]);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    r[e] = caxpy(cneg(a), v[e], r[e]);
+  }
+}
+
+// t = A s; (t^H s, t^H t) -> omega
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_dslash_omega(const typename cplx_t<R>::type *__restrict__ U,
+                                                         const typename cplx_t<R>::type *__restrict__ sv,
+                                                         typename cplx_t<R>::type *__restrict__ t, Geom g, int b,
+                                                         int logb, R diag, Scal *sc, Reduce red) {
+  typedef typename cplx_t<R>::type C;
+  __shared__ double2 tot[128];
+  double2 acc[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+  const int64_t n = (int64_t)g.V << logb;
+  const int j = threadIdx.x & (b - 1);
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n; it += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(it >> logb);
+    C o[12], self[12];
+    dslash_site<1, R>(U, sv, g, b, s, j, diag, o, self);
+    const int64_t base = (int64_t)s * 12 * b + j;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      t[base + c * b] = o[c];
+      acc[0] = dot_acc(acc[0], o[c], self[c]);
+      acc[1].x += (double)o[c].x * o[c].x + (double)o[c].y * o[c].y;
+    }
+  }
+  if (block_reduce<2>(acc, b, red.partial, red.counter, tot)) {
+    if (threadIdx.x < b) fin_omega(sc, threadIdx.x, tot[threadIdx.x], tot[b + threadIdx.x]);
+  }
+}
+
+// x += alpha p + omega s; r = s - omega t; (rhat^H r, r^H r) -> beta, convergence
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_xr_update(typename cplx_t<R>::type *__restrict__ x,
+                                                      typename cplx_t<R>::type *__restrict__ r,
+                                                      const typename cplx_t<R>::type *__restrict__ p,
+                                                      const typename cplx_t<R>::type *__restrict__ t,
+                                                      const typename cplx_t<R>::type *__restrict__ rhat, int64_t n,
+                                                      int b, Scal *sc, Reduce red) {
+  typedef typename cplx_t<R>::type C;
+  __shared__ double2 tot[128];
+  double2 acc[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+  const int j = threadIdx.x & (b - 1);
+  const C a = scal_as<C>(sc->alpha[j]);
+  const C w = scal_as<C>(sc->omega[j]);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const C s = r[e];
+    x[e] = caxpy(w, s, caxpy(a, p[e], x[e]));
+    const C rn = caxpy(cneg(w), t[e], s);
+    r[e] = rn;
+    acc[0] = dot_acc(acc[0], rhat[e], rn);
+    acc[1].x += (double)rn.x * rn.x + (double)rn.y * rn.y;
+  }
+  if (block_reduce<2>(acc, b, red.partial, red.counter, tot)) {
+    if (threadIdx.x < b) fin_beta(sc, threadIdx.x, tot[threadIdx.x], tot[b + threadIdx.x]);
+    __syncthreads();
+    if (threadIdx.x == 0) count_active(sc, b);
+  }
+}
+
+// p = r + beta (p - omega v) for active columns
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_pupdate(typename cplx_t<R>::type *__restrict__ p,
+                                                    const typename cplx_t<R>::type *__restrict__ r,
+                                                    const typename cplx_t<R>::type *__restrict__ v, int64_t n, int b,
+                                                    const Scal *__restrict__ sc) {
+  typedef typename cplx_t<R>::type C;
+  const int j = threadIdx.x & (b - 1);
+  if (!sc->active[j]) return;
+  const C be = scal_as<C>(sc->beta[j]);
+  const C w = scal_as<C>(sc->omega[j]);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    p[e] = caxpy(be, caxpy(cneg(w), v[e], p[e]), r[e]);
+  }
+}
+
+// mixed: r32 = scale * r64, rhat = p = r32, e = 0 (inner columns = outer active)
+__global__ void __launch_bounds__(kBlock) k_mixed_init(const double2 *__restrict__ r64, float2 *__restrict__ r,
+                                                       float2 *__restrict__ rhat, float2 *__restrict__ p,
+                                                       float2 *__restrict__ e, int64_t n, int b,
+                                                       const Scal *__restrict__ outer) {
+  const int j = threadIdx.x & (b - 1);
+  const double sc = outer->active[j] ? outer->scale[j] : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = r64[i];
+    const float2 f = make_float2((float)(v.x * sc), (float)(v.y * sc));
+    r[i] = f;
+    rhat[i] = f;
+    p[i] = f;
+    e[i] = make_float2(0.f, 0.f);
+  }
+}
+
+__global__ void k_mixed_scal_init(const Scal *__restrict__ outer, Scal *inner, int b, double inner_tol2,
+                                  int inner_maxiter) {
+  const int j = threadIdx.x;
+  if (j < b) {
+    const int act = outer->active[j];
+    inner->active[j] = act;
+    inner->rho[j] = make_double2(1.0, 0.0);
+    inner->bnorm2[j] = 1.0;
+    inner->rnorm2[j] = 1.0;
+    inner->iters[j] = 0;
+    inner->flags[j] = 0;
+    inner->alpha[j] = inner->omega[j] = inner->beta[j] = make_double2(0.0, 0.0);
+  }
+  if (j == 0) {
+    int n = 0;
+    for (int q = 0; q < b; ++q) n += outer->active[q];
+    inner->n_active = n;
+    inner->tol2 = inner_tol2;
+    inner->maxiter = inner_maxiter;
+  }
+}
+
+// x64 += e / scale for outer-active columns; fold inner iteration counts.
+__global__ void __launch_bounds__(kBlock) k_mixed_accum(double2 *__restrict__ x, const float2 *__restrict__ e,
+                                                        int64_t n, int b, Scal *outer, const Scal *__restrict__ inner) {
+  const int j = threadIdx.x & (b - 1);
+  const int act = outer->active[j];
+  const double inv = act ? 1.0 / outer->scale[j] : 0.0;
+  if (act) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      const float2 v = e[i];
+      double2 xv = x[i];
+      xv.x = fma((double)v.x, inv, xv.x);
+      xv.y = fma((double)v.y, inv, xv.y);
+      x[i] = xv;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x < b) {
+    outer->iters[threadIdx.x] += inner->iters[threadIdx.x];
+    outer->flags[threadIdx.x] |= inner->flags[threadIdx.x] & ~kFlagBreakdown;
+  }
+}
+
+__global__ void k_scal_init(Scal *sc, int b, double tol2, int maxiter) {
+  const int j = threadIdx.x;
+  if (j < 64) {
+    sc->active[j] = 0;
+    sc->iters[j] = 0;
+    sc->restarts[j] = 0;
+    sc->conv[j] = 0;
+    sc->flags[j] = 0;
+    sc->rho[j] = sc->alpha[j] = sc->omega[j] = sc->beta[j] = make_double2(0.0, 0.0);
+    sc->rnorm2[j] = sc->bnorm2[j] = sc->rtrue2[j] = 0.0;
+    sc->scale[j] = 1.0;
+  }
+  if (j == 0) {
+    sc->n_active = 0;
+    sc->tol2 = tol2;
+    sc->maxiter = maxiter;
+  }
+}
+
+// ------------------------------------------------------------------ drivers
+static int ilog2i(int b) {
+  int l = 0;
+  while ((1 << l) < b) ++l;
+  return l;
+}
+
+static int *pinned_flag() {
+  static thread_local int *p = nullptr;
+  if (!p) {
+    if (cudaMallocHost((void **)&p, sizeof(int) * 4) != cudaSuccess) p = nullptr;
+  }
+  return p;
+}
+
+static int read_n_active(const Scal *sc, cudaStream_t st, int *out) {
+  int *h = pinned_flag();
+  if (!h) return fail(DTR_ECUDA, "cudaMallocHost for the convergence flag failed");
+  DTR_CUDA(cudaMemcpyAsync(h, &sc->n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DTR_CUDA(cudaStreamSynchronize(st));
+  *out = *h;
+  return DTR_OK;
+}
+
+template <typename R>
+static void launch_iteration(const typename cplx_t<R>::type *U, KrylovVecs<R> &K, const Geom &g, int b, double m0,
+                             Scal *sc, Reduce red, cudaStream_t st) {
+  const int sms = device_sms();
+  const int logb = ilog2i(b);
+  const int64_t sites_items = (int64_t)g.V * b;
+  const int64_t n = sites_items * 12;
+  const unsigned gd = reduce_grid(sites_items, sms);
+  const unsigned gv = reduce_grid(n, sms);
+  const R diag = (R)(4.0 + m0);
+  k_dslash_alpha<R><<<gd, kBlock, 0, st>>>(U, K.p, K.rhat, K.v, g, b, logb, diag, sc, red);
+  k_supdate<R><<<gv, kBlock, 0, st>>>(K.r, K.v, n, b, sc);
+  k_dslash_omega<R><<<gd, kBlock, 0, st>>>(U, K.r, K.t, g, b, logb, diag, sc, red);
+  k_xr_update<R><<<gv, kBlock, 0, st>>>(K.x, K.r, K.p, K.t, K.rhat, n, b, sc, red);
+  k_pupdate<R><<<gv, kBlock, 0, st>>>(K.p, K.r, K.v, n, b, sc);
+}
+
+template <typename R>
+static int iterate(const typename cplx_t<R>::type *U, KrylovVecs<R> &K, const Geom &g, int b, double m0, Scal *sc,
+                   Reduce red, int check_every, int max_total, cudaStream_t st) {
+  int done = 0;
+  while (done < max_total) {
+    for (int c = 0; c < check_every; ++c) launch_iteration<R>(U, K, g, b, m0, sc, red, st);
+    DTR_LAUNCH_CHECK("bicgstab iteration launch");
+    done += check_every;
+    int n_active = 0;
+    int rc = read_n_active(sc, st, &n_active);
+    if (rc) return rc;
+    if (n_active == 0) break;
+  }
+  return DTR_OK;
+}
+
+size_t solver_scratch_bytes(int64_t V, int b, int solver) {
+  const size_t vec64 = ((size_t)V * 12 * b * sizeof(double2) + 255) / 256 * 256;
+  const size_t vec32 = ((size_t)V * 12 * b * sizeof(float2) + 255) / 256 * 256;
+  const size_t red = 256 + (size_t)kMaxGrid * 2 * 64 * sizeof(double2);
+  const size_t scal = 2 * ((sizeof(Scal) + 255) / 256) * 256;
+  const size_t fixed = 256 + red + scal + 256;
+  if (solver == DTR_SOLVER_MIXED_F32) return fixed + vec64 + 6 * vec32;
+  return fixed + 5 * vec64;
+}
+
+static char *align256(char *p) { return (char *)(((uintptr_t)p + 255) & ~(uintptr_t)255); }
+
+// x (internal FP64, initial guess in / solution out), z (internal FP64)
+int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double2 *z, int b,
+                   const dtr_solve_params *p, void *work, size_t work_bytes, cudaStream_t st, Scal **scal_out) {
+  const Geom g = geom_of(gauge->lat);
+  const int64_t n = (int64_t)g.V * 12 * b;
+  if (work_bytes < solver_scratch_bytes(g.V, b, p->solver)) return fail(DTR_ENOMEM, "solver workspace too small");
+  char *w = align256((char *)work);
+  Reduce red;
+  red.counter = (unsigned int *)w;
+  w = align256(w + 256);
+  red.partial = (double2 *)w;
+  w = align256(w + (size_t)kMaxGrid * 2 * 64 * sizeof(double2));
+  Scal *outer = (Scal *)w;
+  w = align256(w + sizeof(Scal));
+  Scal *inner = (Scal *)w;
+  w = align256(w + sizeof(Scal));
+  DTR_CUDA(cudaMemsetAsync(red.counter, 0, 256, st));
+  const int sms = device_sms();
+  const int logb = ilog2i(b);
+  const unsigned gd = reduce_grid((int64_t)g.V * b, sms);
+  const unsigned gv = reduce_grid(n, sms);
+  const int check = p->check_every > 0 ? p->check_every : 8;
+  k_scal_init<<<1, 64, 0, st>>>(outer, b, p->tol * p->tol, p->maxiter);
+  DTR_LAUNCH_CHECK("scalar init");
+  *scal_out = outer;
+
+  if (p->solver == DTR_SOLVER_BICGSTAB_F64) {
+    KrylovVecs<double> K;
+    K.x = x;
+    K.r = (double2 *)w;    w = align256(w + n * sizeof(double2));
+    K.rhat = (double2 *)w; w = align256(w + n * sizeof(double2));
+    K.p = (double2 *)w;    w = align256(w + n * sizeof(double2));
+    K.v = (double2 *)w;    w = align256(w + n * sizeof(double2));
+    K.t = (double2 *)w;    w = align256(w + n * sizeof(double2));
+    for (int cycle = 0; cycle < 64; ++cycle) {
+      k_resid<double, 1><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, K.r, K.rhat, K.p, g, b, logb, 4.0 + m0, outer, red,
+                                                 1);
+      DTR_LAUNCH_CHECK("residual");
+      int n_active = 0;
+      int rc = read_n_active(outer, st, &n_active);
+      if (rc) return rc;
+      if (n_active == 0) break;
+      rc = iterate<double>(gauge->U64, K, g, b, m0, outer, red, check, p->maxiter + check, st);
+      if (rc) return rc;
+    }
+    // final true residual for the statistics (no restart)
+    k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, K.r, K.rhat, K.p, g, b, logb, 4.0 + m0, outer, red, 0);
+    DTR_LAUNCH_CHECK("final residual");
+    return DTR_OK;
+  }
+  if (p->solver == DTR_SOLVER_MIXED_F32) {
+    double2 *r64 = (double2 *)w; w = align256(w + n * sizeof(double2));
+    KrylovVecs<float> K;
+    K.x = (float2 *)w;    w = align256(w + n * sizeof(float2));
+    K.r = (float2 *)w;    w = align256(w + n * sizeof(float2));
+    K.rhat = (float2 *)w; w = align256(w + n * sizeof(float2));
+    K.p = (float2 *)w;    w = align256(w + n * sizeof(float2));
+    K.v = (float2 *)w;    w = align256(w + n * sizeof(float2));
+    K.t = (float2 *)w;    w = align256(w + n * sizeof(float2));
+    const double itol = p->inner_tol > 0 ? p->inner_tol : 1e-5;
+    for (int cycle = 0; cycle < 64; ++cycle) {
+      k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0, outer,
+                                                 red, 1);
+      DTR_LAUNCH_CHECK("outer residual");
+      int n_active = 0;
+      int rc = read_n_active(outer, st, &n_active);
+      if (rc) return rc;
+      if (n_active == 0) break;
+      k_mixed_init<<<gv, kBlock, 0, st>>>(r64, K.r, K.rhat, K.p, K.x, n, b, outer);
+      k_mixed_scal_init<<<1, 64, 0, st>>>(outer, inner, b, itol * itol, p->maxiter);
+      DTR_LAUNCH_CHECK("inner init");
+      rc = iterate<float>(gauge->U32, K, g, b, m0, inner, red, check, p->maxiter + check, st);
+      if (rc) return rc;
+      k_mixed_accum<<<gv, kBlock, 0, st>>>(x, K.x, n, b, outer, inner);
+      DTR_LAUNCH_CHECK("defect accumulate");
+    }
+    k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0, outer,
+                                               red, 0);
+    DTR_LAUNCH_CHECK("final residual");
+    return DTR_OK;
+  }
+  return fail(DTR_EINVAL, "unknown solver");
+}
+
+}  // namespace dtr

@@ -1,0 +1,34 @@
+// Solver state shared between the solver and the estimator driver.
+#pragma once
+
+#include "dtr_internal.cuh"
+
+namespace dtr {
+
+constexpr int kFlagNaN = 1;
+constexpr int kFlagBreakdown = 2;
+
+// Per-column Krylov scalars, resident in device memory (b <= 64 columns).
+struct Scal {
+  double2 rho[64], alpha[64], omega[64], beta[64];
+  double rnorm2[64], bnorm2[64], rtrue2[64], scale[64];
+  int active[64], iters[64], restarts[64], conv[64], flags[64];
+  int n_active;
+  int maxiter;
+  double tol2;
+};
+
+template <typename R> struct KrylovVecs {
+  typename cplx_t<R>::type *x, *r, *rhat, *p, *v, *t;
+};
+
+// Scratch the solver needs beyond the solution and right-hand-side blocks.
+size_t solver_scratch_bytes(int64_t V, int b, int solver);
+
+// Solve A x = z on internal-layout FP64 blocks of width b.  x holds the
+// initial guess on entry.  *scal receives the device pointer of the final
+// per-column statistics (inside `work`).
+int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double2 *z, int b,
+                   const dtr_solve_params *p, void *work, size_t work_bytes, cudaStream_t st, Scal **scal);
+
+}  // namespace dtr

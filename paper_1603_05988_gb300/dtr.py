@@ -1,0 +1,327 @@
+"""Thin ctypes binding of libdtr (C ABI in include/dtr.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  PyTorch provides device memory (fields, workspaces) and the current
+stream.  Fields are torch.complex128 CUDA tensors of shape (nrhs, N), i.e.
+the C ABI's column-major N x nrhs block (column j = row j here), N = 12 V,
+dof i = 12*site + 3*spin + colour.
+
+There is no fallback: if the shared library is missing or fails to load,
+importing this module raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libdtr.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libdtr.so not built: run `python -m paper_1603_05988_gb300.build` "
+                      "(or __graft_entry__.build()) first")
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---------------------------------------------------------------- C structs
+DTR_OK, DTR_EINVAL, DTR_ENOMEM, DTR_ECUDA, DTR_ENOTCONV, DTR_ENAN = range(6)
+DTR_F64, DTR_F32, DTR_BF16, DTR_F16 = range(4)
+SOLVER_F64, SOLVER_MIXED_F32 = 0, 1
+_PREC = {"f64": DTR_F64, "f32": DTR_F32, "bf16": DTR_BF16, "f16": DTR_F16}
+_SOLVER = {"f64": SOLVER_F64, "mixed_f32": SOLVER_MIXED_F32}
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("solver", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("inner_tol", ctypes.c_double)]
+
+
+class SolveStat(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
+                ("pad_", ctypes.c_int), ("true_residual", ctypes.c_double)]
+
+
+class TraceParams(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("z0_first", ctypes.c_int64), ("n_z0", ctypes.c_int),
+                ("ncolors", ctypes.c_int), ("nvec", ctypes.c_int), ("dilute12", ctypes.c_int),
+                ("block", ctypes.c_int), ("use_x0", ctypes.c_int), ("solve", SolveParams)]
+
+
+class TraceResult(ctypes.Structure):
+    _fields_ = [("trace", ctypes.c_double * 2), ("T_D", ctypes.c_double * 2), ("var_runs", ctypes.c_double),
+                ("jk_err", ctypes.c_double), ("var_samples", ctypes.c_double), ("n_solves", ctypes.c_int64),
+                ("iterations", ctypes.c_int64), ("max_true_residual", ctypes.c_double),
+                ("all_converged", ctypes.c_int), ("pad_", ctypes.c_int),
+                ("samples", ctypes.POINTER(ctypes.c_double)), ("trace_runs", ctypes.POINTER(ctypes.c_double)),
+                ("replay", ctypes.POINTER(ctypes.c_double))]
+
+
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_i = ctypes.c_int
+_d = ctypes.c_double
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("dtr_last_error", ctypes.c_char_p, [])
+_sig("dtr_version", ctypes.c_char_p, [])
+_sig("dtr_make_lattice", _i, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_vp)])
+_sig("dtr_destroy_lattice", None, [_vp])
+_sig("dtr_lattice_info", _i, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64), ctypes.POINTER(_i64)])
+_sig("dtr_make_gauge", _i, [_vp, _vp, ctypes.POINTER(_vp)])
+_sig("dtr_gauge_to_host", _i, [_vp, _vp])
+_sig("dtr_destroy_gauge", None, [_vp])
+_sig("dtr_dslash_workspace_bytes", _sz, [_vp, _i])
+_sig("dtr_dslash", _i, [_vp, _d, _vp, _vp, _i, _i, _i, _vp, _sz, _vp])
+_sig("dtr_gen_noise", _i, [_vp, _u64, _i64, _i, _i, _i64, _i, _vp, _vp])
+_sig("dtr_solve_params_default", None, [ctypes.POINTER(SolveParams)])
+_sig("dtr_solve_workspace_bytes", _sz, [_vp, _i, ctypes.POINTER(SolveParams)])
+_sig("dtr_solve_batch", _i, [_vp, _d, _vp, _vp, _i, ctypes.POINTER(SolveParams), _vp, _sz,
+                             ctypes.POINTER(SolveStat), _vp])
+_sig("dtr_defl_create", _i, [_vp, _i, _i, _vp, _vp, ctypes.POINTER(_vp)])
+_sig("dtr_defl_trace", _i, [_vp, ctypes.POINTER(ctypes.c_double)])
+_sig("dtr_destroy_defl", None, [_vp])
+_sig("dtr_deflate_workspace_bytes", _sz, [_vp, _i])
+_sig("dtr_deflate_project", _i, [_vp, _vp, _i, _vp, _vp, _vp, _vp, _sz, _vp])
+_sig("dtr_trace_workspace_bytes", _sz, [_vp, _vp, ctypes.POINTER(TraceParams)])
+_sig("dtr_trace_estimate", _i, [_vp, _d, _vp, ctypes.POINTER(TraceParams), _vp, _sz,
+                                ctypes.POINTER(TraceResult), _vp])
+
+
+class DtrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("dtr error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _check(rc, allow=()):
+    if rc != DTR_OK and rc not in allow:
+        raise DtrError(rc, _lib.dtr_last_error().decode())
+    return rc
+
+
+def version():
+    return _lib.dtr_version().decode()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    return _vp(_torch().cuda.current_stream().cuda_stream)
+
+
+def _workspace(nbytes):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device="cuda")
+
+
+def _ptr(t):
+    return _vp(t.data_ptr())
+
+
+def _field(t, N, name):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128):
+        raise TypeError("%s must be a CUDA complex128 tensor" % name)
+    if t.dim() == 1:
+        t = t.reshape(1, -1)
+    if t.shape[-1] != N or not t.is_contiguous():
+        raise ValueError("%s must be contiguous with shape (nrhs, %d)" % (name, N))
+    return t
+
+
+# ------------------------------------------------------------------- handles
+class Lattice:
+    def __init__(self, dims):
+        d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+        h = _vp()
+        _check(_lib.dtr_make_lattice(d, ctypes.byref(h)))
+        self._h = h
+        self.dims = tuple(int(x) for x in dims)
+        self.V = int(np.prod(self.dims))
+        self.N = 12 * self.V
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.dtr_destroy_lattice(self._h)
+            self._h = None
+
+
+def make_lattice(dims):
+    return Lattice(dims)
+
+
+class Gauge:
+    def __init__(self, lat, links):
+        links = np.ascontiguousarray(links, dtype=np.complex128)
+        if links.shape != (lat.V, 4, 3, 3):
+            raise ValueError("links must have shape (V, 4, 3, 3)")
+        h = _vp()
+        _check(_lib.dtr_make_gauge(lat._h, links.ctypes.data_as(_vp), ctypes.byref(h)))
+        self._h = h
+        self.lat = lat
+
+    def to_host(self):
+        out = np.empty((self.lat.V, 4, 3, 3), dtype=np.complex128)
+        _check(_lib.dtr_gauge_to_host(self._h, out.ctypes.data_as(_vp)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.dtr_destroy_gauge(self._h)
+            self._h = None
+
+
+def make_gauge(lat, links):
+    return Gauge(lat, links)
+
+
+def dslash(gauge, m0, x, dagger=False, prec="f64"):
+    """out = A x (or A^H x) for x of shape (nrhs, N), nrhs <= 64."""
+    torch = _torch()
+    lat = gauge.lat
+    x = _field(x, lat.N, "x")
+    nrhs = x.shape[0]
+    out = torch.empty_like(x)
+    nb = _lib.dtr_dslash_workspace_bytes(lat._h, nrhs)
+    w = _workspace(nb)
+    _check(_lib.dtr_dslash(gauge._h, float(m0), _ptr(x), _ptr(out), nrhs, int(bool(dagger)), _PREC[prec],
+                           _ptr(w), nb, _stream()))
+    return out
+
+
+def gen_noise(lat, seed, z0_index, ncolors, dilute12, q0, nrhs):
+    """Probing vectors z = z0 .* z_h, shape (nrhs, N) complex128 on the GPU."""
+    torch = _torch()
+    out = torch.empty((nrhs, lat.N), dtype=torch.complex128, device="cuda")
+    _check(_lib.dtr_gen_noise(lat._h, int(seed), int(z0_index), int(ncolors), int(bool(dilute12)), int(q0),
+                              int(nrhs), _ptr(out), _stream()))
+    return out
+
+
+def solve_params(tol=1e-10, maxiter=5000, solver="f64", check_every=8, inner_tol=1e-5):
+    p = SolveParams()
+    _lib.dtr_solve_params_default(ctypes.byref(p))
+    p.tol, p.maxiter, p.solver, p.check_every, p.inner_tol = tol, maxiter, _SOLVER[solver], check_every, inner_tol
+    return p
+
+
+def solve_batch(gauge, m0, z, y0=None, params=None, allow_notconv=False):
+    """Solve A y = z for z of shape (nrhs, N); returns (y, stats list of dicts)."""
+    torch = _torch()
+    lat = gauge.lat
+    z = _field(z, lat.N, "z")
+    nrhs = z.shape[0]
+    y = torch.zeros_like(z) if y0 is None else _field(y0, lat.N, "y0").clone()
+    p = params if params is not None else solve_params()
+    nb = _lib.dtr_solve_workspace_bytes(lat._h, nrhs, ctypes.byref(p))
+    w = _workspace(nb)
+    st = (SolveStat * nrhs)()
+    rc = _lib.dtr_solve_batch(gauge._h, float(m0), _ptr(z), _ptr(y), nrhs, ctypes.byref(p), _ptr(w), nb, st,
+                              _stream())
+    _check(rc, allow=(DTR_ENOTCONV,) if allow_notconv else ())
+    stats = [dict(iterations=s.iterations, restarts=s.restarts, converged=bool(s.converged), flags=s.pad_,
+                  true_residual=s.true_residual) for s in st]
+    return y, stats
+
+
+class Deflation:
+    def __init__(self, lat, V, lam, prec="f64"):
+        V = np.asarray(V, dtype=np.complex128)
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        if V.ndim != 2 or V.shape[0] != lat.N or V.shape[1] != lam.shape[0]:
+            raise ValueError("V must be (N, k) and lambda (k,)")
+        k = V.shape[1]
+        Vc = np.asfortranarray(V)   # column-major N x k
+        h = _vp()
+        _check(_lib.dtr_defl_create(lat._h, k, _PREC[prec], Vc.ctypes.data_as(_vp), lam.ctypes.data_as(_vp),
+                                    ctypes.byref(h)))
+        self._h = h
+        self.lat = lat
+        self.k = k
+
+    def T_D(self):
+        td = (ctypes.c_double * 2)()
+        _check(_lib.dtr_defl_trace(self._h, td))
+        return complex(td[0], td[1])
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.dtr_destroy_defl(self._h)
+            self._h = None
+
+
+def defl_create(lat, V, lam, prec="f64"):
+    return Deflation(lat, V, lam, prec)
+
+
+def deflate_project(defl, z, want_coeff=False, want_x0=False):
+    """Returns (d, C or None, x0 or None): d_j = z_j^H V diag(1/lambda) V^H g5 z_j."""
+    torch = _torch()
+    lat = defl.lat
+    z = _field(z, lat.N, "z")
+    nrhs = z.shape[0]
+    d = torch.empty(nrhs, dtype=torch.complex128, device="cuda")
+    C = torch.empty((2 * nrhs, defl.k), dtype=torch.complex128, device="cuda") if want_coeff else None
+    x0 = torch.empty_like(z) if want_x0 else None
+    nb = _lib.dtr_deflate_workspace_bytes(defl._h, nrhs)
+    w = _workspace(nb)
+    _check(_lib.dtr_deflate_project(defl._h, _ptr(z), nrhs, _ptr(d), _ptr(C) if C is not None else None,
+                                    _ptr(x0) if x0 is not None else None, _ptr(w), nb, _stream()))
+    return d, C, x0
+
+
+def trace_params(seed=0, z0_first=0, n_z0=1, ncolors=1, nvec=1, dilute12=False, block=16, use_x0=False,
+                 solve=None):
+    p = TraceParams()
+    p.seed, p.z0_first, p.n_z0, p.ncolors, p.nvec = int(seed), int(z0_first), int(n_z0), int(ncolors), int(nvec)
+    p.dilute12, p.block, p.use_x0 = int(bool(dilute12)), int(block), int(bool(use_x0))
+    p.solve = solve if solve is not None else solve_params()
+    return p
+
+
+class TraceWorkspace:
+    """Reusable device workspace for repeated trace_estimate calls."""
+
+    def __init__(self, gauge, defl, params):
+        self.nbytes = _lib.dtr_trace_workspace_bytes(gauge._h, defl._h if defl else None, ctypes.byref(params))
+        self.buf = _workspace(self.nbytes)
+
+
+def trace_estimate(gauge, m0, defl, params, workspace=None, want_samples=True, want_replay=False,
+                   allow_notconv=False):
+    """Algorithm 1 over params.n_z0 runs; returns a dict of results."""
+    R, s = params.n_z0, params.nvec
+    k = defl.k if defl is not None else 0
+    ws = workspace if workspace is not None else TraceWorkspace(gauge, defl, params)
+    res = TraceResult()
+    samples = np.zeros(2 * R * s) if want_samples else None
+    runs = np.zeros(2 * R)
+    replay = np.zeros(2 * R * s * max(k, 1)) if (want_replay and k) else None
+    dp = ctypes.POINTER(ctypes.c_double)
+    res.samples = samples.ctypes.data_as(dp) if samples is not None else None
+    res.trace_runs = runs.ctypes.data_as(dp)
+    res.replay = replay.ctypes.data_as(dp) if replay is not None else None
+    rc = _lib.dtr_trace_estimate(gauge._h, float(m0), defl._h if defl is not None else None, ctypes.byref(params),
+                                 _ptr(ws.buf), ws.nbytes, ctypes.byref(res), _stream())
+    _check(rc, allow=(DTR_ENOTCONV,) if allow_notconv else ())
+    out = dict(trace=complex(res.trace[0], res.trace[1]), T_D=complex(res.T_D[0], res.T_D[1]),
+               var_runs=res.var_runs, jk_err=res.jk_err, var_samples=res.var_samples, n_solves=res.n_solves,
+               iterations=res.iterations, max_true_residual=res.max_true_residual,
+               all_converged=bool(res.all_converged), status=rc,
+               trace_runs=runs[0::2] + 1j * runs[1::2])
+    if samples is not None:
+        out["samples"] = (samples[0::2] + 1j * samples[1::2]).reshape(R, s)
+    if replay is not None:
+        out["replay"] = (replay[0::2] + 1j * replay[1::2]).reshape(R, s, k)
+    return out

@@ -174,6 +174,20 @@ def test_deflated_quadrature_equals_gamma5_form():
     V, lam, sig = deflation.smallest_triplets(Ad, 16)
     Z = noise.noise_vectors((2, 2, 2, 4), 4, 1, 16, False, 0, 16)
     d_paper = deflation.quadrature(AH, V, sig, Z)
-    g5Z = wilson.gamma5_vec(Z)
-    d_g5 = np.sum(np.conj(V.conj().T @ Z) * ((V.conj().T @ g5Z) / lam[:, None]), axis=0)
+    d_g5 = deflation.quadrature_gamma5(V, lam, Z)
     assert np.abs(d_paper - d_g5).max() < 1e-12 * np.abs(d_paper).max()
+    assert abs(deflation.T_D(AH, V, sig) - deflation.T_D_gamma5(V, lam)) < 1e-12 * abs(deflation.T_D(AH, V, sig))
+
+
+def test_gamma5_form_unbiased_for_any_deflation_space():
+    """Complete probing at 4^4: T_D_gamma5 + mean(t) = Tr(A^-1) for a random
+    V and random signed lambda (trace linearity)."""
+    dims = (4, 4, 4, 4)
+    U, A, AH, Ad, tr, Ainv = _small_problem(dims)
+    N = Ad.shape[0]
+    V = synth.random_orthonormal(N, 12, 8)
+    lam = np.linspace(-1.5, 1.7, 12) + 0.05
+    Z = noise.noise_vectors(dims, 4, 0, 256, True, 0, 3072)
+    t = np.einsum("ij,ij->j", np.conj(Z), Ainv @ Z) - deflation.quadrature_gamma5(V, lam, Z)
+    est = deflation.T_D_gamma5(V, lam) + t.sum() / 256
+    assert abs(est - tr) < 1e-11 * abs(tr)
