@@ -1,0 +1,337 @@
+#!/usr/bin/env python3
+"""Benchmark of the deflated hierarchical-probing trace estimator (Algorithm 1)
+on the 8^4 Wilson-Dirac workload: eps 0.7, m0 -0.6, 16-colour hierarchical
+probing per Z4 vector z0, blocks of 16 right-hand sides per launch, k = 100
+FP64 deflation vectors, solves to a true relative residual of 1e-10.
+
+One step = one z0 run of the whole path (noise + HP mask, deflation
+projection, 16 batched solves, FP64 z^H y reductions and run statistics) =
+16 right-hand sides.  Metric: right-hand sides solved per second (whole job),
+plus the variance x time figure of merit (time to a 1e-3 relative trace error)
+for the mixed-precision path and for the plain FP64 path on the same seeds.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the program the CUDA path is
+checked against) on a bounded sample of the same workload.  Under torchrun
+(N > 1) every rank runs its own z0 runs (weak scaling, no data-path
+collective); rank 0 prints the line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "wilson8x8x8x8_hp16x256_k100"
+METRIC = "RHS solves/s (deflated HP Tr(A^-1) estimator, true residual 1e-10)"
+UNIT = "RHS/s"
+L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--solver", default="mixed_f32", choices=["mixed_f32", "f64"])
+    ap.add_argument("--f64-steps", type=int, default=6, help="steps of the plain FP64 path timed for comparison")
+    ap.add_argument("--cpu-sample-rhs", type=int, default=1, help="RHS in the CPU-oracle baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms in a thread."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle
+CPU_SAMPLE_CODE = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_1603_05988_gb300 import synth
+from oracle import noise, solve, wilson, deflation
+w = synth.WORKLOADS[sys.argv[2]]
+nrhs, reps = int(sys.argv[3]), int(sys.argv[4])
+U = synth.random_su3_links(w.dims, w.eps, w.gauge_seed)
+A = wilson.explicit(U, w.dims, w.m0)
+AH = wilson.explicit_dagger(U, w.dims, w.m0)
+V = synth.random_orthonormal(w.N, w.k, 0)
+sig = np.linspace(0.9, 1.4, w.k)
+times = []
+for r in range(reps):
+    t0 = time.perf_counter()
+    Z = noise.noise_vectors(w.dims, w.noise_seed, 100000 + r, w.ncolors, False, 0, nrhs)
+    Y, it, res = solve.cgnr(A, Z, tol=w.tol)
+    t = np.einsum("ij,ij->j", np.conj(Z), Y) - deflation.quadrature(AH, V, sig, Z)
+    times.append(time.perf_counter() - t0)
+print(json.dumps({"times": times, "iters": int(it), "res": float(np.max(res))}))
+"""
+
+
+def cpu_oracle_sample(nrhs, reps):
+    """Run the FP64 oracle (one thread) on `reps` samples of `nrhs` RHS each."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    out = subprocess.run([sys.executable, "-c", CPU_SAMPLE_CODE, ROOT, WORKLOAD, str(nrhs), str(reps)],
+                         capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError("CPU oracle sample failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    steps, warm = args.steps, args.warmup
+    # one RHS per step: the oracle's Algorithm 1 quadrature on one probing vector
+    r = cpu_oracle_sample(1, steps + warm)
+    ts = r["times"][warm:]
+    value = len(ts) / sum(ts)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * sum(ts) / len(ts), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step": "1 RHS (CPU oracle sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d steps x 1 RHS at 8^4, CGNR to 1e-10 + deflation quadrature (paper A^H form)"
+                                   % steps},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU path
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+
+    from paper_1603_05988_gb300 import build as _build
+    if not os.path.exists(_build.LIB):
+        _build.build()
+    from paper_1603_05988_gb300 import dtr, eigensolver, synth
+
+    w = synth.WORKLOADS[WORKLOAD]
+    U = synth.random_su3_links(w.dims, w.eps, w.gauge_seed)
+    lat = dtr.make_lattice(w.dims)
+    gauge = dtr.make_gauge(lat, U)
+    t0 = time.perf_counter()
+    V, lam, eres, eit = eigensolver.smallest_gamma5_eigpairs(gauge, w.m0, w.k, iters=60, tol=1e-2, seed=rank)
+    t_setup = time.perf_counter() - t0
+    defl = dtr.defl_create(lat, V, lam, prec=w.defl_prec)
+
+    def params(solver, z0):
+        return dtr.trace_params(seed=w.noise_seed, z0_first=z0, n_z0=1, ncolors=w.ncolors, nvec=w.ncolors,
+                                block=w.block, solve=dtr.solve_params(tol=w.tol, solver=solver))
+
+    wss = {s: dtr.TraceWorkspace(gauge, defl, params(s, 0)) for s in {args.solver, "f64"}}
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    base = rank * 1000003
+
+    def run_steps(solver, nsteps, first, timed):
+        ms, traces, iters = [], [], 0
+        for i in range(nsteps):
+            flush.fill_(i & 0xFF)                       # evict L2 between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = dtr.trace_estimate(gauge, w.m0, defl, params(solver, first + i), workspace=wss[solver])
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            traces.append(out["trace_runs"][0])
+            iters += out["iterations"]
+            if not out["all_converged"] or out["max_true_residual"] > w.tol:
+                raise RuntimeError("step did not converge: %r" % (out["max_true_residual"],))
+        return ms, traces, iters
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # warm-up
+    run_steps(args.solver, args.warmup, base + 900000, False)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = dtr.kernel_launches()
+    ms, traces, iters = run_steps(args.solver, args.steps, base, True)
+    launches = dtr.kernel_launches() - launches0
+    barrier()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(sum(ms))
+    rhs_per_step = w.ncolors
+    value = rhs_per_step * args.steps * world / (total_ms / 1e3)
+
+    # end-to-end through the public call with host-side results (host wall clock)
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        out = dtr.trace_estimate(gauge, w.m0, defl, params(args.solver, base + i), workspace=wss[args.solver])
+        _ = out["samples"].sum()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = rhs_per_step * args.steps * world / e2e_s
+
+    # plain FP64 path on the same seeds (reference GPU path of the metric)
+    nf = min(args.f64_steps, args.steps)
+    run_steps("f64", 1, base + 900000, False)
+    ms64, traces64, iters64 = run_steps("f64", nf, base, True)
+    value64 = rhs_per_step * nf / (sum(ms64) / 1e3)
+    trace_diff = max(abs(a - b) / abs(b) for a, b in zip(traces[:nf], traces64))
+
+    # variance x time: Var_T over the timed runs, t_run the mean step time
+    tr_mean = complex(np.mean(traces))
+    var_T = float(np.sum(np.abs(np.array(traces) - tr_mean) ** 2) / (len(traces) - 1))
+    t_run = (total_ms / args.steps) / 1e3
+    t_run64 = (sum(ms64) / nf) / 1e3
+    ttr = t_run * var_T / (1e-3 * abs(tr_mean)) ** 2
+    ttr64 = t_run64 * var_T / (1e-3 * abs(tr_mean)) ** 2
+
+    # roofline of the dominant kernel: the FP32 stencil the inner solver runs
+    # twice per iteration (the fused dslash+dot kernels share its core)
+    dsl_ms = dtr.time_dslash(gauge, w.m0, w.block, prec="f32" if args.solver == "mixed_f32" else "f64", reps=200)
+    Vs = w.V
+    flops = Vs * w.block * 1368.0                      # 1320 hopping + 48 diagonal per site and RHS
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12          # TFLOP/s: SMs x FP32 lanes x FMA x max clock
+    achieved = flops / (dsl_ms / 1e3) / 1e12
+    bytes_alg = Vs * w.block * (96 + 96) + Vs * 288     # FP32: psi in + out per RHS, links once
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+            "traffic": None, "kernel": "dslash FP32, 16 RHS, 8^4 (L2-resident)",
+            "avg_launch_ms": dsl_ms, "alg_bytes_per_launch": bytes_alg,
+            "achieved_gbs_if_dram": bytes_alg / (dsl_ms / 1e3) / 1e9,
+            "peak_note": "FP32 CUDA-core peak derived from 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+
+    # CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1:
+        r = cpu_oracle_sample(args.cpu_sample_rhs, 2)
+        tcpu = r["times"][-1]
+        cpu = {"value": args.cpu_sample_rhs / tcpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d RHS of the 8^4 workload: CGNR to 1e-10 (%d iters) + deflation quadrature, "
+                         "%.1f s" % (args.cpu_sample_rhs, r["iters"], tcpu)}
+
+    scal_bytes = 7440
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (FP32 inner BiCGStab, FP64 defect correction, "
+                                                            "FP64 deflation and reductions)"
+            if args.solver == "mixed_f32" else "f64",
+            "data": "synthetic (random SU(3) links, seeded)",
+            "config": {"workload": WORKLOAD, "lattice": list(w.dims), "eps": w.eps, "m0": w.m0,
+                       "rhs_per_step": rhs_per_step, "block": w.block, "ncolors": w.ncolors, "k": w.k,
+                       "defl_prec": w.defl_prec, "tol": w.tol, "solver": args.solver,
+                       "l2": "flushed (256 MiB write) before every timed step",
+                       "deflation_space": "subspace iteration on (g5 A)^-1: %d its, max rel residual %.2e, "
+                                          "setup %.1f s (untimed)" % (eit, float(np.max(eres)), t_setup)},
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": rhs_per_step * 16 + scal_bytes,
+                    "note": "host wall clock around dtr_trace_estimate, results read back to host each step"},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "fp64_path": {"value": value64, "unit": UNIT, "steps": nf, "ms_per_step": sum(ms64) / nf,
+                          "iterations_per_rhs": iters64 / (nf * rhs_per_step),
+                          "max_rel_trace_diff_vs_mixed": trace_diff},
+            "iterations_per_rhs": iters / (args.steps * rhs_per_step),
+            "variance_x_time": {"trace": [tr_mean.real, tr_mean.imag], "var_T": var_T, "runs": len(traces),
+                                "time_to_1e-3_s": ttr, "time_to_1e-3_s_fp64_path": ttr64,
+                                "speedup_vs_fp64_path": ttr64 / ttr},
+            "speedup_vs_fp64_path": value / value64,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

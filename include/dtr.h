@@ -80,6 +80,10 @@ const char *dtr_last_error(void);
 /* Library version string. */
 const char *dtr_version(void);
 
+/* Number of CUDA kernels the library has launched in this process (all
+ * threads, all devices), for launch accounting by callers. */
+uint64_t dtr_kernel_launches(void);
+
 /* ------------------------------------------------------------------ lattice */
 /* Describe a periodic 4D lattice (Section 6: 4D lattice, 12 dof per site).
  * dims: host array of 4 positive even extents.  *out receives the handle.
@@ -109,6 +113,16 @@ void dtr_destroy_gauge(dtr_gauge g);
 size_t dtr_dslash_workspace_bytes(dtr_lattice lat, int nrhs);
 int dtr_dslash(dtr_gauge g, double m0, const double *in, double *out, int nrhs, int dagger,
                dtr_prec prec, void *work, size_t work_bytes, void *stream);
+
+/* Benchmark hook for the stencil of the operator above: launches the
+ * library's internal dslash kernel (the one the solver's fused kernels share)
+ * `reps` times back to back on internal-layout fields of width nrhs held in
+ * `work` (zero-filled first), times the launches with CUDA events recorded on
+ * `stream`, and writes the average duration of one launch in milliseconds to
+ * *avg_ms (host).  work: dtr_dslash_workspace_bytes(lat, nrhs) bytes.
+ * Synchronises `stream`. */
+int dtr_time_dslash(dtr_gauge g, double m0, int nrhs, dtr_prec prec, int reps, void *work, size_t work_bytes,
+                    double *avg_ms, void *stream);
 
 /* -------------------------------------------------------------------- noise */
 /* Probing vectors z = z0 .* z_h (Algorithm 1, lines 3-6; Section 5.2).

@@ -2,6 +2,7 @@
 // handle management, layout conversion at the boundary and dispatch to the
 // kernels.  No exception or trap crosses the boundary; failures return a
 // status code and leave a message for dtr_last_error().
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -15,6 +16,9 @@
 namespace dtr {
 
 static thread_local std::string g_err;
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 void set_error(const std::string &msg) { g_err = msg; }
 int fail(int code, const std::string &msg) {
@@ -85,6 +89,8 @@ extern "C" {
 const char *dtr_last_error(void) { return g_err.c_str(); }
 const char *dtr_version(void) { return "dtr 0.1 (sm_103a)"; }
 
+uint64_t dtr_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
+
 int dtr_make_lattice(const int dims[4], dtr_lattice *out) {
   if (!dims || !out) return fail(DTR_EINVAL, "null argument");
   int64_t V = 1;
@@ -125,7 +131,7 @@ int dtr_make_gauge(dtr_lattice lat, const double *links_host, dtr_gauge *out) {
   if (e == cudaSuccess) e = cudaMalloc((void **)&g->U32, n * sizeof(float2));
   if (e == cudaSuccess) e = cudaMemcpy(g->U64, links_host, n * sizeof(double2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    k_to_f32<<<grid1d(n), 256>>>(g->U64, g->U32, n);
+    k_to_f32<<<grid1d(n), 256>>>(g->U64, g->U32, n); count_launches(1);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -181,6 +187,39 @@ int dtr_dslash(dtr_gauge g, double m0, const double *in, double *out, int nrhs, 
     launch_unpack<float>(o, (double2 *)out, g->lat.V, nrhs, b, st);
   }
   DTR_LAUNCH_CHECK("dslash");
+  return DTR_OK;
+}
+
+int dtr_time_dslash(dtr_gauge g, double m0, int nrhs, dtr_prec prec, int reps, void *work, size_t work_bytes,
+                    double *avg_ms, void *stream) {
+  if (!g || !work || !avg_ms) return fail(DTR_EINVAL, "null argument");
+  if (nrhs < 1 || nrhs > 64 || reps < 1) return fail(DTR_EINVAL, "nrhs must be in [1, 64] and reps >= 1");
+  if (prec != DTR_F64 && prec != DTR_F32) return fail(DTR_EINVAL, "dslash precision must be DTR_F64 or DTR_F32");
+  if (work_bytes < dtr_dslash_workspace_bytes(&g->lat, nrhs)) return fail(DTR_ENOMEM, "dslash workspace too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int b = pad_rhs(nrhs);
+  const Geom geo = geom_of(g->lat);
+  const size_t vb = ((size_t)g->lat.V * 12 * b * sizeof(double2) + 255) / 256 * 256;
+  char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+  DTR_CUDA(cudaMemsetAsync(w, 0, 2 * vb, st));
+  cudaEvent_t e0, e1;
+  DTR_CUDA(cudaEventCreate(&e0));
+  DTR_CUDA(cudaEventCreate(&e1));
+  DTR_CUDA(cudaEventRecord(e0, st));
+  for (int r = 0; r < reps; ++r) {
+    if (prec == DTR_F64)
+      launch_dslash<double>(g->U64, (const double2 *)w, (double2 *)(w + vb), geo, b, m0, 0, st);
+    else
+      launch_dslash<float>(g->U32, (const float2 *)w, (float2 *)(w + vb), geo, b, m0, 0, st);
+  }
+  DTR_CUDA(cudaEventRecord(e1, st));
+  DTR_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  DTR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  DTR_LAUNCH_CHECK("dslash timing");
+  *avg_ms = (double)ms / reps;
   return DTR_OK;
 }
 
@@ -302,7 +341,7 @@ int dtr_defl_create(dtr_lattice lat, int k, dtr_prec prec, const double *V_host,
       if (e == cudaSuccess) e = cudaMalloc(&tmp, (size_t)N * k * sizeof(double2));
       if (e == cudaSuccess) e = cudaMemcpy(tmp, rowmajor.data(), (size_t)N * k * sizeof(double2), cudaMemcpyHostToDevice);
       if (e == cudaSuccess) {
-        k_to_f32<<<grid1d((int64_t)N * k), 256>>>(tmp, (float2 *)D->V, (int64_t)N * k);
+        k_to_f32<<<grid1d((int64_t)N * k), 256>>>(tmp, (float2 *)D->V, (int64_t)N * k); count_launches(1);
         e = cudaGetLastError();
       }
       if (e == cudaSuccess) e = cudaDeviceSynchronize();

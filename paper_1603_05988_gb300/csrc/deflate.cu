@@ -194,9 +194,10 @@ int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 
   else
     k_defl_partial<float2><<<nch * tiles, kDeflBlock, 0, st>>>((const float2 *)D->V, Z, k, b, logb, (int)V, nch,
                                                                partial);
+  count_launches(1);
   const int64_t nkb = (int64_t)k * b;
-  k_defl_reduce<<<(unsigned)((nkb + 255) / 256), 256, 0, st>>>(partial, k, b, nch, C);
-  k_defl_d<<<1, 64, 0, st>>>(C, D->inv_lambda, k, b, d_dev, terms_dev);
+  k_defl_reduce<<<(unsigned)((nkb + 255) / 256), 256, 0, st>>>(partial, k, b, nch, C); count_launches(1);
+  k_defl_d<<<1, 64, 0, st>>>(C, D->inv_lambda, k, b, d_dev, terms_dev); count_launches(1);
   if (x0_internal) {
     const int64_t n = V * 12 * b;
     unsigned grid = (unsigned)((n + 255) / 256);
@@ -206,6 +207,7 @@ int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 
                                                    x0_internal);
     else
       k_defl_expand<float2><<<grid, 256, 0, st>>>((const float2 *)D->V, C, D->inv_lambda, k, b, V * 12, x0_internal);
+    count_launches(1);
   }
   DTR_LAUNCH_CHECK("deflation projection");
   if (C_out) *C_out = C;
@@ -224,7 +226,8 @@ int defl_trace_TD(dtr_defl_s *D, cudaStream_t st) {
     k_defl_td_partial<double2><<<nch, 256, 0, st>>>((const double2 *)D->V, k, N, nch, part);
   else
     k_defl_td_partial<float2><<<nch, 256, 0, st>>>((const float2 *)D->V, k, N, nch, part);
-  k_defl_td_reduce<<<1, 1, 0, st>>>(part, D->inv_lambda, k, nch, td);
+  count_launches(1);
+  k_defl_td_reduce<<<1, 1, 0, st>>>(part, D->inv_lambda, k, nch, td); count_launches(1);
   cudaError_t e = cudaGetLastError();
   double h = 0.0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, td, sizeof(double), cudaMemcpyDeviceToHost, st);

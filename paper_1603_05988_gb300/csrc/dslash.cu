@@ -38,6 +38,7 @@ void launch_dslash(const typename cplx_t<R>::type *U, const typename cplx_t<R>::
     dslash_kernel<R, -1><<<grid, T, 0, st>>>(U, in, out, g, b, ilog2(b), (R)(4.0 + m0));
   else
     dslash_kernel<R, 1><<<grid, T, 0, st>>>(U, in, out, g, b, ilog2(b), (R)(4.0 + m0));
+  count_launches(1);
 }
 
 template void launch_dslash<double>(const double2 *, const double2 *, double2 *, const Geom &, int, double, int,
@@ -82,12 +83,12 @@ static unsigned grid_for(int64_t n) {
 template <typename R>
 void launch_pack(const double2 *canon, typename cplx_t<R>::type *internal, int64_t V, int nrhs, int b,
                  cudaStream_t st) {
-  pack_kernel<R><<<grid_for(V * 12 * b), 256, 0, st>>>(canon, internal, V, nrhs, b);
+  pack_kernel<R><<<grid_for(V * 12 * b), 256, 0, st>>>(canon, internal, V, nrhs, b); count_launches(1);
 }
 template <typename R>
 void launch_unpack(const typename cplx_t<R>::type *internal, double2 *canon, int64_t V, int nrhs, int b,
                    cudaStream_t st) {
-  unpack_kernel<R><<<grid_for(V * 12 * nrhs), 256, 0, st>>>(internal, canon, V, nrhs, b);
+  unpack_kernel<R><<<grid_for(V * 12 * nrhs), 256, 0, st>>>(internal, canon, V, nrhs, b); count_launches(1);
 }
 
 template void launch_pack<double>(const double2 *, double2 *, int64_t, int, int, cudaStream_t);

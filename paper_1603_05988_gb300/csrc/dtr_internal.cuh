@@ -21,6 +21,8 @@ namespace dtr {
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
+// process-wide count of kernels launched by the library
+void count_launches(int n);
 
 #define DTR_CUDA(call)                                   \
   do {                                                   \

@@ -114,14 +114,14 @@ void launch_noise(double2 *out, const Geom &g, uint64_t seed, int64_t z0_index, 
   const int64_t n = (int64_t)g.V * b;
   const int T = 256;
   noise_internal_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(out, g, seed, z0_index, ncolors, dilute12, q0,
-                                                                    nrhs, b);
+                                                                    nrhs, b); count_launches(1);
 }
 
 void launch_noise_canon(double2 *out, const Geom &g, uint64_t seed, int64_t z0_index, int ncolors, int dilute12,
                         int64_t q0, int nrhs, cudaStream_t st) {
   const int64_t n = (int64_t)g.V * 12 * nrhs;
   const int T = 256;
-  noise_canon_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(out, g, seed, z0_index, ncolors, dilute12, q0, nrhs);
+  noise_canon_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(out, g, seed, z0_index, ncolors, dilute12, q0, nrhs); count_launches(1);
 }
 
 }  // namespace dtr

@@ -391,11 +391,11 @@ static void launch_iteration(const typename cplx_t<R>::type *U, KrylovVecs<R> &K
   const unsigned gd = reduce_grid(sites_items, sms);
   const unsigned gv = reduce_grid(n, sms);
   const R diag = (R)(4.0 + m0);
-  k_dslash_alpha<R><<<gd, kBlock, 0, st>>>(U, K.p, K.rhat, K.v, g, b, logb, diag, sc, red);
-  k_supdate<R><<<gv, kBlock, 0, st>>>(K.r, K.v, n, b, sc);
-  k_dslash_omega<R><<<gd, kBlock, 0, st>>>(U, K.r, K.t, g, b, logb, diag, sc, red);
-  k_xr_update<R><<<gv, kBlock, 0, st>>>(K.x, K.r, K.p, K.t, K.rhat, n, b, sc, red);
-  k_pupdate<R><<<gv, kBlock, 0, st>>>(K.p, K.r, K.v, n, b, sc);
+  k_dslash_alpha<R><<<gd, kBlock, 0, st>>>(U, K.p, K.rhat, K.v, g, b, logb, diag, sc, red); count_launches(1);
+  k_supdate<R><<<gv, kBlock, 0, st>>>(K.r, K.v, n, b, sc); count_launches(1);
+  k_dslash_omega<R><<<gd, kBlock, 0, st>>>(U, K.r, K.t, g, b, logb, diag, sc, red); count_launches(1);
+  k_xr_update<R><<<gv, kBlock, 0, st>>>(K.x, K.r, K.p, K.t, K.rhat, n, b, sc, red); count_launches(1);
+  k_pupdate<R><<<gv, kBlock, 0, st>>>(K.p, K.r, K.v, n, b, sc); count_launches(1);
 }
 
 template <typename R>
@@ -448,7 +448,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
   const unsigned gd = reduce_grid((int64_t)g.V * b, sms);
   const unsigned gv = reduce_grid(n, sms);
   const int check = p->check_every > 0 ? p->check_every : 8;
-  k_scal_init<<<1, 64, 0, st>>>(outer, b, p->tol * p->tol, p->maxiter);
+  k_scal_init<<<1, 64, 0, st>>>(outer, b, p->tol * p->tol, p->maxiter); count_launches(1);
   DTR_LAUNCH_CHECK("scalar init");
   *scal_out = outer;
 
@@ -462,7 +462,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     K.t = (double2 *)w;    w = align256(w + n * sizeof(double2));
     for (int cycle = 0; cycle < 64; ++cycle) {
       k_resid<double, 1><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, K.r, K.rhat, K.p, g, b, logb, 4.0 + m0, outer, red,
-                                                 1);
+                                                 1); count_launches(1);
       DTR_LAUNCH_CHECK("residual");
       int n_active = 0;
       int rc = read_n_active(outer, st, &n_active);
@@ -472,7 +472,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
       if (rc) return rc;
     }
     // final true residual for the statistics (no restart)
-    k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, K.r, K.rhat, K.p, g, b, logb, 4.0 + m0, outer, red, 0);
+    k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, K.r, K.rhat, K.p, g, b, logb, 4.0 + m0, outer, red, 0); count_launches(1);
     DTR_LAUNCH_CHECK("final residual");
     return DTR_OK;
   }
@@ -488,22 +488,22 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     const double itol = p->inner_tol > 0 ? p->inner_tol : 1e-5;
     for (int cycle = 0; cycle < 64; ++cycle) {
       k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0, outer,
-                                                 red, 1);
+                                                 red, 1); count_launches(1);
       DTR_LAUNCH_CHECK("outer residual");
       int n_active = 0;
       int rc = read_n_active(outer, st, &n_active);
       if (rc) return rc;
       if (n_active == 0) break;
-      k_mixed_init<<<gv, kBlock, 0, st>>>(r64, K.r, K.rhat, K.p, K.x, n, b, outer);
-      k_mixed_scal_init<<<1, 64, 0, st>>>(outer, inner, b, itol * itol, p->maxiter);
+      k_mixed_init<<<gv, kBlock, 0, st>>>(r64, K.r, K.rhat, K.p, K.x, n, b, outer); count_launches(1);
+      k_mixed_scal_init<<<1, 64, 0, st>>>(outer, inner, b, itol * itol, p->maxiter); count_launches(1);
       DTR_LAUNCH_CHECK("inner init");
       rc = iterate<float>(gauge->U32, K, g, b, m0, inner, red, check, p->maxiter + check, st);
       if (rc) return rc;
-      k_mixed_accum<<<gv, kBlock, 0, st>>>(x, K.x, n, b, outer, inner);
+      k_mixed_accum<<<gv, kBlock, 0, st>>>(x, K.x, n, b, outer, inner); count_launches(1);
       DTR_LAUNCH_CHECK("defect accumulate");
     }
     k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0, outer,
-                                               red, 0);
+                                               red, 0); count_launches(1);
     DTR_LAUNCH_CHECK("final residual");
     return DTR_OK;
   }

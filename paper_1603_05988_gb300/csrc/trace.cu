@@ -109,7 +109,7 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
       Scal *sc = nullptr;
       int rc = solve_internal(gauge, m0, X, Z, b, &p->solve, solver_work, L.solver, st, &sc);
       if (rc) return rc;
-      k_zdot<<<reduce_grid(n, sms), kBlock, 0, st>>>(Z, X, n, b, D ? d_dev : nullptr, t_dev, red);
+      k_zdot<<<reduce_grid(n, sms), kBlock, 0, st>>>(Z, X, n, b, D ? d_dev : nullptr, t_dev, red); count_launches(1);
       DTR_LAUNCH_CHECK("z^H y reduction");
       DTR_CUDA(cudaMemcpyAsync(tbuf.data(), t_dev, sizeof(double2) * b, cudaMemcpyDeviceToHost, st));
       DTR_CUDA(cudaMemcpyAsync(&sc_host, sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));

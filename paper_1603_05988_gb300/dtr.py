@@ -72,6 +72,8 @@ def _sig(name, res, args):
 
 _sig("dtr_last_error", ctypes.c_char_p, [])
 _sig("dtr_version", ctypes.c_char_p, [])
+_sig("dtr_kernel_launches", ctypes.c_uint64, [])
+_sig("dtr_time_dslash", _i, [_vp, _d, _i, _i, _i, _vp, _sz, ctypes.POINTER(ctypes.c_double), _vp])
 _sig("dtr_make_lattice", _i, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_vp)])
 _sig("dtr_destroy_lattice", None, [_vp])
 _sig("dtr_lattice_info", _i, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64), ctypes.POINTER(_i64)])
@@ -198,6 +200,30 @@ def dslash(gauge, m0, x, dagger=False, prec="f64"):
     _check(_lib.dtr_dslash(gauge._h, float(m0), _ptr(x), _ptr(out), nrhs, int(bool(dagger)), _PREC[prec],
                            _ptr(w), nb, _stream()))
     return out
+
+
+def dslash_many(gauge, m0, X, dagger=False, prec="f64", chunk=64):
+    """dslash over any number of rows of X (chunks of <= 64 right-hand sides)."""
+    torch = _torch()
+    out = torch.empty_like(X)
+    for c0 in range(0, X.shape[0], chunk):
+        out[c0:c0 + chunk] = dslash(gauge, m0, X[c0:c0 + chunk].contiguous(), dagger=dagger, prec=prec)
+    return out
+
+
+def kernel_launches():
+    """Kernels the library launched so far in this process."""
+    return int(_lib.dtr_kernel_launches())
+
+
+def time_dslash(gauge, m0, nrhs, prec="f32", reps=50):
+    """Average duration (ms) of one internal dslash launch of width nrhs (CUDA events)."""
+    nb = _lib.dtr_dslash_workspace_bytes(gauge.lat._h, nrhs)
+    w = _workspace(nb)
+    ms = ctypes.c_double()
+    _check(_lib.dtr_time_dslash(gauge._h, float(m0), int(nrhs), _PREC[prec], int(reps), _ptr(w), nb,
+                                ctypes.byref(ms), _stream()))
+    return ms.value
 
 
 def gen_noise(lat, seed, z0_index, ncolors, dilute12, q0, nrhs):
