@@ -204,6 +204,25 @@ size_t dtr_deflate_workspace_bytes(dtr_defl d, int nrhs);
 int dtr_deflate_project(dtr_defl d, const double *z, int nrhs, double *d_out, double *coeff_out,
                         double *x0_out, void *work, size_t work_bytes, void *stream);
 
+/* Allocation-free variant of dtr_deflate_project, for callers that cannot
+ * allocate device memory or supply a workspace (for instance an application
+ * whose device memory is wholly owned by its own pool allocator, or a
+ * fixed-memory production run that reserves all device memory up front).
+ * There is no counterpart in the paper: it computes the same d_out (and
+ * optionally coeff_out, same layouts as dtr_deflate_project; no x0) with its
+ * scratch held in a fixed file-scope device array of about 4.3 MB, present on
+ * every GPU that loads the library until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ * Limits: nrhs <= DTR_STATIC_MAX_RHS and k <= DTR_STATIC_MAX_K, else
+ * DTR_EINVAL.  The first call on a device (with that device current) looks up
+ * the array's device address; make that first call before any stream capture.
+ * All calls share the array: calls whose GPU work overlaps (other streams or
+ * host threads) race, so serialise them. */
+#define DTR_STATIC_MAX_K 128
+#define DTR_STATIC_MAX_RHS 16
+int dtr_deflate_project_static(dtr_defl d, const double *z, int nrhs, double *d_out, double *coeff_out,
+                               void *stream);
+
 /* ---------------------------------------------------------------- estimator */
 typedef struct {
   uint64_t seed;       /* noise seed (Philox key) */

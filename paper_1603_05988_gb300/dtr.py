@@ -92,6 +92,7 @@ _sig("dtr_defl_trace", _i, [_vp, ctypes.POINTER(ctypes.c_double)])
 _sig("dtr_destroy_defl", None, [_vp])
 _sig("dtr_deflate_workspace_bytes", _sz, [_vp, _i])
 _sig("dtr_deflate_project", _i, [_vp, _vp, _i, _vp, _vp, _vp, _vp, _sz, _vp])
+_sig("dtr_deflate_project_static", _i, [_vp, _vp, _i, _vp, _vp, _vp])
 _sig("dtr_trace_workspace_bytes", _sz, [_vp, _vp, ctypes.POINTER(TraceParams)])
 _sig("dtr_trace_estimate", _i, [_vp, _d, _vp, ctypes.POINTER(TraceParams), _vp, _sz,
                                 ctypes.POINTER(TraceResult), _vp])
@@ -305,6 +306,23 @@ def deflate_project(defl, z, want_coeff=False, want_x0=False):
     _check(_lib.dtr_deflate_project(defl._h, _ptr(z), nrhs, _ptr(d), _ptr(C) if C is not None else None,
                                     _ptr(x0) if x0 is not None else None, _ptr(w), nb, _stream()))
     return d, C, x0
+
+
+STATIC_MAX_K, STATIC_MAX_RHS = 128, 16
+
+
+def deflate_project_static(defl, z, want_coeff=False):
+    """Allocation-free deflation projection (the library uses a fixed device
+    array as scratch; no workspace, no device allocation by the library).
+    Returns (d, C or None) like deflate_project.  nrhs <= 16, k <= 128."""
+    torch = _torch()
+    z = _field(z, defl.lat.N, "z")
+    nrhs = z.shape[0]
+    d = torch.empty(nrhs, dtype=torch.complex128, device="cuda")
+    C = torch.empty((2 * nrhs, defl.k), dtype=torch.complex128, device="cuda") if want_coeff else None
+    _check(_lib.dtr_deflate_project_static(defl._h, _ptr(z), nrhs, _ptr(d), _ptr(C) if C is not None else None,
+                                           _stream()))
+    return d, C
 
 
 def trace_params(seed=0, z0_first=0, n_z0=1, ncolors=1, nvec=1, dilute12=False, block=16, use_x0=False,
