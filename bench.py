@@ -193,7 +193,7 @@ def main():
     lat = dtr.make_lattice(w.dims)
     gauge = dtr.make_gauge(lat, U)
     t0 = time.perf_counter()
-    V, lam, eres, eit = eigensolver.smallest_gamma5_eigpairs(gauge, w.m0, w.k, iters=60, tol=1e-2, seed=rank)
+    V, lam, eres, eit = eigensolver.smallest_gamma5_eigpairs(gauge, w.m0, w.k, iters=150, tol=1e-2, seed=rank)
     t_setup = time.perf_counter() - t0
     defl = dtr.defl_create(lat, V, lam, prec=w.defl_prec)
 
@@ -240,7 +240,9 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = dtr.kernel_launches()
+    torch.cuda.nvtx.range_push("timed")
     ms, traces, iters = run_steps(args.solver, args.steps, base, True)
+    torch.cuda.nvtx.range_pop()
     launches = dtr.kernel_launches() - launches0
     barrier()
     clk = clocks.stop()
