@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--solver", default="mixed_f32", choices=["mixed_f32", "f64"])
     ap.add_argument("--f64-steps", type=int, default=6, help="steps of the plain FP64 path timed for comparison")
+    ap.add_argument("--eig-iters", type=int, default=150,
+                    help="cap on setup eigensolver iterations (deflation-space quality; untimed)")
     ap.add_argument("--cpu-sample-rhs", type=int, default=1, help="RHS in the CPU-oracle baseline sample")
     return ap.parse_args()
 
@@ -193,7 +195,8 @@ def main():
     lat = dtr.make_lattice(w.dims)
     gauge = dtr.make_gauge(lat, U)
     t0 = time.perf_counter()
-    V, lam, eres, eit = eigensolver.smallest_gamma5_eigpairs(gauge, w.m0, w.k, iters=150, tol=1e-2, seed=rank)
+    V, lam, eres, eit = eigensolver.smallest_gamma5_eigpairs(gauge, w.m0, w.k, iters=args.eig_iters, tol=1e-2,
+                                                                     seed=rank)
     t_setup = time.perf_counter() - t0
     defl = dtr.defl_create(lat, V, lam, prec=w.defl_prec)
 

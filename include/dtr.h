@@ -60,6 +60,7 @@ extern "C" {
 #define DTR_ECUDA 3      /* a CUDA runtime call failed; message has the CUDA error */
 #define DTR_ENOTCONV 4   /* solver hit maxiter; results and per-RHS stats still written */
 #define DTR_ENAN 5       /* NaN/Inf met in a residual norm; per-RHS stats still written */
+#define DTR_ETIMEOUT 6   /* a grid barrier of the persistent solver timed out (no hang: the kernel exits) */
 
 typedef struct dtr_lattice_s *dtr_lattice;
 typedef struct dtr_gauge_s *dtr_gauge;
@@ -83,6 +84,15 @@ const char *dtr_version(void);
 /* Number of CUDA kernels the library has launched in this process (all
  * threads, all devices), for launch accounting by callers. */
 uint64_t dtr_kernel_launches(void);
+
+/* Self-test of the bounded grid barrier the persistent solver uses (its
+ * failure-detection path, exercised without faulting anything): one block
+ * waits at a barrier that expects two blocks, so the wait must give up after
+ * about budget_cycles SM clock cycles (1 .. 2^31).  *timed_out (host)
+ * receives 1 if the wait gave up, *error_word the barrier's error flag after
+ * the kernel.  Synchronises `stream`.  The solver itself uses a budget of
+ * about two seconds and turns a timed-out barrier into DTR_ETIMEOUT. */
+int dtr_selftest_barrier(int64_t budget_cycles, int *timed_out, int *error_word, void *stream);
 
 /* ------------------------------------------------------------------ lattice */
 /* Describe a periodic 4D lattice (Section 6: 4D lattice, 12 dof per site).
@@ -150,6 +160,9 @@ typedef struct {
   int solver;          /* dtr_solver */
   int check_every;     /* iterations between host convergence checks (>= 1) */
   double inner_tol;    /* mixed solver: relative residual reduction per inner solve */
+  int engine;          /* 0: persistent cooperative kernel (one launch per solve / inner solve);
+                          1: one kernel per BiCGStab step, host polls every check_every iterations */
+  int pad_;
 } dtr_solve_params;
 
 typedef struct {
@@ -161,7 +174,7 @@ typedef struct {
 } dtr_solve_stat;
 
 /* Fill *p with defaults: tol 1e-10, maxiter 5000, FP64 BiCGStab, check 8,
- * inner_tol 1e-5. */
+ * inner_tol 1e-5, persistent engine. */
 void dtr_solve_params_default(dtr_solve_params *p);
 
 /* Solve A y = z for nrhs right-hand sides at once (Algorithm 1, line 7).

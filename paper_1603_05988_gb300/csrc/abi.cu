@@ -11,6 +11,7 @@
 
 #include "deflate.cuh"
 #include "dtr_internal.cuh"
+#include "persist.cuh"
 #include "solver.cuh"
 
 namespace dtr {
@@ -88,6 +89,12 @@ extern "C" {
 
 const char *dtr_last_error(void) { return g_err.c_str(); }
 const char *dtr_version(void) { return "dtr 0.1 (sm_103a)"; }
+
+int dtr_selftest_barrier(int64_t budget_cycles, int *timed_out, int *error_word, void *stream) {
+  if (!timed_out || !error_word || budget_cycles < 1 || budget_cycles > (1LL << 31))
+    return fail(DTR_EINVAL, "budget_cycles must be in [1, 2^31] and outputs non-null");
+  return selftest_barrier((long long)budget_cycles, timed_out, error_word, (cudaStream_t)stream);
+}
 
 uint64_t dtr_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
@@ -242,6 +249,8 @@ void dtr_solve_params_default(dtr_solve_params *p) {
   p->solver = DTR_SOLVER_BICGSTAB_F64;
   p->check_every = 8;
   p->inner_tol = 1e-5;
+  p->engine = 0;
+  p->pad_ = 0;
 }
 
 static int check_solve_params(const dtr_solve_params *p) {
@@ -249,6 +258,7 @@ static int check_solve_params(const dtr_solve_params *p) {
   if (!(p->tol > 0.0) || p->maxiter < 1) return fail(DTR_EINVAL, "tol must be > 0 and maxiter >= 1");
   if (p->solver != DTR_SOLVER_BICGSTAB_F64 && p->solver != DTR_SOLVER_MIXED_F32)
     return fail(DTR_EINVAL, "unknown solver");
+  if (p->engine != 0 && p->engine != 1) return fail(DTR_EINVAL, "engine must be 0 (persistent) or 1 (per-step)");
   return DTR_OK;
 }
 

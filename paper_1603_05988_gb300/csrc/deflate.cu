@@ -88,19 +88,32 @@ __global__ void k_defl_reduce(const double2 *__restrict__ partial, int k, int b,
   }
 }
 
-// d_j = sum_m conj(C[m, j]) C[m, b+j] / lambda_m ; optional per-m terms
+// d_j = sum_m conj(C[m, j]) C[m, b+j] / lambda_m ; optional per-m terms.
+// One block per column; fixed-order block tree, so the result is reproducible.
 __global__ void k_defl_d(const double2 *__restrict__ C, const double *__restrict__ inv_lambda, int k, int b,
                          double2 *__restrict__ d, double2 *__restrict__ terms) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= b) return;
+  __shared__ double2 sh[128];
+  const int j = blockIdx.x;
   double2 acc = make_double2(0.0, 0.0);
-  for (int m = 0; m < k; ++m) {
+  for (int m = threadIdx.x; m < k; m += blockDim.x) {
     const double2 a = C[(int64_t)j * k + m], g = C[(int64_t)(b + j) * k + m];
     const double2 t = cscale(cjmul(a, g), inv_lambda[m]);
     if (terms) terms[(int64_t)j * k + m] = t;
     acc = cadd(acc, t);
   }
-  d[j] = acc;
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int stride = 64; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride) sh[threadIdx.x] = cadd(sh[threadIdx.x], sh[threadIdx.x + stride]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d[j] = sh[0];
+}
+
+void launch_defl_d(const double2 *C, const double *inv_lambda, int k, int b, double2 *d, double2 *terms,
+                   cudaStream_t st) {
+  k_defl_d<<<b, 128, 0, st>>>(C, inv_lambda, k, b, d, terms);
+  count_launches(1);
 }
 
 // x0 (internal [site][12][b]) = V diag(1/lambda) C[:, b:2b]
@@ -197,7 +210,7 @@ int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 
   count_launches(1);
   const int64_t nkb = (int64_t)k * b;
   k_defl_reduce<<<(unsigned)((nkb + 255) / 256), 256, 0, st>>>(partial, k, b, nch, C); count_launches(1);
-  k_defl_d<<<1, 64, 0, st>>>(C, D->inv_lambda, k, b, d_dev, terms_dev); count_launches(1);
+  launch_defl_d(C, D->inv_lambda, k, b, d_dev, terms_dev, st);
   if (x0_internal) {
     const int64_t n = V * 12 * b;
     unsigned grid = (unsigned)((n + 255) / 256);

@@ -15,6 +15,18 @@ int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 
                           double2 *x0_internal, double2 **C_out, void *work, size_t work_bytes, int sms,
                           cudaStream_t st);
 
+// d_j (and per-m terms, or NULL) from C (column-major k x 2b).
+void launch_defl_d(const double2 *C, const double *inv_lambda, int k, int b, double2 *d, double2 *terms,
+                   cudaStream_t st);
+
+// Projection of an HP block (all columns share one z0 run; columns are
+// probing indices q0 .. q0+nrhs-1) from per-colour sums of V^H z0.
+// sites_by_colour: V site indices grouped by colour, V/ncolors per colour.
+size_t defl_hp_scratch_bytes(int64_t V, int k, int b, int ncolors, int sms);
+int defl_project_hp(const dtr_defl_s *D, const int *sites_by_colour, int ncolors, uint64_t seed, int64_t run,
+                    int64_t q0, int nrhs, int dilute12, int b, double2 *d_dev, double2 *terms_dev, void *work,
+                    size_t work_bytes, int sms, cudaStream_t st);
+
 // T_D = sum_m v_m^H g5 v_m / lambda_m from the stored V (FP64 accumulation).
 int defl_trace_TD(dtr_defl_s *D, cudaStream_t st);
 

@@ -22,6 +22,19 @@
 
 namespace dtr {
 
+// Field loaders: value of the input field at internal index (site*12 + c)*b + j.
+template <typename C> struct PlainLoad {
+  const C *__restrict__ f;
+  __device__ __forceinline__ C operator()(int64_t idx) const { return f[idx]; }
+};
+// s = r - a v evaluated on the fly (a is this thread's column scalar)
+template <typename C> struct AxpyLoad {
+  const C *__restrict__ r;
+  const C *__restrict__ v;
+  C a;
+  __device__ __forceinline__ C operator()(int64_t idx) const { return caxpy(cneg(a), v[idx], r[idx]); }
+};
+
 // B_mu applied to a 2-spin vector l (component-wise over colour)
 template <int MU, typename C> __device__ __forceinline__ C applyB(const C &l0, const C &l1, int row) {
   if (MU == 0) return row == 0 ? cneg(cmuli(l1)) : cneg(cmuli(l0));  // (-i l1, -i l0)
@@ -38,9 +51,8 @@ template <int MU, typename C> __device__ __forceinline__ C applyBH(const C &w0, 
 }
 
 // One direction mu: accumulate S_u += w_f + w_b, S_l += B^H (w_f - w_b).
-template <int MU, int SGN, typename R>
-__device__ __forceinline__ void hop_dir(const typename cplx_t<R>::type *__restrict__ U,
-                                        const typename cplx_t<R>::type *__restrict__ in, const Geom &g,
+template <int MU, int SGN, typename R, class LD>
+__device__ __forceinline__ void hop_dir(const typename cplx_t<R>::type *__restrict__ U, const LD &in, const Geom &g,
                                         const int xc[4], int s, int b, int j, typename cplx_t<R>::type Su[2][3],
                                         typename cplx_t<R>::type Sl[2][3]) {
   typedef typename cplx_t<R>::type C;
@@ -53,14 +65,14 @@ __device__ __forceinline__ void hop_dir(const typename cplx_t<R>::type *__restri
 
   C wf[2][3], wb[2][3];
   {  // forward: h = u - sgn B l from psi(x+mu); w_f = U_mu(x) h
-    const C *p = in + (int64_t)sf * 12 * b + j;
+    const int64_t p = (int64_t)sf * 12 * b + j;
     C u[2][3], l[2][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      u[0][a] = p[(0 * 3 + a) * b];
-      u[1][a] = p[(1 * 3 + a) * b];
-      l[0][a] = p[(2 * 3 + a) * b];
-      l[1][a] = p[(3 * 3 + a) * b];
+      u[0][a] = in(p + (0 * 3 + a) * b);
+      u[1][a] = in(p + (1 * 3 + a) * b);
+      l[0][a] = in(p + (2 * 3 + a) * b);
+      l[1][a] = in(p + (3 * 3 + a) * b);
     }
     C h[2][3];
 #pragma unroll
@@ -88,14 +100,14 @@ __device__ __forceinline__ void hop_dir(const typename cplx_t<R>::type *__restri
       }
   }
   {  // backward: h' = u + sgn B l from psi(x-mu); w_b = U_mu(x-mu)^H h'
-    const C *p = in + (int64_t)sb * 12 * b + j;
+    const int64_t p = (int64_t)sb * 12 * b + j;
     C u[2][3], l[2][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      u[0][a] = p[(0 * 3 + a) * b];
-      u[1][a] = p[(1 * 3 + a) * b];
-      l[0][a] = p[(2 * 3 + a) * b];
-      l[1][a] = p[(3 * 3 + a) * b];
+      u[0][a] = in(p + (0 * 3 + a) * b);
+      u[1][a] = in(p + (1 * 3 + a) * b);
+      l[0][a] = in(p + (2 * 3 + a) * b);
+      l[1][a] = in(p + (3 * 3 + a) * b);
     }
     C h[2][3];
 #pragma unroll
@@ -136,11 +148,10 @@ __device__ __forceinline__ void hop_dir(const typename cplx_t<R>::type *__restri
 }
 
 // out[c] (c = 3*spin + colour) = (A psi)(s) for right-hand side j; self = psi(s).
-template <int SGN, typename R>
-__device__ __forceinline__ void dslash_site(const typename cplx_t<R>::type *__restrict__ U,
-                                            const typename cplx_t<R>::type *__restrict__ in, const Geom &g, int b,
-                                            int s, int j, R diag, typename cplx_t<R>::type out[12],
-                                            typename cplx_t<R>::type self[12]) {
+template <int SGN, typename R, class LD>
+__device__ __forceinline__ void dslash_site_ld(const typename cplx_t<R>::type *__restrict__ U, const LD &in,
+                                               const Geom &g, int b, int s, int j, R diag,
+                                               typename cplx_t<R>::type out[12], typename cplx_t<R>::type self[12]) {
   typedef typename cplx_t<R>::type C;
   int xc[4];
   site_coords(g, s, xc);
@@ -156,9 +167,9 @@ __device__ __forceinline__ void dslash_site(const typename cplx_t<R>::type *__re
   hop_dir<1, SGN, R>(U, in, g, xc, s, b, j, Su, Sl);
   hop_dir<2, SGN, R>(U, in, g, xc, s, b, j, Su, Sl);
   hop_dir<3, SGN, R>(U, in, g, xc, s, b, j, Su, Sl);
-  const C *p = in + (int64_t)s * 12 * b + j;
+  const int64_t p = (int64_t)s * 12 * b + j;
 #pragma unroll
-  for (int c = 0; c < 12; ++c) self[c] = p[c * b];
+  for (int c = 0; c < 12; ++c) self[c] = in(p + c * b);
   const R half = (R)0.5;
 #pragma unroll
   for (int r = 0; r < 2; ++r)
@@ -170,6 +181,15 @@ __device__ __forceinline__ void dslash_site(const typename cplx_t<R>::type *__re
       out[(r + 2) * 3 + a] = SGN > 0 ? mk<C>(diag * pl.x + half * sl.x, diag * pl.y + half * sl.y)
                                      : mk<C>(diag * pl.x - half * sl.x, diag * pl.y - half * sl.y);
     }
+}
+
+template <int SGN, typename R>
+__device__ __forceinline__ void dslash_site(const typename cplx_t<R>::type *__restrict__ U,
+                                            const typename cplx_t<R>::type *__restrict__ in, const Geom &g, int b,
+                                            int s, int j, R diag, typename cplx_t<R>::type out[12],
+                                            typename cplx_t<R>::type self[12]) {
+  PlainLoad<typename cplx_t<R>::type> ld{in};
+  dslash_site_ld<SGN, R>(U, ld, g, b, s, j, diag, out, self);
 }
 
 }  // namespace dtr

@@ -99,7 +99,7 @@ __device__ __forceinline__ int site_of(const Geom &g, const int c[4]) {
 }
 
 // Hierarchical-probing colour of a site; ncolors in {1, 2, 16, 32, 256, ...}.
-__device__ __forceinline__ int hp_colour(const int c[4], int ncolors) {
+__host__ __device__ __forceinline__ int hp_colour(const int c[4], int ncolors) {
   if (ncolors <= 1) return 0;
   int col = (c[0] + c[1] + c[2] + c[3]) & 1;
   int n = 2;
@@ -176,9 +176,11 @@ template <typename R>
 void launch_dslash(const typename cplx_t<R>::type *U, const typename cplx_t<R>::type *in,
                    typename cplx_t<R>::type *out, const Geom &g, int b, double m0, int dagger, cudaStream_t st);
 
-// noise into internal FP64 layout of width b: columns q0..q0+nrhs-1 (padding zero)
-void launch_noise(double2 *out, const Geom &g, uint64_t seed, int64_t z0_index, int ncolors, int dilute12,
-                  int64_t q0, int nrhs, int b, cudaStream_t st);
+// noise into internal FP64 layout of width b: block column k is global column
+// g0 + k of the run-major sequence (ncols probing columns per run, runs from
+// run0); columns nrhs..b-1 are zero padding
+void launch_noise(double2 *out, const Geom &g, uint64_t seed, int64_t run0, int ncolors, int dilute12, int64_t g0,
+                  int64_t ncols, int nrhs, int b, cudaStream_t st);
 // noise into canonical layout
 void launch_noise_canon(double2 *out, const Geom &g, uint64_t seed, int64_t z0_index, int ncolors,
                         int dilute12, int64_t q0, int nrhs, cudaStream_t st);

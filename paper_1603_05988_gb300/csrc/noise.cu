@@ -7,54 +7,15 @@
 // hierarchical-probing colouring (Section 5.2).  All arithmetic is integer,
 // so the result is bit-identical to any other implementation of the same
 // definition.
-#include "dtr_internal.cuh"
+#include "philox.cuh"
 
 namespace dtr {
 
-__device__ __forceinline__ void philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0,
-                                              uint64_t k1, uint64_t out[4]) {
-  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
-  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r) {
-      k0 += W0;
-      k1 += W1;
-    }
-    const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
-    const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
-    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-    c0 = n0;
-    c1 = lo1;
-    c2 = n2;
-    c3 = lo0;
-  }
-  out[0] = c0;
-  out[1] = c1;
-  out[2] = c2;
-  out[3] = c3;
-}
-
-// 2-bit Z4 code of dof i for run `run`.
-__device__ __forceinline__ int z4_code(uint64_t seed, int64_t run, int64_t i) {
-  uint64_t w[4];
-  philox4x64_10((uint64_t)(i >> 7), (uint64_t)run, 0ull, 0ull, seed, 0ull, w);
-  return (int)((w[(i >> 5) & 3] >> (2 * (i & 31))) & 3ull);
-}
-
-// i^code * sign
-template <typename C> __device__ __forceinline__ C z4_value(int code, int sign) {
-  C z;
-  z.x = (code == 0) ? 1.0 : (code == 2 ? -1.0 : 0.0);
-  z.y = (code == 1) ? 1.0 : (code == 3 ? -1.0 : 0.0);
-  z.x *= sign;
-  z.y *= sign;
-  return z;
-}
-
-// Internal layout [site][12][b]; one thread per (site, column).
-__global__ void noise_internal_kernel(double2 *out, Geom g, uint64_t seed, int64_t run, int ncolors, int dilute12,
-                                      int64_t q0, int nrhs, int b) {
+// Internal layout [site][12][b]; one thread per (site, column).  Column k of
+// the block is global column G = g0 + k of the run-major sequence
+// (run = run0 + G / ncols, probing index q = G % ncols).
+__global__ void noise_internal_kernel(double2 *out, Geom g, uint64_t seed, int64_t run0, int ncolors, int dilute12,
+                                      int64_t g0, int64_t ncols, int nrhs, int b) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (int64_t)g.V * b) return;
   const int j = (int)(tid % b);
@@ -68,7 +29,9 @@ __global__ void noise_internal_kernel(double2 *out, Geom g, uint64_t seed, int64
   int xc[4];
   site_coords(g, s, xc);
   const int colour = hp_colour(xc, ncolors);
-  const int64_t q = q0 + j;
+  const int64_t G = g0 + j;
+  const int64_t run = run0 + G / ncols;
+  const int64_t q = G % ncols;
   const int64_t hcol = dilute12 ? q / 12 : q;
   const int keep = dilute12 ? (int)(q % 12) : -1;
   const int sign = (__popcll((unsigned long long)(colour & hcol)) & 1) ? -1 : 1;
@@ -109,11 +72,11 @@ __global__ void noise_canon_kernel(double2 *out, Geom g, uint64_t seed, int64_t 
   out[tid] = z;
 }
 
-void launch_noise(double2 *out, const Geom &g, uint64_t seed, int64_t z0_index, int ncolors, int dilute12,
-                  int64_t q0, int nrhs, int b, cudaStream_t st) {
+void launch_noise(double2 *out, const Geom &g, uint64_t seed, int64_t run0, int ncolors, int dilute12, int64_t g0,
+                  int64_t ncols, int nrhs, int b, cudaStream_t st) {
   const int64_t n = (int64_t)g.V * b;
   const int T = 256;
-  noise_internal_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(out, g, seed, z0_index, ncolors, dilute12, q0,
+  noise_internal_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(out, g, seed, run0, ncolors, dilute12, g0, ncols,
                                                                     nrhs, b); count_launches(1);
 }
 

@@ -1,0 +1,39 @@
+// Persistent (single cooperative launch) batched BiCGStab.
+#pragma once
+
+#include "solver.cuh"
+
+namespace dtr {
+
+// Grid barrier state, zeroed before every launch.
+struct GridSync {
+  unsigned int count;
+  unsigned int gen;
+  int error;
+  int pad;
+};
+
+template <typename R> struct PArgs {
+  const typename cplx_t<R>::type *U;
+  typename cplx_t<R>::type *x, *r, *rhat, *p, *v, *s, *t;
+  const typename cplx_t<R>::type *z;  // right-hand sides (true-residual cycles only)
+  Geom g;
+  int b, logb;
+  R diag;
+  Scal *sc;
+  double2 *partial;  // [grid][2][b]
+  GridSync *gs;
+  int max_iters;     // iteration cap of one cycle (safety; per-column maxiter is in Scal)
+  int max_cycles;    // true-residual restart cycles (with_resid only)
+};
+
+// with_resid = 1: cycles of (true residual r = z - A x, restart decision,
+// iterations) until every column meets tol in the true residual (FP64 path);
+// with_resid = 0: iterations only, from the caller-initialised state.
+template <typename R> int launch_persistent(const PArgs<R> &pa, int with_resid, cudaStream_t st);
+
+// Launch one block at a barrier that expects two (the peer never arrives);
+// reports whether the bounded wait gave up and the barrier's error word.
+int selftest_barrier(long long budget, int *timed_out, int *error_word, cudaStream_t st);
+
+}  // namespace dtr

@@ -50,11 +50,20 @@ __device__ __forceinline__ bool block_reduce(const double2 (&v)[NV], int b, doub
   const int P = NV * b;
   const int S = kBlock / P;
   const int p = t % P, sl = t / P;
-  double2 acc = make_double2(0.0, 0.0);
+  double2 a0 = make_double2(0.0, 0.0), a1 = a0, a2 = a0, a3 = a0;
   if (sl < S) {
     const int q = p / b, j = p % b;
-    for (int blk = sl; blk < (int)gridDim.x; blk += S) acc = cadd(acc, __ldcg(&partial[((int64_t)blk * NV + q) * b + j]));
+    const int G = (int)gridDim.x;
+    int blk = sl;
+    for (; blk + 3 * S < G; blk += 4 * S) {
+      a0 = cadd(a0, __ldcg(&partial[((int64_t)blk * NV + q) * b + j]));
+      a1 = cadd(a1, __ldcg(&partial[((int64_t)(blk + S) * NV + q) * b + j]));
+      a2 = cadd(a2, __ldcg(&partial[((int64_t)(blk + 2 * S) * NV + q) * b + j]));
+      a3 = cadd(a3, __ldcg(&partial[((int64_t)(blk + 3 * S) * NV + q) * b + j]));
+    }
+    for (; blk < G; blk += S) a0 = cadd(a0, __ldcg(&partial[((int64_t)blk * NV + q) * b + j]));
   }
+  const double2 acc = cadd(cadd(a0, a1), cadd(a2, a3));
   __syncthreads();
   sh[t] = acc;
   __syncthreads();
@@ -70,7 +79,7 @@ __device__ __forceinline__ bool block_reduce(const double2 (&v)[NV], int b, doub
 
 inline unsigned reduce_grid(int64_t items, int sms) {
   int64_t g = (items + kBlock - 1) / kBlock;
-  int64_t cap = (int64_t)sms * 4;
+  int64_t cap = (int64_t)sms * 2;
   if (cap > kMaxGrid) cap = kMaxGrid;
   if (g > cap) g = cap;
   return (unsigned)(g < 1 ? 1 : g);

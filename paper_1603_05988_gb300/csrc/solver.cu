@@ -15,6 +15,8 @@
 #include "dslash_core.cuh"
 #include "reduce.cuh"
 #include "solver.cuh"
+#include "krylov_fin.cuh"
+#include "persist.cuh"
 
 namespace dtr {
 
@@ -29,101 +31,20 @@ int device_sms() {
   return sms;
 }
 
-// ------------------------------------------------------------- finalizers
-// All run in the last block, thread j < b, with the block totals of column j.
-
-__device__ __forceinline__ void count_active(Scal *sc, int b) {
-  // called by thread 0 after a __syncthreads in the caller
-  int n = 0;
-  for (int j = 0; j < b; ++j) n += sc->active[j];
-  sc->n_active = n;
-}
-
-// true residual r = z - A x: tot = (||r||^2, ||z||^2)
-__device__ __forceinline__ void fin_resid(Scal *sc, int j, double2 t0, int restart) {
-  const double r2 = t0.x, z2 = t0.y;
-  sc->bnorm2[j] = z2;
-  sc->rtrue2[j] = r2;
-  const bool nan = !(r2 == r2) || !(z2 == z2) || isinf(r2);
-  const bool conv = (z2 == 0.0) || (r2 <= sc->tol2 * z2);
-  sc->conv[j] = conv ? 1 : 0;
-  if (nan) sc->flags[j] |= kFlagNaN;
-  if (!conv && !nan && sc->iters[j] < sc->maxiter && restart) {
-    sc->active[j] = 1;
-    sc->restarts[j] += 1;
-    sc->rho[j] = make_double2(r2, 0.0);
-    sc->rnorm2[j] = r2;
-    sc->scale[j] = 1.0 / sqrt(r2);
-  } else {
-    sc->active[j] = 0;
-  }
-}
-
-__device__ __forceinline__ void fin_alpha(Scal *sc, int j, double2 sigma) {
-  if (!sc->active[j]) {
-    sc->alpha[j] = make_double2(0.0, 0.0);
-    return;
-  }
-  if (sigma.x == 0.0 && sigma.y == 0.0) {
-    sc->flags[j] |= kFlagBreakdown;
-    sc->active[j] = 0;
-    sc->alpha[j] = make_double2(0.0, 0.0);
-    return;
-  }
-  sc->alpha[j] = cdiv(sc->rho[j], sigma);
-}
-
-__device__ __forceinline__ void fin_omega(Scal *sc, int j, double2 ts, double2 tt) {
-  if (!sc->active[j] || tt.x == 0.0) {
-    sc->omega[j] = make_double2(0.0, 0.0);
-    return;
-  }
-  sc->omega[j] = make_double2(ts.x / tt.x, ts.y / tt.x);
-}
-
-__device__ __forceinline__ void fin_beta(Scal *sc, int j, double2 rr0, double2 rr) {
-  if (!sc->active[j]) {
-    sc->beta[j] = make_double2(0.0, 0.0);
-    return;
-  }
-  sc->iters[j] += 1;
-  const double rn2 = rr.x;
-  sc->rnorm2[j] = rn2;
-  if (!(rn2 == rn2) || isinf(rn2)) {
-    sc->flags[j] |= kFlagNaN;
-    sc->active[j] = 0;
-    return;
-  }
-  if (rn2 <= sc->tol2 * sc->bnorm2[j]) {  // converged on the recursive residual
-    sc->active[j] = 0;
-    sc->beta[j] = make_double2(0.0, 0.0);
-    return;
-  }
-  if (sc->iters[j] >= sc->maxiter) {
-    sc->active[j] = 0;
-    return;
-  }
-  const double2 om = sc->omega[j];
-  const double2 rho = sc->rho[j];
-  if ((om.x == 0.0 && om.y == 0.0) || (rho.x == 0.0 && rho.y == 0.0)) {
-    sc->flags[j] |= kFlagBreakdown;
-    sc->active[j] = 0;
-    return;
-  }
-  sc->beta[j] = cmul(cdiv(rr0, rho), cdiv(sc->alpha[j], om));
-  sc->rho[j] = rr0;
-}
-
 // ------------------------------------------------------------------ kernels
 template <typename R> struct Vec { typedef typename cplx_t<R>::type C; };
 
 template <typename C> __device__ __forceinline__ C scal_as(double2 v) { return mk<C>(v.x, v.y); }
 
-template <typename C> __device__ __forceinline__ double2 dot_acc(double2 acc, C a, C b) {
-  // acc += conj(a) * b in double
-  const double ax = a.x, ay = a.y, bx = b.x, by = b.y;
-  return make_double2(acc.x + ax * bx + ay * by, acc.y + ax * by - ay * bx);
+// acc += conj(a) * b, in the field's own precision (FP64 work on GB300 costs
+// 61 FP32 operations; the block and grid sums that follow are FP64)
+__device__ __forceinline__ double2 dot_acc(double2 acc, double2 a, double2 b) {
+  return make_double2(acc.x + a.x * b.x + a.y * b.y, acc.y + a.x * b.y - a.y * b.x);
 }
+__device__ __forceinline__ float2 dot_acc(float2 acc, float2 a, float2 b) {
+  return make_float2(acc.x + a.x * b.x + a.y * b.y, acc.y + a.x * b.y - a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ double2 to_d2(C a) { return make_double2((double)a.x, (double)a.y); }
 
 // r = z - A x; optionally rhat = p = r.  tot = (||r||^2, ||z||^2).
 template <typename R, int KRYLOV>
@@ -164,6 +85,25 @@ __global__ void __launch_bounds__(kBlock) k_resid(const typename cplx_t<R>::type
   }
 }
 
+// x == 0: r = z (no stencil); tot = (||z||^2, ||z||^2)
+__global__ void __launch_bounds__(kBlock) k_resid_zero(const double2 *__restrict__ z, double2 *__restrict__ r,
+                                                       int64_t n, int b, Scal *sc, Reduce red) {
+  __shared__ double2 tot[64];
+  double2 acc[1] = {make_double2(0.0, 0.0)};
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 zz = z[e];
+    r[e] = zz;
+    const double q = zz.x * zz.x + zz.y * zz.y;
+    acc[0].x += q;
+    acc[0].y += q;
+  }
+  if (block_reduce<1>(acc, b, red.partial, red.counter, tot)) {
+    if (threadIdx.x < b) fin_resid(sc, threadIdx.x, tot[threadIdx.x], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) count_active(sc, b);
+  }
+}
+
 // v = A p; sigma = rhat^H v -> alpha
 template <typename R>
 __global__ void __launch_bounds__(kBlock) k_dslash_alpha(const typename cplx_t<R>::type *__restrict__ U,
@@ -173,7 +113,7 @@ __global__ void __launch_bounds__(kBlock) k_dslash_alpha(const typename cplx_t<R
                                                          int logb, R diag, Scal *sc, Reduce red) {
   typedef typename cplx_t<R>::type C;
   __shared__ double2 tot[64];
-  double2 acc[1] = {make_double2(0.0, 0.0)};
+  C a0 = mk<C>(0.0, 0.0);
   const int64_t n = (int64_t)g.V << logb;
   const int j = threadIdx.x & (b - 1);
   for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n; it += (int64_t)gridDim.x * blockDim.x) {
@@ -184,9 +124,10 @@ __global__ void __launch_bounds__(kBlock) k_dslash_alpha(const typename cplx_t<R
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
       v[base + c * b] = o[c];
-      acc[0] = dot_acc(acc[0], rhat[base + c * b], o[c]);
+      a0 = dot_acc(a0, rhat[base + c * b], o[c]);
     }
   }
+  double2 acc[1] = {to_d2(a0)};
   if (block_reduce<1>(acc, b, red.partial, red.counter, tot)) {
     if (threadIdx.x < b) fin_alpha(sc, threadIdx.x, tot[threadIdx.x]);
   }
@@ -213,7 +154,8 @@ __global__ void __launch_bounds__(kBlock) k_dslash_omega(const typename cplx_t<R
                                                          int logb, R diag, Scal *sc, Reduce red) {
   typedef typename cplx_t<R>::type C;
   __shared__ double2 tot[128];
-  double2 acc[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+  C a0 = mk<C>(0.0, 0.0);
+  R tt = 0;
   const int64_t n = (int64_t)g.V << logb;
   const int j = threadIdx.x & (b - 1);
   for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n; it += (int64_t)gridDim.x * blockDim.x) {
@@ -224,10 +166,11 @@ __global__ void __launch_bounds__(kBlock) k_dslash_omega(const typename cplx_t<R
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
       t[base + c * b] = o[c];
-      acc[0] = dot_acc(acc[0], o[c], self[c]);
-      acc[1].x += (double)o[c].x * o[c].x + (double)o[c].y * o[c].y;
+      a0 = dot_acc(a0, o[c], self[c]);
+      tt += o[c].x * o[c].x + o[c].y * o[c].y;
     }
   }
+  double2 acc[2] = {to_d2(a0), make_double2((double)tt, 0.0)};
   if (block_reduce<2>(acc, b, red.partial, red.counter, tot)) {
     if (threadIdx.x < b) fin_omega(sc, threadIdx.x, tot[threadIdx.x], tot[b + threadIdx.x]);
   }
@@ -243,7 +186,8 @@ __global__ void __launch_bounds__(kBlock) k_xr_update(typename cplx_t<R>::type *
                                                       int b, Scal *sc, Reduce red) {
   typedef typename cplx_t<R>::type C;
   __shared__ double2 tot[128];
-  double2 acc[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+  C a0 = mk<C>(0.0, 0.0);
+  R rr = 0;
   const int j = threadIdx.x & (b - 1);
   const C a = scal_as<C>(sc->alpha[j]);
   const C w = scal_as<C>(sc->omega[j]);
@@ -252,9 +196,10 @@ __global__ void __launch_bounds__(kBlock) k_xr_update(typename cplx_t<R>::type *
     x[e] = caxpy(w, s, caxpy(a, p[e], x[e]));
     const C rn = caxpy(cneg(w), t[e], s);
     r[e] = rn;
-    acc[0] = dot_acc(acc[0], rhat[e], rn);
-    acc[1].x += (double)rn.x * rn.x + (double)rn.y * rn.y;
+    a0 = dot_acc(a0, rhat[e], rn);
+    rr += rn.x * rn.x + rn.y * rn.y;
   }
+  double2 acc[2] = {to_d2(a0), make_double2((double)rr, 0.0)};
   if (block_reduce<2>(acc, b, red.partial, red.counter, tot)) {
     if (threadIdx.x < b) fin_beta(sc, threadIdx.x, tot[threadIdx.x], tot[b + threadIdx.x]);
     __syncthreads();
@@ -419,16 +364,26 @@ size_t solver_scratch_bytes(int64_t V, int b, int solver) {
   const size_t vec32 = ((size_t)V * 12 * b * sizeof(float2) + 255) / 256 * 256;
   const size_t red = 256 + (size_t)kMaxGrid * 2 * 64 * sizeof(double2);
   const size_t scal = 2 * ((sizeof(Scal) + 255) / 256) * 256;
-  const size_t fixed = 256 + red + scal + 256;
-  if (solver == DTR_SOLVER_MIXED_F32) return fixed + vec64 + 6 * vec32;
-  return fixed + 5 * vec64;
+  const size_t fixed = 256 + red + scal + 256 + 256;
+  if (solver == DTR_SOLVER_MIXED_F32) return fixed + vec64 + 7 * vec32;
+  return fixed + 6 * vec64;
 }
 
 static char *align256(char *p) { return (char *)(((uintptr_t)p + 255) & ~(uintptr_t)255); }
 
+static int read_gs_error(const GridSync *gs, cudaStream_t st) {
+  int *h = pinned_flag();
+  if (!h) return fail(DTR_ECUDA, "cudaMallocHost for the convergence flag failed");
+  DTR_CUDA(cudaMemcpyAsync(h + 1, &gs->error, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DTR_CUDA(cudaStreamSynchronize(st));
+  if (h[1]) return fail(DTR_ETIMEOUT, "persistent solver barrier timed out");
+  return DTR_OK;
+}
+
 // x (internal FP64, initial guess in / solution out), z (internal FP64)
 int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double2 *z, int b,
-                   const dtr_solve_params *p, void *work, size_t work_bytes, cudaStream_t st, Scal **scal_out) {
+                   const dtr_solve_params *p, void *work, size_t work_bytes, cudaStream_t st, Scal **scal_out,
+                   int x_is_zero) {
   const Geom g = geom_of(gauge->lat);
   const int64_t n = (int64_t)g.V * 12 * b;
   if (work_bytes < solver_scratch_bytes(g.V, b, p->solver)) return fail(DTR_ENOMEM, "solver workspace too small");
@@ -442,12 +397,15 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
   w = align256(w + sizeof(Scal));
   Scal *inner = (Scal *)w;
   w = align256(w + sizeof(Scal));
+  GridSync *gs = (GridSync *)w;
+  w = align256(w + sizeof(GridSync));
   DTR_CUDA(cudaMemsetAsync(red.counter, 0, 256, st));
   const int sms = device_sms();
   const int logb = ilog2i(b);
   const unsigned gd = reduce_grid((int64_t)g.V * b, sms);
   const unsigned gv = reduce_grid(n, sms);
   const int check = p->check_every > 0 ? p->check_every : 8;
+  const bool persistent = p->engine == 0;
   k_scal_init<<<1, 64, 0, st>>>(outer, b, p->tol * p->tol, p->maxiter); count_launches(1);
   DTR_LAUNCH_CHECK("scalar init");
   *scal_out = outer;
@@ -460,9 +418,23 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     K.p = (double2 *)w;    w = align256(w + n * sizeof(double2));
     K.v = (double2 *)w;    w = align256(w + n * sizeof(double2));
     K.t = (double2 *)w;    w = align256(w + n * sizeof(double2));
-    for (int cycle = 0; cycle < 64; ++cycle) {
+    double2 *sv = (double2 *)w; w = align256(w + n * sizeof(double2));
+    if (persistent) {
+      DTR_CUDA(cudaMemsetAsync(gs, 0, sizeof(GridSync), st));
+      PArgs<double> pa;
+      pa.U = gauge->U64;
+      pa.x = x; pa.r = K.r; pa.rhat = K.rhat; pa.p = K.p; pa.v = K.v; pa.s = sv; pa.t = K.t; pa.z = z;
+      pa.g = g; pa.b = b; pa.logb = logb; pa.diag = 4.0 + m0;
+      pa.sc = outer; pa.partial = red.partial; pa.gs = gs;
+      pa.max_iters = p->maxiter + 1;
+      pa.max_cycles = kMaxRestarts + 2;
+      int rc = launch_persistent<double>(pa, 1, st);
+      if (rc) return rc;
+      return read_gs_error(gs, st);
+    }
+    for (int cycle = 0; cycle <= kMaxRestarts; ++cycle) {
       k_resid<double, 1><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, K.r, K.rhat, K.p, g, b, logb, 4.0 + m0, outer, red,
-                                                 1); count_launches(1);
+                                                 cycle < kMaxRestarts); count_launches(1);
       DTR_LAUNCH_CHECK("residual");
       int n_active = 0;
       int rc = read_n_active(outer, st, &n_active);
@@ -471,9 +443,6 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
       rc = iterate<double>(gauge->U64, K, g, b, m0, outer, red, check, p->maxiter + check, st);
       if (rc) return rc;
     }
-    // final true residual for the statistics (no restart)
-    k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, K.r, K.rhat, K.p, g, b, logb, 4.0 + m0, outer, red, 0); count_launches(1);
-    DTR_LAUNCH_CHECK("final residual");
     return DTR_OK;
   }
   if (p->solver == DTR_SOLVER_MIXED_F32) {
@@ -485,10 +454,16 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     K.p = (float2 *)w;    w = align256(w + n * sizeof(float2));
     K.v = (float2 *)w;    w = align256(w + n * sizeof(float2));
     K.t = (float2 *)w;    w = align256(w + n * sizeof(float2));
+    float2 *sv = (float2 *)w; w = align256(w + n * sizeof(float2));
     const double itol = p->inner_tol > 0 ? p->inner_tol : 1e-5;
-    for (int cycle = 0; cycle < 64; ++cycle) {
-      k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0, outer,
-                                                 red, 1); count_launches(1);
+    for (int cycle = 0; cycle <= kMaxRestarts; ++cycle) {
+      const int restart = cycle < kMaxRestarts;
+      if (cycle == 0 && x_is_zero)
+        k_resid_zero<<<gv, kBlock, 0, st>>>(z, r64, n, b, outer, red);
+      else
+        k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0,
+                                                   outer, red, restart);
+      count_launches(1);
       DTR_LAUNCH_CHECK("outer residual");
       int n_active = 0;
       int rc = read_n_active(outer, st, &n_active);
@@ -497,14 +472,25 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
       k_mixed_init<<<gv, kBlock, 0, st>>>(r64, K.r, K.rhat, K.p, K.x, n, b, outer); count_launches(1);
       k_mixed_scal_init<<<1, 64, 0, st>>>(outer, inner, b, itol * itol, p->maxiter); count_launches(1);
       DTR_LAUNCH_CHECK("inner init");
-      rc = iterate<float>(gauge->U32, K, g, b, m0, inner, red, check, p->maxiter + check, st);
-      if (rc) return rc;
+      if (persistent) {
+        DTR_CUDA(cudaMemsetAsync(gs, 0, sizeof(GridSync), st));
+        PArgs<float> pa;
+        pa.U = gauge->U32;
+        pa.x = K.x; pa.r = K.r; pa.rhat = K.rhat; pa.p = K.p; pa.v = K.v; pa.s = sv; pa.t = K.t; pa.z = nullptr;
+        pa.g = g; pa.b = b; pa.logb = logb; pa.diag = (float)(4.0 + m0);
+        pa.sc = inner; pa.partial = red.partial; pa.gs = gs;
+        pa.max_iters = p->maxiter + 1;
+        pa.max_cycles = 1;
+        rc = launch_persistent<float>(pa, 0, st);
+        if (rc) return rc;
+      } else {
+        rc = iterate<float>(gauge->U32, K, g, b, m0, inner, red, check, p->maxiter + check, st);
+        if (rc) return rc;
+      }
       k_mixed_accum<<<gv, kBlock, 0, st>>>(x, K.x, n, b, outer, inner); count_launches(1);
       DTR_LAUNCH_CHECK("defect accumulate");
     }
-    k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0, outer,
-                                               red, 0); count_launches(1);
-    DTR_LAUNCH_CHECK("final residual");
+    if (persistent) return read_gs_error(gs, st);
     return DTR_OK;
   }
   return fail(DTR_EINVAL, "unknown solver");

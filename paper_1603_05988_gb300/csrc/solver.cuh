@@ -7,6 +7,7 @@ namespace dtr {
 
 constexpr int kFlagNaN = 1;
 constexpr int kFlagBreakdown = 2;
+constexpr int kMaxRestarts = 32;  // true-residual restarts / defect-correction cycles per column
 
 // Per-column Krylov scalars, resident in device memory (b <= 64 columns).
 struct Scal {
@@ -28,7 +29,9 @@ size_t solver_scratch_bytes(int64_t V, int b, int solver);
 // Solve A x = z on internal-layout FP64 blocks of width b.  x holds the
 // initial guess on entry.  *scal receives the device pointer of the final
 // per-column statistics (inside `work`).
+// x_is_zero: the caller guarantees x == 0 on entry (skips one FP64 stencil).
 int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double2 *z, int b,
-                   const dtr_solve_params *p, void *work, size_t work_bytes, cudaStream_t st, Scal **scal);
+                   const dtr_solve_params *p, void *work, size_t work_bytes, cudaStream_t st, Scal **scal,
+                   int x_is_zero = 0);
 
 }  // namespace dtr

@@ -38,7 +38,7 @@ static size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
 struct TraceLayout {
   int b;
-  size_t vec, zdot_red, solver, defl, small, total;
+  size_t vec, zdot_red, solver, defl, hp, sites, small, total;
 };
 
 static TraceLayout trace_layout(const dtr_gauge_s *g, const dtr_defl_s *D, const dtr_trace_params *p) {
@@ -49,9 +49,12 @@ static TraceLayout trace_layout(const dtr_gauge_s *g, const dtr_defl_s *D, const
   L.zdot_red = al(256 + (size_t)kMaxGrid * 64 * sizeof(double2));
   L.solver = al(solver_scratch_bytes(V, L.b, p->solve.solver));
   L.defl = D ? al(defl_scratch_bytes(V, D->k, L.b, device_sms())) : 0;
+  const bool hp = D && p->ncolors > 1;
+  L.hp = hp ? al(defl_hp_scratch_bytes(V, D->k, L.b, p->ncolors, device_sms())) : 0;
+  L.sites = hp ? al((size_t)V * sizeof(int)) : 0;
   const int k = D ? D->k : 0;
   L.small = al(3 * 64 * sizeof(double2) + (size_t)k * 64 * sizeof(double2));
-  L.total = 256 + 2 * L.vec + L.zdot_red + L.solver + L.defl + L.small;
+  L.total = 256 + 2 * L.vec + L.zdot_red + L.solver + L.defl + L.hp + L.sites + L.small;
   return L;
 }
 
@@ -75,6 +78,8 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
   w += L.zdot_red;
   void *solver_work = w;      w += L.solver;
   void *defl_work = w;        w += L.defl;
+  void *hp_work = w;          w += L.hp;
+  int *sites_dev = (int *)w;  w += L.sites;
   double2 *d_dev = (double2 *)w;
   double2 *t_dev = d_dev + 64;
   double2 *terms_dev = d_dev + 192;
@@ -95,19 +100,55 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
   const int sms = device_sms();
   if (res->replay) std::memset(res->replay, 0, sizeof(double) * 2 * (size_t)R * p->nvec * (k > 0 ? k : 1));
 
-  for (int r = 0; r < R; ++r) {
-    for (int q0 = 0; q0 < ncols; q0 += p->block) {
-      const int nb = (ncols - q0) < p->block ? (ncols - q0) : p->block;
-      launch_noise(Z, g, p->seed, p->z0_first + r, p->ncolors, p->dilute12, q0, nb, b, st);
+  // sites grouped by colour for the HP-structured projection (host counting sort)
+  bool hp_ok = false;
+  if (L.hp) {
+    const int nc = p->ncolors;
+    std::vector<int> count(nc, 0), col(g.V);
+    for (int sidx = 0; sidx < g.V; ++sidx) {
+      int xc[4];
+      int r0 = sidx;
+      xc[0] = r0 % g.L[0]; r0 /= g.L[0];
+      xc[1] = r0 % g.L[1]; r0 /= g.L[1];
+      xc[2] = r0 % g.L[2];
+      xc[3] = r0 / g.L[2];
+      col[sidx] = hp_colour(xc, nc);
+      count[col[sidx]]++;
+    }
+    hp_ok = true;
+    for (int c = 0; c < nc; ++c)
+      if (count[c] != g.V / nc) hp_ok = false;
+    if (hp_ok) {
+      std::vector<int> list(g.V), pos(nc);
+      for (int c = 0; c < nc; ++c) pos[c] = c * (g.V / nc);
+      for (int sidx = 0; sidx < g.V; ++sidx) list[pos[col[sidx]]++] = sidx;
+      DTR_CUDA(cudaMemcpyAsync(sites_dev, list.data(), sizeof(int) * g.V, cudaMemcpyHostToDevice, st));
+      DTR_CUDA(cudaStreamSynchronize(st));
+    }
+  }
+
+  // run-major sequence of (run, probing column) pairs, processed in blocks
+  const int64_t total_cols = (int64_t)R * ncols;
+  for (int64_t G0 = 0; G0 < total_cols; G0 += p->block) {
+    {
+      const int nb = (int)((total_cols - G0) < p->block ? (total_cols - G0) : p->block);
+      const int64_t q0 = G0 % ncols;
+      const bool one_run = q0 + nb <= ncols;
+      launch_noise(Z, g, p->seed, p->z0_first, p->ncolors, p->dilute12, G0, ncols, nb, b, st);
       DTR_LAUNCH_CHECK("noise");
       if (D) {
-        int rc = defl_project_internal(D, Z, b, d_dev, res->replay ? terms_dev : nullptr,
-                                       p->use_x0 ? X : nullptr, nullptr, defl_work, L.defl, sms, st);
+        int rc;
+        if (hp_ok && one_run && !p->use_x0)
+          rc = defl_project_hp(D, sites_dev, p->ncolors, p->seed, p->z0_first + G0 / ncols, q0, nb, p->dilute12, b,
+                               d_dev, res->replay ? terms_dev : nullptr, hp_work, L.hp, sms, st);
+        else
+          rc = defl_project_internal(D, Z, b, d_dev, res->replay ? terms_dev : nullptr, p->use_x0 ? X : nullptr,
+                                     nullptr, defl_work, L.defl, sms, st);
         if (rc) return rc;
       }
       if (!D || !p->use_x0) DTR_CUDA(cudaMemsetAsync(X, 0, (size_t)n * sizeof(double2), st));
       Scal *sc = nullptr;
-      int rc = solve_internal(gauge, m0, X, Z, b, &p->solve, solver_work, L.solver, st, &sc);
+      int rc = solve_internal(gauge, m0, X, Z, b, &p->solve, solver_work, L.solver, st, &sc, !D || !p->use_x0);
       if (rc) return rc;
       k_zdot<<<reduce_grid(n, sms), kBlock, 0, st>>>(Z, X, n, b, D ? d_dev : nullptr, t_dev, red); count_launches(1);
       DTR_LAUNCH_CHECK("z^H y reduction");
@@ -117,7 +158,9 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
         DTR_CUDA(cudaMemcpyAsync(termbuf.data(), terms_dev, sizeof(double2) * k * b, cudaMemcpyDeviceToHost, st));
       DTR_CUDA(cudaStreamSynchronize(st));
       for (int jj = 0; jj < nb; ++jj) {
-        const int q = q0 + jj;
+        const int64_t Gc = G0 + jj;
+        const int r = (int)(Gc / ncols);
+        const int q = (int)(Gc % ncols);
         const int jv = p->dilute12 ? q / 12 : q;
         double2 &s = samples[(size_t)r * p->nvec + jv];
         s.x += tbuf[jj].x;

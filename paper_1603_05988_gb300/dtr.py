@@ -23,7 +23,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 # ---------------------------------------------------------------- C structs
-DTR_OK, DTR_EINVAL, DTR_ENOMEM, DTR_ECUDA, DTR_ENOTCONV, DTR_ENAN = range(6)
+DTR_OK, DTR_EINVAL, DTR_ENOMEM, DTR_ECUDA, DTR_ENOTCONV, DTR_ENAN, DTR_ETIMEOUT = range(7)
 DTR_F64, DTR_F32, DTR_BF16, DTR_F16 = range(4)
 SOLVER_F64, SOLVER_MIXED_F32 = 0, 1
 _PREC = {"f64": DTR_F64, "f32": DTR_F32, "bf16": DTR_BF16, "f16": DTR_F16}
@@ -32,7 +32,8 @@ _SOLVER = {"f64": SOLVER_F64, "mixed_f32": SOLVER_MIXED_F32}
 
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("solver", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("inner_tol", ctypes.c_double)]
+                ("check_every", ctypes.c_int), ("inner_tol", ctypes.c_double), ("engine", ctypes.c_int),
+                ("pad_", ctypes.c_int)]
 
 
 class SolveStat(ctypes.Structure):
@@ -74,6 +75,7 @@ _sig("dtr_last_error", ctypes.c_char_p, [])
 _sig("dtr_version", ctypes.c_char_p, [])
 _sig("dtr_kernel_launches", ctypes.c_uint64, [])
 _sig("dtr_time_dslash", _i, [_vp, _d, _i, _i, _i, _vp, _sz, ctypes.POINTER(ctypes.c_double), _vp])
+_sig("dtr_selftest_barrier", _i, [_i64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _vp])
 _sig("dtr_make_lattice", _i, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_vp)])
 _sig("dtr_destroy_lattice", None, [_vp])
 _sig("dtr_lattice_info", _i, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64), ctypes.POINTER(_i64)])
@@ -212,6 +214,14 @@ def dslash_many(gauge, m0, X, dagger=False, prec="f64", chunk=64):
     return out
 
 
+def selftest_barrier(budget_cycles=2_000_000):
+    """Run the bounded-barrier self-test; returns (timed_out, error_word)."""
+    t = ctypes.c_int()
+    e = ctypes.c_int()
+    _check(_lib.dtr_selftest_barrier(int(budget_cycles), ctypes.byref(t), ctypes.byref(e), _stream()))
+    return t.value, e.value
+
+
 def kernel_launches():
     """Kernels the library launched so far in this process."""
     return int(_lib.dtr_kernel_launches())
@@ -236,10 +246,14 @@ def gen_noise(lat, seed, z0_index, ncolors, dilute12, q0, nrhs):
     return out
 
 
-def solve_params(tol=1e-10, maxiter=5000, solver="f64", check_every=8, inner_tol=1e-5):
+_ENGINE = {"persistent": 0, "kernels": 1}
+
+
+def solve_params(tol=1e-10, maxiter=5000, solver="f64", check_every=8, inner_tol=1e-5, engine="persistent"):
     p = SolveParams()
     _lib.dtr_solve_params_default(ctypes.byref(p))
     p.tol, p.maxiter, p.solver, p.check_every, p.inner_tol = tol, maxiter, _SOLVER[solver], check_every, inner_tol
+    p.engine = _ENGINE[engine]
     return p
 
 

@@ -21,6 +21,18 @@ and the re-orthonormalisation use torch/numpy, off the estimator's hot path.
 import numpy as np
 
 
+def _orthonormalise_rows(X):
+    """CholeskyQR2 on the rows of X (p x N): Gram on the GPU, p x p Cholesky on the host."""
+    import torch
+    for _ in range(2):
+        G = (X.conj() @ X.T).cpu().numpy()           # G[a, b] = x_a^H x_b
+        G = 0.5 * (G + G.conj().T)
+        L = np.linalg.cholesky(G)                     # G = L L^H
+        Linv = np.linalg.inv(L)
+        X = (torch.from_numpy(np.ascontiguousarray(Linv.conj())).to(X.device) @ X).contiguous()
+    return X
+
+
 def _gamma5(X):
     p, N = X.shape
     Y = X.clone()
@@ -37,9 +49,9 @@ def smallest_gamma5_eigpairs(gauge, m0, k, p=None, iters=100, tol=1e-2, seed=0, 
     N = gauge.lat.N
     p = p or int(np.ceil(1.5 * k)) + 8
     gen = torch.Generator(device="cpu").manual_seed(int(seed))
-    X = (torch.randn((N, p), generator=gen, dtype=torch.float64)
-         + 1j * torch.randn((N, p), generator=gen, dtype=torch.float64)).to("cuda")
-    X = torch.linalg.qr(X)[0].T.contiguous()          # rows: orthonormal basis vectors
+    X = (torch.randn((p, N), generator=gen, dtype=torch.float64)
+         + 1j * torch.randn((p, N), generator=gen, dtype=torch.float64)).to("cuda")
+    X = _orthonormalise_rows(X)                       # rows: orthonormal basis vectors
     params = dtr.solve_params(tol=solve_tol, solver=solver)
     res = np.full(k, np.inf)
     lam = None
@@ -69,6 +81,6 @@ def smallest_gamma5_eigpairs(gauge, m0, k, p=None, iters=100, tol=1e-2, seed=0, 
                       % (it, res.max(), abs(lam[0]), abs(lam[k - 1])))
             if res.max() <= tol:
                 break
-        X = torch.linalg.qr((Ct.T @ W).T)[0].T.contiguous()
+        X = _orthonormalise_rows((Ct.T @ W).contiguous())
     V = Xr[:k].cpu().numpy().T.copy()
     return V, np.asarray(lam[:k]), res, it

@@ -89,13 +89,14 @@ def test_gauge_roundtrip(dtr):
     assert np.array_equal(g.to_host(), U)
 
 
+@pytest.mark.parametrize("engine", ["persistent", "kernels"])
 @pytest.mark.parametrize("solver", ["f64", "mixed_f32"])
-@pytest.mark.parametrize("dims,nrhs", [((4, 4, 4, 4), 8), ((4, 4, 4, 8), 13)])
-def test_solve_true_residual(dtr, solver, dims, nrhs):
+@pytest.mark.parametrize("dims,nrhs", [((4, 4, 4, 4), 8), ((4, 4, 4, 8), 13), ((8, 8, 8, 8), 64)])
+def test_solve_true_residual(dtr, solver, dims, nrhs, engine):
     import torch
     U, lat, g = _setup(dtr, dims, 0.5, -0.4, 1000)
-    Z = noise.noise_vectors(dims, 5, 0, 16, False, 0, nrhs)
-    p = dtr.solve_params(tol=1e-10, solver=solver)
+    Z = noise.noise_vectors(dims, 5, 0, 16 if nrhs <= 16 else 512, False, 0, nrhs)
+    p = dtr.solve_params(tol=1e-10, solver=solver, engine=engine)
     y, stats = dtr.solve_batch(g, -0.4, torch.from_numpy(np.ascontiguousarray(Z.T)).cuda(), params=p)
     Y = _cpu(y).T
     A = wilson.explicit(U, dims, -0.4)
@@ -118,6 +119,16 @@ def test_solve_initial_guess_and_zero_rhs(dtr):
     assert st[0]["converged"] and st[1]["converged"]
     assert np.abs(_cpu(y)[1]).max() == 0.0
     assert st[0]["iterations"] == 0              # exact guess: nothing to do
+
+
+def test_barrier_timeout_is_reported(dtr):
+    """A barrier whose peer never arrives gives up within its budget and raises
+    the error word (the solver maps it to DTR_ETIMEOUT); the context stays usable."""
+    timed_out, err = dtr.selftest_barrier(2_000_000)      # ~1 ms at 2 GHz
+    assert timed_out == 1 and err == 1
+    lat = dtr.make_lattice((4, 4, 4, 4))
+    z = dtr.gen_noise(lat, 1, 0, 1, False, 0, 1)           # GPU still answers
+    assert z.abs().max().item() == 1.0
 
 
 def test_solve_not_converged_reports(dtr):
@@ -200,6 +211,35 @@ def test_trace_mixed_matches_fp64(dtr, cfg1):
         outs.append(dtr.trace_estimate(c["g"], c["m0"], D, p))
     assert np.abs(outs[0]["samples"] - outs[1]["samples"]).max() <= 1e-8 * np.abs(outs[0]["samples"]).max()
     assert abs(outs[0]["trace"] - outs[1]["trace"]) <= 1e-10 * abs(outs[0]["trace"])
+
+
+def test_trace_hp_projection_matches_generic(dtr, cfg1):
+    """The HP-structured deflation projection (per-colour sums of V^H z0) and
+    the generic contraction V^H [Z, g5 Z] give the same per-m terms."""
+    c = cfg1
+    D = dtr.defl_create(c["lat"], c["V"], c["lam"])
+    outs = []
+    for use_x0 in (False, True):     # use_x0 forces the generic projection
+        p = dtr.trace_params(seed=8, n_z0=2, ncolors=32, nvec=32, block=16, use_x0=use_x0,
+                             solve=dtr.solve_params(tol=1e-12))
+        outs.append(dtr.trace_estimate(c["g"], c["m0"], D, p, want_replay=True))
+    a, b = outs[0]["replay"], outs[1]["replay"]
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    assert np.abs(outs[0]["samples"] - outs[1]["samples"]).max() <= 1e-8 * np.abs(outs[1]["samples"]).max()
+
+
+def test_trace_deflated_blocks_spanning_runs(dtr, cfg1):
+    """Blocks that straddle two z0 runs take the generic projection."""
+    c = cfg1
+    D = dtr.defl_create(c["lat"], c["V"], c["lam"])
+    p = dtr.trace_params(seed=3, z0_first=2, n_z0=3, ncolors=32, nvec=20, block=8,
+                         solve=dtr.solve_params(tol=1e-12, solver="mixed_f32"))
+    out = dtr.trace_estimate(c["g"], c["m0"], D, p)
+    for r in range(3):
+        Z = noise.noise_vectors(c["dims"], 3, 2 + r, 32, False, 0, 20)
+        ref = estimator.deflated_hp(c["AH"], lambda Z: c["Ainv"] @ Z, Z, c["V"], c["sig"])
+        assert np.abs(out["samples"][r] - ref["t"]).max() <= 1e-8 * np.abs(ref["t"]).max()
+        assert abs(out["trace_runs"][r] - ref["trace"][-1]) <= 1e-10 * abs(ref["trace"][-1])
 
 
 def test_trace_complete_probing_exact(dtr, cfg1):
