@@ -162,7 +162,8 @@ typedef struct {
   double inner_tol;    /* mixed solver: relative residual reduction per inner solve */
   int engine;          /* 0: persistent cooperative kernel (one launch per solve / inner solve);
                           1: one kernel per BiCGStab step, host polls every check_every iterations */
-  int pad_;
+  int grid;            /* persistent engine: CTAs to launch (0 = every SM; clamped to what can be
+                          co-resident) */
 } dtr_solve_params;
 
 typedef struct {

@@ -250,7 +250,7 @@ void dtr_solve_params_default(dtr_solve_params *p) {
   p->check_every = 8;
   p->inner_tol = 1e-5;
   p->engine = 0;
-  p->pad_ = 0;
+  p->grid = 0;
 }
 
 static int check_solve_params(const dtr_solve_params *p) {
@@ -259,6 +259,7 @@ static int check_solve_params(const dtr_solve_params *p) {
   if (p->solver != DTR_SOLVER_BICGSTAB_F64 && p->solver != DTR_SOLVER_MIXED_F32)
     return fail(DTR_EINVAL, "unknown solver");
   if (p->engine != 0 && p->engine != 1) return fail(DTR_EINVAL, "engine must be 0 (persistent) or 1 (per-step)");
+  if (p->grid < 0) return fail(DTR_EINVAL, "grid must be >= 0");
   return DTR_OK;
 }
 

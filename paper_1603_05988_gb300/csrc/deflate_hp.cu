@@ -124,10 +124,10 @@ __global__ void k_hp_finish(const double2 *__restrict__ W, int nc, int k, int b,
 }
 
 static int hp_split(int nc, int per_colour, int k, int sms) {
-  // enough blocks (about 8 per SM) to hide the DRAM latency of the V stream
+  // about two blocks per SM; more splits make the split reduction latency-bound
   const int mt = (k + kHPThreads - 1) / kHPThreads;
-  int ns = (8 * sms + nc * mt - 1) / (nc * mt);
-  const int max_by_sites = per_colour / 4 > 0 ? per_colour / 4 : 1;
+  int ns = (2 * sms + nc * mt - 1) / (nc * mt);
+  const int max_by_sites = per_colour / 16 > 0 ? per_colour / 16 : 1;
   if (ns > max_by_sites) ns = max_by_sites;
   if (ns < 1) ns = 1;
   return ns;

@@ -90,4 +90,54 @@ __device__ __forceinline__ void fin_beta(Scal *sc, int j, double2 rr0, double2 r
   sc->rho[j] = rr0;
 }
 
+// Merged omega/beta step of the three-barrier iteration.  From the reductions
+// of the t = A s phase -- ts = t^H s, tt = t^H t, rs = rhat^H s, rt = rhat^H t,
+// ss = s^H s -- everything the rest of the iteration needs follows without a
+// further grid reduction:
+//   omega  = ts / tt
+//   rho'   = rhat^H (s - omega t)      = rs - omega rt
+//   |r'|^2 = |s - omega t|^2            = ss - |ts|^2 / tt
+//   beta   = (rho' / rho) (alpha / omega)
+// (|r'|^2 is the recursive residual used only for the convergence test; the
+// FP64 true residual certifies the result.)
+__device__ __forceinline__ void fin_omega_beta(Scal *sc, int j, double2 ts, double2 tt, double2 rs, double2 rt,
+                                               double2 ss) {
+  if (!sc->active[j]) {
+    sc->omega[j] = make_double2(0.0, 0.0);
+    sc->beta[j] = make_double2(0.0, 0.0);
+    return;
+  }
+  sc->iters[j] += 1;
+  double2 om = make_double2(0.0, 0.0);
+  double rn2 = ss.x;
+  if (tt.x > 0.0) {
+    om = make_double2(ts.x / tt.x, ts.y / tt.x);
+    rn2 = ss.x - (ts.x * ts.x + ts.y * ts.y) / tt.x;
+    if (rn2 < 0.0) rn2 = 0.0;
+  }
+  sc->omega[j] = om;
+  sc->rnorm2[j] = rn2;
+  if (!(rn2 == rn2) || isinf(rn2)) {
+    sc->flags[j] |= kFlagNaN;
+    sc->active[j] = 0;
+    sc->beta[j] = make_double2(0.0, 0.0);
+    return;
+  }
+  if (rn2 <= sc->tol2 * sc->bnorm2[j] || sc->iters[j] >= sc->maxiter) {
+    sc->active[j] = 0;                 // x and r still take this iteration's update
+    sc->beta[j] = make_double2(0.0, 0.0);
+    return;
+  }
+  const double2 rho = sc->rho[j];
+  if ((om.x == 0.0 && om.y == 0.0) || (rho.x == 0.0 && rho.y == 0.0)) {
+    sc->flags[j] |= kFlagBreakdown;
+    sc->active[j] = 0;
+    sc->beta[j] = make_double2(0.0, 0.0);
+    return;
+  }
+  const double2 rho_new = csub(rs, cmul(om, rt));
+  sc->beta[j] = cmul(cdiv(rho_new, rho), cdiv(sc->alpha[j], om));
+  sc->rho[j] = rho_new;
+}
+
 }  // namespace dtr

@@ -2,13 +2,14 @@
 // right-hand sides in ONE cooperative launch (one CTA per SM, co-resident),
 // with grid-wide barriers instead of kernel boundaries and no host polling.
 //
-// Per iteration, four phases separated by barriers:
-//   P1  v = A p                      partial  rhat^H v          -> alpha
-//   P2  t = A s, s = r - alpha v     partials t^H s, t^H t      -> omega
-//       (s is formed on the fly at the neighbours and stored at the own site)
-//   P3  x += alpha p + omega s, r = s - omega t
-//                                    partials rhat^H r, r^H r   -> beta, convergence
-//   P4  p = r + beta (p - omega v)
+// Per iteration, three phases separated by barriers:
+//   P1  v = A p                      partial  rhat^H v                 -> alpha
+//   P2  t = A s, s = r - alpha v     partials t^H s, t^H t, rhat^H s,
+//       (s formed on the fly at       rhat^H t, s^H s                  -> omega, and
+//        neighbours, stored at own    rho' = rhat^H s - omega rhat^H t, |r'|^2 =
+//        site)                        s^H s - |t^H s|^2 / t^H t -> beta, convergence
+//   P3  x += alpha p + omega s, r = s - omega t, p = r + beta (p - omega v)
+// so the r-reduction of textbook BiCGStab folds into the omega reduction.
 // Each reduction is finished by the LAST block to reach the barrier: it sums
 // the per-block partials in a fixed order (deterministic), runs the scalar
 // algebra once per column and only then releases the barrier, so every block
@@ -53,7 +54,7 @@ __device__ __forceinline__ bool gsync_n(GridSync *gs, unsigned int expected, lon
           s_err = 1;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(20);
       }
     }
     __threadfence();
@@ -132,9 +133,24 @@ template <int NV, int T>
 __device__ __forceinline__ void grid_total(int b, const double2 *__restrict__ partial, double2 *sh, double2 *tot) {
   const int t = threadIdx.x;
   const int P = NV * b;
+  const int G = gridDim.x;
+  if (P > T) {  // more (value, column) pairs than threads: one thread per pair
+    for (int p = t; p < P; p += T) {
+      const int q = p / b, j = p % b;
+      double2 a0 = make_double2(0.0, 0.0), a1 = a0;
+      int blk = 0;
+      for (; blk + 1 < G; blk += 2) {
+        a0 = cadd(a0, __ldcg(&partial[((int64_t)blk * NV + q) * b + j]));
+        a1 = cadd(a1, __ldcg(&partial[((int64_t)(blk + 1) * NV + q) * b + j]));
+      }
+      if (blk < G) a0 = cadd(a0, __ldcg(&partial[((int64_t)blk * NV + q) * b + j]));
+      tot[p] = cadd(a0, a1);
+    }
+    __syncthreads();
+    return;
+  }
   const int S = T / P;
   const int p = t % P, sl = t / P;
-  const int G = gridDim.x;
   double2 a0 = make_double2(0.0, 0.0), a1 = a0, a2 = a0, a3 = a0;
   if (sl < S) {
     const int q = p / b, j = p % b;
@@ -167,8 +183,8 @@ template <typename C> __device__ __forceinline__ C ldcg_scal(const double2 *p) {
 template <typename R, int T, int WITH_RESID>
 __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
   typedef typename cplx_t<R>::type C;
-  __shared__ double2 sh[2 * T];
-  __shared__ double2 tot[128];
+  __shared__ double2 sh[5 * T];
+  __shared__ double2 tot[5 * 64];
   const int b = a.b, logb = a.logb;
   const int j = threadIdx.x & (b - 1);
   const int64_t nsite = (int64_t)a.g.V << logb;
@@ -231,10 +247,10 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
         });
         if (!ok) return;
       }
-      {  // P2: t = A s with s = r - alpha v on the fly ; (t^H s, t^H t) -> omega
+      {  // P2: t = A s with s = r - alpha v on the fly ; five dots -> omega, beta, convergence
         const C al = ldcg_scal<C>(&sc->alpha[j]);
         AxpyLoad<C> ld{a.r, a.v, al};
-        R tsx = 0, tsy = 0, tt = 0;
+        R tsx = 0, tsy = 0, tt = 0, rsx = 0, rsy = 0, rtx = 0, rty = 0, ss = 0;
         for (int64_t it = t0; it < nsite; it += stride) {
           const int s = (int)(it >> logb);
           C o[12], self[12];
@@ -244,67 +260,65 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
           for (int c = 0; c < 12; ++c) {
             a.t[base + c * b] = o[c];
             a.s[base + c * b] = self[c];
+            const C rh = a.rhat[base + c * b];
             tsx += o[c].x * self[c].x + o[c].y * self[c].y;
             tsy += o[c].x * self[c].y - o[c].y * self[c].x;
             tt += o[c].x * o[c].x + o[c].y * o[c].y;
+            rsx += rh.x * self[c].x + rh.y * self[c].y;
+            rsy += rh.x * self[c].y - rh.y * self[c].x;
+            rtx += rh.x * o[c].x + rh.y * o[c].y;
+            rty += rh.x * o[c].y - rh.y * o[c].x;
+            ss += self[c].x * self[c].x + self[c].y * self[c].y;
           }
         }
-        double2 acc[2] = {make_double2((double)tsx, (double)tsy), make_double2((double)tt, 0.0)};
-        block_partial<2, T>(acc, b, a.partial, sh);
+        double2 acc[5] = {make_double2((double)tsx, (double)tsy), make_double2((double)tt, 0.0),
+                          make_double2((double)rsx, (double)rsy), make_double2((double)rtx, (double)rty),
+                          make_double2((double)ss, 0.0)};
+        block_partial<5, T>(acc, b, a.partial, sh);
         const bool ok = gsync(a.gs, [&] {
-          grid_total<2, T>(b, a.partial, sh, tot);
-          if (threadIdx.x < b) fin_omega(sc, threadIdx.x, tot[threadIdx.x], tot[b + threadIdx.x]);
-        });
-        if (!ok) return;
-      }
-      {  // P3: x += alpha p + omega s ; r = s - omega t ; (rhat^H r, r^H r) -> beta, convergence
-        const C al = ldcg_scal<C>(&sc->alpha[j]);
-        const C om = ldcg_scal<C>(&sc->omega[j]);
-        R rrx = 0, rry = 0, rr = 0;
-        for (int64_t e = t0; e < nel; e += stride) {
-          const C sv = a.s[e];
-          a.x[e] = caxpy(om, sv, caxpy(al, a.p[e], a.x[e]));
-          const C rn = caxpy(cneg(om), a.t[e], sv);
-          a.r[e] = rn;
-          const C rh = a.rhat[e];
-          rrx += rh.x * rn.x + rh.y * rn.y;
-          rry += rh.x * rn.y - rh.y * rn.x;
-          rr += rn.x * rn.x + rn.y * rn.y;
-        }
-        double2 acc[2] = {make_double2((double)rrx, (double)rry), make_double2((double)rr, 0.0)};
-        block_partial<2, T>(acc, b, a.partial, sh);
-        const bool ok = gsync(a.gs, [&] {
-          grid_total<2, T>(b, a.partial, sh, tot);
-          if (threadIdx.x < b) fin_beta(sc, threadIdx.x, tot[threadIdx.x], tot[b + threadIdx.x]);
+          grid_total<5, T>(b, a.partial, sh, tot);
+          if (threadIdx.x < b)
+            fin_omega_beta(sc, threadIdx.x, tot[threadIdx.x], tot[b + threadIdx.x], tot[2 * b + threadIdx.x],
+                           tot[3 * b + threadIdx.x], tot[4 * b + threadIdx.x]);
           __syncthreads();
           if (threadIdx.x == 0) count_active(sc, b);
         });
         if (!ok) return;
       }
-      if (__ldcg(&sc->n_active) == 0) break;
-      {  // P4: p = r + beta (p - omega v)
-        if (__ldcg(&sc->active[j])) {
-          const C be = ldcg_scal<C>(&sc->beta[j]);
-          const C om = ldcg_scal<C>(&sc->omega[j]);
-          for (int64_t e = t0; e < nel; e += stride) a.p[e] = caxpy(be, caxpy(cneg(om), a.v[e], a.p[e]), a.r[e]);
+      {  // P3: x += alpha p + omega s ; r = s - omega t ; p = r + beta (p - omega v)
+        const C al = ldcg_scal<C>(&sc->alpha[j]);
+        const C om = ldcg_scal<C>(&sc->omega[j]);
+        const C be = ldcg_scal<C>(&sc->beta[j]);
+        const bool act = __ldcg(&sc->active[j]) != 0;
+        for (int64_t e = t0; e < nel; e += stride) {
+          const C sv = a.s[e];
+          const C pv = a.p[e];
+          a.x[e] = caxpy(om, sv, caxpy(al, pv, a.x[e]));
+          const C rn = caxpy(cneg(om), a.t[e], sv);
+          a.r[e] = rn;
+          if (act) a.p[e] = caxpy(be, caxpy(cneg(om), a.v[e], pv), rn);
         }
-        const bool ok = gsync(a.gs, [] {});
+        const bool stop = __ldcg(&sc->n_active) == 0;
+        if (stop && !WITH_RESID) break;  // kernel exit orders these writes for the host
+        const bool ok = gsync(a.gs, [] {});  // p (and x for the residual phase) read at neighbours next
         if (!ok) return;
+        if (stop) break;
       }
     }
   }
 }
 
 template <typename R, int T, int W> static int launch_one(const PArgs<R> &pa, cudaStream_t st) {
-  static int grid = 0;
-  if (!grid) {
+  static int max_grid = 0;
+  if (!max_grid) {
     int nb = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bicgstab_persistent<R, T, W>, T, 0);
     if (e != cudaSuccess) return cuda_fail(e, "persistent solver occupancy");
     if (nb < 1) return fail(DTR_ECUDA, "persistent solver cannot be resident");
-    grid = nb * device_sms();
-    if (grid > kMaxGrid) grid = kMaxGrid;
+    max_grid = nb * device_sms();
+    if (max_grid > kMaxGrid) max_grid = kMaxGrid;
   }
+  const int grid = (pa.grid > 0 && pa.grid < max_grid) ? pa.grid : max_grid;
   PArgs<R> copy = pa;
   void *args[] = {&copy};
   DTR_CUDA(cudaLaunchCooperativeKernel((const void *)k_bicgstab_persistent<R, T, W>, dim3(grid), dim3(T), args, 0,

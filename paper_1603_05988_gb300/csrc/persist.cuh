@@ -25,6 +25,7 @@ template <typename R> struct PArgs {
   GridSync *gs;
   int max_iters;     // iteration cap of one cycle (safety; per-column maxiter is in Scal)
   int max_cycles;    // true-residual restart cycles (with_resid only)
+  int grid;          // requested CTAs (0 = all co-resident)
 };
 
 // with_resid = 1: cycles of (true residual r = z - A x, restart decision,

@@ -362,7 +362,7 @@ static int iterate(const typename cplx_t<R>::type *U, KrylovVecs<R> &K, const Ge
 size_t solver_scratch_bytes(int64_t V, int b, int solver) {
   const size_t vec64 = ((size_t)V * 12 * b * sizeof(double2) + 255) / 256 * 256;
   const size_t vec32 = ((size_t)V * 12 * b * sizeof(float2) + 255) / 256 * 256;
-  const size_t red = 256 + (size_t)kMaxGrid * 2 * 64 * sizeof(double2);
+  const size_t red = 256 + (size_t)kMaxGrid * 5 * 64 * sizeof(double2);
   const size_t scal = 2 * ((sizeof(Scal) + 255) / 256) * 256;
   const size_t fixed = 256 + red + scal + 256 + 256;
   if (solver == DTR_SOLVER_MIXED_F32) return fixed + vec64 + 7 * vec32;
@@ -392,7 +392,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
   red.counter = (unsigned int *)w;
   w = align256(w + 256);
   red.partial = (double2 *)w;
-  w = align256(w + (size_t)kMaxGrid * 2 * 64 * sizeof(double2));
+  w = align256(w + (size_t)kMaxGrid * 5 * 64 * sizeof(double2));
   Scal *outer = (Scal *)w;
   w = align256(w + sizeof(Scal));
   Scal *inner = (Scal *)w;
@@ -428,6 +428,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
       pa.sc = outer; pa.partial = red.partial; pa.gs = gs;
       pa.max_iters = p->maxiter + 1;
       pa.max_cycles = kMaxRestarts + 2;
+      pa.grid = p->grid;
       int rc = launch_persistent<double>(pa, 1, st);
       if (rc) return rc;
       return read_gs_error(gs, st);
@@ -481,6 +482,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
         pa.sc = inner; pa.partial = red.partial; pa.gs = gs;
         pa.max_iters = p->maxiter + 1;
         pa.max_cycles = 1;
+        pa.grid = p->grid;
         rc = launch_persistent<float>(pa, 0, st);
         if (rc) return rc;
       } else {

@@ -33,7 +33,7 @@ _SOLVER = {"f64": SOLVER_F64, "mixed_f32": SOLVER_MIXED_F32}
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("solver", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("inner_tol", ctypes.c_double), ("engine", ctypes.c_int),
-                ("pad_", ctypes.c_int)]
+                ("grid", ctypes.c_int)]
 
 
 class SolveStat(ctypes.Structure):
@@ -249,11 +249,13 @@ def gen_noise(lat, seed, z0_index, ncolors, dilute12, q0, nrhs):
 _ENGINE = {"persistent": 0, "kernels": 1}
 
 
-def solve_params(tol=1e-10, maxiter=5000, solver="f64", check_every=8, inner_tol=1e-5, engine="persistent"):
+def solve_params(tol=1e-10, maxiter=5000, solver="f64", check_every=8, inner_tol=1e-5, engine="persistent",
+                 grid=0):
     p = SolveParams()
     _lib.dtr_solve_params_default(ctypes.byref(p))
     p.tol, p.maxiter, p.solver, p.check_every, p.inner_tol = tol, maxiter, _SOLVER[solver], check_every, inner_tol
     p.engine = _ENGINE[engine]
+    p.grid = int(grid)
     return p
 
 
