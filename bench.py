@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--f64-steps", type=int, default=6, help="steps of the plain FP64 path timed for comparison")
     ap.add_argument("--eig-iters", type=int, default=150,
                     help="cap on setup eigensolver iterations (deflation-space quality; untimed)")
+    ap.add_argument("--skip-hbm", action="store_true", help="skip the 32^3x64 half-precision stencil measurement")
     ap.add_argument("--cpu-sample-rhs", type=int, default=1, help="RHS in the CPU-oracle baseline sample")
     return ap.parse_args()
 
@@ -243,9 +244,11 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = dtr.kernel_launches()
+    dtr.profile_persistent(1)                          # event-time every persistent solver launch
     torch.cuda.nvtx.range_push("timed")
     ms, traces, iters = run_steps(args.solver, args.steps, base, True)
     torch.cuda.nvtx.range_pop()
+    prof = dtr.profile_persistent(0)
     launches = dtr.kernel_launches() - launches0
     barrier()
     clk = clocks.stop()
@@ -278,19 +281,41 @@ def main():
     ttr = t_run * var_T / (1e-3 * abs(tr_mean)) ** 2
     ttr64 = t_run64 * var_T / (1e-3 * abs(tr_mean)) ** 2
 
-    # roofline of the dominant kernel: the FP32 stencil the inner solver runs
-    # twice per iteration (the fused dslash+dot kernels share its core)
-    dsl_ms = dtr.time_dslash(gauge, w.m0, w.block, prec="f32" if args.solver == "mixed_f32" else "f64", reps=200)
-    Vs = w.V
-    flops = Vs * w.block * 1368.0                      # 1320 hopping + 48 diagonal per site and RHS
+    # roofline of the dominant kernel: the persistent BiCGStab kernel (one
+    # cooperative launch per inner solve), event-timed inside the timed region;
+    # algorithmic FP32 flops per site, RHS and iteration: two stencils
+    # (2 x 1368) plus the fused vector work (12 complex x 104 flops)
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12          # TFLOP/s: SMs x FP32 lanes x FMA x max clock
-    achieved = flops / (dsl_ms / 1e3) / 1e12
-    bytes_alg = Vs * w.block * (96 + 96) + Vs * 288     # FP32: psi in + out per RHS, links once
+    flop_per_unit = 2 * 1368.0 + 12 * 104.0
+    pms = prof["ms"] / max(prof["launches"], 1)
+    pflops = prof["site_rhs_iterations"] * flop_per_unit / max(prof["launches"], 1)
+    achieved = pflops / (pms / 1e3) / 1e12 if pms > 0 else 0.0
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-            "traffic": None, "kernel": "dslash FP32, 16 RHS, 8^4 (L2-resident)",
-            "avg_launch_ms": dsl_ms, "alg_bytes_per_launch": bytes_alg,
-            "achieved_gbs_if_dram": bytes_alg / (dsl_ms / 1e3) / 1e9,
-            "peak_note": "FP32 CUDA-core peak derived from 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+            "traffic": None, "kernel": "k_bicgstab_persistent<float,512> (FP32 inner solve, 16 RHS, 8^4, L2-resident)",
+            "avg_launch_ms": pms, "launches": prof["launches"], "flops_per_launch": pflops,
+            "peak_note": "FP32 peak derived from 152 SMs x 128 lanes x 2 flop x 2.07 GHz (of nominal clocks)",
+            "share_note": "share of GPU time in the timed region: see profiles/launches_wilson8x8x8x8_hp16x256_k100.md"}
+
+    # the stencil core alone at the bench's shape, and the half-precision stencil
+    # on a lattice far larger than L2 (HBM roofline)
+    from paper_1603_05988_gb300 import kbench
+    st8 = kbench.dslash_case(gauge, w.dims, "f32", w.block, 200)
+    roof_stencil = {"bound": "alu", "achieved": st8["achieved_tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": st8["achieved_tflops"] / fp32_peak, "traffic": None,
+                    "kernel": "dslash FP32, 16 RHS, 8^4", "avg_launch_ms": st8["avg_launch_ms"]}
+    hbm_peak = 6793.4
+    roof_hbm = None
+    if not args.skip_hbm:
+        dims_big = (32, 32, 32, 64)
+        lat_big = dtr.make_lattice(dims_big)
+        g_big = dtr.make_gauge(lat_big, kbench.tiled_links(dims_big))
+        hb = kbench.dslash_case(g_big, dims_big, "bf16", 1, 30)
+        roof_hbm = {"bound": "hbm", "achieved": hb["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hb["achieved_gbs"] / hbm_peak, "traffic": None,
+                    "kernel": "dslash BF16 storage (two-row links), FP32 math, 1 RHS, 32^3x64",
+                    "avg_launch_ms": hb["avg_launch_ms"], "alg_bytes_per_launch": hb["alg_bytes_per_launch"],
+                    "peak_note": "hbm_gbs of MEASURED_PEAKS.json (of measured)"}
+        del g_big, lat_big
 
     # CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -322,6 +347,8 @@ def main():
                     "note": "host wall clock around dtr_trace_estimate, results read back to host each step"},
             "gpu_launches": launches,
             "roofline": roof,
+            "roofline_stencil_fp32": roof_stencil,
+            "roofline_stencil_bf16_hbm": roof_hbm,
             "cpu_baseline": cpu,
             "fp64_path": {"value": value64, "unit": UNIT, "steps": nf, "ms_per_step": sum(ms64) / nf,
                           "iterations_per_rhs": iters64 / (nf * rhs_per_step),

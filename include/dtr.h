@@ -81,6 +81,16 @@ const char *dtr_last_error(void);
 /* Library version string. */
 const char *dtr_version(void);
 
+/* Launch accounting of the persistent solver kernel (roofline figures).
+ * Writes the totals accumulated since the last reset -- summed CUDA-event
+ * duration of the persistent launches (ms, events recorded on the launching
+ * stream), number of launches, and the sum over launches of (iterations
+ * executed x lattice sites x block width) -- to the non-NULL outputs (host),
+ * then, if enable >= 0, resets the totals and switches accounting on
+ * (enable = 1) or off (0).  enable = -1 only reads.  Accounting adds two
+ * event records per launch. */
+int dtr_profile_persistent(int enable, double *ms, int64_t *launches, double *site_rhs_iterations);
+
 /* Number of CUDA kernels the library has launched in this process (all
  * threads, all devices), for launch accounting by callers. */
 uint64_t dtr_kernel_launches(void);
@@ -117,8 +127,12 @@ void dtr_destroy_gauge(dtr_gauge g);
 /* out = A in (dagger = 0) or out = A^H in (dagger = 1), for nrhs fields.
  * Operator definition above (the matrix of Algorithm 1; A^H is the product
  * of Algorithm 1, lines 2 and 8).  in, out: device, canonical N x nrhs
- * complex128, must not overlap.  prec selects the arithmetic: DTR_F64, or
- * DTR_F32 (fields rounded to FP32, FP32 math, result widened to FP64).
+ * complex128, must not overlap.  prec selects the arithmetic: DTR_F64;
+ * DTR_F32 (fields rounded to FP32, FP32 math, result widened to FP64);
+ * DTR_BF16 / DTR_F16 (half-precision storage of the fields and of the links,
+ * which are kept as their first two rows -- the third row of an SU(3) matrix
+ * is the conjugated cross product of the first two -- FP32 math; dagger = 0
+ * only).
  * work: device workspace of dtr_dslash_workspace_bytes(lat, nrhs) bytes. */
 size_t dtr_dslash_workspace_bytes(dtr_lattice lat, int nrhs);
 int dtr_dslash(dtr_gauge g, double m0, const double *in, double *out, int nrhs, int dagger,

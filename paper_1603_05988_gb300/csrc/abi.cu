@@ -96,6 +96,20 @@ int dtr_selftest_barrier(int64_t budget_cycles, int *timed_out, int *error_word,
   return selftest_barrier((long long)budget_cycles, timed_out, error_word, (cudaStream_t)stream);
 }
 
+int dtr_profile_persistent(int enable, double *ms, int64_t *launches, double *site_rhs_iterations) {
+  PersistProfile &p = persist_profile();
+  if (ms) *ms = p.ms;
+  if (launches) *launches = p.launches;
+  if (site_rhs_iterations) *site_rhs_iterations = p.site_rhs_iters;
+  if (enable >= 0) {
+    p.on = enable != 0;
+    p.ms = 0.0;
+    p.launches = 0;
+    p.site_rhs_iters = 0.0;
+  }
+  return DTR_OK;
+}
+
 uint64_t dtr_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
 int dtr_make_lattice(const int dims[4], dtr_lattice *out) {
@@ -133,18 +147,26 @@ int dtr_make_gauge(dtr_lattice lat, const double *links_host, dtr_gauge *out) {
   g->lat = *lat;
   g->U64 = nullptr;
   g->U32 = nullptr;
+  g->Ubf16 = nullptr;
+  g->Uf16 = nullptr;
   const int64_t n = lat->V * 4 * 9;
   cudaError_t e = cudaMalloc((void **)&g->U64, n * sizeof(double2));
   if (e == cudaSuccess) e = cudaMalloc((void **)&g->U32, n * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&g->Ubf16, half_links_bytes(lat->V));
+  if (e == cudaSuccess) e = cudaMalloc(&g->Uf16, half_links_bytes(lat->V));
   if (e == cudaSuccess) e = cudaMemcpy(g->U64, links_host, n * sizeof(double2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
     k_to_f32<<<grid1d(n), 256>>>(g->U64, g->U32, n); count_launches(1);
+    launch_pack_links_half(g->U64, g->Ubf16, lat->V, 1, 0);
+    launch_pack_links_half(g->U64, g->Uf16, lat->V, 0, 0);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     cudaFree(g->U64);
     cudaFree(g->U32);
+    cudaFree(g->Ubf16);
+    cudaFree(g->Uf16);
     delete g;
     return cuda_fail(e, "gauge upload");
   }
@@ -162,6 +184,8 @@ void dtr_destroy_gauge(dtr_gauge g) {
   if (!g) return;
   cudaFree(g->U64);
   cudaFree(g->U32);
+  cudaFree(g->Ubf16);
+  cudaFree(g->Uf16);
   delete g;
 }
 
@@ -175,14 +199,23 @@ int dtr_dslash(dtr_gauge g, double m0, const double *in, double *out, int nrhs, 
                void *work, size_t work_bytes, void *stream) {
   if (!g || !in || !out || !work) return fail(DTR_EINVAL, "null argument");
   if (nrhs < 1 || nrhs > 64) return fail(DTR_EINVAL, "nrhs must be in [1, 64]");
-  if (prec != DTR_F64 && prec != DTR_F32) return fail(DTR_EINVAL, "dslash precision must be DTR_F64 or DTR_F32");
+  if (prec != DTR_F64 && prec != DTR_F32 && prec != DTR_BF16 && prec != DTR_F16)
+    return fail(DTR_EINVAL, "unknown dslash precision");
+  if ((prec == DTR_BF16 || prec == DTR_F16) && dagger)
+    return fail(DTR_EINVAL, "half-precision storage dslash supports dagger = 0 only");
+  if ((prec == DTR_BF16 || prec == DTR_F16) && g->lat.V * nrhs * 3 >= (1LL << 31))
+    return fail(DTR_EINVAL, "half-precision storage dslash: V * nrhs too large");
   if (work_bytes < dtr_dslash_workspace_bytes(&g->lat, nrhs)) return fail(DTR_ENOMEM, "dslash workspace too small");
   cudaStream_t st = (cudaStream_t)stream;
   const int b = pad_rhs(nrhs);
   const Geom geo = geom_of(g->lat);
   const size_t vb = ((size_t)g->lat.V * 12 * b * sizeof(double2) + 255) / 256 * 256;
   char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
-  if (prec == DTR_F64) {
+  if (prec == DTR_BF16 || prec == DTR_F16) {
+    const int bf = prec == DTR_BF16;
+    launch_dslash_half_canon(bf ? g->Ubf16 : g->Uf16, (const double2 *)in, (double2 *)out, w, geo, nrhs, nrhs, m0,
+                             bf, st);
+  } else if (prec == DTR_F64) {
     double2 *a = (double2 *)w, *o = (double2 *)(w + vb);
     launch_pack<double>((const double2 *)in, a, g->lat.V, nrhs, b, st);
     launch_dslash<double>(g->U64, a, o, geo, b, m0, dagger, st);
@@ -201,7 +234,8 @@ int dtr_time_dslash(dtr_gauge g, double m0, int nrhs, dtr_prec prec, int reps, v
                     double *avg_ms, void *stream) {
   if (!g || !work || !avg_ms) return fail(DTR_EINVAL, "null argument");
   if (nrhs < 1 || nrhs > 64 || reps < 1) return fail(DTR_EINVAL, "nrhs must be in [1, 64] and reps >= 1");
-  if (prec != DTR_F64 && prec != DTR_F32) return fail(DTR_EINVAL, "dslash precision must be DTR_F64 or DTR_F32");
+  if (prec != DTR_F64 && prec != DTR_F32 && prec != DTR_BF16 && prec != DTR_F16)
+    return fail(DTR_EINVAL, "unknown dslash precision");
   if (work_bytes < dtr_dslash_workspace_bytes(&g->lat, nrhs)) return fail(DTR_ENOMEM, "dslash workspace too small");
   cudaStream_t st = (cudaStream_t)stream;
   const int b = pad_rhs(nrhs);
@@ -209,6 +243,24 @@ int dtr_time_dslash(dtr_gauge g, double m0, int nrhs, dtr_prec prec, int reps, v
   const size_t vb = ((size_t)g->lat.V * 12 * b * sizeof(double2) + 255) / 256 * 256;
   char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
   DTR_CUDA(cudaMemsetAsync(w, 0, 2 * vb, st));
+  if (prec == DTR_BF16 || prec == DTR_F16) {  // half fields use b = nrhs exactly (no padding)
+    const int bf = prec == DTR_BF16;
+    cudaEvent_t h0, h1;
+    DTR_CUDA(cudaEventCreate(&h0));
+    DTR_CUDA(cudaEventCreate(&h1));
+    launch_dslash_half_raw(bf ? g->Ubf16 : g->Uf16, w, geo, nrhs, m0, bf, 1, st);  // warm
+    DTR_CUDA(cudaEventRecord(h0, st));
+    launch_dslash_half_raw(bf ? g->Ubf16 : g->Uf16, w, geo, nrhs, m0, bf, reps, st);
+    DTR_CUDA(cudaEventRecord(h1, st));
+    DTR_CUDA(cudaEventSynchronize(h1));
+    float hms = 0.f;
+    DTR_CUDA(cudaEventElapsedTime(&hms, h0, h1));
+    cudaEventDestroy(h0);
+    cudaEventDestroy(h1);
+    DTR_LAUNCH_CHECK("half dslash timing");
+    *avg_ms = (double)hms / reps;
+    return DTR_OK;
+  }
   cudaEvent_t e0, e1;
   DTR_CUDA(cudaEventCreate(&e0));
   DTR_CUDA(cudaEventCreate(&e1));

@@ -128,6 +128,8 @@ struct dtr_gauge_s {
   dtr_lattice_s lat;
   double2 *U64;   // [site][mu][3][3], FP64
   float2 *U32;    // same layout, FP32
+  void *Ubf16;    // [site][mu][8] BF16 complex: two stored rows + 2 padding slots
+  void *Uf16;     // same, FP16
 };
 
 struct dtr_defl_s {
@@ -175,6 +177,15 @@ void launch_unpack(const typename cplx_t<R>::type *internal, double2 *canon, int
 template <typename R>
 void launch_dslash(const typename cplx_t<R>::type *U, const typename cplx_t<R>::type *in,
                    typename cplx_t<R>::type *out, const Geom &g, int b, double m0, int dagger, cudaStream_t st);
+
+// half-precision-storage stencil (dslash_half.cu)
+size_t half_links_bytes(int64_t V);
+size_t half_field_bytes(int64_t V, int b);
+void launch_pack_links_half(const double2 *U64, void *out, int64_t V, int bf16, cudaStream_t st);
+void launch_dslash_half_canon(const void *Uh, const double2 *in, double2 *out, void *work, const Geom &g, int nrhs,
+                              int b, double m0, int bf16, cudaStream_t st);
+void launch_dslash_half_raw(const void *Uh, void *work, const Geom &g, int b, double m0, int bf16, int reps,
+                            cudaStream_t st);
 
 // noise into internal FP64 layout of width b: block column k is global column
 // g0 + k of the run-major sequence (ncols probing columns per run, runs from

@@ -20,6 +20,9 @@
 // in co-residency can never hang the GPU; the host turns the error word into
 // DTR_ETIMEOUT.  Launch is cooperative (cudaLaunchCooperativeKernel refuses a
 // grid that cannot be co-resident).
+#include <mutex>
+#include <vector>
+
 #include "dslash_core.cuh"
 #include "krylov_fin.cuh"
 #include "persist.cuh"
@@ -193,6 +196,7 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
   const int64_t t0 = (int64_t)blockIdx.x * T + threadIdx.x;
   Scal *sc = a.sc;
   const int cycles = WITH_RESID ? a.max_cycles : 1;
+  int done = 0;
 
   for (int cycle = 0; cycle < cycles; ++cycle) {
     if (WITH_RESID) {  // r = z - A x ; rhat = p = r ; (||r||^2, ||z||^2) -> restart decision
@@ -224,6 +228,8 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
       if (__ldcg(&sc->n_active) == 0) break;
     }
     for (int iter = 0; iter < a.max_iters; ++iter) {
+      ++done;
+      if (blockIdx.x == 0 && threadIdx.x == 0) a.gs->iters = done;
       {  // P1: v = A p ; rhat^H v -> alpha   (per-thread sums in R, block/grid sums in FP64)
         R ax = 0, ay = 0;
         for (int64_t it = t0; it < nsite; it += stride) {
@@ -308,6 +314,36 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
   }
 }
 
+// ----------------------------------------------------------- launch profile
+struct PendingLaunch {
+  cudaEvent_t e0, e1;
+  GridSync *gs;
+  double site_rhs;
+};
+static PersistProfile g_prof = {false, 0.0, 0, 0.0};
+static std::vector<PendingLaunch> g_pending;
+static std::mutex g_prof_mu;
+
+PersistProfile &persist_profile() { return g_prof; }
+
+void persist_profile_flush(cudaStream_t st) {
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  for (auto &pl : g_pending) {
+    float ms = 0.f;
+    GridSync h;
+    if (cudaEventElapsedTime(&ms, pl.e0, pl.e1) == cudaSuccess &&
+        cudaMemcpy(&h, pl.gs, sizeof(GridSync), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      g_prof.ms += ms;
+      g_prof.launches += 1;
+      g_prof.site_rhs_iters += (double)h.iters * pl.site_rhs;
+    }
+    cudaEventDestroy(pl.e0);
+    cudaEventDestroy(pl.e1);
+  }
+  g_pending.clear();
+  (void)st;
+}
+
 template <typename R, int T, int W> static int launch_one(const PArgs<R> &pa, cudaStream_t st) {
   static int max_grid = 0;
   if (!max_grid) {
@@ -321,9 +357,23 @@ template <typename R, int T, int W> static int launch_one(const PArgs<R> &pa, cu
   const int grid = (pa.grid > 0 && pa.grid < max_grid) ? pa.grid : max_grid;
   PArgs<R> copy = pa;
   void *args[] = {&copy};
+  PendingLaunch pl;
+  const bool prof = g_prof.on;
+  if (prof) {
+    DTR_CUDA(cudaEventCreate(&pl.e0));
+    DTR_CUDA(cudaEventCreate(&pl.e1));
+    DTR_CUDA(cudaEventRecord(pl.e0, st));
+  }
   DTR_CUDA(cudaLaunchCooperativeKernel((const void *)k_bicgstab_persistent<R, T, W>, dim3(grid), dim3(T), args, 0,
                                        st));
   count_launches(1);
+  if (prof) {
+    DTR_CUDA(cudaEventRecord(pl.e1, st));
+    pl.gs = pa.gs;
+    pl.site_rhs = (double)pa.g.V * pa.b;
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    g_pending.push_back(pl);
+  }
   return DTR_OK;
 }
 

@@ -10,7 +10,7 @@ struct GridSync {
   unsigned int count;
   unsigned int gen;
   int error;
-  int pad;
+  int iters;  // BiCGStab iterations the launch executed (written by block 0 at exit)
 };
 
 template <typename R> struct PArgs {
@@ -32,6 +32,17 @@ template <typename R> struct PArgs {
 // iterations) until every column meets tol in the true residual (FP64 path);
 // with_resid = 0: iterations only, from the caller-initialised state.
 template <typename R> int launch_persistent(const PArgs<R> &pa, int with_resid, cudaStream_t st);
+
+// Optional event timing of persistent launches (for roofline accounting).
+struct PersistProfile {
+  bool on;
+  double ms;
+  long long launches;
+  double site_rhs_iters;  // sum over launches of iterations * V * b
+};
+PersistProfile &persist_profile();
+// Called after the stream has been synchronised: folds the recorded launches in.
+void persist_profile_flush(cudaStream_t st);
 
 // Launch one block at a barrier that expects two (the peer never arrives);
 // reports whether the bounded wait gave up and the barrier's error word.

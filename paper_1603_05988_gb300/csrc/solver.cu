@@ -376,6 +376,7 @@ static int read_gs_error(const GridSync *gs, cudaStream_t st) {
   if (!h) return fail(DTR_ECUDA, "cudaMallocHost for the convergence flag failed");
   DTR_CUDA(cudaMemcpyAsync(h + 1, &gs->error, sizeof(int), cudaMemcpyDeviceToHost, st));
   DTR_CUDA(cudaStreamSynchronize(st));
+  if (persist_profile().on) persist_profile_flush(st);
   if (h[1]) return fail(DTR_ETIMEOUT, "persistent solver barrier timed out");
   return DTR_OK;
 }
@@ -469,6 +470,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
       int n_active = 0;
       int rc = read_n_active(outer, st, &n_active);
       if (rc) return rc;
+      if (persistent && persist_profile().on) persist_profile_flush(st);
       if (n_active == 0) break;
       k_mixed_init<<<gv, kBlock, 0, st>>>(r64, K.r, K.rhat, K.p, K.x, n, b, outer); count_launches(1);
       k_mixed_scal_init<<<1, 64, 0, st>>>(outer, inner, b, itol * itol, p->maxiter); count_launches(1);

@@ -74,6 +74,8 @@ def _sig(name, res, args):
 _sig("dtr_last_error", ctypes.c_char_p, [])
 _sig("dtr_version", ctypes.c_char_p, [])
 _sig("dtr_kernel_launches", ctypes.c_uint64, [])
+_sig("dtr_profile_persistent", _i, [_i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64),
+                                    ctypes.POINTER(ctypes.c_double)])
 _sig("dtr_time_dslash", _i, [_vp, _d, _i, _i, _i, _vp, _sz, ctypes.POINTER(ctypes.c_double), _vp])
 _sig("dtr_selftest_barrier", _i, [_i64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _vp])
 _sig("dtr_make_lattice", _i, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_vp)])
@@ -220,6 +222,16 @@ def selftest_barrier(budget_cycles=2_000_000):
     e = ctypes.c_int()
     _check(_lib.dtr_selftest_barrier(int(budget_cycles), ctypes.byref(t), ctypes.byref(e), _stream()))
     return t.value, e.value
+
+
+def profile_persistent(enable=-1):
+    """Read (and with enable 0/1 reset and switch) persistent-kernel accounting:
+    returns dict(ms, launches, site_rhs_iterations)."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    w = ctypes.c_double()
+    _check(_lib.dtr_profile_persistent(int(enable), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
+    return {"ms": ms.value, "launches": n.value, "site_rhs_iterations": w.value}
 
 
 def kernel_launches():

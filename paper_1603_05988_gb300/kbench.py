@@ -1,0 +1,84 @@
+"""Kernel micro-benchmarks of libdtr (CUDA-event timing through the C ABI).
+
+    python -m paper_1603_05988_gb300.kbench dslash --lattice 32,32,32,64 --prec bf16 --nrhs 1 --reps 20
+
+Large lattices take their links from the seeded 16^3x32 field repeated
+periodically (exact SU(3) matrices; the stencil's cost does not depend on
+their values), so set-up does not spend a minute drawing 8 M random links.
+Prints one JSON line per measurement: average launch time, algorithmic bytes
+and flops per launch, achieved GB/s and TFLOP/s.
+"""
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# bytes per site and right-hand side (in + out) and per site for the links, by storage
+SPINOR_BYTES = {"f64": 2 * 192, "f32": 2 * 96, "bf16": 2 * 48, "f16": 2 * 48}
+LINK_BYTES = {"f64": 576, "f32": 288, "bf16": 96, "f16": 96}   # half storage keeps two rows per link
+FLOPS_PER_SITE = 1368.0   # 1320 hopping (8 directions x (12 + 2 x 66 + 24) - 24) + 48 diagonal
+
+
+def tiled_links(dims, eps=0.8, seed=1002, base=(16, 16, 16, 32)):
+    """Seeded links on min(dims, base), repeated periodically to fill dims."""
+    from . import synth
+    b = tuple(min(d, bb) for d, bb in zip(dims, base))
+    if any(d % s for d, s in zip(dims, b)):
+        raise ValueError("lattice extents must be multiples of the tile %r" % (b,))
+    small = synth.random_su3_links(b, eps, seed)
+    if b == tuple(dims):
+        return small
+    s7 = small.reshape(b[3], b[2], b[1], b[0], 4, 3, 3)          # (t, z, y, x, mu, a, b)
+    reps = (dims[3] // b[3], dims[2] // b[2], dims[1] // b[1], dims[0] // b[0], 1, 1, 1)
+    return np.ascontiguousarray(np.tile(s7, reps).reshape(-1, 4, 3, 3))
+
+
+def dslash_case(gauge, dims, prec, nrhs, reps, m0=-0.75):
+    from . import dtr
+    ms = dtr.time_dslash(gauge, m0, nrhs, prec=prec, reps=reps)
+    V = int(np.prod(dims))
+    b = nrhs if prec in ("bf16", "f16") else dtr_pad(nrhs)
+    alg_bytes = V * nrhs * SPINOR_BYTES[prec] + V * LINK_BYTES[prec]
+    flops = V * nrhs * FLOPS_PER_SITE
+    return {"kernel": "dslash", "lattice": list(dims), "prec": prec, "nrhs": nrhs, "padded_width": b,
+            "avg_launch_ms": ms, "alg_bytes_per_launch": alg_bytes, "flops_per_launch": flops,
+            "achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9, "achieved_tflops": flops / (ms * 1e-3) / 1e12}
+
+
+def dtr_pad(n):
+    b = 1
+    while b < n:
+        b <<= 1
+    return b
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["dslash"])
+    ap.add_argument("--lattice", default="32,32,32,64")
+    ap.add_argument("--prec", default="bf16")
+    ap.add_argument("--nrhs", default="1")
+    ap.add_argument("--reps", type=int, default=20)
+    a = ap.parse_args(argv)
+    import torch
+    torch.cuda.set_device(0)
+    from . import build as _b
+    if not os.path.exists(_b.LIB):
+        _b.build()
+    from . import dtr
+    dims = tuple(int(x) for x in a.lattice.split(","))
+    lat = dtr.make_lattice(dims)
+    g = dtr.make_gauge(lat, tiled_links(dims))
+    for prec in a.prec.split(","):
+        for n in a.nrhs.split(","):
+            print(json.dumps(dslash_case(g, dims, prec, int(n), a.reps)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -84,6 +84,23 @@ def test_dslash_fp32(dtr):
     assert np.abs(out - ref).max() <= 2e-6 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("prec,tol", [("bf16", 3e-2), ("f16", 4e-3)])
+@pytest.mark.parametrize("dims,nrhs", [((4, 4, 4, 4), 1), ((4, 4, 4, 8), 3), ((8, 4, 4, 8), 8)])
+def test_dslash_half_storage(dtr, prec, tol, dims, nrhs):
+    """BF16/FP16 storage of fields and two-row links, FP32 math: max-norm error
+    relative to the largest output entry within the storage precision."""
+    import torch
+    U, lat, g = _setup(dtr, dims, 0.8, -0.75, 13)
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((nrhs, lat.N)) + 1j * rng.standard_normal((nrhs, lat.N))
+    out = _cpu(dtr.dslash(g, -0.75, torch.from_numpy(X).cuda(), prec=prec))
+    ref = (wilson.explicit(U, dims, -0.75) @ X.T).T
+    err = np.abs(out - ref).max() / np.abs(ref).max()
+    assert err <= tol, err
+    with pytest.raises(dtr.DtrError):
+        dtr.dslash(g, -0.75, torch.from_numpy(X).cuda(), prec=prec, dagger=True)
+
+
 def test_gauge_roundtrip(dtr):
     U, lat, g = _setup(dtr, (4, 4, 2, 2), 0.5, -0.4, 3)
     assert np.array_equal(g.to_host(), U)
