@@ -65,6 +65,7 @@ extern "C" {
 typedef struct dtr_lattice_s *dtr_lattice;
 typedef struct dtr_gauge_s *dtr_gauge;
 typedef struct dtr_defl_s *dtr_defl;
+typedef struct dtr_net_s *dtr_net;
 
 /* Storage precision of a field or of the deflation space. */
 typedef enum { DTR_F64 = 0, DTR_F32 = 1, DTR_BF16 = 2, DTR_F16 = 3 } dtr_prec;
@@ -72,7 +73,10 @@ typedef enum { DTR_F64 = 0, DTR_F32 = 1, DTR_BF16 = 2, DTR_F16 = 3 } dtr_prec;
 /* Krylov solver for A y = z (Algorithm 1, line 7; the paper does not name one). */
 typedef enum {
   DTR_SOLVER_BICGSTAB_F64 = 0,   /* plain FP64 BiCGStab */
-  DTR_SOLVER_MIXED_F32 = 1       /* FP32 BiCGStab inner solves inside FP64 defect correction */
+  DTR_SOLVER_MIXED_F32 = 1,      /* FP32 BiCGStab inner solves inside FP64 defect correction */
+  DTR_SOLVER_FGMRES_NET = 2      /* FP32 flexible GMRES(m) inner solves, right-preconditioned by a
+                                    dtr_net, inside FP64 defect correction; falls back to the BiCGStab
+                                    inner solve if a cycle cuts the true residual less than 10x */
 } dtr_solver;
 
 /* Message of the last failure on this thread ("" if none).  Never NULL. */
@@ -178,6 +182,9 @@ typedef struct {
                           1: one kernel per BiCGStab step, host polls every check_every iterations */
   int grid;            /* persistent engine: CTAs to launch (0 = every SM; clamped to what can be
                           co-resident) */
+  dtr_net net;         /* DTR_SOLVER_FGMRES_NET: preconditioner (NULL = unpreconditioned FGMRES) */
+  int gmres_m;         /* DTR_SOLVER_FGMRES_NET: restart length, 1..32 */
+  int pad_;
 } dtr_solve_params;
 
 typedef struct {
@@ -250,6 +257,44 @@ int dtr_deflate_project(dtr_defl d, const double *z, int nrhs, double *d_out, do
 #define DTR_STATIC_MAX_RHS 16
 int dtr_deflate_project_static(dtr_defl d, const double *z, int nrhs, double *d_out, double *coeff_out,
                                void *stream);
+
+/* --------------------------------------------------- learned preconditioner */
+/* A 4-layer 4D convolutional network M ~ A^-1 (the learned preconditioner of
+ * the FGMRES solver; no counterpart in the paper, which does not name its
+ * solver).  A field's 12 complex dofs per site are 24 real channels
+ * (channel 2c+p = real (p=0) / imaginary (p=1) part of dof c).  Layer l is a
+ * periodic 3^4 stencil W_l[o][co][ci], o = ((dt*3+dz)*3+dy)*3+dx for the
+ * displacement (dx-1, dy-1, dz-1, dt-1), no bias:
+ *   y = W_3 * phi(W_2 * phi(W_1 * phi(W_0 * x)))
+ * phi = identity (act = 0) or leaky ReLU with slope 1/4 (act = 1).  Weights
+ * are used in BF16 (FP32 master copy and Adam moments on the device);
+ * arithmetic accumulates in FP32.  Weight arrays (host) are 4*81*24*24 FP32
+ * in [l][o][co][ci] order. */
+#define DTR_NET_LAYERS 4
+#define DTR_NET_WEIGHTS (4 * 81 * 24 * 24)
+/* weights_host NULL: identity at the centre offset (first layer times
+ * init_scale) plus N(0, noise^2) from `seed`. */
+int dtr_net_create(dtr_lattice lat, int act, const float *weights_host, double init_scale, double noise,
+                   uint64_t seed, dtr_net *out);
+void dtr_destroy_net(dtr_net net);
+/* Copy the weights to host: master FP32 (bf16_rounded = 0) or the BF16 values
+ * the kernels use (1). */
+int dtr_net_get_weights(dtr_net net, int bf16_rounded, float *weights_host);
+size_t dtr_net_workspace_bytes(dtr_net net, int nrhs);
+/* out = M in for nrhs fields (device, canonical N x nrhs complex128). */
+int dtr_net_apply(dtr_net net, const double *in, double *out, int nrhs, void *work, size_t work_bytes,
+                  void *stream);
+/* One training step on (residual, error) pairs (in_j, target_j) with
+ * A target_j = in_j (device, canonical).  Loss (host *loss):
+ *   g == NULL:  L = sum_j |M in_j - target_j|^2 / |target_j|^2
+ *   g != NULL:  L = sum_j |A M in_j - in_j|^2 / |in_j|^2  (A from g and m0;
+ *               the residual norm of A M, which governs right preconditioning)
+ * gradient dL/dW with respect to the BF16 weights (copied to grad_host if
+ * non-NULL), and, if do_step, one Adam step (lr, beta1 0.9, beta2 0.999,
+ * eps 1e-8). */
+int dtr_net_train_step(dtr_net net, dtr_gauge g, double m0, const double *in, const double *target, int nrhs,
+                       double lr, int do_step, double *loss, float *grad_host, void *work, size_t work_bytes,
+                       void *stream);
 
 /* ---------------------------------------------------------------- estimator */
 typedef struct {

@@ -11,6 +11,7 @@
 
 #include "deflate.cuh"
 #include "dtr_internal.cuh"
+#include "net.cuh"
 #include "persist.cuh"
 #include "solver.cuh"
 
@@ -303,13 +304,18 @@ void dtr_solve_params_default(dtr_solve_params *p) {
   p->inner_tol = 1e-5;
   p->engine = 0;
   p->grid = 0;
+  p->net = nullptr;
+  p->gmres_m = 16;
+  p->pad_ = 0;
 }
 
 static int check_solve_params(const dtr_solve_params *p) {
   if (!p) return fail(DTR_EINVAL, "null solve params");
   if (!(p->tol > 0.0) || p->maxiter < 1) return fail(DTR_EINVAL, "tol must be > 0 and maxiter >= 1");
-  if (p->solver != DTR_SOLVER_BICGSTAB_F64 && p->solver != DTR_SOLVER_MIXED_F32)
+  if (p->solver != DTR_SOLVER_BICGSTAB_F64 && p->solver != DTR_SOLVER_MIXED_F32 && p->solver != DTR_SOLVER_FGMRES_NET)
     return fail(DTR_EINVAL, "unknown solver");
+  if (p->solver == DTR_SOLVER_FGMRES_NET && (p->gmres_m < 1 || p->gmres_m > 32))
+    return fail(DTR_EINVAL, "gmres_m must be in [1, 32]");
   if (p->engine != 0 && p->engine != 1) return fail(DTR_EINVAL, "engine must be 0 (persistent) or 1 (per-step)");
   if (p->grid < 0) return fail(DTR_EINVAL, "grid must be >= 0");
   return DTR_OK;
@@ -319,7 +325,7 @@ size_t dtr_solve_workspace_bytes(dtr_lattice lat, int nrhs, const dtr_solve_para
   if (!lat || !p || nrhs < 1 || nrhs > 64) return 0;
   const int b = pad_rhs(nrhs);
   const size_t vb = ((size_t)lat->V * 12 * b * sizeof(double2) + 255) / 256 * 256;
-  return 256 + 2 * vb + solver_scratch_bytes(lat->V, b, p->solver);
+  return 256 + 2 * vb + solver_scratch_bytes(lat->V, b, p->solver, p->gmres_m);
 }
 
 int dtr_solve_batch(dtr_gauge g, double m0, const double *z, double *y, int nrhs, const dtr_solve_params *p,
@@ -478,6 +484,115 @@ int dtr_deflate_project(dtr_defl d, const double *z, int nrhs, double *d_out, do
   if (x0_out) launch_unpack<double>(X0, (double2 *)x0_out, d->lat.V, nrhs, b, st);
   DTR_LAUNCH_CHECK("deflate project");
   return DTR_OK;
+}
+
+// ------------------------------------------------------------ network
+int dtr_net_create(dtr_lattice lat, int act, const float *weights_host, double init_scale, double noise,
+                   uint64_t seed, dtr_net *out) {
+  if (!lat || !out) return fail(DTR_EINVAL, "null argument");
+  if (act != 0 && act != 1) return fail(DTR_EINVAL, "act must be 0 (identity) or 1 (leaky ReLU)");
+  const int L = DTR_NET_LAYERS;
+  const size_t per = 81 * 24 * 24, nw = L * per;
+  std::vector<float> w(nw, 0.f);
+  if (weights_host) {
+    std::memcpy(w.data(), weights_host, nw * sizeof(float));
+  } else {
+    uint64_t st = seed * 6364136223846793005ull + 1442695040888963407ull;
+    auto unif = [&]() {  // 64-bit LCG (Knuth MMIX constants), top 53 bits
+      st = st * 6364136223846793005ull + 1442695040888963407ull;
+      return ((st >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
+    for (size_t i = 0; i < nw; i += 2) {  // Box-Muller
+      const double u1 = unif(), u2 = unif();
+      const double r = std::sqrt(-2.0 * std::log(u1));
+      w[i] = (float)(noise * r * std::cos(6.283185307179586 * u2));
+      if (i + 1 < nw) w[i + 1] = (float)(noise * r * std::sin(6.283185307179586 * u2));
+    }
+    for (int l = 0; l < L; ++l)
+      for (int c = 0; c < 24; ++c) w[l * per + 40 * 576 + c * 24 + c] += (float)(l == 0 ? init_scale : 1.0);
+  }
+  dtr_net_s *n = new (std::nothrow) dtr_net_s;
+  if (!n) return fail(DTR_ENOMEM, "host allocation failed");
+  n->lat = *lat;
+  n->L = L;
+  n->act = act;
+  n->step = 0;
+  n->w = n->m = n->v = n->grad = n->wf = n->wb = nullptr;
+  float **bufs[6] = {&n->w, &n->m, &n->v, &n->grad, &n->wf, &n->wb};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaMalloc((void **)bufs[i], nw * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(n->w, w.data(), nw * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(n->m, 0, nw * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(n->v, 0, nw * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(n->grad, 0, nw * sizeof(float));
+  if (e == cudaSuccess) {
+    net_refresh(n, 0);
+    e = cudaDeviceSynchronize();
+  }
+  if (e != cudaSuccess) {
+    for (int i = 0; i < 6; ++i) cudaFree(*bufs[i]);
+    delete n;
+    return cuda_fail(e, "network create");
+  }
+  *out = n;
+  return DTR_OK;
+}
+
+void dtr_destroy_net(dtr_net n) {
+  if (!n) return;
+  cudaFree(n->w);
+  cudaFree(n->m);
+  cudaFree(n->v);
+  cudaFree(n->grad);
+  cudaFree(n->wf);
+  cudaFree(n->wb);
+  delete n;
+}
+
+int dtr_net_get_weights(dtr_net n, int bf16_rounded, float *host) {
+  if (!n || !host) return fail(DTR_EINVAL, "null argument");
+  DTR_CUDA(cudaMemcpy(host, bf16_rounded ? n->wb : n->w, sizeof(float) * DTR_NET_WEIGHTS, cudaMemcpyDeviceToHost));
+  return DTR_OK;
+}
+
+size_t dtr_net_workspace_bytes(dtr_net n, int nrhs) {
+  if (!n || nrhs < 1 || nrhs > 64) return 0;
+  const int b = pad_rhs(nrhs);
+  const size_t vec = ((size_t)n->lat.V * 12 * b * sizeof(float2) + 255) / 256 * 256;
+  return 256 + 2 * vec + net_workspace_bytes(n, b);
+}
+
+int dtr_net_apply(dtr_net n, const double *in, double *out, int nrhs, void *work, size_t work_bytes, void *stream) {
+  if (!n || !in || !out || !work) return fail(DTR_EINVAL, "null argument");
+  if (nrhs < 1 || nrhs > 64) return fail(DTR_EINVAL, "nrhs must be in [1, 64]");
+  if (work_bytes < dtr_net_workspace_bytes(n, nrhs)) return fail(DTR_ENOMEM, "network workspace too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int b = pad_rhs(nrhs);
+  const size_t vec = ((size_t)n->lat.V * 12 * b * sizeof(float2) + 255) / 256 * 256;
+  char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+  float2 *x = (float2 *)w, *y = (float2 *)(w + vec), *t0 = (float2 *)(w + 2 * vec), *t1 = (float2 *)(w + 3 * vec);
+  launch_pack<float>((const double2 *)in, x, n->lat.V, nrhs, b, st);
+  net_apply(n, x, y, b, t0, t1, st);
+  launch_unpack<float>(y, (double2 *)out, n->lat.V, nrhs, b, st);
+  DTR_LAUNCH_CHECK("network apply");
+  return DTR_OK;
+}
+
+int dtr_net_train_step(dtr_net n, dtr_gauge g, double m0, const double *in, const double *target, int nrhs, double lr,
+                       int do_step, double *loss, float *grad_host, void *work, size_t work_bytes, void *stream) {
+  if (!n || !in || !target || !loss || !work) return fail(DTR_EINVAL, "null argument");
+  if (nrhs < 1 || nrhs > 64) return fail(DTR_EINVAL, "nrhs must be in [1, 64]");
+  if (work_bytes < dtr_net_workspace_bytes(n, nrhs)) return fail(DTR_ENOMEM, "network workspace too small");
+  if (g && g->lat.V != n->lat.V) return fail(DTR_EINVAL, "gauge field on another lattice");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int b = pad_rhs(nrhs);
+  const size_t vec = ((size_t)n->lat.V * 12 * b * sizeof(float2) + 255) / 256 * 256;
+  char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+  float2 *x = (float2 *)w, *e = (float2 *)(w + vec);
+  launch_pack<float>((const double2 *)in, x, n->lat.V, nrhs, b, st);
+  launch_pack<float>((const double2 *)target, e, n->lat.V, nrhs, b, st);
+  DTR_LAUNCH_CHECK("pack training pair");
+  return net_train(n, g, m0, x, e, b, nrhs, lr, do_step, grad_host, loss, w + 2 * vec, work_bytes - 2 * vec - 256, st);
 }
 
 static int check_trace_params(const dtr_gauge_s *g, const dtr_defl_s *D, const dtr_trace_params *p) {

@@ -16,6 +16,7 @@
 #include "reduce.cuh"
 #include "solver.cuh"
 #include "krylov_fin.cuh"
+#include "net.cuh"
 #include "persist.cuh"
 
 namespace dtr {
@@ -359,13 +360,14 @@ static int iterate(const typename cplx_t<R>::type *U, KrylovVecs<R> &K, const Ge
   return DTR_OK;
 }
 
-size_t solver_scratch_bytes(int64_t V, int b, int solver) {
+size_t solver_scratch_bytes(int64_t V, int b, int solver, int gmres_m) {
   const size_t vec64 = ((size_t)V * 12 * b * sizeof(double2) + 255) / 256 * 256;
   const size_t vec32 = ((size_t)V * 12 * b * sizeof(float2) + 255) / 256 * 256;
   const size_t red = 256 + (size_t)kMaxGrid * 5 * 64 * sizeof(double2);
   const size_t scal = 2 * ((sizeof(Scal) + 255) / 256) * 256;
   const size_t fixed = 256 + red + scal + 256 + 256;
   if (solver == DTR_SOLVER_MIXED_F32) return fixed + vec64 + 7 * vec32;
+  if (solver == DTR_SOLVER_FGMRES_NET) return fixed + vec64 + 7 * vec32 + fgmres_scratch_bytes(V, b, gmres_m) + 256;
   return fixed + 6 * vec64;
 }
 
@@ -387,7 +389,8 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
                    int x_is_zero) {
   const Geom g = geom_of(gauge->lat);
   const int64_t n = (int64_t)g.V * 12 * b;
-  if (work_bytes < solver_scratch_bytes(g.V, b, p->solver)) return fail(DTR_ENOMEM, "solver workspace too small");
+  if (work_bytes < solver_scratch_bytes(g.V, b, p->solver, p->gmres_m))
+    return fail(DTR_ENOMEM, "solver workspace too small");
   char *w = align256((char *)work);
   Reduce red;
   red.counter = (unsigned int *)w;
@@ -401,6 +404,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
   GridSync *gs = (GridSync *)w;
   w = align256(w + sizeof(GridSync));
   DTR_CUDA(cudaMemsetAsync(red.counter, 0, 256, st));
+  DTR_CUDA(cudaMemsetAsync(gs, 0, sizeof(GridSync), st));  // error word read at exit even without a launch
   const int sms = device_sms();
   const int logb = ilog2i(b);
   const unsigned gd = reduce_grid((int64_t)g.V * b, sms);
@@ -447,7 +451,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     }
     return DTR_OK;
   }
-  if (p->solver == DTR_SOLVER_MIXED_F32) {
+  if (p->solver == DTR_SOLVER_MIXED_F32 || p->solver == DTR_SOLVER_FGMRES_NET) {
     double2 *r64 = (double2 *)w; w = align256(w + n * sizeof(double2));
     KrylovVecs<float> K;
     K.x = (float2 *)w;    w = align256(w + n * sizeof(float2));
@@ -457,7 +461,11 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     K.v = (float2 *)w;    w = align256(w + n * sizeof(float2));
     K.t = (float2 *)w;    w = align256(w + n * sizeof(float2));
     float2 *sv = (float2 *)w; w = align256(w + n * sizeof(float2));
+    void *fg_work = w;
+    const size_t fg_bytes = p->solver == DTR_SOLVER_FGMRES_NET ? fgmres_scratch_bytes(g.V, b, p->gmres_m) : 0;
     const double itol = p->inner_tol > 0 ? p->inner_tol : 1e-5;
+    bool fgmres = p->solver == DTR_SOLVER_FGMRES_NET;
+    std::vector<double> prev_rel(64, -1.0);
     for (int cycle = 0; cycle <= kMaxRestarts; ++cycle) {
       const int restart = cycle < kMaxRestarts;
       if (cycle == 0 && x_is_zero)
@@ -475,7 +483,31 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
       k_mixed_init<<<gv, kBlock, 0, st>>>(r64, K.r, K.rhat, K.p, K.x, n, b, outer); count_launches(1);
       k_mixed_scal_init<<<1, 64, 0, st>>>(outer, inner, b, itol * itol, p->maxiter); count_launches(1);
       DTR_LAUNCH_CHECK("inner init");
-      if (persistent) {
+      if (fgmres) {
+        // fall back to the BiCGStab inner solve if the last FGMRES cycle cut the true residual < 10x
+        Scal h;
+        DTR_CUDA(cudaMemcpyAsync(&h, outer, sizeof(Scal), cudaMemcpyDeviceToHost, st));
+        DTR_CUDA(cudaStreamSynchronize(st));
+        bool stagnated = false;
+        for (int j = 0; j < b; ++j) {
+          if (!h.active[j]) continue;
+          const double rel = h.bnorm2[j] > 0 ? std::sqrt(h.rtrue2[j] / h.bnorm2[j]) : 0.0;
+          if (prev_rel[j] > 0 && rel > 0.1 * prev_rel[j]) stagnated = true;
+          prev_rel[j] = rel;
+        }
+        if (stagnated) fgmres = false;
+      }
+      if (fgmres) {
+        Scal h;
+        DTR_CUDA(cudaMemcpyAsync(&h, outer, sizeof(Scal), cudaMemcpyDeviceToHost, st));
+        DTR_CUDA(cudaStreamSynchronize(st));
+        std::vector<int> act(b), its(b, 0);
+        for (int j = 0; j < b; ++j) act[j] = h.active[j];
+        rc = fgmres_solve(gauge, m0, (const dtr_net_s *)p->net, K.r, K.x, b, act.data(), p->gmres_m, itol, p->maxiter,
+                          fg_work, fg_bytes, its.data(), st);
+        if (rc) return rc;
+        DTR_CUDA(cudaMemcpyAsync(inner->iters, its.data(), sizeof(int) * b, cudaMemcpyHostToDevice, st));
+      } else if (persistent) {
         DTR_CUDA(cudaMemsetAsync(gs, 0, sizeof(GridSync), st));
         PArgs<float> pa;
         pa.U = gauge->U32;

@@ -24,7 +24,7 @@ template <typename R> struct KrylovVecs {
 };
 
 // Scratch the solver needs beyond the solution and right-hand-side blocks.
-size_t solver_scratch_bytes(int64_t V, int b, int solver);
+size_t solver_scratch_bytes(int64_t V, int b, int solver, int gmres_m = 16);
 
 // Solve A x = z on internal-layout FP64 blocks of width b.  x holds the
 // initial guess on entry.  *scal receives the device pointer of the final

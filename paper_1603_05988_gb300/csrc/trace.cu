@@ -47,7 +47,7 @@ static TraceLayout trace_layout(const dtr_gauge_s *g, const dtr_defl_s *D, const
   const int64_t V = g->lat.V;
   L.vec = al((size_t)V * 12 * L.b * sizeof(double2));
   L.zdot_red = al(256 + (size_t)kMaxGrid * 64 * sizeof(double2));
-  L.solver = al(solver_scratch_bytes(V, L.b, p->solve.solver));
+  L.solver = al(solver_scratch_bytes(V, L.b, p->solve.solver, p->solve.gmres_m));
   L.defl = D ? al(defl_scratch_bytes(V, D->k, L.b, device_sms())) : 0;
   const bool hp = D && p->ncolors > 1;
   L.hp = hp ? al(defl_hp_scratch_bytes(V, D->k, L.b, p->ncolors, device_sms())) : 0;

@@ -25,15 +25,15 @@ _lib = ctypes.CDLL(LIB_PATH)
 # ---------------------------------------------------------------- C structs
 DTR_OK, DTR_EINVAL, DTR_ENOMEM, DTR_ECUDA, DTR_ENOTCONV, DTR_ENAN, DTR_ETIMEOUT = range(7)
 DTR_F64, DTR_F32, DTR_BF16, DTR_F16 = range(4)
-SOLVER_F64, SOLVER_MIXED_F32 = 0, 1
+SOLVER_F64, SOLVER_MIXED_F32, SOLVER_FGMRES_NET = 0, 1, 2
 _PREC = {"f64": DTR_F64, "f32": DTR_F32, "bf16": DTR_BF16, "f16": DTR_F16}
-_SOLVER = {"f64": SOLVER_F64, "mixed_f32": SOLVER_MIXED_F32}
+_SOLVER = {"f64": SOLVER_F64, "mixed_f32": SOLVER_MIXED_F32, "fgmres_net": SOLVER_FGMRES_NET}
 
 
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("solver", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("inner_tol", ctypes.c_double), ("engine", ctypes.c_int),
-                ("grid", ctypes.c_int)]
+                ("grid", ctypes.c_int), ("net", ctypes.c_void_p), ("gmres_m", ctypes.c_int), ("pad_", ctypes.c_int)]
 
 
 class SolveStat(ctypes.Structure):
@@ -97,6 +97,13 @@ _sig("dtr_destroy_defl", None, [_vp])
 _sig("dtr_deflate_workspace_bytes", _sz, [_vp, _i])
 _sig("dtr_deflate_project", _i, [_vp, _vp, _i, _vp, _vp, _vp, _vp, _sz, _vp])
 _sig("dtr_deflate_project_static", _i, [_vp, _vp, _i, _vp, _vp, _vp])
+_sig("dtr_net_create", _i, [_vp, _i, _vp, _d, _d, _u64, ctypes.POINTER(_vp)])
+_sig("dtr_destroy_net", None, [_vp])
+_sig("dtr_net_get_weights", _i, [_vp, _i, _vp])
+_sig("dtr_net_workspace_bytes", _sz, [_vp, _i])
+_sig("dtr_net_apply", _i, [_vp, _vp, _vp, _i, _vp, _sz, _vp])
+_sig("dtr_net_train_step", _i, [_vp, _vp, _d, _vp, _vp, _i, _d, _i, ctypes.POINTER(ctypes.c_double), _vp, _vp, _sz,
+                                _vp])
 _sig("dtr_trace_workspace_bytes", _sz, [_vp, _vp, ctypes.POINTER(TraceParams)])
 _sig("dtr_trace_estimate", _i, [_vp, _d, _vp, ctypes.POINTER(TraceParams), _vp, _sz,
                                 ctypes.POINTER(TraceResult), _vp])
@@ -262,13 +269,70 @@ _ENGINE = {"persistent": 0, "kernels": 1}
 
 
 def solve_params(tol=1e-10, maxiter=5000, solver="f64", check_every=8, inner_tol=1e-5, engine="persistent",
-                 grid=0):
+                 grid=0, net=None, gmres_m=16):
     p = SolveParams()
     _lib.dtr_solve_params_default(ctypes.byref(p))
     p.tol, p.maxiter, p.solver, p.check_every, p.inner_tol = tol, maxiter, _SOLVER[solver], check_every, inner_tol
     p.engine = _ENGINE[engine]
     p.grid = int(grid)
+    p.net = net._h.value if net is not None else None
+    p.gmres_m = int(gmres_m)
     return p
+
+
+NET_WEIGHTS = 4 * 81 * 24 * 24
+
+
+class Net:
+    """Learned preconditioner network (4 layers, 3^4 stencil, 24 real channels)."""
+
+    def __init__(self, lat, act=0, weights=None, init_scale=1.0, noise=0.0, seed=0):
+        h = _vp()
+        wp = None
+        if weights is not None:
+            wa = np.ascontiguousarray(weights, dtype=np.float32).reshape(-1)
+            if wa.size != NET_WEIGHTS:
+                raise ValueError("weights must have 4*81*24*24 entries")
+            self._w = wa
+            wp = wa.ctypes.data_as(_vp)
+        _check(_lib.dtr_net_create(lat._h, int(act), wp, float(init_scale), float(noise), int(seed), ctypes.byref(h)))
+        self._h = h
+        self.lat = lat
+        self.act = act
+
+    def weights(self, bf16_rounded=False):
+        out = np.empty(NET_WEIGHTS, dtype=np.float32)
+        _check(_lib.dtr_net_get_weights(self._h, int(bool(bf16_rounded)), out.ctypes.data_as(_vp)))
+        return out.reshape(4, 81, 24, 24)
+
+    def apply(self, x):
+        torch = _torch()
+        x = _field(x, self.lat.N, "x")
+        out = torch.empty_like(x)
+        nb = _lib.dtr_net_workspace_bytes(self._h, x.shape[0])
+        w = _workspace(nb)
+        _check(_lib.dtr_net_apply(self._h, _ptr(x), _ptr(out), x.shape[0], _ptr(w), nb, _stream()))
+        return out
+
+    def train_step(self, x, target, lr=1e-3, step=True, want_grad=False, gauge=None, m0=0.0):
+        """One Adam step on pairs (x, target) with A target = x; residual-weighted
+        loss |A M x - x|^2 / |x|^2 if a gauge field is given, else the error loss."""
+        x = _field(x, self.lat.N, "x")
+        target = _field(target, self.lat.N, "target")
+        nb = _lib.dtr_net_workspace_bytes(self._h, x.shape[0])
+        w = _workspace(nb)
+        loss = ctypes.c_double()
+        grad = np.empty(NET_WEIGHTS, dtype=np.float32) if want_grad else None
+        _check(_lib.dtr_net_train_step(self._h, gauge._h if gauge is not None else None, float(m0), _ptr(x),
+                                       _ptr(target), x.shape[0], float(lr), int(bool(step)), ctypes.byref(loss),
+                                       grad.ctypes.data_as(_vp) if grad is not None else None, _ptr(w), nb,
+                                       _stream()))
+        return (loss.value, grad.reshape(4, 81, 24, 24)) if want_grad else loss.value
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.dtr_destroy_net(self._h)
+            self._h = None
 
 
 def solve_batch(gauge, m0, z, y0=None, params=None, allow_notconv=False):
