@@ -62,8 +62,8 @@ __host__ __device__ __forceinline__ float2 cjmul(float2 a, float2 b) {
   return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 __host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
-  double d = b.x * b.x + b.y * b.y;
-  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+  const double inv = 1.0 / (b.x * b.x + b.y * b.y);  // one division (FP64 divides are slow on this part)
+  return make_double2((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
 }
 __host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }

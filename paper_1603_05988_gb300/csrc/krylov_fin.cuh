@@ -111,8 +111,9 @@ __device__ __forceinline__ void fin_omega_beta(Scal *sc, int j, double2 ts, doub
   double2 om = make_double2(0.0, 0.0);
   double rn2 = ss.x;
   if (tt.x > 0.0) {
-    om = make_double2(ts.x / tt.x, ts.y / tt.x);
-    rn2 = ss.x - (ts.x * ts.x + ts.y * ts.y) / tt.x;
+    const double inv_tt = 1.0 / tt.x;
+    om = make_double2(ts.x * inv_tt, ts.y * inv_tt);
+    rn2 = ss.x - (ts.x * ts.x + ts.y * ts.y) * inv_tt;
     if (rn2 < 0.0) rn2 = 0.0;
   }
   sc->omega[j] = om;
@@ -136,7 +137,7 @@ __device__ __forceinline__ void fin_omega_beta(Scal *sc, int j, double2 ts, doub
     return;
   }
   const double2 rho_new = csub(rs, cmul(om, rt));
-  sc->beta[j] = cmul(cdiv(rho_new, rho), cdiv(sc->alpha[j], om));
+  sc->beta[j] = cdiv(cmul(rho_new, sc->alpha[j]), cmul(rho, om));  // (rho'/rho)(alpha/omega), one division
   sc->rho[j] = rho_new;
 }
 

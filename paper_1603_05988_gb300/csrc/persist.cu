@@ -10,10 +10,17 @@
 //        site)                        s^H s - |t^H s|^2 / t^H t -> beta, convergence
 //   P3  x += alpha p + omega s, r = s - omega t, p = r + beta (p - omega v)
 // so the r-reduction of textbook BiCGStab folds into the omega reduction.
-// Each reduction is finished by the LAST block to reach the barrier: it sums
-// the per-block partials in a fixed order (deterministic), runs the scalar
-// algebra once per column and only then releases the barrier, so every block
-// reads the same scalars afterwards.
+//
+// Reductions are all-reduce barriers: each block reduces its per-thread sums
+// (warp shuffles, then a fixed order over warps) to one partial per value and
+// column, arrives at a counting barrier, and once every block has arrived
+// EVERY block sums all partials in the same fixed order and runs the scalar
+// algebra on its own shared-memory copy of the per-column scalars.  All blocks
+// therefore hold bit-identical scalars without a second (release) round trip;
+// block 0 writes the scalars back to global memory when the kernel ends.
+// Partials are double-buffered by barrier parity: a block can be at most one
+// barrier ahead of the slowest block, so it never overwrites partials that
+// another block is still reading.
 //
 // Barriers are bounded: a block that waits longer than kSpinBudget clock
 // cycles sets an error word and the whole grid leaves the kernel, so a fault
@@ -31,59 +38,43 @@
 namespace dtr {
 
 constexpr long long kSpinBudget = 4000000000LL;  // ~2 s at 2 GHz
+// Largest persistent grid: two buffers of 5 x 64 partials per block fit the
+// solver's reduction scratch (kMaxGrid x 5 x 64 double2).
+constexpr int kPersistMaxGrid = kMaxGrid / 2;
 
-// Bounded grid barrier for `expected` blocks; `fin` runs in the last-arriving
-// block (all its threads) before the barrier opens.  Returns false if the
+// Counting grid barrier: arrive, then wait until `target` arrivals in total
+// (the barrier's sequence number times the grid size).  Returns false if the
 // wait exceeded `budget` clock cycles or another block reported an error.
-template <class F>
-__device__ __forceinline__ bool gsync_n(GridSync *gs, unsigned int expected, long long budget, F &&fin) {
-  __shared__ int s_last, s_err;
+__device__ __forceinline__ bool grid_arrive_wait(GridSync *gs, unsigned int target, long long budget) {
+  __shared__ int s_err;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int g0 = *(volatile unsigned int *)&gs->gen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&gs->count, 1u);
-    s_last = (arrived == expected - 1);
     s_err = 0;
-    if (!s_last) {
-      const long long t0 = clock64();
-      while (*(volatile unsigned int *)&gs->gen == g0) {
-        if (*(volatile int *)&gs->error) {
-          s_err = 1;
-          break;
-        }
-        if (clock64() - t0 > budget) {
-          atomicExch(&gs->error, 1);
-          s_err = 1;
-          break;
-        }
-        __nanosleep(20);
+    __threadfence();
+    atomicAdd(&gs->count, 1u);
+    const long long t0 = clock64();
+    while (*(volatile unsigned int *)&gs->count < target) {
+      if (*(volatile int *)&gs->error) {
+        s_err = 1;
+        break;
       }
+      if (clock64() - t0 > budget) {
+        atomicExch(&gs->error, 1);
+        s_err = 1;
+        break;
+      }
+      __nanosleep(32);
     }
     __threadfence();
   }
   __syncthreads();
-  if (s_last) {
-    fin();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      gs->count = 0u;
-      __threadfence();
-      atomicAdd(&gs->gen, 1u);
-    }
-    __syncthreads();
-  }
   return !s_err;
 }
 
-template <class F> __device__ __forceinline__ bool gsync(GridSync *gs, F &&fin) {
-  return gsync_n(gs, gridDim.x, kSpinBudget, fin);
-}
-
-// Self-test: one block waits at a barrier that expects two blocks, so the
+// Self-test: one block waits at a barrier that expects two arrivals, so the
 // peer never arrives and the bounded wait must give up with the error word set.
 __global__ void k_barrier_probe(GridSync *gs, long long budget, int *out) {
-  const bool ok = gsync_n(gs, 2u, budget, [] {});
+  const bool ok = grid_arrive_wait(gs, 2u, budget);
   if (threadIdx.x == 0) out[0] = ok ? 0 : 1;
 }
 
@@ -110,95 +101,140 @@ int selftest_barrier(long long budget, int *timed_out, int *error_word, cudaStre
   return DTR_OK;
 }
 
-// Reduce NV values per column over the block (fixed tree) into partial[block][q][j].
-template <int NV, int T>
-__device__ __forceinline__ void block_partial(const double2 (&v)[NV], int b, double2 *__restrict__ partial,
-                                              double2 *sh) {
-  const int t = threadIdx.x;
+// Block sums of NV complex per-thread values (type A) of column
+// j = threadIdx.x & (b-1): butterfly over the lanes of one column inside a
+// warp, then a fixed-order sum over the warps holding that column; written to
+// part[block * NV*b + q*b + j].
+template <int NV, int T, typename A>
+__device__ __forceinline__ void block_sums(A (&vx)[NV], A (&vy)[NV], int b, typename cplx_t<A>::type *part,
+                                           A *shw) {
+  typedef typename cplx_t<A>::type CA;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int off = 16; off >= b; off >>= 1) {
 #pragma unroll
-  for (int q = 0; q < NV; ++q) sh[q * T + t] = v[q];
-  __syncthreads();
-  for (int stride = T / 2; stride >= b; stride >>= 1) {
-    if (t < stride) {
-#pragma unroll
-      for (int q = 0; q < NV; ++q) sh[q * T + t] = cadd(sh[q * T + t], sh[q * T + t + stride]);
+    for (int q = 0; q < NV; ++q) {
+      vx[q] += __shfl_xor_sync(0xffffffffu, vx[q], off);
+      vy[q] += __shfl_xor_sync(0xffffffffu, vy[q], off);
     }
-    __syncthreads();
   }
-  if (t < b) {
+  const int bw = b < 32 ? b : 32;  // distinct columns per warp
+  if (lane < bw) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) partial[((int64_t)blockIdx.x * NV + q) * b + t] = sh[q * T + t];
-    __threadfence();
+    for (int q = 0; q < NV; ++q) {
+      shw[((w * NV + q) * 2 + 0) * 32 + lane] = vx[q];
+      shw[((w * NV + q) * 2 + 1) * 32 + lane] = vy[q];
+    }
   }
-}
-
-// Last block: tot[q*b + j] = sum over all blocks of partial[blk][q][j], fixed order.
-// (A warp-parallel variant with shuffle trees measured slower on GB300 at the
-// 8^4 workload: 2.9 vs 2.3 ms per 16-RHS solve.)
-template <int NV, int T>
-__device__ __forceinline__ void grid_total(int b, const double2 *__restrict__ partial, double2 *sh, double2 *tot) {
-  const int t = threadIdx.x;
+  __syncthreads();
   const int P = NV * b;
+  const int cw = b > 32 ? b / 32 : 1;  // warps per full set of columns
+  for (int pp = threadIdx.x; pp < P; pp += T) {
+    const int q = pp / b, j = pp % b;
+    A sx = 0, sy = 0;
+    for (int ww = j >> 5; ww < T / 32; ww += cw) {
+      sx += shw[((ww * NV + q) * 2 + 0) * 32 + (j & 31)];
+      sy += shw[((ww * NV + q) * 2 + 1) * 32 + (j & 31)];
+    }
+    CA v;
+    v.x = sx;
+    v.y = sy;
+    part[(int64_t)blockIdx.x * P + pp] = v;
+  }
+  // (ordered for the other blocks by the barrier: __syncthreads, then thread
+  // 0's fence before its arrival)
+}
+
+// Every block: tot[p] = sum over blocks of part[blk * P + p], fixed order
+// (slices of contiguous blocks, 16 independent loads in flight per thread;
+// the threads of a warp read consecutive p, so the loads coalesce).  The sums
+// run in the partials' own precision: FP32 for the FP32 engine, whose inner
+// solve is certified by the FP64 true residual of the outer loop (FP64
+// arithmetic runs at 1/64 of the FP32 rate on this part, and every block
+// repeats these sums).
+template <int T, typename CA>
+__device__ __forceinline__ void grid_sums(int P, const CA *__restrict__ part, CA *sh, double2 *tot) {
+  typedef decltype(CA().x) A;
+  const int t = threadIdx.x;
   const int G = gridDim.x;
-  if (P > T) {
-    for (int p = t; p < P; p += T) {
-      const int q = p / b, j = p % b;
-      double2 a0 = make_double2(0.0, 0.0);
-      for (int blk = 0; blk < G; ++blk) a0 = cadd(a0, __ldcg(&partial[((int64_t)blk * NV + q) * b + j]));
-      tot[p] = a0;
+  const int S = P <= T ? T / P : 1;
+  const int ch = (G + S - 1) / S;
+  for (int p0 = 0; p0 < P; p0 += T) {  // one pass unless P > T
+    const int pp = p0 + (P <= T ? t % P : t);
+    const int sl = P <= T ? t / P : 0;
+    A ax = 0, ay = 0;
+    if (sl < S && pp < P) {
+      const int lo = sl * ch;
+      const int hi = min(G, lo + ch);
+      const CA *src = part + pp;
+      for (int k0 = lo; k0 < hi; k0 += 16) {
+        CA v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          if (k0 + u < hi) {
+            v[u] = __ldcg(src + (int64_t)(k0 + u) * P);
+          } else {
+            v[u].x = 0;
+            v[u].y = 0;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          ax += v[u].x;
+          ay += v[u].y;
+        }
+      }
     }
-    __syncthreads();
-    return;
-  }
-  const int S = T / P;
-  const int p = t % P, sl = t / P;
-  double2 a0 = make_double2(0.0, 0.0), a1 = a0, a2 = a0, a3 = a0;
-  if (sl < S) {
-    const int q = p / b, j = p % b;
-    int blk = sl;
-    for (; blk + 3 * S < G; blk += 4 * S) {
-      a0 = cadd(a0, __ldcg(&partial[((int64_t)blk * NV + q) * b + j]));
-      a1 = cadd(a1, __ldcg(&partial[((int64_t)(blk + S) * NV + q) * b + j]));
-      a2 = cadd(a2, __ldcg(&partial[((int64_t)(blk + 2 * S) * NV + q) * b + j]));
-      a3 = cadd(a3, __ldcg(&partial[((int64_t)(blk + 3 * S) * NV + q) * b + j]));
+    if (P <= T) {
+      sh[t].x = ax;
+      sh[t].y = ay;
+      __syncthreads();
+      if (t < P) {
+        A sx = sh[t].x, sy = sh[t].y;
+        for (int k = 1; k < S; ++k) {
+          sx += sh[k * P + t].x;
+          sy += sh[k * P + t].y;
+        }
+        tot[t] = make_double2((double)sx, (double)sy);
+      }
+      __syncthreads();
+    } else if (pp < P) {
+      tot[pp] = make_double2((double)ax, (double)ay);
     }
-    for (; blk < G; blk += S) a0 = cadd(a0, __ldcg(&partial[((int64_t)blk * NV + q) * b + j]));
-  }
-  const double2 acc = cadd(cadd(a0, a1), cadd(a2, a3));
-  __syncthreads();
-  sh[t] = acc;
-  __syncthreads();
-  if (t < P) {
-    double2 s = sh[t];
-    for (int k = 1; k < S; ++k) s = cadd(s, sh[k * P + t]);
-    tot[t] = s;
   }
   __syncthreads();
 }
 
-template <typename C> __device__ __forceinline__ C ldcg_scal(const double2 *p) {
-  const double2 v = __ldcg(p);
-  return mk<C>(v.x, v.y);
-}
+template <typename C> __device__ __forceinline__ C mkc(const double2 v) { return mk<C>(v.x, v.y); }
 
 template <typename R, int T, int WITH_RESID>
 __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
   typedef typename cplx_t<R>::type C;
-  __shared__ double2 sh[5 * T];
+  __shared__ typename cplx_t<R>::type sh[T];
   __shared__ double2 tot[5 * 64];
+  __shared__ R shw[(T / 32) * 5 * 2 * 32];
+  __shared__ Scal ss;  // this block's copy of the per-column scalars
   const int b = a.b, logb = a.logb;
   const int j = threadIdx.x & (b - 1);
   const int64_t nsite = (int64_t)a.g.V << logb;
   const int64_t nel = nsite * 12;
   const int64_t stride = (int64_t)gridDim.x * T;
   const int64_t t0 = (int64_t)blockIdx.x * T + threadIdx.x;
-  Scal *sc = a.sc;
+  const unsigned int G = gridDim.x;
+  C *part[2] = {(C *)a.partial, (C *)a.partial + (int64_t)5 * 64 * G};
+  unsigned int nbar = 0;  // barriers passed
+  {
+    const int *src = (const int *)a.sc;
+    int *dst = (int *)&ss;
+    for (int i = threadIdx.x; i < (int)(sizeof(Scal) / sizeof(int)); i += T) dst[i] = __ldcg(src + i);
+  }
+  __syncthreads();
   const int cycles = WITH_RESID ? a.max_cycles : 1;
   int done = 0;
+  bool ok = true;
 
-  for (int cycle = 0; cycle < cycles; ++cycle) {
+  for (int cycle = 0; ok && cycle < cycles; ++cycle) {
     if (WITH_RESID) {  // r = z - A x ; rhat = p = r ; (||r||^2, ||z||^2) -> restart decision
-      double2 acc[1] = {make_double2(0.0, 0.0)};
+      R vx[1] = {0}, vy[1] = {0};
       for (int64_t it = t0; it < nsite; it += stride) {
         const int s = (int)(it >> logb);
         C o[12], self[12];
@@ -211,25 +247,25 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
           a.r[base + c * b] = rr;
           a.rhat[base + c * b] = rr;
           a.p[base + c * b] = rr;
-          acc[0].x += (double)rr.x * rr.x + (double)rr.y * rr.y;
-          acc[0].y += (double)zz.x * zz.x + (double)zz.y * zz.y;
+          vx[0] += rr.x * rr.x + rr.y * rr.y;
+          vy[0] += zz.x * zz.x + zz.y * zz.y;
         }
       }
-      block_partial<1, T>(acc, b, a.partial, sh);
-      const bool ok = gsync(a.gs, [&] {
-        grid_total<1, T>(b, a.partial, sh, tot);
-        if (threadIdx.x < b) fin_resid(sc, threadIdx.x, tot[threadIdx.x], 1);
-        const int na = __syncthreads_count(threadIdx.x < b && sc->active[threadIdx.x]);
-        if (threadIdx.x == 0) sc->n_active = na;
-      });
-      if (!ok) return;
-      if (__ldcg(&sc->n_active) == 0) break;
+      C *pb = part[nbar & 1];
+      block_sums<1, T, R>(vx, vy, b, pb, shw);
+      ok = grid_arrive_wait(a.gs, ++nbar * G, kSpinBudget);
+      if (!ok) break;
+      grid_sums<T>(b, pb, sh, tot);
+      if (threadIdx.x < b) fin_resid(&ss, threadIdx.x, tot[threadIdx.x], 1);
+      const int na = __syncthreads_count(threadIdx.x < b && ss.active[threadIdx.x]);
+      if (threadIdx.x == 0) ss.n_active = na;
+      if (na == 0) break;
     }
     for (int iter = 0; iter < a.max_iters; ++iter) {
       ++done;
       if (blockIdx.x == 0 && threadIdx.x == 0) a.gs->iters = done;
       {  // P1: v = A p ; rhat^H v -> alpha   (per-thread sums in R, block/grid sums in FP64)
-        R ax = 0, ay = 0;
+        R vx[1] = {0}, vy[1] = {0};
         for (int64_t it = t0; it < nsite; it += stride) {
           const int s = (int)(it >> logb);
           C o[12], self[12];
@@ -239,22 +275,23 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
           for (int c = 0; c < 12; ++c) {
             a.v[base + c * b] = o[c];
             const C rh = a.rhat[base + c * b];
-            ax += rh.x * o[c].x + rh.y * o[c].y;
-            ay += rh.x * o[c].y - rh.y * o[c].x;
+            vx[0] += rh.x * o[c].x + rh.y * o[c].y;
+            vy[0] += rh.x * o[c].y - rh.y * o[c].x;
           }
         }
-        double2 acc[1] = {make_double2((double)ax, (double)ay)};
-        block_partial<1, T>(acc, b, a.partial, sh);
-        const bool ok = gsync(a.gs, [&] {
-          grid_total<1, T>(b, a.partial, sh, tot);
-          if (threadIdx.x < b) fin_alpha(sc, threadIdx.x, tot[threadIdx.x]);
-        });
-        if (!ok) return;
+        C *pb = part[nbar & 1];
+        block_sums<1, T, R>(vx, vy, b, pb, shw);
+        ok = grid_arrive_wait(a.gs, ++nbar * G, kSpinBudget);
+        if (!ok) break;
+        grid_sums<T>(b, pb, sh, tot);
+        if (threadIdx.x < b) fin_alpha(&ss, threadIdx.x, tot[threadIdx.x]);
+        __syncthreads();
       }
+      int n_active = 0;
       {  // P2: t = A s with s = r - alpha v on the fly ; five dots -> omega, beta, convergence
-        const C al = ldcg_scal<C>(&sc->alpha[j]);
+        const C al = mkc<C>(ss.alpha[j]);
         AxpyLoad<C> ld{a.r, a.v, al};
-        R tsx = 0, tsy = 0, tt = 0, rsx = 0, rsy = 0, rtx = 0, rty = 0, ss = 0;
+        R vx[5] = {0, 0, 0, 0, 0}, vy[5] = {0, 0, 0, 0, 0};
         for (int64_t it = t0; it < nsite; it += stride) {
           const int s = (int)(it >> logb);
           C o[12], self[12];
@@ -265,50 +302,122 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
             a.t[base + c * b] = o[c];
             a.s[base + c * b] = self[c];
             const C rh = a.rhat[base + c * b];
-            tsx += o[c].x * self[c].x + o[c].y * self[c].y;
-            tsy += o[c].x * self[c].y - o[c].y * self[c].x;
-            tt += o[c].x * o[c].x + o[c].y * o[c].y;
-            rsx += rh.x * self[c].x + rh.y * self[c].y;
-            rsy += rh.x * self[c].y - rh.y * self[c].x;
-            rtx += rh.x * o[c].x + rh.y * o[c].y;
-            rty += rh.x * o[c].y - rh.y * o[c].x;
-            ss += self[c].x * self[c].x + self[c].y * self[c].y;
+            vx[0] += o[c].x * self[c].x + o[c].y * self[c].y;  // t^H s
+            vy[0] += o[c].x * self[c].y - o[c].y * self[c].x;
+            vx[1] += o[c].x * o[c].x + o[c].y * o[c].y;        // t^H t
+            vx[2] += rh.x * self[c].x + rh.y * self[c].y;      // rhat^H s
+            vy[2] += rh.x * self[c].y - rh.y * self[c].x;
+            vx[3] += rh.x * o[c].x + rh.y * o[c].y;            // rhat^H t
+            vy[3] += rh.x * o[c].y - rh.y * o[c].x;
+            vx[4] += self[c].x * self[c].x + self[c].y * self[c].y;  // s^H s
           }
         }
-        double2 acc[5] = {make_double2((double)tsx, (double)tsy), make_double2((double)tt, 0.0),
-                          make_double2((double)rsx, (double)rsy), make_double2((double)rtx, (double)rty),
-                          make_double2((double)ss, 0.0)};
-        block_partial<5, T>(acc, b, a.partial, sh);
-        const bool ok = gsync(a.gs, [&] {
-          grid_total<5, T>(b, a.partial, sh, tot);
-          if (threadIdx.x < b)
-            fin_omega_beta(sc, threadIdx.x, tot[threadIdx.x], tot[b + threadIdx.x], tot[2 * b + threadIdx.x],
-                           tot[3 * b + threadIdx.x], tot[4 * b + threadIdx.x]);
-          const int na = __syncthreads_count(threadIdx.x < b && sc->active[threadIdx.x]);
-          if (threadIdx.x == 0) sc->n_active = na;
-        });
-        if (!ok) return;
+        C *pb = part[nbar & 1];
+        block_sums<5, T, R>(vx, vy, b, pb, shw);
+        ok = grid_arrive_wait(a.gs, ++nbar * G, kSpinBudget);
+        if (!ok) break;
+        grid_sums<T>(5 * b, pb, sh, tot);
+        if (threadIdx.x < b)
+          fin_omega_beta(&ss, threadIdx.x, tot[threadIdx.x], tot[b + threadIdx.x], tot[2 * b + threadIdx.x],
+                         tot[3 * b + threadIdx.x], tot[4 * b + threadIdx.x]);
+        n_active = __syncthreads_count(threadIdx.x < b && ss.active[threadIdx.x]);
+        if (threadIdx.x == 0) ss.n_active = n_active;
       }
       {  // P3: x += alpha p + omega s ; r = s - omega t ; p = r + beta (p - omega v)
-        const C al = ldcg_scal<C>(&sc->alpha[j]);
-        const C om = ldcg_scal<C>(&sc->omega[j]);
-        const C be = ldcg_scal<C>(&sc->beta[j]);
-        const bool act = __ldcg(&sc->active[j]) != 0;
-        for (int64_t e = t0; e < nel; e += stride) {
+        const C al = mkc<C>(ss.alpha[j]);
+        const C om = mkc<C>(ss.omega[j]);
+        const C be = mkc<C>(ss.beta[j]);
+        const C mom = cneg(om);
+        const bool act = ss.active[j] != 0;
+        constexpr int U = 4;  // independent elements (or FP32 pairs) in flight per thread
+        int64_t e = t0;
+        if constexpr (sizeof(R) == 4) {
+          if (b >= 2) {  // FP32: two adjacent columns j, j+1 per 16-byte access
+          const int j0 = (2 * threadIdx.x) & (b - 1);
+          const C al1 = mkc<C>(ss.alpha[j0 + 1]), om1 = mkc<C>(ss.omega[j0 + 1]);
+          const C be1 = mkc<C>(ss.beta[j0 + 1]), mom1 = cneg(om1);
+          const C al0 = mkc<C>(ss.alpha[j0]), om0 = mkc<C>(ss.omega[j0]);
+          const C be0 = mkc<C>(ss.beta[j0]), mom0 = cneg(om0);
+          const bool act0 = ss.active[j0] != 0, act1 = ss.active[j0 + 1] != 0;
+          const int64_t n2 = nel >> 1;
+          float4 *X = (float4 *)a.x, *Rr = (float4 *)a.r, *Pp = (float4 *)a.p;
+          const float4 *Ss = (const float4 *)a.s, *Tt = (const float4 *)a.t, *Vv = (const float4 *)a.v;
+          auto upd = [&](float4 sv, float4 pv, float4 xv, float4 tv, float4 vv, int64_t q) {
+            const C s0 = mk<C>(sv.x, sv.y), s1 = mk<C>(sv.z, sv.w);
+            const C p0 = mk<C>(pv.x, pv.y), p1 = mk<C>(pv.z, pv.w);
+            const C x0 = caxpy(om0, s0, caxpy(al0, p0, mk<C>(xv.x, xv.y)));
+            const C x1 = caxpy(om1, s1, caxpy(al1, p1, mk<C>(xv.z, xv.w)));
+            X[q] = make_float4(x0.x, x0.y, x1.x, x1.y);
+            const C r0 = caxpy(mom0, mk<C>(tv.x, tv.y), s0);
+            const C r1 = caxpy(mom1, mk<C>(tv.z, tv.w), s1);
+            Rr[q] = make_float4(r0.x, r0.y, r1.x, r1.y);
+            if (act0 || act1) {
+              const C q0 = act0 ? caxpy(be0, caxpy(mom0, mk<C>(vv.x, vv.y), p0), r0) : p0;
+              const C q1 = act1 ? caxpy(be1, caxpy(mom1, mk<C>(vv.z, vv.w), p1), r1) : p1;
+              Pp[q] = make_float4(q0.x, q0.y, q1.x, q1.y);
+            }
+          };
+          int64_t f = t0;
+          for (; f + (U - 1) * stride < n2; f += U * stride) {
+            float4 sv[U], pv[U], xv[U], tv[U], vv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int64_t q = f + u * stride;
+              sv[u] = Ss[q];
+              pv[u] = Pp[q];
+              xv[u] = X[q];
+              tv[u] = Tt[q];
+              vv[u] = (act0 || act1) ? Vv[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) upd(sv[u], pv[u], xv[u], tv[u], vv[u], f + u * stride);
+          }
+          for (; f < n2; f += stride)
+            upd(Ss[f], Pp[f], X[f], Tt[f], (act0 || act1) ? Vv[f] : make_float4(0.f, 0.f, 0.f, 0.f), f);
+          e = nel;  // done
+          }
+        }
+        for (; e + (U - 1) * stride < nel; e += U * stride) {
+          C sv[U], pv[U], xv[U], tv[U], vv[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int64_t q = e + u * stride;
+            sv[u] = a.s[q];
+            pv[u] = a.p[q];
+            xv[u] = a.x[q];
+            tv[u] = a.t[q];
+            if (act) vv[u] = a.v[q];
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int64_t q = e + u * stride;
+            a.x[q] = caxpy(om, sv[u], caxpy(al, pv[u], xv[u]));
+            const C rn = caxpy(mom, tv[u], sv[u]);
+            a.r[q] = rn;
+            if (act) a.p[q] = caxpy(be, caxpy(mom, vv[u], pv[u]), rn);
+          }
+        }
+        for (; e < nel; e += stride) {
           const C sv = a.s[e];
           const C pv = a.p[e];
           a.x[e] = caxpy(om, sv, caxpy(al, pv, a.x[e]));
-          const C rn = caxpy(cneg(om), a.t[e], sv);
+          const C rn = caxpy(mom, a.t[e], sv);
           a.r[e] = rn;
-          if (act) a.p[e] = caxpy(be, caxpy(cneg(om), a.v[e], pv), rn);
+          if (act) a.p[e] = caxpy(be, caxpy(mom, a.v[e], pv), rn);
         }
-        const bool stop = __ldcg(&sc->n_active) == 0;
+        const bool stop = n_active == 0;
         if (stop && !WITH_RESID) break;  // kernel exit orders these writes for the host
-        const bool ok = gsync(a.gs, [] {});  // p (and x for the residual phase) read at neighbours next
-        if (!ok) return;
-        if (stop) break;
+        ok = grid_arrive_wait(a.gs, ++nbar * G, kSpinBudget);  // p (and x) are read at neighbours next
+        if (!ok || stop) break;
       }
     }
+  }
+  // block 0 publishes the per-column scalars (identical in every block)
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    const int *src = (const int *)&ss;
+    int *dst = (int *)a.sc;
+    for (int i = threadIdx.x; i < (int)(sizeof(Scal) / sizeof(int)); i += T) dst[i] = src[i];
   }
 }
 
@@ -350,7 +459,7 @@ template <typename R, int T, int W> static int launch_one(const PArgs<R> &pa, cu
     if (e != cudaSuccess) return cuda_fail(e, "persistent solver occupancy");
     if (nb < 1) return fail(DTR_ECUDA, "persistent solver cannot be resident");
     max_grid = nb * device_sms();
-    if (max_grid > kMaxGrid) max_grid = kMaxGrid;
+    if (max_grid > kPersistMaxGrid) max_grid = kPersistMaxGrid;
   }
   const int grid = (pa.grid > 0 && pa.grid < max_grid) ? pa.grid : max_grid;
   PArgs<R> copy = pa;

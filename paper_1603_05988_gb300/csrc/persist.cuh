@@ -7,8 +7,8 @@ namespace dtr {
 
 // Grid barrier state, zeroed before every launch.
 struct GridSync {
-  unsigned int count;
-  unsigned int gen;
+  unsigned int count;  // arrivals so far (barrier n completes at n * gridDim.x)
+  unsigned int gen;    // unused (layout kept)
   int error;
   int iters;  // BiCGStab iterations the launch executed (written by block 0 at exit)
 };
