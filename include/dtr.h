@@ -99,6 +99,11 @@ int dtr_profile_persistent(int enable, double *ms, int64_t *launches, double *si
  * threads, all devices), for launch accounting by callers. */
 uint64_t dtr_kernel_launches(void);
 
+/* CUDA-graph use of the mixed solver (no_graph = 0, persistent engine): graphs captured so far and
+ * graph launches, process-wide.  A graph is captured once per distinct argument set (device,
+ * gauge, lattice, m0, buffers, block, tolerances, limits) and reused; at most 8 are cached. */
+int dtr_graph_stats(uint64_t *captures, uint64_t *launches);
+
 /* Self-test of the bounded grid barrier the persistent solver uses (its
  * failure-detection path, exercised without faulting anything): one block
  * waits at a barrier that expects two blocks, so the wait must give up after
@@ -184,7 +189,10 @@ typedef struct {
                           co-resident) */
   dtr_net net;         /* DTR_SOLVER_FGMRES_NET: preconditioner (NULL = unpreconditioned FGMRES) */
   int gmres_m;         /* DTR_SOLVER_FGMRES_NET: restart length, 1..32 */
-  int pad_;
+  int no_graph;        /* DTR_SOLVER_MIXED_F32 with the persistent engine: 0 = run the whole
+                          defect-correction loop as one CUDA graph (a device-driven WHILE node,
+                          no host round trip between cycles; the graph is captured on first use
+                          and cached per argument set), 1 = host-driven launches */
 } dtr_solve_params;
 
 typedef struct {

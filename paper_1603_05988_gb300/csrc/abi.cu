@@ -20,7 +20,15 @@ namespace dtr {
 static thread_local std::string g_err;
 static std::atomic<unsigned long long> g_launches{0};
 
-void count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+static thread_local int t_capture_depth = 0;  // > 0 while this thread captures a CUDA graph
+
+// Host-side count of kernel launches; launches recorded while capturing a
+// graph are not executions and are counted when the graph runs instead.
+void count_launches(int n) {
+  if (!t_capture_depth) g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed);
+}
+void capture_begin() { ++t_capture_depth; }
+void capture_end() { --t_capture_depth; }
 
 void set_error(const std::string &msg) { g_err = msg; }
 int fail(int code, const std::string &msg) {
@@ -99,6 +107,10 @@ int dtr_selftest_barrier(int64_t budget_cycles, int *timed_out, int *error_word,
 
 int dtr_profile_persistent(int enable, double *ms, int64_t *launches, double *site_rhs_iterations) {
   PersistProfile &p = persist_profile();
+  if (p.on) {
+    DTR_CUDA(cudaDeviceSynchronize());
+    persist_profile_flush(nullptr);
+  }
   if (ms) *ms = p.ms;
   if (launches) *launches = p.launches;
   if (site_rhs_iterations) *site_rhs_iterations = p.site_rhs_iters;
@@ -111,7 +123,18 @@ int dtr_profile_persistent(int enable, double *ms, int64_t *launches, double *si
   return DTR_OK;
 }
 
-uint64_t dtr_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
+int dtr_graph_stats(uint64_t *captures, uint64_t *launches) {
+  if (!captures || !launches) return fail(DTR_EINVAL, "null argument");
+  unsigned long long c = 0, l = 0;
+  graph_counters(&c, &l);
+  *captures = c;
+  *launches = l;
+  return DTR_OK;
+}
+
+uint64_t dtr_kernel_launches(void) {
+  return (uint64_t)g_launches.load(std::memory_order_relaxed) + (uint64_t)device_launch_count();
+}
 
 int dtr_make_lattice(const int dims[4], dtr_lattice *out) {
   if (!dims || !out) return fail(DTR_EINVAL, "null argument");
@@ -306,7 +329,7 @@ void dtr_solve_params_default(dtr_solve_params *p) {
   p->grid = 0;
   p->net = nullptr;
   p->gmres_m = 16;
-  p->pad_ = 0;
+  p->no_graph = 0;
 }
 
 static int check_solve_params(const dtr_solve_params *p) {

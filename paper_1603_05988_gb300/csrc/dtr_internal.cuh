@@ -23,6 +23,8 @@ int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 // process-wide count of kernels launched by the library
 void count_launches(int n);
+void capture_begin();
+void capture_end();
 
 #define DTR_CUDA(call)                                   \
   do {                                                   \

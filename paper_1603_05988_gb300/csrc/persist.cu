@@ -42,6 +42,12 @@ constexpr long long kSpinBudget = 4000000000LL;  // ~2 s at 2 GHz
 // solver's reduction scratch (kMaxGrid x 5 x 64 double2).
 constexpr int kPersistMaxGrid = kMaxGrid / 2;
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Counting grid barrier: arrive, then wait until `target` arrivals in total
 // (the barrier's sequence number times the grid size).  Returns false if the
 // wait exceeded `budget` clock cycles or another block reported an error.
@@ -222,6 +228,7 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
   const unsigned int G = gridDim.x;
   C *part[2] = {(C *)a.partial, (C *)a.partial + (int64_t)5 * 64 * G};
   unsigned int nbar = 0;  // barriers passed
+  if (threadIdx.x == 0) atomicMax(&a.gs->nt0, ~global_ns());
   {
     const int *src = (const int *)a.sc;
     int *dst = (int *)&ss;
@@ -419,36 +426,60 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
     int *dst = (int *)a.sc;
     for (int i = threadIdx.x; i < (int)(sizeof(Scal) / sizeof(int)); i += T) dst[i] = src[i];
   }
+  if (threadIdx.x == 0) atomicMax(&a.gs->t1, global_ns());
 }
 
 // ----------------------------------------------------------- launch profile
-struct PendingLaunch {
-  cudaEvent_t e0, e1;
-  GridSync *gs;
-  double site_rhs;
+struct DevProf {
+  unsigned long long launches;
+  unsigned long long ns;
+  double site_rhs_iters;
 };
+__device__ DevProf g_devprof;
+__device__ unsigned long long g_dev_launches;  // kernels launched inside device-driven graph loops
+
+__global__ void k_persist_account(const GridSync *__restrict__ gs, double site_rhs) {
+  if (threadIdx.x == 0) {
+    const unsigned long long t0 = ~gs->nt0, t1 = gs->t1;
+    atomicAdd(&g_devprof.launches, 1ull);
+    atomicAdd(&g_devprof.ns, t1 > t0 ? t1 - t0 : 0ull);
+    atomicAdd(&g_devprof.site_rhs_iters, (double)gs->iters * site_rhs);
+  }
+}
+
 static PersistProfile g_prof = {false, 0.0, 0, 0.0};
-static std::vector<PendingLaunch> g_pending;
 static std::mutex g_prof_mu;
 
 PersistProfile &persist_profile() { return g_prof; }
 
 void persist_profile_flush(cudaStream_t st) {
   std::lock_guard<std::mutex> lock(g_prof_mu);
-  for (auto &pl : g_pending) {
-    float ms = 0.f;
-    GridSync h;
-    if (cudaEventElapsedTime(&ms, pl.e0, pl.e1) == cudaSuccess &&
-        cudaMemcpy(&h, pl.gs, sizeof(GridSync), cudaMemcpyDeviceToHost) == cudaSuccess) {
-      g_prof.ms += ms;
-      g_prof.launches += 1;
-      g_prof.site_rhs_iters += (double)h.iters * pl.site_rhs;
-    }
-    cudaEventDestroy(pl.e0);
-    cudaEventDestroy(pl.e1);
-  }
-  g_pending.clear();
+  DevProf h, z = {0, 0, 0.0};
+  if (cudaMemcpyFromSymbol(&h, g_devprof, sizeof(DevProf)) != cudaSuccess) return;
+  if (cudaMemcpyToSymbol(g_devprof, &z, sizeof(DevProf)) != cudaSuccess) return;
+  g_prof.ms += (double)h.ns * 1e-6;
+  g_prof.launches += (long long)h.launches;
+  g_prof.site_rhs_iters += h.site_rhs_iters;
   (void)st;
+}
+
+int persist_account(const GridSync *gs, double site_rhs, cudaStream_t st) {
+  k_persist_account<<<1, 32, 0, st>>>(gs, site_rhs);
+  count_launches(1);
+  DTR_CUDA(cudaGetLastError());
+  return DTR_OK;
+}
+
+unsigned long long device_launch_count() {
+  unsigned long long h = 0;
+  if (cudaMemcpyFromSymbol(&h, g_dev_launches, sizeof(h)) != cudaSuccess) return 0;
+  return h;
+}
+
+unsigned long long *device_launch_counter() {
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_dev_launches) != cudaSuccess) return nullptr;
+  return (unsigned long long *)p;
 }
 
 template <typename R, int T, int W> static int launch_one(const PArgs<R> &pa, cudaStream_t st) {
@@ -464,23 +495,10 @@ template <typename R, int T, int W> static int launch_one(const PArgs<R> &pa, cu
   const int grid = (pa.grid > 0 && pa.grid < max_grid) ? pa.grid : max_grid;
   PArgs<R> copy = pa;
   void *args[] = {&copy};
-  PendingLaunch pl;
-  const bool prof = g_prof.on;
-  if (prof) {
-    DTR_CUDA(cudaEventCreate(&pl.e0));
-    DTR_CUDA(cudaEventCreate(&pl.e1));
-    DTR_CUDA(cudaEventRecord(pl.e0, st));
-  }
   DTR_CUDA(cudaLaunchCooperativeKernel((const void *)k_bicgstab_persistent<R, T, W>, dim3(grid), dim3(T), args, 0,
                                        st));
   count_launches(1);
-  if (prof) {
-    DTR_CUDA(cudaEventRecord(pl.e1, st));
-    pl.gs = pa.gs;
-    pl.site_rhs = (double)pa.g.V * pa.b;
-    std::lock_guard<std::mutex> lock(g_prof_mu);
-    g_pending.push_back(pl);
-  }
+  if (g_prof.on) return persist_account(pa.gs, (double)pa.g.V * pa.b, st);
   return DTR_OK;
 }
 

@@ -5,13 +5,18 @@
 
 namespace dtr {
 
-// Grid barrier state, zeroed before every launch.
+// Grid barrier state.  The per-launch part (up to `error`) is zeroed before
+// every persistent launch; `error` and `cycles` are zeroed once per solve, so
+// a timeout in any cycle stays visible to the host.
 struct GridSync {
-  unsigned int count;  // arrivals so far (barrier n completes at n * gridDim.x)
-  unsigned int gen;    // unused (layout kept)
-  int error;
-  int iters;  // BiCGStab iterations the launch executed (written by block 0 at exit)
+  unsigned int count;       // arrivals so far (barrier n completes at n * gridDim.x)
+  int iters;                // BiCGStab iterations the launch executed (written by block 0)
+  unsigned long long nt0;   // ~(earliest block entry), device global timer (ns), via atomicMax
+  unsigned long long t1;    // latest block exit (ns)
+  int error;                // sticky: a barrier wait gave up
+  unsigned int cycles;      // defect-correction cycles run by the graph-driven loop
 };
+constexpr size_t kGridSyncLaunchBytes = offsetof(GridSync, error);
 
 template <typename R> struct PArgs {
   const typename cplx_t<R>::type *U;
@@ -33,7 +38,11 @@ template <typename R> struct PArgs {
 // with_resid = 0: iterations only, from the caller-initialised state.
 template <typename R> int launch_persistent(const PArgs<R> &pa, int with_resid, cudaStream_t st);
 
-// Optional event timing of persistent launches (for roofline accounting).
+// Optional timing of persistent launches (for roofline accounting): every
+// block stamps the device global timer at entry and exit, and a one-thread
+// kernel after the launch folds (last exit - first entry) and the iterations
+// into a device accumulator (works inside CUDA graphs, where events cannot be
+// recorded in a conditional body).
 struct PersistProfile {
   bool on;
   double ms;
@@ -41,8 +50,14 @@ struct PersistProfile {
   double site_rhs_iters;  // sum over launches of iterations * V * b
 };
 PersistProfile &persist_profile();
-// Called after the stream has been synchronised: folds the recorded launches in.
+// Called after the stream has been synchronised: folds the device accumulator in.
 void persist_profile_flush(cudaStream_t st);
+// Enqueue the accounting kernel for the launch that just used `gs` (profiling on).
+int persist_account(const GridSync *gs, double site_rhs, cudaStream_t st);
+// Kernels launched by device-driven graph loops (counted on the device).
+unsigned long long device_launch_count();
+// Pointer to the device counter of graph-launched kernels.
+unsigned long long *device_launch_counter();
 
 // Launch one block at a barrier that expects two (the peer never arrives);
 // reports whether the bounded wait gave up and the barrier's error word.

@@ -10,6 +10,7 @@
 // last block of the reducing kernel, so the host only polls a device-side
 // active-column count every `check_every` iterations.
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "dslash_core.cuh"
@@ -383,6 +384,247 @@ static int read_gs_error(const GridSync *gs, cudaStream_t st) {
   return DTR_OK;
 }
 
+// ------------------------------------------------ graph-driven mixed solve
+// The whole defect-correction loop of the mixed solver as ONE CUDA graph: the
+// first FP64 residual, then a conditional WHILE node whose body is one cycle
+// (FP32 inner init, persistent inner BiCGStab, FP64 accumulate, FP64 true
+// residual) and ends with k_loop_cond, which sets the loop condition from the
+// number of columns still active.  No host round trip between cycles.
+
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const Scal *__restrict__ outer, GridSync *gs,
+                            unsigned int max_cycles, int first, unsigned long long *dev_launches,
+                            unsigned int body_kernels) {
+  if (threadIdx.x == 0) {
+    if (first) {
+      gs->cycles = 0;
+    } else {
+      gs->cycles += 1;
+      if (dev_launches) atomicAdd(dev_launches, (unsigned long long)body_kernels);
+    }
+    const unsigned int go = (outer->n_active > 0 && gs->error == 0 && gs->cycles < max_cycles) ? 1u : 0u;
+    cudaGraphSetConditional(h, go);
+  }
+}
+
+namespace {
+
+struct MixedState {
+  const dtr_gauge_s *gauge;
+  Geom g;
+  int b, logb;
+  double m0;
+  double2 *x;
+  const double2 *z;
+  double2 *r64;
+  KrylovVecs<float> K;
+  float2 *sv;
+  Scal *outer, *inner;
+  Reduce red;
+  GridSync *gs;
+  unsigned gd, gv;
+  double itol;
+  int maxiter, grid;
+};
+
+// One defect-correction cycle after a residual: returns the kernels it launched.
+int enqueue_inner(const MixedState &S, cudaStream_t st, int *kernels) {
+  const int64_t n = (int64_t)S.g.V * 12 * S.b;
+  k_mixed_init<<<S.gv, kBlock, 0, st>>>(S.r64, S.K.r, S.K.rhat, S.K.p, S.K.x, n, S.b, S.outer); count_launches(1);
+  k_mixed_scal_init<<<1, 64, 0, st>>>(S.outer, S.inner, S.b, S.itol * S.itol, S.maxiter); count_launches(1);
+  DTR_LAUNCH_CHECK("inner init");
+  DTR_CUDA(cudaMemsetAsync(S.gs, 0, kGridSyncLaunchBytes, st));
+  PArgs<float> pa;
+  pa.U = S.gauge->U32;
+  pa.x = S.K.x; pa.r = S.K.r; pa.rhat = S.K.rhat; pa.p = S.K.p; pa.v = S.K.v; pa.s = S.sv; pa.t = S.K.t;
+  pa.z = nullptr;
+  pa.g = S.g; pa.b = S.b; pa.logb = S.logb; pa.diag = (float)(4.0 + S.m0);
+  pa.sc = S.inner; pa.partial = S.red.partial; pa.gs = S.gs;
+  pa.max_iters = S.maxiter + 1;
+  pa.max_cycles = 1;
+  pa.grid = S.grid;
+  int rc = launch_persistent<float>(pa, 0, st);
+  if (rc) return rc;
+  *kernels = 3 + (persist_profile().on ? 1 : 0);
+  return DTR_OK;
+}
+
+struct GraphKey {
+  int device;
+  const void *U64, *U32;
+  int L[4];
+  double m0;
+  const void *x, *z, *work;
+  int b, x_is_zero, maxiter, grid, prof, pad;
+  double tol, itol;
+};
+
+struct GraphEntry {
+  GraphKey key;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  unsigned long long last_use;
+};
+
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;
+unsigned long long g_graph_tick = 0;
+unsigned long long g_graph_captures = 0, g_graph_launches = 0;
+constexpr size_t kMaxGraphs = 8;
+
+struct CaptureStreams {
+  cudaStream_t a = nullptr, b = nullptr;
+};
+thread_local CaptureStreams t_cap;
+
+int capture_streams(cudaStream_t *a, cudaStream_t *b) {
+  if (!t_cap.a) DTR_CUDA(cudaStreamCreateWithFlags(&t_cap.a, cudaStreamNonBlocking));
+  if (!t_cap.b) DTR_CUDA(cudaStreamCreateWithFlags(&t_cap.b, cudaStreamNonBlocking));
+  *a = t_cap.a;
+  *b = t_cap.b;
+  return DTR_OK;
+}
+
+// Record the graph; on any failure the capture is ended and nothing is kept.
+int capture_mixed_graph(const MixedState &S, int x_is_zero, double tol2, int maxiter, cudaGraph_t *out) {
+  cudaStream_t cs, cs2;
+  int rc = capture_streams(&cs, &cs2);
+  if (rc) return rc;
+  cudaGraph_t graph = nullptr;
+  DTR_CUDA(cudaGraphCreate(&graph, 0));
+  capture_begin();
+  int open = 0;  // captures in progress: 1 = cs, 2 = cs and cs2
+  auto bail = [&](int code) {
+    cudaGraph_t tmp = nullptr;
+    if (open >= 2) cudaStreamEndCapture(cs2, &tmp);
+    if (open >= 1) cudaStreamEndCapture(cs, &tmp);
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    capture_end();
+    return code;
+  };
+#define CAP_CHECK(call)                                                        \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) return bail(cuda_fail(e_, "graph capture: " #call)); \
+  } while (0)
+  cudaGraphConditionalHandle h;
+  CAP_CHECK(cudaGraphConditionalHandleCreate(&h, graph, 0, 0));
+  CAP_CHECK(cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  open = 1;
+  const int64_t n = (int64_t)S.g.V * 12 * S.b;
+  k_scal_init<<<1, 64, 0, cs>>>(S.outer, S.b, tol2, maxiter);
+  if (x_is_zero)
+    k_resid_zero<<<S.gv, kBlock, 0, cs>>>(S.z, S.r64, n, S.b, S.outer, S.red);
+  else
+    k_resid<double, 0><<<S.gd, kBlock, 0, cs>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
+                                                4.0 + S.m0, S.outer, S.red, 1);
+  unsigned long long *devcnt = device_launch_counter();
+  k_loop_cond<<<1, 32, 0, cs>>>(h, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 1, devcnt, 0);
+  CAP_CHECK(cudaGetLastError());
+  cudaStreamCaptureStatus stc;
+  cudaGraph_t capg = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  CAP_CHECK(cudaStreamGetCaptureInfo(cs, &stc, nullptr, &capg, &deps, nullptr, &nd));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  CAP_CHECK(cudaGraphAddNode(&cnode, capg, deps, nullptr, nd, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CAP_CHECK(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  CAP_CHECK(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  open = 2;
+  int kin = 0;
+  rc = enqueue_inner(S, cs2, &kin);
+  if (rc) return bail(rc);
+  k_mixed_accum<<<S.gv, kBlock, 0, cs2>>>(S.x, S.K.x, n, S.b, S.outer, S.inner);
+  k_resid<double, 0><<<S.gd, kBlock, 0, cs2>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
+                                               4.0 + S.m0, S.outer, S.red, 1);
+  k_loop_cond<<<1, 32, 0, cs2>>>(h, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 0, devcnt, (unsigned)(kin + 3));
+  CAP_CHECK(cudaGetLastError());
+  cudaGraph_t tmp = nullptr;
+  CAP_CHECK(cudaStreamEndCapture(cs2, &tmp));
+  open = 1;
+  CAP_CHECK(cudaStreamEndCapture(cs, &tmp));
+  open = 0;
+#undef CAP_CHECK
+  capture_end();
+  *out = graph;
+  return DTR_OK;
+}
+
+}  // namespace
+
+int graph_counters(unsigned long long *captures, unsigned long long *launches) {
+  std::lock_guard<std::mutex> lock(g_graph_mu);
+  *captures = g_graph_captures;
+  *launches = g_graph_launches;
+  return DTR_OK;
+}
+
+void graphs_release() {
+  std::lock_guard<std::mutex> lock(g_graph_mu);
+  for (auto &e : g_graphs) {
+    cudaGraphExecDestroy(e.exec);
+    cudaGraphDestroy(e.graph);
+  }
+  g_graphs.clear();
+}
+
+static int solve_mixed_graph(const MixedState &S, int x_is_zero, double tol2, int maxiter, const void *work,
+                             cudaStream_t st) {
+  GraphKey key;
+  memset(&key, 0, sizeof(key));
+  DTR_CUDA(cudaGetDevice(&key.device));
+  key.U64 = S.gauge->U64;
+  key.U32 = S.gauge->U32;
+  for (int i = 0; i < 4; ++i) key.L[i] = S.g.L[i];
+  key.m0 = S.m0;
+  key.x = S.x;
+  key.z = S.z;
+  key.work = work;
+  key.b = S.b;
+  key.x_is_zero = x_is_zero;
+  key.maxiter = maxiter;
+  key.grid = S.grid;
+  key.prof = persist_profile().on ? 1 : 0;
+  key.tol = tol2;
+  key.itol = S.itol;
+  std::lock_guard<std::mutex> lock(g_graph_mu);
+  GraphEntry *hit = nullptr;
+  for (auto &e : g_graphs)
+    if (!memcmp(&e.key, &key, sizeof(key))) hit = &e;
+  if (!hit) {
+    if (g_graphs.size() >= kMaxGraphs) {
+      size_t lru = 0;
+      for (size_t i = 1; i < g_graphs.size(); ++i)
+        if (g_graphs[i].last_use < g_graphs[lru].last_use) lru = i;
+      cudaGraphExecDestroy(g_graphs[lru].exec);
+      cudaGraphDestroy(g_graphs[lru].graph);
+      g_graphs.erase(g_graphs.begin() + lru);
+    }
+    GraphEntry e;
+    e.key = key;
+    int rc = capture_mixed_graph(S, x_is_zero, tol2, maxiter, &e.graph);
+    if (rc) return rc;
+    cudaError_t ce = cudaGraphInstantiate(&e.exec, e.graph, 0);
+    if (ce != cudaSuccess) {
+      cudaGraphDestroy(e.graph);
+      return cuda_fail(ce, "graph instantiate");
+    }
+    ++g_graph_captures;
+    g_graphs.push_back(e);
+    hit = &g_graphs.back();
+  }
+  hit->last_use = ++g_graph_tick;
+  DTR_CUDA(cudaGraphLaunch(hit->exec, st));
+  count_launches(3);  // k_scal_init, first residual, k_loop_cond (the body counts itself on the device)
+  ++g_graph_launches;
+  return DTR_OK;
+}
+
 // x (internal FP64, initial guess in / solution out), z (internal FP64)
 int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double2 *z, int b,
                    const dtr_solve_params *p, void *work, size_t work_bytes, cudaStream_t st, Scal **scal_out,
@@ -411,6 +653,26 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
   const unsigned gv = reduce_grid(n, sms);
   const int check = p->check_every > 0 ? p->check_every : 8;
   const bool persistent = p->engine == 0;
+  if (p->solver == DTR_SOLVER_MIXED_F32 && persistent && !p->no_graph) {
+    MixedState S;
+    S.gauge = gauge; S.g = g; S.b = b; S.logb = logb; S.m0 = m0; S.x = x; S.z = z;
+    S.r64 = (double2 *)w; w = align256(w + n * sizeof(double2));
+    S.K.x = (float2 *)w;    w = align256(w + n * sizeof(float2));
+    S.K.r = (float2 *)w;    w = align256(w + n * sizeof(float2));
+    S.K.rhat = (float2 *)w; w = align256(w + n * sizeof(float2));
+    S.K.p = (float2 *)w;    w = align256(w + n * sizeof(float2));
+    S.K.v = (float2 *)w;    w = align256(w + n * sizeof(float2));
+    S.K.t = (float2 *)w;    w = align256(w + n * sizeof(float2));
+    S.sv = (float2 *)w;     w = align256(w + n * sizeof(float2));
+    S.outer = outer; S.inner = inner; S.red = red; S.gs = gs; S.gd = gd; S.gv = gv;
+    S.itol = p->inner_tol > 0 ? p->inner_tol : 1e-5;
+    S.maxiter = p->maxiter;
+    S.grid = p->grid;
+    *scal_out = outer;
+    int rc = solve_mixed_graph(S, x_is_zero, p->tol * p->tol, p->maxiter, work, st);
+    if (rc) return rc;
+    return read_gs_error(gs, st);
+  }
   k_scal_init<<<1, 64, 0, st>>>(outer, b, p->tol * p->tol, p->maxiter); count_launches(1);
   DTR_LAUNCH_CHECK("scalar init");
   *scal_out = outer;
@@ -425,7 +687,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     K.t = (double2 *)w;    w = align256(w + n * sizeof(double2));
     double2 *sv = (double2 *)w; w = align256(w + n * sizeof(double2));
     if (persistent) {
-      DTR_CUDA(cudaMemsetAsync(gs, 0, sizeof(GridSync), st));
+      DTR_CUDA(cudaMemsetAsync(gs, 0, kGridSyncLaunchBytes, st));
       PArgs<double> pa;
       pa.U = gauge->U64;
       pa.x = x; pa.r = K.r; pa.rhat = K.rhat; pa.p = K.p; pa.v = K.v; pa.s = sv; pa.t = K.t; pa.z = z;
@@ -478,7 +740,6 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
       int n_active = 0;
       int rc = read_n_active(outer, st, &n_active);
       if (rc) return rc;
-      if (persistent && persist_profile().on) persist_profile_flush(st);
       if (n_active == 0) break;
       k_mixed_init<<<gv, kBlock, 0, st>>>(r64, K.r, K.rhat, K.p, K.x, n, b, outer); count_launches(1);
       k_mixed_scal_init<<<1, 64, 0, st>>>(outer, inner, b, itol * itol, p->maxiter); count_launches(1);
@@ -508,7 +769,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
         if (rc) return rc;
         DTR_CUDA(cudaMemcpyAsync(inner->iters, its.data(), sizeof(int) * b, cudaMemcpyHostToDevice, st));
       } else if (persistent) {
-        DTR_CUDA(cudaMemsetAsync(gs, 0, sizeof(GridSync), st));
+        DTR_CUDA(cudaMemsetAsync(gs, 0, kGridSyncLaunchBytes, st));
         PArgs<float> pa;
         pa.U = gauge->U32;
         pa.x = K.x; pa.r = K.r; pa.rhat = K.rhat; pa.p = K.p; pa.v = K.v; pa.s = sv; pa.t = K.t; pa.z = nullptr;

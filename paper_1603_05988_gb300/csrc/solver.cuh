@@ -34,4 +34,8 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
                    const dtr_solve_params *p, void *work, size_t work_bytes, cudaStream_t st, Scal **scal,
                    int x_is_zero = 0);
 
+// Graph-driven mixed solve: process-wide counts of captured graphs and of
+// graph launches.
+int graph_counters(unsigned long long *captures, unsigned long long *launches);
+
 }  // namespace dtr

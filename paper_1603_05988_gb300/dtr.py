@@ -33,7 +33,7 @@ _SOLVER = {"f64": SOLVER_F64, "mixed_f32": SOLVER_MIXED_F32, "fgmres_net": SOLVE
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("solver", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("inner_tol", ctypes.c_double), ("engine", ctypes.c_int),
-                ("grid", ctypes.c_int), ("net", ctypes.c_void_p), ("gmres_m", ctypes.c_int), ("pad_", ctypes.c_int)]
+                ("grid", ctypes.c_int), ("net", ctypes.c_void_p), ("gmres_m", ctypes.c_int), ("no_graph", ctypes.c_int)]
 
 
 class SolveStat(ctypes.Structure):
@@ -74,6 +74,7 @@ def _sig(name, res, args):
 _sig("dtr_last_error", ctypes.c_char_p, [])
 _sig("dtr_version", ctypes.c_char_p, [])
 _sig("dtr_kernel_launches", ctypes.c_uint64, [])
+_sig("dtr_graph_stats", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)])
 _sig("dtr_profile_persistent", _i, [_i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64),
                                     ctypes.POINTER(ctypes.c_double)])
 _sig("dtr_time_dslash", _i, [_vp, _d, _i, _i, _i, _vp, _sz, ctypes.POINTER(ctypes.c_double), _vp])
@@ -242,8 +243,16 @@ def profile_persistent(enable=-1):
 
 
 def kernel_launches():
-    """Kernels the library launched so far in this process."""
+    """Kernels the library launched so far in this process (host-launched kernels
+    plus the kernels of device-driven graph loops, which the device counts)."""
     return int(_lib.dtr_kernel_launches())
+
+
+def graph_stats():
+    """(graphs captured, graph launches) of the graph-driven mixed solver."""
+    c, l = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(_lib.dtr_graph_stats(ctypes.byref(c), ctypes.byref(l)))
+    return int(c.value), int(l.value)
 
 
 def time_dslash(gauge, m0, nrhs, prec="f32", reps=50):
@@ -269,7 +278,7 @@ _ENGINE = {"persistent": 0, "kernels": 1}
 
 
 def solve_params(tol=1e-10, maxiter=5000, solver="f64", check_every=8, inner_tol=1e-5, engine="persistent",
-                 grid=0, net=None, gmres_m=16):
+                 grid=0, net=None, gmres_m=16, graph=True):
     p = SolveParams()
     _lib.dtr_solve_params_default(ctypes.byref(p))
     p.tol, p.maxiter, p.solver, p.check_every, p.inner_tol = tol, maxiter, _SOLVER[solver], check_every, inner_tol
@@ -277,6 +286,7 @@ def solve_params(tol=1e-10, maxiter=5000, solver="f64", check_every=8, inner_tol
     p.grid = int(grid)
     p.net = net._h.value if net is not None else None
     p.gmres_m = int(gmres_m)
+    p.no_graph = 0 if graph else 1
     return p
 
 

@@ -138,6 +138,39 @@ def test_solve_initial_guess_and_zero_rhs(dtr):
     assert st[0]["iterations"] == 0              # exact guess: nothing to do
 
 
+@pytest.mark.parametrize("dims,nrhs", [((4, 4, 4, 4), 8), ((8, 8, 8, 8), 16)])
+def test_mixed_graph_matches_host_loop(dtr, dims, nrhs):
+    """The CUDA-graph solve (device-driven WHILE loop over defect-correction
+    cycles) runs the same kernels in the same order as the host-driven loop:
+    bit-identical solutions and iteration counts."""
+    import torch
+    U, lat, g = _setup(dtr, dims, 0.5, -0.4, 1000)
+    Z = noise.noise_vectors(dims, 7, 1, 16, False, 0, nrhs)
+    z = torch.from_numpy(np.ascontiguousarray(Z.T)).cuda()
+    outs = []
+    for graph in (False, True):
+        p = dtr.solve_params(tol=1e-10, solver="mixed_f32", graph=graph)
+        y, st = dtr.solve_batch(g, -0.4, z, params=p)
+        outs.append((_cpu(y), [s["iterations"] for s in st], [s["restarts"] for s in st]))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1] and outs[0][2] == outs[1][2]
+    A = wilson.explicit(U, dims, -0.4)
+    res = np.linalg.norm(Z - A @ outs[1][0].T, axis=0) / np.linalg.norm(Z, axis=0)
+    assert np.all(res <= 1e-10), res
+
+
+def test_mixed_graph_not_converged_reports(dtr):
+    """An iteration cap ends the graph's loop: DTR_ENOTCONV with the statistics written."""
+    import torch
+    dims = (4, 4, 4, 4)
+    U, lat, g = _setup(dtr, dims, 0.5, -0.4, 1000)
+    Z = noise.noise_vectors(dims, 1, 0, 2, False, 0, 2)
+    p = dtr.solve_params(tol=1e-12, maxiter=3, solver="mixed_f32")
+    y, st = dtr.solve_batch(g, -0.4, torch.from_numpy(np.ascontiguousarray(Z.T)).cuda(), params=p,
+                            allow_notconv=True)
+    assert not st[0]["converged"] and st[0]["iterations"] <= 8
+
+
 def test_barrier_timeout_is_reported(dtr):
     """A barrier whose peer never arrives gives up within its budget and raises
     the error word (the solver maps it to DTR_ETIMEOUT); the context stays usable."""
@@ -228,6 +261,28 @@ def test_trace_mixed_matches_fp64(dtr, cfg1):
         outs.append(dtr.trace_estimate(c["g"], c["m0"], D, p))
     assert np.abs(outs[0]["samples"] - outs[1]["samples"]).max() <= 1e-8 * np.abs(outs[0]["samples"]).max()
     assert abs(outs[0]["trace"] - outs[1]["trace"]) <= 1e-10 * abs(outs[0]["trace"])
+
+
+def test_trace_graph_captured_once_and_reused(dtr, cfg1):
+    """Repeated trace runs on one workspace reuse one captured graph; the
+    kernels of its device-driven loop are counted on the device."""
+    c = cfg1
+    D = dtr.defl_create(c["lat"], c["V"], c["lam"])
+    p = dtr.trace_params(seed=9, n_z0=1, ncolors=16, nvec=16, block=16,
+                         solve=dtr.solve_params(tol=1e-10, solver="mixed_f32"))
+    ws = dtr.TraceWorkspace(c["g"], D, p)
+    dtr.trace_estimate(c["g"], c["m0"], D, p, workspace=ws)
+    c0, l0 = dtr.graph_stats()
+    k0 = dtr.kernel_launches()
+    for r in range(1, 4):
+        p.z0_first = r
+        out = dtr.trace_estimate(c["g"], c["m0"], D, p, workspace=ws)
+        assert out["all_converged"]
+    c1, l1 = dtr.graph_stats()
+    assert c1 == c0 and l1 - l0 == 3
+    # per run: pre-part (3) + at least one cycle body (init, scal init, persistent, accumulate,
+    # residual, loop condition), plus the estimator's own kernels
+    assert dtr.kernel_launches() - k0 >= 3 * (3 + 6)
 
 
 def test_trace_hp_projection_matches_generic(dtr, cfg1):
