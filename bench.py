@@ -4,11 +4,14 @@ on the 8^4 Wilson-Dirac workload: eps 0.7, m0 -0.6, 16-colour hierarchical
 probing per Z4 vector z0, blocks of 16 right-hand sides per launch, k = 100
 FP64 deflation vectors, solves to a true relative residual of 1e-10.
 
-One step = one z0 run of the whole path (noise + HP mask, deflation
-projection, 16 batched solves, FP64 z^H y reductions and run statistics) =
-16 right-hand sides.  Metric: right-hand sides solved per second (whole job),
-plus the variance x time figure of merit (time to a 1e-3 relative trace error)
-for the mixed-precision path and for the plain FP64 path on the same seeds.
+One step = one wave of L z0 runs of the whole path (noise + HP mask,
+deflation projection, 16 batched solves per run, FP64 z^H y reductions and run
+statistics) = 16 L right-hand sides, where L (runs in flight at once, each on
+its own stream and SM share; every solve is still one 16-RHS block) is chosen
+by the library's autotuner before the timed region.  Metric: right-hand sides
+solved per second (whole job), plus the variance x time figure of merit (time
+to a 1e-3 relative trace error) for the mixed-precision path and for the plain
+FP64 path (autotuned the same way) on the same seeds.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -50,6 +53,7 @@ def parse():
                     help="cap on setup eigensolver iterations (deflation-space quality; untimed)")
     ap.add_argument("--skip-hbm", action="store_true", help="skip the 32^3x64 half-precision stencil measurement")
     ap.add_argument("--cpu-sample-rhs", type=int, default=1, help="RHS in the CPU-oracle baseline sample")
+    ap.add_argument("--lanes", type=int, default=0, help="z0 runs in flight per step (0 = autotune)")
     return ap.parse_args()
 
 
@@ -201,26 +205,37 @@ def main():
     t_setup = time.perf_counter() - t0
     defl = dtr.defl_create(lat, V, lam, prec=w.defl_prec)
 
-    def params(solver, z0):
-        return dtr.trace_params(seed=w.noise_seed, z0_first=z0, n_z0=1, ncolors=w.ncolors, nvec=w.ncolors,
-                                block=w.block, solve=dtr.solve_params(tol=w.tol, solver=solver))
+    def params(solver, z0, lanes):
+        return dtr.trace_params(seed=w.noise_seed, z0_first=z0, n_z0=lanes, ncolors=w.ncolors, nvec=w.ncolors,
+                                block=w.block, solve=dtr.solve_params(tol=w.tol, solver=solver), lanes=lanes)
 
-    wss = {s: dtr.TraceWorkspace(gauge, defl, params(s, 0)) for s in {args.solver, "f64"}}
+    # launch shape: the library's autotuner times 1, 2, 4, 8 lanes (untimed setup)
+    tune = {}
+    for s_ in (args.solver, "f64"):
+        if s_ in tune:
+            continue
+        if args.lanes > 0:
+            tune[s_] = {"lanes": args.lanes, "block": w.block, "rhs_per_s": None, "table": [], "forced": True}
+        else:
+            tune[s_] = dtr.trace_autotune(gauge, w.m0, defl, params(s_, 0, 1), reps=3 if s_ == args.solver else 1)
+    lanes = {s_: t["lanes"] for s_, t in tune.items()}
+    wss = {s_: dtr.TraceWorkspace(gauge, defl, params(s_, 0, lanes[s_])) for s_ in lanes}
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     base = rank * 1000003
 
     def run_steps(solver, nsteps, first, timed):
+        L = lanes[solver]
         ms, traces, iters = [], [], 0
         for i in range(nsteps):
             flush.fill_(i & 0xFF)                       # evict L2 between timed steps
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            out = dtr.trace_estimate(gauge, w.m0, defl, params(solver, first + i), workspace=wss[solver])
+            out = dtr.trace_estimate(gauge, w.m0, defl, params(solver, first + i * L, L), workspace=wss[solver])
             e1.record()
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
-            traces.append(out["trace_runs"][0])
+            traces.extend(out["trace_runs"])
             iters += out["iterations"]
             if not out["all_converged"] or out["max_true_residual"] > w.tol:
                 raise RuntimeError("step did not converge: %r" % (out["max_true_residual"],))
@@ -238,13 +253,14 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
+    L = lanes[args.solver]
     # warm-up
     run_steps(args.solver, args.warmup, base + 900000, False)
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = dtr.kernel_launches()
-    dtr.profile_persistent(1)                          # event-time every persistent solver launch
+    dtr.profile_persistent(1)                          # device-timed persistent solver launches
     torch.cuda.nvtx.range_push("timed")
     ms, traces, iters = run_steps(args.solver, args.steps, base, True)
     torch.cuda.nvtx.range_pop()
@@ -253,7 +269,7 @@ def main():
     barrier()
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(ms))
-    rhs_per_step = w.ncolors
+    rhs_per_step = w.ncolors * L
     value = rhs_per_step * args.steps * world / (total_ms / 1e3)
 
     # end-to-end through the public calls from host-resident inputs (host wall
@@ -266,7 +282,8 @@ def main():
     defl_e = dtr.defl_create(lat, V_host, lam_host, prec=w.defl_prec)
     t_up = time.perf_counter() - t0
     for i in range(args.steps):
-        out = dtr.trace_estimate(gauge_e, w.m0, defl_e, params(args.solver, base + i), workspace=wss[args.solver])
+        out = dtr.trace_estimate(gauge_e, w.m0, defl_e, params(args.solver, base + i * L, L),
+                                 workspace=wss[args.solver])
         _ = out["samples"].sum()
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
@@ -277,40 +294,53 @@ def main():
     barrier()
     t0 = time.perf_counter()
     for i in range(args.steps):
-        out = dtr.trace_estimate(gauge, w.m0, defl, params(args.solver, base + i), workspace=wss[args.solver])
+        out = dtr.trace_estimate(gauge, w.m0, defl, params(args.solver, base + i * L, L), workspace=wss[args.solver])
         _ = out["samples"].sum()
     torch.cuda.synchronize()
     e2e_res_value = rhs_per_step * args.steps * world / max_over_ranks(time.perf_counter() - t0)
 
     # plain FP64 path on the same seeds (reference GPU path of the metric)
-    nf = min(args.f64_steps, args.steps)
+    L64 = lanes["f64"]
+    nf = max(1, min(args.f64_steps, (args.steps * L) // L64))
     run_steps("f64", 1, base + 900000, False)
     ms64, traces64, iters64 = run_steps("f64", nf, base, True)
-    value64 = rhs_per_step * nf / (sum(ms64) / 1e3)
-    trace_diff = max(abs(a - b) / abs(b) for a, b in zip(traces[:nf], traces64))
+    value64 = w.ncolors * L64 * nf / (sum(ms64) / 1e3)
+    ncmp = min(len(traces), len(traces64))
+    trace_diff = max(abs(a - b) / abs(b) for a, b in zip(traces[:ncmp], traces64[:ncmp]))
 
-    # variance x time: Var_T over the timed runs, t_run the mean step time
+    # variance x time: Var_T over the timed runs, t_run the mean time per run
     tr_mean = complex(np.mean(traces))
     var_T = float(np.sum(np.abs(np.array(traces) - tr_mean) ** 2) / (len(traces) - 1))
-    t_run = (total_ms / args.steps) / 1e3
-    t_run64 = (sum(ms64) / nf) / 1e3
+    t_run = (total_ms / (args.steps * L)) / 1e3
+    t_run64 = (sum(ms64) / (nf * L64)) / 1e3
     ttr = t_run * var_T / (1e-3 * abs(tr_mean)) ** 2
     ttr64 = t_run64 * var_T / (1e-3 * abs(tr_mean)) ** 2
 
     # roofline of the dominant kernel: the persistent BiCGStab kernel (one
-    # cooperative launch per inner solve), event-timed inside the timed region;
+    # cooperative launch per inner solve), timed inside the timed region by
+    # device global-timer stamps (first block entry to last block exit; the
+    # launches sit in CUDA-graph loop bodies, where events cannot be recorded);
     # algorithmic FP32 flops per site, RHS and iteration: two stencils
     # (2 x 1368) plus the fused vector work (12 complex x 104 flops)
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12          # TFLOP/s: SMs x FP32 lanes x FMA x max clock
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32_peak = sms * 128 * 2 * 2.07e9 / 1e12          # TFLOP/s: SMs x FP32 lanes x FMA x max clock
     flop_per_unit = 2 * 1368.0 + 12 * 104.0
     pms = prof["ms"] / max(prof["launches"], 1)
     pflops = prof["site_rhs_iterations"] * flop_per_unit / max(prof["launches"], 1)
     achieved = pflops / (pms / 1e3) / 1e12 if pms > 0 else 0.0
-    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-            "traffic": None, "kernel": "k_bicgstab_persistent<float,512> (FP32 inner solve, 16 RHS, 8^4, L2-resident)",
+    grid = sms // L if L > 1 else sms                   # CTAs (one per SM) of one launch
+    share = grid / sms
+    agg = prof["site_rhs_iterations"] * flop_per_unit / (total_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak * share, "unit": "TFLOP/s",
+            "frac": achieved / (fp32_peak * share), "traffic": None,
+            "kernel": "k_bicgstab_persistent<float,512> (FP32 inner solve, 16 RHS, 8^4, L2-resident)",
             "avg_launch_ms": pms, "launches": prof["launches"], "flops_per_launch": pflops,
-            "peak_note": "FP32 peak derived from 152 SMs x 128 lanes x 2 flop x 2.07 GHz (of nominal clocks)",
-            "share_note": "share of GPU time in the timed region: see profiles/launches_wilson8x8x8x8_hp16x256_k100.md"}
+            "ctas_per_launch": grid, "concurrent_launches": L,
+            "peak_note": "FP32 peak = %d SMs x 128 lanes x 2 flop x 2.07 GHz (of nominal clocks) = %.1f TFLOP/s, "
+                         "times the launch's SM share %d/%d" % (sms, fp32_peak, grid, sms),
+            "aggregate": {"achieved": agg, "peak": fp32_peak, "frac": agg / fp32_peak,
+                          "note": "all persistent-kernel flops in the timed region / timed wall time"},
+            "share_note": "share of GPU time in the timed region: profiles/launches_wilson8x8x8x8_hp16x256_k100.md"}
 
     # the stencil core alone at the bench's shape, and the half-precision stencil
     # on a lattice far larger than L2 (HBM roofline)
@@ -353,13 +383,17 @@ def main():
             "data": "synthetic (random SU(3) links, seeded)",
             "config": {"workload": WORKLOAD, "lattice": list(w.dims), "eps": w.eps, "m0": w.m0,
                        "rhs_per_step": rhs_per_step, "block": w.block, "ncolors": w.ncolors, "k": w.k,
+                       "lanes": L, "z0_runs_per_step": L,
+                       "autotune": {s_: {"lanes": t["lanes"], "table": [(c["lanes"], round(c["rhs_per_s"]))
+                                                                        for c in t["table"]]}
+                                    for s_, t in tune.items()},
                        "defl_prec": w.defl_prec, "tol": w.tol, "solver": args.solver,
                        "l2": "flushed (256 MiB write) before every timed step",
                        "deflation_space": "subspace iteration on (g5 A)^-1: %d its, max rel residual %.2e, "
                                           "setup %.1f s (untimed)" % (eit, float(np.max(eres)), t_setup)},
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": up_bytes / args.steps,
-                    "d2h_bytes_per_step": rhs_per_step * 16 + scal_bytes,
+                    "d2h_bytes_per_step": rhs_per_step * 16 + scal_bytes * L,
                     "upload_s": t_up,
                     "note": "host wall clock: dtr_make_gauge + dtr_defl_create from host arrays (links %d B, "
                             "V + lambda %d B; h2d_bytes_per_step = that / steps), then %d dtr_trace_estimate "
@@ -373,7 +407,7 @@ def main():
             "roofline_stencil_bf16_hbm": roof_hbm,
             "cpu_baseline": cpu,
             "fp64_path": {"value": value64, "unit": UNIT, "steps": nf, "ms_per_step": sum(ms64) / nf,
-                          "iterations_per_rhs": iters64 / (nf * rhs_per_step),
+                          "lanes": L64, "iterations_per_rhs": iters64 / (nf * w.ncolors * L64),
                           "max_rel_trace_diff_vs_mixed": trace_diff},
             "iterations_per_rhs": iters / (args.steps * rhs_per_step),
             "variance_x_time": {"trace": [tr_mean.real, tr_mean.imag], "var_T": var_T, "runs": len(traces),

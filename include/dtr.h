@@ -315,6 +315,12 @@ typedef struct {
   int block;           /* right-hand sides solved per launch */
   int use_x0;          /* start each solve from the deflated solution A_D^-1 z */
   dtr_solve_params solve;
+  int lanes;           /* blocks in flight at once (0 or 1 = one at a time): each lane has its own
+                          stream and workspace slice, and a solve whose grid is 0 runs on
+                          (SMs / lanes) CTAs, so independent blocks share the GPU.  Used by the
+                          persistent engine with the graph-driven mixed solver or the FP64 solver;
+                          otherwise one lane.  Results do not depend on the lane count. */
+  int pad_;
 } dtr_trace_params;
 
 typedef struct {
@@ -344,10 +350,36 @@ typedef struct {
  * of probing vectors: generate z = z0_r .* z_h, project onto the deflation
  * space, solve A y = z, reduce t_j = z^H y - d_j in FP64; Trace_r = T_D +
  * mean_j t_j.  defl may be NULL (no deflation, T_D = 0).  work: device
- * workspace of dtr_trace_workspace_bytes bytes.  Synchronises `stream`. */
+ * workspace of dtr_trace_workspace_bytes bytes (it grows with lanes).  Waits for
+ * the work already queued on `stream`, and returns with all its own work done. */
 size_t dtr_trace_workspace_bytes(dtr_gauge g, dtr_defl d, const dtr_trace_params *p);
 int dtr_trace_estimate(dtr_gauge g, double m0, dtr_defl d, const dtr_trace_params *p,
                        void *work, size_t work_bytes, dtr_trace_result *res, void *stream);
+
+/* ------------------------------------------------------------- autotuner */
+typedef struct {
+  int lanes;                  /* chosen blocks in flight (trace_params.lanes) */
+  int block;                  /* chosen right-hand sides per block (trace_params.block) */
+  double rhs_per_s;           /* its measured throughput */
+  int n_tried;                /* candidates timed (table below, in the order tried) */
+  int cached;                 /* 1 if returned from the cache without timing */
+  int table_lanes[16];
+  int table_block[16];
+  double table_rhs_per_s[16];
+} dtr_tune_result;
+
+/* Pick the launch shape of dtr_trace_estimate for this problem by timing it:
+ * every candidate lane count (1, 2, 4, 8), and every RHS block (8, 16, 32, 64)
+ * if p->block <= 0 (else p->block only), runs one warm-up and `reps` timed
+ * waves of real trace estimates (lanes blocks each, on z0 runs reserved for
+ * tuning) on `stream`; the fastest in RHS solves per second wins.  The choice
+ * is cached per (device, lattice, k, solver, engine, graph use, ncolors, nvec,
+ * block, dilution); force = 1 re-times.  work must hold
+ * dtr_trace_autotune_workspace_bytes bytes (candidates that do not fit are
+ * skipped).  The caller then sets p->lanes and p->block from the result. */
+size_t dtr_trace_autotune_workspace_bytes(dtr_gauge g, dtr_defl d, const dtr_trace_params *p);
+int dtr_trace_autotune(dtr_gauge g, double m0, dtr_defl d, const dtr_trace_params *p, int reps, int force,
+                       void *work, size_t work_bytes, dtr_tune_result *out, void *stream);
 
 #ifdef __cplusplus
 }

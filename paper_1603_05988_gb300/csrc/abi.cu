@@ -41,6 +41,9 @@ int cuda_fail(cudaError_t e, const char *what) {
 }
 
 size_t trace_workspace_bytes(const dtr_gauge_s *g, const dtr_defl_s *D, const dtr_trace_params *p);
+size_t tune_workspace_bytes(const dtr_gauge_s *g, const dtr_defl_s *D, const dtr_trace_params *p);
+int trace_autotune(const dtr_gauge_s *g, double m0, const dtr_defl_s *D, const dtr_trace_params *p, int reps,
+                   int force, void *work, size_t work_bytes, dtr_tune_result *out, cudaStream_t st);
 int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, const dtr_trace_params *p, void *work,
                    size_t work_bytes, dtr_trace_result *res, cudaStream_t st);
 
@@ -643,6 +646,22 @@ int dtr_trace_estimate(dtr_gauge g, double m0, dtr_defl d, const dtr_trace_param
   int rc = check_trace_params(g, d, p);
   if (rc) return rc;
   return trace_estimate(g, m0, d, p, work, work_bytes, res, (cudaStream_t)stream);
+}
+
+size_t dtr_trace_autotune_workspace_bytes(dtr_gauge g, dtr_defl d, const dtr_trace_params *p) {
+  if (!g || !p || p->block > 64) return 0;
+  return tune_workspace_bytes(g, d, p);
+}
+
+int dtr_trace_autotune(dtr_gauge g, double m0, dtr_defl d, const dtr_trace_params *p, int reps, int force,
+                       void *work, size_t work_bytes, dtr_tune_result *out, void *stream) {
+  if (!g || !p || !work || !out) return fail(DTR_EINVAL, "null argument");
+  if (p->block > 64) return fail(DTR_EINVAL, "block must be <= 64 (or <= 0 to tune it)");
+  dtr_trace_params q = *p;
+  if (q.block <= 0) q.block = 16;  // for the parameter checks only
+  int rc = check_trace_params(g, d, &q);
+  if (rc) return rc;
+  return trace_autotune(g, m0, d, p, reps, force, work, work_bytes, out, (cudaStream_t)stream);
 }
 
 }  // extern "C"

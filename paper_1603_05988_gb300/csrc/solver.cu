@@ -625,10 +625,24 @@ static int solve_mixed_graph(const MixedState &S, int x_is_zero, double tol2, in
   return DTR_OK;
 }
 
+bool solve_can_run_async(const dtr_solve_params *p) {
+  if (p->engine != 0) return false;
+  return p->solver == DTR_SOLVER_BICGSTAB_F64 || (p->solver == DTR_SOLVER_MIXED_F32 && !p->no_graph);
+}
+
+int *solver_error_word(void *work) {
+  char *w = align256((char *)work);
+  w = align256(w + 256);
+  w = align256(w + (size_t)kMaxGrid * 5 * 64 * sizeof(double2));
+  w = align256(w + sizeof(Scal));
+  w = align256(w + sizeof(Scal));
+  return &((GridSync *)w)->error;
+}
+
 // x (internal FP64, initial guess in / solution out), z (internal FP64)
 int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double2 *z, int b,
                    const dtr_solve_params *p, void *work, size_t work_bytes, cudaStream_t st, Scal **scal_out,
-                   int x_is_zero) {
+                   int x_is_zero, int async) {
   const Geom g = geom_of(gauge->lat);
   const int64_t n = (int64_t)g.V * 12 * b;
   if (work_bytes < solver_scratch_bytes(g.V, b, p->solver, p->gmres_m))
@@ -671,7 +685,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     *scal_out = outer;
     int rc = solve_mixed_graph(S, x_is_zero, p->tol * p->tol, p->maxiter, work, st);
     if (rc) return rc;
-    return read_gs_error(gs, st);
+    return async ? DTR_OK : read_gs_error(gs, st);
   }
   k_scal_init<<<1, 64, 0, st>>>(outer, b, p->tol * p->tol, p->maxiter); count_launches(1);
   DTR_LAUNCH_CHECK("scalar init");
@@ -698,7 +712,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
       pa.grid = p->grid;
       int rc = launch_persistent<double>(pa, 1, st);
       if (rc) return rc;
-      return read_gs_error(gs, st);
+      return async ? DTR_OK : read_gs_error(gs, st);
     }
     for (int cycle = 0; cycle <= kMaxRestarts; ++cycle) {
       k_resid<double, 1><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, K.r, K.rhat, K.p, g, b, logb, 4.0 + m0, outer, red,

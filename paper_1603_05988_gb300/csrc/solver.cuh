@@ -30,9 +30,17 @@ size_t solver_scratch_bytes(int64_t V, int b, int solver, int gmres_m = 16);
 // initial guess on entry.  *scal receives the device pointer of the final
 // per-column statistics (inside `work`).
 // x_is_zero: the caller guarantees x == 0 on entry (skips one FP64 stencil).
+// async: with the persistent engine (FP64, or the graph-driven mixed solver)
+// return as soon as the work is queued, without synchronising `st`; the caller
+// reads *solver_error_word(work) after synchronising (non-zero = a grid barrier
+// timed out, DTR_ETIMEOUT).  Other solvers synchronise regardless.
 int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double2 *z, int b,
                    const dtr_solve_params *p, void *work, size_t work_bytes, cudaStream_t st, Scal **scal,
-                   int x_is_zero = 0);
+                   int x_is_zero = 0, int async = 0);
+// True if solve_internal honours `async` for these parameters.
+bool solve_can_run_async(const dtr_solve_params *p);
+// Device address of the solver's sticky barrier error word inside `work`.
+int *solver_error_word(void *work);
 
 // Graph-driven mixed solve: process-wide counts of captured graphs and of
 // graph launches.

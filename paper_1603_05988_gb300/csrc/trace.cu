@@ -36,10 +36,21 @@ __global__ void __launch_bounds__(kBlock) k_zdot(const double2 *__restrict__ Z, 
 
 static size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
+constexpr int kMaxLanes = 8;
+
 struct TraceLayout {
-  int b;
-  size_t vec, zdot_red, solver, defl, hp, sites, small, total;
+  int b, lanes;
+  size_t vec, zdot_red, solver, defl, hp, sites, small, lane, total;
 };
+
+// Lanes actually used: concurrency needs a solver that can run without
+// synchronising the host.
+static int trace_lanes(const dtr_trace_params *p) {
+  int l = p->lanes < 1 ? 1 : p->lanes;
+  if (l > kMaxLanes) l = kMaxLanes;
+  if (l > 1 && !solve_can_run_async(&p->solve)) l = 1;
+  return l;
+}
 
 static TraceLayout trace_layout(const dtr_gauge_s *g, const dtr_defl_s *D, const dtr_trace_params *p) {
   TraceLayout L;
@@ -54,12 +65,56 @@ static TraceLayout trace_layout(const dtr_gauge_s *g, const dtr_defl_s *D, const
   L.sites = hp ? al((size_t)V * sizeof(int)) : 0;
   const int k = D ? D->k : 0;
   L.small = al(3 * 64 * sizeof(double2) + (size_t)k * 64 * sizeof(double2));
-  L.total = 256 + 2 * L.vec + L.zdot_red + L.solver + L.defl + L.hp + L.sites + L.small;
+  L.lanes = trace_lanes(p);
+  L.lane = 2 * L.vec + L.zdot_red + L.solver + L.defl + L.hp + L.small;
+  L.total = 256 + L.sites + L.lanes * L.lane;
   return L;
 }
 
 size_t trace_workspace_bytes(const dtr_gauge_s *g, const dtr_defl_s *D, const dtr_trace_params *p) {
   return trace_layout(g, D, p).total;
+}
+
+// Per-lane device buffers, stream and pinned host staging.
+struct Lane {
+  cudaStream_t s = nullptr;
+  double2 *Z = nullptr, *X = nullptr;
+  Reduce red;
+  void *solver_work = nullptr, *defl_work = nullptr, *hp_work = nullptr;
+  double2 *d_dev = nullptr, *t_dev = nullptr, *terms_dev = nullptr;
+  double2 *t_h = nullptr, *terms_h = nullptr;  // pinned
+  Scal *sc_h = nullptr;                         // pinned
+  int *err_h = nullptr;                         // pinned
+  size_t terms_cap = 0;
+  int64_t G0 = 0;
+  int nb = 0;
+};
+
+// Library-owned streams and pinned staging of the extra lanes (per host thread).
+struct LanePool {
+  cudaStream_t s[kMaxLanes] = {};
+  cudaEvent_t start = nullptr;
+  double2 *t_h[kMaxLanes] = {}, *terms_h[kMaxLanes] = {};
+  Scal *sc_h[kMaxLanes] = {};
+  int *err_h[kMaxLanes] = {};
+  size_t terms_cap[kMaxLanes] = {};
+};
+static thread_local LanePool t_pool;
+
+static int lane_host_buffers(int l, int k) {
+  LanePool &P = t_pool;
+  if (!P.t_h[l]) DTR_CUDA(cudaMallocHost((void **)&P.t_h[l], 64 * sizeof(double2)));
+  if (!P.sc_h[l]) DTR_CUDA(cudaMallocHost((void **)&P.sc_h[l], sizeof(Scal)));
+  if (!P.err_h[l]) DTR_CUDA(cudaMallocHost((void **)&P.err_h[l], 4 * sizeof(int)));
+  const size_t need = (size_t)(k > 0 ? k : 1) * 64;
+  if (P.terms_cap[l] < need) {
+    if (P.terms_h[l]) cudaFreeHost(P.terms_h[l]);
+    P.terms_h[l] = nullptr;
+    P.terms_cap[l] = 0;
+    DTR_CUDA(cudaMallocHost((void **)&P.terms_h[l], need * sizeof(double2)));
+    P.terms_cap[l] = need;
+  }
+  return DTR_OK;
 }
 
 int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, const dtr_trace_params *p, void *work,
@@ -69,35 +124,56 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
   const int b = L.b;
   const Geom g = geom_of(gauge->lat);
   const int64_t n = (int64_t)g.V * 12 * b;
+  const int k = D ? D->k : 0;
+  const int nlanes = L.lanes;
+  const int sms = device_sms();
   char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
-  double2 *Z = (double2 *)w;  w += L.vec;
-  double2 *X = (double2 *)w;  w += L.vec;
-  Reduce red;
-  red.counter = (unsigned int *)w;
-  red.partial = (double2 *)(w + 256);
-  w += L.zdot_red;
-  void *solver_work = w;      w += L.solver;
-  void *defl_work = w;        w += L.defl;
-  void *hp_work = w;          w += L.hp;
-  int *sites_dev = (int *)w;  w += L.sites;
-  double2 *d_dev = (double2 *)w;
-  double2 *t_dev = d_dev + 64;
-  double2 *terms_dev = d_dev + 192;
-  DTR_CUDA(cudaMemsetAsync(red.counter, 0, 256, st));
+  int *sites_dev = (int *)w;
+  w += L.sites;
+  Lane lanes[kMaxLanes];
+  for (int l = 0; l < nlanes; ++l) {
+    Lane &ln = lanes[l];
+    char *q = w + (size_t)l * L.lane;
+    ln.Z = (double2 *)q;  q += L.vec;
+    ln.X = (double2 *)q;  q += L.vec;
+    ln.red.counter = (unsigned int *)q;
+    ln.red.partial = (double2 *)(q + 256);
+    q += L.zdot_red;
+    ln.solver_work = q;   q += L.solver;
+    ln.defl_work = q;     q += L.defl;
+    ln.hp_work = q;       q += L.hp;
+    ln.d_dev = (double2 *)q;
+    ln.t_dev = ln.d_dev + 64;
+    ln.terms_dev = ln.d_dev + 192;
+    int rc = lane_host_buffers(l, k);
+    if (rc) return rc;
+    ln.t_h = t_pool.t_h[l];
+    ln.terms_h = t_pool.terms_h[l];
+    ln.sc_h = t_pool.sc_h[l];
+    ln.err_h = t_pool.err_h[l];
+    if (nlanes == 1) {
+      ln.s = st;
+    } else {
+      if (!t_pool.s[l]) DTR_CUDA(cudaStreamCreateWithFlags(&t_pool.s[l], cudaStreamNonBlocking));
+      ln.s = t_pool.s[l];
+    }
+  }
+  // the solve of each lane runs on its share of the SMs unless the caller fixed the grid
+  dtr_solve_params sp = p->solve;
+  if (nlanes > 1 && sp.grid == 0) sp.grid = sms / nlanes > 0 ? sms / nlanes : 1;
+  auto drain = [&]() {
+    for (int l = 0; l < nlanes; ++l) cudaStreamSynchronize(lanes[l].s);
+  };
 
   const int ncols = p->nvec * (p->dilute12 ? 12 : 1);
   const int R = p->n_z0;
-  const int k = D ? D->k : 0;
   const double td = D ? D->td[0] : 0.0;
   const double td_im = D ? D->td[1] : 0.0;
   std::vector<double2> samples((size_t)R * p->nvec, make_double2(0.0, 0.0));
-  std::vector<double2> tbuf(64), termbuf((size_t)k * 64);
-  Scal sc_host;
   int64_t iters = 0, nsolves = 0;
   double maxres = 0.0;
   int all_conv = 1;
   int status = DTR_OK;
-  const int sms = device_sms();
   if (res->replay) std::memset(res->replay, 0, sizeof(double) * 2 * (size_t)R * p->nvec * (k > 0 ? k : 1));
 
   // sites grouped by colour for the HP-structured projection (host counting sort)
@@ -123,62 +199,96 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
       for (int c = 0; c < nc; ++c) pos[c] = c * (g.V / nc);
       for (int sidx = 0; sidx < g.V; ++sidx) list[pos[col[sidx]]++] = sidx;
       DTR_CUDA(cudaMemcpyAsync(sites_dev, list.data(), sizeof(int) * g.V, cudaMemcpyHostToDevice, st));
-      DTR_CUDA(cudaStreamSynchronize(st));
     }
   }
+  // the lanes start after everything queued on the caller's stream
+  if (nlanes > 1) {
+    if (!t_pool.start) DTR_CUDA(cudaEventCreateWithFlags(&t_pool.start, cudaEventDisableTiming));
+    DTR_CUDA(cudaEventRecord(t_pool.start, st));
+    for (int l = 0; l < nlanes; ++l) DTR_CUDA(cudaStreamWaitEvent(lanes[l].s, t_pool.start, 0));
+  }
+  for (int l = 0; l < nlanes; ++l) DTR_CUDA(cudaMemsetAsync(lanes[l].red.counter, 0, 256, lanes[l].s));
 
-  // run-major sequence of (run, probing column) pairs, processed in blocks
-  const int64_t total_cols = (int64_t)R * ncols;
-  for (int64_t G0 = 0; G0 < total_cols; G0 += p->block) {
-    {
-      const int nb = (int)((total_cols - G0) < p->block ? (total_cols - G0) : p->block);
-      const int64_t q0 = G0 % ncols;
-      const bool one_run = q0 + nb <= ncols;
-      launch_noise(Z, g, p->seed, p->z0_first, p->ncolors, p->dilute12, G0, ncols, nb, b, st);
-      DTR_LAUNCH_CHECK("noise");
-      if (D) {
-        int rc;
-        if (hp_ok && one_run && !p->use_x0)
-          rc = defl_project_hp(D, sites_dev, p->ncolors, p->seed, p->z0_first + G0 / ncols, q0, nb, p->dilute12, b,
-                               d_dev, res->replay ? terms_dev : nullptr, hp_work, L.hp, sms, st);
-        else
-          rc = defl_project_internal(D, Z, b, d_dev, res->replay ? terms_dev : nullptr, p->use_x0 ? X : nullptr,
-                                     nullptr, defl_work, L.defl, sms, st);
-        if (rc) return rc;
-      }
-      if (!D || !p->use_x0) DTR_CUDA(cudaMemsetAsync(X, 0, (size_t)n * sizeof(double2), st));
-      Scal *sc = nullptr;
-      int rc = solve_internal(gauge, m0, X, Z, b, &p->solve, solver_work, L.solver, st, &sc, !D || !p->use_x0);
+  // Enqueue the whole pipeline of one block of probing columns on its lane.
+  auto enqueue_block = [&](Lane &ln, int64_t G0) -> int {
+    const cudaStream_t s = ln.s;
+    const int nb = (int)((R * (int64_t)ncols - G0) < p->block ? (R * (int64_t)ncols - G0) : p->block);
+    ln.G0 = G0;
+    ln.nb = nb;
+    const int64_t q0 = G0 % ncols;
+    const bool one_run = q0 + nb <= ncols;
+    launch_noise(ln.Z, g, p->seed, p->z0_first, p->ncolors, p->dilute12, G0, ncols, nb, b, s);
+    DTR_LAUNCH_CHECK("noise");
+    if (D) {
+      int rc;
+      if (hp_ok && one_run && !p->use_x0)
+        rc = defl_project_hp(D, sites_dev, p->ncolors, p->seed, p->z0_first + G0 / ncols, q0, nb, p->dilute12, b,
+                             ln.d_dev, res->replay ? ln.terms_dev : nullptr, ln.hp_work, L.hp, sms, s);
+      else
+        rc = defl_project_internal(D, ln.Z, b, ln.d_dev, res->replay ? ln.terms_dev : nullptr,
+                                   p->use_x0 ? ln.X : nullptr, nullptr, ln.defl_work, L.defl, sms, s);
       if (rc) return rc;
-      k_zdot<<<reduce_grid(n, sms), kBlock, 0, st>>>(Z, X, n, b, D ? d_dev : nullptr, t_dev, red); count_launches(1);
-      DTR_LAUNCH_CHECK("z^H y reduction");
-      DTR_CUDA(cudaMemcpyAsync(tbuf.data(), t_dev, sizeof(double2) * b, cudaMemcpyDeviceToHost, st));
-      DTR_CUDA(cudaMemcpyAsync(&sc_host, sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
-      if (D && res->replay)
-        DTR_CUDA(cudaMemcpyAsync(termbuf.data(), terms_dev, sizeof(double2) * k * b, cudaMemcpyDeviceToHost, st));
-      DTR_CUDA(cudaStreamSynchronize(st));
-      for (int jj = 0; jj < nb; ++jj) {
-        const int64_t Gc = G0 + jj;
-        const int r = (int)(Gc / ncols);
-        const int q = (int)(Gc % ncols);
-        const int jv = p->dilute12 ? q / 12 : q;
-        double2 &s = samples[(size_t)r * p->nvec + jv];
-        s.x += tbuf[jj].x;
-        s.y += tbuf[jj].y;
-        iters += sc_host.iters[jj];
-        const double rel = sc_host.bnorm2[jj] > 0 ? std::sqrt(sc_host.rtrue2[jj] / sc_host.bnorm2[jj]) : 0.0;
-        if (rel > maxres || rel != rel) maxres = rel;
-        if (!sc_host.conv[jj]) all_conv = 0;
-        if (sc_host.flags[jj] & kFlagNaN) status = DTR_ENAN;
-        if (res->replay && D) {
-          double *rp = res->replay + 2 * (((size_t)r * p->nvec + jv) * k);
-          for (int m = 0; m < k; ++m) {
-            rp[2 * m] += termbuf[(size_t)jj * k + m].x;
-            rp[2 * m + 1] += termbuf[(size_t)jj * k + m].y;
-          }
+    }
+    if (!D || !p->use_x0) DTR_CUDA(cudaMemsetAsync(ln.X, 0, (size_t)n * sizeof(double2), s));
+    Scal *sc = nullptr;
+    int rc = solve_internal(gauge, m0, ln.X, ln.Z, b, &sp, ln.solver_work, L.solver, s, &sc, !D || !p->use_x0,
+                            nlanes > 1);
+    if (rc) return rc;
+    k_zdot<<<reduce_grid(n, sms), kBlock, 0, s>>>(ln.Z, ln.X, n, b, D ? ln.d_dev : nullptr, ln.t_dev, ln.red);
+    count_launches(1);
+    DTR_LAUNCH_CHECK("z^H y reduction");
+    DTR_CUDA(cudaMemcpyAsync(ln.t_h, ln.t_dev, sizeof(double2) * b, cudaMemcpyDeviceToHost, s));
+    DTR_CUDA(cudaMemcpyAsync(ln.sc_h, sc, sizeof(Scal), cudaMemcpyDeviceToHost, s));
+    if (D && res->replay)
+      DTR_CUDA(cudaMemcpyAsync(ln.terms_h, ln.terms_dev, sizeof(double2) * k * b, cudaMemcpyDeviceToHost, s));
+    if (nlanes > 1)
+      DTR_CUDA(cudaMemcpyAsync(ln.err_h, solver_error_word(ln.solver_work), sizeof(int), cudaMemcpyDeviceToHost, s));
+    return DTR_OK;
+  };
+  // Fold one finished block into the host records (in block order: the
+  // result does not depend on the lane count).
+  auto fold_block = [&](const Lane &ln) {
+    for (int jj = 0; jj < ln.nb; ++jj) {
+      const int64_t Gc = ln.G0 + jj;
+      const int r = (int)(Gc / ncols);
+      const int q = (int)(Gc % ncols);
+      const int jv = p->dilute12 ? q / 12 : q;
+      double2 &sm = samples[(size_t)r * p->nvec + jv];
+      sm.x += ln.t_h[jj].x;
+      sm.y += ln.t_h[jj].y;
+      iters += ln.sc_h->iters[jj];
+      const double rel = ln.sc_h->bnorm2[jj] > 0 ? std::sqrt(ln.sc_h->rtrue2[jj] / ln.sc_h->bnorm2[jj]) : 0.0;
+      if (rel > maxres || rel != rel) maxres = rel;
+      if (!ln.sc_h->conv[jj]) all_conv = 0;
+      if (ln.sc_h->flags[jj] & kFlagNaN) status = DTR_ENAN;
+      if (res->replay && D) {
+        double *rp = res->replay + 2 * (((size_t)r * p->nvec + jv) * k);
+        for (int m = 0; m < k; ++m) {
+          rp[2 * m] += ln.terms_h[(size_t)jj * k + m].x;
+          rp[2 * m + 1] += ln.terms_h[(size_t)jj * k + m].y;
         }
       }
-      nsolves += nb;
+    }
+    nsolves += ln.nb;
+  };
+
+  // run-major sequence of (run, probing column) pairs, in blocks; a wave puts
+  // one block on every lane
+  const int64_t total_cols = (int64_t)R * ncols;
+  for (int64_t G0 = 0; G0 < total_cols; G0 += (int64_t)nlanes * p->block) {
+    int used = 0;
+    for (int l = 0; l < nlanes && G0 + (int64_t)l * p->block < total_cols; ++l) {
+      const int rc = enqueue_block(lanes[l], G0 + (int64_t)l * p->block);
+      if (rc) {
+        drain();
+        return rc;
+      }
+      ++used;
+    }
+    for (int l = 0; l < used; ++l) DTR_CUDA(cudaStreamSynchronize(lanes[l].s));
+    for (int l = 0; l < used; ++l) {
+      if (nlanes > 1 && *lanes[l].err_h) return fail(DTR_ETIMEOUT, "persistent solver barrier timed out");
+      fold_block(lanes[l]);
     }
   }
 

@@ -44,7 +44,8 @@ class SolveStat(ctypes.Structure):
 class TraceParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("z0_first", ctypes.c_int64), ("n_z0", ctypes.c_int),
                 ("ncolors", ctypes.c_int), ("nvec", ctypes.c_int), ("dilute12", ctypes.c_int),
-                ("block", ctypes.c_int), ("use_x0", ctypes.c_int), ("solve", SolveParams)]
+                ("block", ctypes.c_int), ("use_x0", ctypes.c_int), ("solve", SolveParams), ("lanes", ctypes.c_int),
+                ("pad_", ctypes.c_int)]
 
 
 class TraceResult(ctypes.Structure):
@@ -54,6 +55,12 @@ class TraceResult(ctypes.Structure):
                 ("all_converged", ctypes.c_int), ("pad_", ctypes.c_int),
                 ("samples", ctypes.POINTER(ctypes.c_double)), ("trace_runs", ctypes.POINTER(ctypes.c_double)),
                 ("replay", ctypes.POINTER(ctypes.c_double))]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int), ("block", ctypes.c_int), ("rhs_per_s", ctypes.c_double),
+                ("n_tried", ctypes.c_int), ("cached", ctypes.c_int), ("table_lanes", ctypes.c_int * 16),
+                ("table_block", ctypes.c_int * 16), ("table_rhs_per_s", ctypes.c_double * 16)]
 
 
 _vp = ctypes.c_void_p
@@ -108,6 +115,9 @@ _sig("dtr_net_train_step", _i, [_vp, _vp, _d, _vp, _vp, _i, _d, _i, ctypes.POINT
 _sig("dtr_trace_workspace_bytes", _sz, [_vp, _vp, ctypes.POINTER(TraceParams)])
 _sig("dtr_trace_estimate", _i, [_vp, _d, _vp, ctypes.POINTER(TraceParams), _vp, _sz,
                                 ctypes.POINTER(TraceResult), _vp])
+_sig("dtr_trace_autotune_workspace_bytes", _sz, [_vp, _vp, ctypes.POINTER(TraceParams)])
+_sig("dtr_trace_autotune", _i, [_vp, _d, _vp, ctypes.POINTER(TraceParams), _i, _i, _vp, _sz,
+                                ctypes.POINTER(TuneResult), _vp])
 
 
 class DtrError(RuntimeError):
@@ -428,11 +438,12 @@ def deflate_project_static(defl, z, want_coeff=False):
 
 
 def trace_params(seed=0, z0_first=0, n_z0=1, ncolors=1, nvec=1, dilute12=False, block=16, use_x0=False,
-                 solve=None):
+                 solve=None, lanes=1):
     p = TraceParams()
     p.seed, p.z0_first, p.n_z0, p.ncolors, p.nvec = int(seed), int(z0_first), int(n_z0), int(ncolors), int(nvec)
     p.dilute12, p.block, p.use_x0 = int(bool(dilute12)), int(block), int(bool(use_x0))
     p.solve = solve if solve is not None else solve_params()
+    p.lanes = int(lanes)
     return p
 
 
@@ -442,6 +453,22 @@ class TraceWorkspace:
     def __init__(self, gauge, defl, params):
         self.nbytes = _lib.dtr_trace_workspace_bytes(gauge._h, defl._h if defl else None, ctypes.byref(params))
         self.buf = _workspace(self.nbytes)
+
+
+def trace_autotune(gauge, m0, defl, params, reps=3, force=False):
+    """Time the candidate launch shapes (lanes; RHS block too if params.block <= 0)
+    and return a dict with the fastest ("lanes", "block", "rhs_per_s") and the
+    table of candidates; the choice is cached per problem shape."""
+    nb = _lib.dtr_trace_autotune_workspace_bytes(gauge._h, defl._h if defl else None, ctypes.byref(params))
+    if nb == 0:
+        raise DtrError(DTR_EINVAL, "bad autotune parameters")
+    w = _workspace(nb)
+    r = TuneResult()
+    _check(_lib.dtr_trace_autotune(gauge._h, float(m0), defl._h if defl else None, ctypes.byref(params), int(reps),
+                                   int(bool(force)), _ptr(w), nb, ctypes.byref(r), _stream()))
+    table = [dict(lanes=r.table_lanes[i], block=r.table_block[i], rhs_per_s=r.table_rhs_per_s[i])
+             for i in range(r.n_tried)]
+    return dict(lanes=r.lanes, block=r.block, rhs_per_s=r.rhs_per_s, cached=bool(r.cached), table=table)
 
 
 def trace_estimate(gauge, m0, defl, params, workspace=None, want_samples=True, want_replay=False,

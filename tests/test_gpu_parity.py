@@ -285,6 +285,50 @@ def test_trace_graph_captured_once_and_reused(dtr, cfg1):
     assert dtr.kernel_launches() - k0 >= 3 * (3 + 6)
 
 
+@pytest.mark.parametrize("solver", ["mixed_f32", "f64"])
+def test_trace_lanes_bit_identical(dtr, cfg1, solver):
+    """Blocks solved concurrently on several lanes (own streams, workspace
+    slices and SM shares) give the same per-sample records as one lane."""
+    c = cfg1
+    D = dtr.defl_create(c["lat"], c["V"], c["lam"])
+    outs = {}
+    for lanes, grid in ((1, 32), (4, 32), (4, 0)):
+        p = dtr.trace_params(seed=11, n_z0=6, ncolors=16, nvec=16, block=8, lanes=lanes,
+                             solve=dtr.solve_params(tol=1e-10, solver=solver, grid=grid))
+        outs[lanes, grid] = dtr.trace_estimate(c["g"], c["m0"], D, p, want_replay=True)
+    a, b = outs[1, 32], outs[4, 32]        # same grid: same reduction order, bit-identical
+    assert np.array_equal(a["samples"], b["samples"])
+    assert np.array_equal(a["replay"], b["replay"])
+    assert a["iterations"] == b["iterations"]
+    assert a["trace"] == b["trace"] and a["jk_err"] == b["jk_err"]
+    # the default grid of a lane is its share of the SMs: another summation order
+    d = outs[4, 0]
+    assert np.abs(d["samples"] - a["samples"]).max() <= 1e-9 * np.abs(a["samples"]).max()
+
+
+def test_trace_autotune_picks_fastest_measured_candidate(dtr, cfg1):
+    """The autotuner times every lane count on real trace waves, returns the
+    fastest and caches the choice for the problem shape."""
+    c = cfg1
+    D = dtr.defl_create(c["lat"], c["V"], c["lam"])
+    p = dtr.trace_params(seed=3, n_z0=1, ncolors=16, nvec=16, block=16,
+                         solve=dtr.solve_params(tol=1e-10, solver="mixed_f32"))
+    t = dtr.trace_autotune(c["g"], c["m0"], D, p, reps=2, force=True)
+    assert [e["lanes"] for e in t["table"]] == [1, 2, 4, 8]
+    assert all(e["block"] == 16 and e["rhs_per_s"] > 0 for e in t["table"])
+    assert t["rhs_per_s"] == max(e["rhs_per_s"] for e in t["table"])
+    assert t["lanes"] in (1, 2, 4, 8) and not t["cached"]
+    t2 = dtr.trace_autotune(c["g"], c["m0"], D, p)
+    assert t2["cached"] and t2["lanes"] == t["lanes"]
+    # the chosen shape runs and matches the one-lane records on the same grid
+    p1 = dtr.trace_params(seed=3, n_z0=t["lanes"], ncolors=16, nvec=16, block=16, lanes=1,
+                          solve=dtr.solve_params(tol=1e-10, solver="mixed_f32", grid=16))
+    pl = dtr.trace_params(seed=3, n_z0=t["lanes"], ncolors=16, nvec=16, block=16, lanes=t["lanes"],
+                          solve=dtr.solve_params(tol=1e-10, solver="mixed_f32", grid=16))
+    a, b = dtr.trace_estimate(c["g"], c["m0"], D, p1), dtr.trace_estimate(c["g"], c["m0"], D, pl)
+    assert np.array_equal(a["samples"], b["samples"])
+
+
 def test_trace_hp_projection_matches_generic(dtr, cfg1):
     """The HP-structured deflation projection (per-colour sums of V^H z0) and
     the generic contraction V^H [Z, g5 Z] give the same per-m terms."""
