@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--skip-hbm", action="store_true", help="skip the 32^3x64 half-precision stencil measurement")
     ap.add_argument("--cpu-sample-rhs", type=int, default=1, help="RHS in the CPU-oracle baseline sample")
     ap.add_argument("--lanes", type=int, default=0, help="z0 runs in flight per step (0 = autotune)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="host-driven solver cycles instead of the CUDA graph (same kernels and results; lets a "
+                         "profiler list the kernels of the solver loop)")
     return ap.parse_args()
 
 
@@ -207,7 +210,8 @@ def main():
 
     def params(solver, z0, lanes):
         return dtr.trace_params(seed=w.noise_seed, z0_first=z0, n_z0=lanes, ncolors=w.ncolors, nvec=w.ncolors,
-                                block=w.block, solve=dtr.solve_params(tol=w.tol, solver=solver), lanes=lanes)
+                                block=w.block, solve=dtr.solve_params(tol=w.tol, solver=solver, graph=not args.no_graph),
+                                lanes=lanes)
 
     # launch shape: the library's autotuner times 1, 2, 4, 8 lanes (untimed setup)
     tune = {}

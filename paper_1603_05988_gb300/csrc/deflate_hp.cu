@@ -18,62 +18,109 @@
 
 namespace dtr {
 
-constexpr int kHPThreads = 128;
+constexpr int kHPMaxThreads = 512;
 constexpr int kHPTile = 64;  // sites per shared-memory code tile
+constexpr int kHPEpt = 4;    // row elements (dof type a, vector m) per thread and block row chunk
 
-// partial[((split*nc + c)*12 + a)*k + m]
+// Every site's deflation rows are one contiguous run of 12 k values
+// (V[12x + a][m], row-major), so a block streams whole site runs: thread t
+// keeps the elements e = e0 + t + j T (j < kHPEpt, T = blockDim.x) of the run,
+// each with a fixed dof type a = e / k, and accumulates conj(V) z0 over the
+// block's sites of one colour (two sites in flight).  blockIdx.y picks the
+// chunk e0 of the run when 12 k > T kHPEpt.  partial[(split*nc + c) * 12k + e].
 template <typename VC>
-__global__ void __launch_bounds__(kHPThreads)
+__global__ void __launch_bounds__(kHPMaxThreads)
     k_hp_partial(const VC *__restrict__ Vd, const int *__restrict__ sites, int per_colour, int nc, int nsplit, int k,
                  uint64_t seed, int64_t run, double2 *__restrict__ partial) {
   __shared__ unsigned char codes[kHPTile * 12];
   __shared__ int tile_sites[kHPTile];
   const int c = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
-  const int m = blockIdx.y * kHPThreads + threadIdx.x;
+  const int L = 12 * k;
+  const int T = blockDim.x;
+  const int e0 = blockIdx.y * T * kHPEpt + threadIdx.x;
   const int s0 = (int)(((int64_t)per_colour * split) / nsplit);
   const int s1 = (int)(((int64_t)per_colour * (split + 1)) / nsplit);
   const int *list = sites + (int64_t)c * per_colour;
-  double2 acc[12];
+  int aj[kHPEpt];
+  double2 acc[kHPEpt];
 #pragma unroll
-  for (int a = 0; a < 12; ++a) acc[a] = make_double2(0.0, 0.0);
+  for (int j = 0; j < kHPEpt; ++j) {
+    const int e = e0 + j * T;
+    aj[j] = e < L ? e / k : -1;
+    acc[j] = make_double2(0.0, 0.0);
+  }
   for (int t0 = s0; t0 < s1; t0 += kHPTile) {
     const int nt = (s1 - t0) < kHPTile ? (s1 - t0) : kHPTile;
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nt; idx += blockDim.x) tile_sites[idx] = list[t0 + idx];
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nt * 12; idx += blockDim.x)
-      codes[idx] = (unsigned char)z4_code(seed, run, (int64_t)tile_sites[idx / 12] * 12 + (idx % 12));
-    __syncthreads();
-    if (m < k) {
-      for (int u = 0; u < nt; ++u) {
-        const int64_t i0 = (int64_t)tile_sites[u] * 12;
+    for (int tt = threadIdx.x; tt < nt; tt += T) {
+      // the 12 codes of one site: one Philox block of 128 dofs, or two if the site straddles
+      const int x = list[t0 + tt];
+      tile_sites[tt] = x;
+      const int64_t i0 = (int64_t)x * 12;
+      uint64_t w[4];
+      int64_t blk = i0 >> 7;
+      philox4x64_10((uint64_t)blk, (uint64_t)run, 0ull, 0ull, seed, 0ull, w);
 #pragma unroll
-        for (int a = 0; a < 12; ++a) {
-          const VC vv = Vd[(i0 + a) * k + m];
-          const int code = codes[u * 12 + a];
-          const double vx = vv.x, vy = vv.y;
-          // conj(v) * i^code: 0 -> (vx, -vy), 1 -> (vy, vx), 2 -> (-vx, vy), 3 -> (-vy, -vx)
-          double re = (code & 1) ? vy : vx;
-          double im = (code & 1) ? vx : -vy;
-          if (code & 2) {
-            re = -re;
-            im = -im;
-          }
-          acc[a].x += re;
-          acc[a].y += im;
+      for (int a = 0; a < 12; ++a) {
+        const int64_t i = i0 + a;
+        if ((i >> 7) != blk) {
+          blk = i >> 7;
+          philox4x64_10((uint64_t)blk, (uint64_t)run, 0ull, 0ull, seed, 0ull, w);
+        }
+        codes[tt * 12 + a] = (unsigned char)((w[(i >> 5) & 3] >> (2 * (i & 31))) & 3ull);
+      }
+    }
+    __syncthreads();
+    auto add = [&](int j, const VC vv, int code) {
+      const double vx = vv.x, vy = vv.y;
+      // conj(v) * i^code: 0 -> (vx, -vy), 1 -> (vy, vx), 2 -> (-vx, vy), 3 -> (-vy, -vx)
+      double re = (code & 1) ? vy : vx;
+      double im = (code & 1) ? vx : -vy;
+      if (code & 2) {
+        re = -re;
+        im = -im;
+      }
+      acc[j].x += re;
+      acc[j].y += im;
+    };
+    int u = 0;
+    for (; u + 1 < nt; u += 2) {
+      const VC *r0 = Vd + (int64_t)tile_sites[u] * L;
+      const VC *r1 = Vd + (int64_t)tile_sites[u + 1] * L;
+      VC v0[kHPEpt], v1[kHPEpt];
+#pragma unroll
+      for (int j = 0; j < kHPEpt; ++j) {
+        if (aj[j] >= 0) {
+          v0[j] = __ldcs(r0 + e0 + j * T);
+          v1[j] = __ldcs(r1 + e0 + j * T);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kHPEpt; ++j) {
+        if (aj[j] >= 0) {
+          add(j, v0[j], codes[u * 12 + aj[j]]);
+          add(j, v1[j], codes[(u + 1) * 12 + aj[j]]);
         }
       }
     }
-  }
-  if (m < k) {
+    if (u < nt) {
+      const VC *r0 = Vd + (int64_t)tile_sites[u] * L;
 #pragma unroll
-    for (int a = 0; a < 12; ++a) partial[(((int64_t)split * nc + c) * 12 + a) * k + m] = acc[a];
+      for (int j = 0; j < kHPEpt; ++j)
+        if (aj[j] >= 0) add(j, __ldcs(r0 + e0 + j * T), codes[u * 12 + aj[j]]);
+    }
   }
+  double2 *out = partial + ((int64_t)split * nc + c) * L;
+#pragma unroll
+  for (int j = 0; j < kHPEpt; ++j)
+    if (aj[j] >= 0) out[e0 + j * T] = acc[j];
 }
 
-// Sum over splits (fixed order).  With dilution W[(c*12 + a)*k + m] keeps every
-// dof type; without it W[(c*2 + h)*k + m] holds the upper (h = 0, a < 6) and
-// lower (h = 1) spin halves, the only combinations the columns need.
+// Sum over splits (fixed order) and over the dof types of a group.  With
+// dilution W[(c*12 + a)*k + m] keeps every dof type; without it
+// W[(c*2 + h)*k + m] holds the upper (h = 0, a < 6) and lower (h = 1) spin
+// halves, the only combinations the columns need.  Loads of one split are
+// independent (unrolled over the group's dof types).
 __global__ void k_hp_reduce(const double2 *__restrict__ partial, int nc, int nsplit, int k, int dilute12,
                             double2 *__restrict__ W) {
   const int64_t n12 = (int64_t)nc * 12 * k;
@@ -84,9 +131,29 @@ __global__ void k_hp_reduce(const double2 *__restrict__ partial, int nc, int nsp
     const int m = (int)(e % k);
     const int cg = (int)(e / k);
     const int c = cg / groups, h = cg % groups;
+    const double2 *base = partial + ((int64_t)c * 12 + h * per) * k + m;
     double2 s = make_double2(0.0, 0.0);
-    for (int sp = 0; sp < nsplit; ++sp)
-      for (int a = h * per; a < (h + 1) * per; ++a) s = cadd(s, partial[(int64_t)sp * n12 + ((int64_t)c * 12 + a) * k + m]);
+    if (per == 6) {
+      for (int sp = 0; sp < nsplit; ++sp) {
+        const double2 *q = base + (int64_t)sp * n12;
+        double2 v[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) v[a] = q[(int64_t)a * k];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) s = cadd(s, v[a]);
+      }
+    } else {
+      int sp = 0;
+      for (; sp + 3 < nsplit; sp += 4) {
+        const double2 v0 = base[(int64_t)sp * n12], v1 = base[(int64_t)(sp + 1) * n12];
+        const double2 v2 = base[(int64_t)(sp + 2) * n12], v3 = base[(int64_t)(sp + 3) * n12];
+        s = cadd(s, v0);
+        s = cadd(s, v1);
+        s = cadd(s, v2);
+        s = cadd(s, v3);
+      }
+      for (; sp < nsplit; ++sp) s = cadd(s, base[(int64_t)sp * n12]);
+    }
     W[e] = s;
   }
 }
@@ -104,18 +171,32 @@ __global__ void k_hp_finish(const double2 *__restrict__ W, int nc, int k, int b,
       const int64_t q = q0 + col;
       const int64_t j = dilute12 ? q / 12 : q;
       const int asel = dilute12 ? (int)(q % 12) : -1;
-      for (int c = 0; c < nc; ++c) {
-        const double h = (__popcll((unsigned long long)(c & j)) & 1) ? -1.0 : 1.0;
-        double2 up = make_double2(0.0, 0.0), lo = make_double2(0.0, 0.0);
-        if (asel >= 0) {
-          const double2 w = W[((int64_t)c * 12 + asel) * k + m];
-          if (asel < 6) up = w; else lo = w;
-        } else {
-          up = W[((int64_t)c * 2 + 0) * k + m];
-          lo = W[((int64_t)c * 2 + 1) * k + m];
+      constexpr int U = 8;  // colours in flight
+      for (int c0 = 0; c0 < nc; c0 += U) {
+        double2 up[U], lo[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int c = c0 + u;
+          up[u] = lo[u] = make_double2(0.0, 0.0);
+          if (c < nc) {
+            if (asel >= 0) {
+              const double2 w = W[((int64_t)c * 12 + asel) * k + m];
+              if (asel < 6) up[u] = w; else lo[u] = w;
+            } else {
+              up[u] = W[((int64_t)c * 2 + 0) * k + m];
+              lo[u] = W[((int64_t)c * 2 + 1) * k + m];
+            }
+          }
         }
-        cz = cadd(cz, cscale(cadd(up, lo), h));
-        cg = cadd(cg, cscale(csub(up, lo), h));
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int c = c0 + u;
+          if (c < nc) {
+            const double h = (__popcll((unsigned long long)(c & j)) & 1) ? -1.0 : 1.0;
+            cz = cadd(cz, cscale(cadd(up[u], lo[u]), h));
+            cg = cadd(cg, cscale(csub(up[u], lo[u]), h));
+          }
+        }
       }
     }
     C[(int64_t)col * k + m] = cz;
@@ -123,10 +204,22 @@ __global__ void k_hp_finish(const double2 *__restrict__ W, int nc, int k, int b,
   }
 }
 
+// threads of a partial block: the row chunk 12k / kHPEpt, in whole warps, at most kHPMaxThreads
+static int hp_threads(int k) {
+  int t = (12 * k + kHPEpt - 1) / kHPEpt;
+  t = (t + 31) / 32 * 32;
+  return t < kHPMaxThreads ? t : kHPMaxThreads;
+}
+static int hp_rowchunks(int k) {
+  const int per = hp_threads(k) * kHPEpt;
+  return (12 * k + per - 1) / per;
+}
+
 static int hp_split(int nc, int per_colour, int k, int sms) {
-  // about two blocks per SM; more splits make the split reduction latency-bound
-  const int mt = (k + kHPThreads - 1) / kHPThreads;
-  int ns = (2 * sms + nc * mt - 1) / (nc * mt);
+  // about two blocks per SM (at least 16 sites per block, so the split
+  // partials stay small next to the V stream)
+  const int ny = hp_rowchunks(k);
+  int ns = (2 * sms + nc * ny - 1) / (nc * ny);
   const int max_by_sites = per_colour / 16 > 0 ? per_colour / 16 : 1;
   if (ns > max_by_sites) ns = max_by_sites;
   if (ns < 1) ns = 1;
@@ -156,12 +249,13 @@ int defl_project_hp(const dtr_defl_s *D, const int *sites_by_colour, int ncolors
   double2 *W = (double2 *)w;
   w += (((size_t)ncolors * 12 * k * sizeof(double2) + 255) / 256) * 256;
   double2 *C = (double2 *)w;
-  dim3 grid(ncolors * ns, (k + kHPThreads - 1) / kHPThreads);
+  dim3 grid(ncolors * ns, hp_rowchunks(k));
+  const int nthr = hp_threads(k);
   if (D->prec == DTR_F64)
-    k_hp_partial<double2><<<grid, kHPThreads, 0, st>>>((const double2 *)D->V, sites_by_colour, per, ncolors, ns, k,
+    k_hp_partial<double2><<<grid, nthr, 0, st>>>((const double2 *)D->V, sites_by_colour, per, ncolors, ns, k,
                                                         seed, run, partial);
   else
-    k_hp_partial<float2><<<grid, kHPThreads, 0, st>>>((const float2 *)D->V, sites_by_colour, per, ncolors, ns, k, seed,
+    k_hp_partial<float2><<<grid, nthr, 0, st>>>((const float2 *)D->V, sites_by_colour, per, ncolors, ns, k, seed,
                                                        run, partial);
   count_launches(1);
   const int64_t nw = (int64_t)ncolors * 12 * k;

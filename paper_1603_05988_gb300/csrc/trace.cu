@@ -23,7 +23,22 @@ __global__ void __launch_bounds__(kBlock) k_zdot(const double2 *__restrict__ Z, 
                                                  double2 *__restrict__ out, Reduce red) {
   __shared__ double2 tot[64];
   double2 acc[1] = {make_double2(0.0, 0.0)};
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < n; e += 4 * stride) {  // four independent element pairs in flight
+    double2 z[4], y[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      z[u] = __ldcs(Z + e + u * stride);
+      y[u] = __ldcs(Y + e + u * stride);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc[0].x += z[u].x * y[u].x + z[u].y * y[u].y;
+      acc[0].y += z[u].x * y[u].y - z[u].y * y[u].x;
+    }
+  }
+  for (; e < n; e += stride) {
     const double2 z = Z[e], y = Y[e];
     acc[0].x += z.x * y.x + z.y * y.y;
     acc[0].y += z.x * y.y - z.y * y.x;

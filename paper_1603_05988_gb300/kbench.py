@@ -1,6 +1,7 @@
 """Kernel micro-benchmarks of libdtr (CUDA-event timing through the C ABI).
 
     python -m paper_1603_05988_gb300.kbench dslash --lattice 32,32,32,64 --prec bf16 --nrhs 1 --reps 20
+    python -m paper_1603_05988_gb300.kbench solve --lattice 8,8,8,8 --nrhs 16 --reps 3 [--no-graph]
 
 Large lattices take their links from the seeded 16^3x32 field repeated
 periodically (exact SU(3) matrices; the stencil's cost does not depend on
@@ -51,6 +52,30 @@ def dslash_case(gauge, dims, prec, nrhs, reps, m0=-0.75):
             "achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9, "achieved_tflops": flops / (ms * 1e-3) / 1e12}
 
 
+def solve_case(gauge, dims, nrhs, reps, m0, graph=True, grid=0):
+    """Mixed-precision solves of nrhs Z4 right-hand sides to 1e-10 (persistent
+    engine), with the persistent launches timed on the device."""
+    import time
+    import torch
+    from . import dtr
+    lat = gauge.lat
+    z = dtr.gen_noise(lat, 0, 1, 16 if nrhs <= 16 else 512, False, 0, nrhs)
+    p = dtr.solve_params(tol=1e-10, solver="mixed_f32", graph=graph, grid=grid)
+    dtr.solve_batch(gauge, m0, z, params=p)
+    dtr.profile_persistent(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        y, st = dtr.solve_batch(gauge, m0, z, params=p)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    prof = dtr.profile_persistent(0)
+    its = float(np.mean([s["iterations"] for s in st]))
+    return {"kernel": "mixed solve", "lattice": list(dims), "nrhs": nrhs, "graph": graph, "ms_per_solve": dt * 1e3,
+            "iterations_per_rhs": its, "persistent_launches": prof["launches"],
+            "persistent_ms_per_launch": prof["ms"] / max(prof["launches"], 1)}
+
+
 def dtr_pad(n):
     b = 1
     while b < n:
@@ -60,11 +85,13 @@ def dtr_pad(n):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["dslash"])
+    ap.add_argument("what", choices=["dslash", "solve"])
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--prec", default="bf16")
     ap.add_argument("--nrhs", default="1")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--m0", type=float, default=-0.6)
+    ap.add_argument("--no-graph", action="store_true")
     a = ap.parse_args(argv)
     import torch
     torch.cuda.set_device(0)
@@ -74,6 +101,12 @@ def main(argv=None):
     from . import dtr
     dims = tuple(int(x) for x in a.lattice.split(","))
     lat = dtr.make_lattice(dims)
+    if a.what == "solve":
+        from . import synth
+        g = dtr.make_gauge(lat, synth.random_su3_links(dims, 0.7, 1001))
+        for n in a.nrhs.split(","):
+            print(json.dumps(solve_case(g, dims, int(n), a.reps, a.m0, graph=not a.no_graph)), flush=True)
+        return
     g = dtr.make_gauge(lat, tiled_links(dims))
     for prec in a.prec.split(","):
         for n in a.nrhs.split(","):
