@@ -329,6 +329,32 @@ def test_trace_autotune_picks_fastest_measured_candidate(dtr, cfg1):
     assert np.array_equal(a["samples"], b["samples"])
 
 
+def test_sharded_trace_one_process_matches_library(dtr, cfg1):
+    """The sharded driver (records gathered over a process group, statistics
+    formed on the host) reproduces the library's own statistics."""
+    import socket
+    import torch.distributed as dist
+    from paper_1603_05988_gb300 import shard
+    c = cfg1
+    D = dtr.defl_create(c["lat"], c["V"], c["lam"])
+    mk = lambda z0, n: dtr.trace_params(seed=2, z0_first=z0, n_z0=n, ncolors=16, nvec=16, block=16,
+                                         solve=dtr.solve_params(tol=1e-10, solver="mixed_f32"))
+    ref = dtr.trace_estimate(c["g"], c["m0"], D, mk(0, 5))
+    sk = socket.socket()
+    sk.bind(("127.0.0.1", 0))
+    port = sk.getsockname()[1]
+    sk.close()
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=0, world_size=1)
+    try:
+        st = shard.sharded_trace_estimate(c["g"], c["m0"], D, 5, mk)
+    finally:
+        dist.destroy_process_group()
+    assert np.array_equal(st["samples"], ref["samples"])
+    assert abs(st["trace"] - ref["trace"]) <= 1e-14 * abs(ref["trace"])
+    assert abs(st["jk_err"] - ref["jk_err"]) <= 1e-12 * ref["jk_err"]
+    assert abs(st["var_runs"] - ref["var_runs"]) <= 1e-12 * ref["var_runs"]
+
+
 def test_trace_hp_projection_matches_generic(dtr, cfg1):
     """The HP-structured deflation projection (per-colour sums of V^H z0) and
     the generic contraction V^H [Z, g5 Z] give the same per-m terms."""
