@@ -320,7 +320,10 @@ typedef struct {
                           (SMs / lanes) CTAs, so independent blocks share the GPU.  Used by the
                           persistent engine with the graph-driven mixed solver or the FP64 solver;
                           otherwise one lane.  Results do not depend on the lane count. */
-  int pad_;
+  int n_gamma;         /* Gamma-insertion traces Tr(Gamma_n A^-1) estimated alongside (0..16) */
+  int gamma[16];       /* their Clifford indices n (0..15): Gamma_n = g1^n0 g2^n1 g3^n2 g4^n3 for the
+                          bits n0..n3 of n (Gamma_0 = 1, Gamma_15 = g5), chiral basis.  The same noise,
+                          solves and deflation space serve every Gamma (end of Section 5.2). */
 } dtr_trace_params;
 
 typedef struct {
@@ -344,6 +347,16 @@ typedef struct {
   double *samples;
   double *trace_runs;
   double *replay;
+  /* Gamma-insertion outputs (params n_gamma > 0), index q over params.gamma:
+   *   gamma_trace[2q..]  mean over runs of T_D^G + mean_j t_j^G, t_j^G = z^H Gamma y - z^H Gamma D z
+   *   gamma_T_D[2q..]    T_D^G = Tr(Gamma V Lambda^-1 V^H g5) = sum_m v_m^H g5 Gamma v_m / lambda_m
+   *   gamma_var_runs[q], gamma_jk_err[q]  as var_runs, jk_err
+   *   gamma_samples      optional caller-owned HOST 2 * n_gamma * n_z0 * nvec doubles (q-major) */
+  double *gamma_samples;
+  double gamma_trace[32];
+  double gamma_T_D[32];
+  double gamma_var_runs[16];
+  double gamma_jk_err[16];
 } dtr_trace_result;
 
 /* Algorithm 1 (deflatedHP) for R = n_z0 runs: for each run r and each block

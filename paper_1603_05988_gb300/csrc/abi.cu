@@ -415,6 +415,7 @@ int dtr_defl_create(dtr_lattice lat, int k, dtr_prec prec, const double *V_host,
   for (int m = 0; m < k; ++m)
     for (int64_t i = 0; i < N; ++i) rowmajor[(size_t)i * k + m] = src[(size_t)m * N + i];
   dtr_defl_s *D = new (std::nothrow) dtr_defl_s;
+  if (D) D->tdg_ok = 0u;
   if (!D) return fail(DTR_ENOMEM, "host allocation failed");
   D->lat = *lat;
   D->k = k;
@@ -632,6 +633,9 @@ static int check_trace_params(const dtr_gauge_s *g, const dtr_defl_s *D, const d
   if (p->ncolors > 1 && p->nvec > p->ncolors) return fail(DTR_EINVAL, "nvec must be <= ncolors");
   if (p->ncolors == 1 && p->nvec != 1) return fail(DTR_EINVAL, "plain Z4 noise (ncolors = 1) has nvec = 1");
   if (D && (D->lat.V != g->lat.V)) return fail(DTR_EINVAL, "deflation space built for another lattice");
+  if (p->n_gamma < 0 || p->n_gamma > 16) return fail(DTR_EINVAL, "n_gamma must be in [0, 16]");
+  for (int q = 0; q < p->n_gamma; ++q)
+    if (p->gamma[q] < 0 || p->gamma[q] > 15) return fail(DTR_EINVAL, "Gamma indices must be in [0, 15]");
   return DTR_OK;
 }
 

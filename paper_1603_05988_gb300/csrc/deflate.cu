@@ -90,13 +90,14 @@ __global__ void k_defl_reduce(const double2 *__restrict__ partial, int k, int b,
 
 // d_j = sum_m conj(C[m, j]) C[m, b+j] / lambda_m ; optional per-m terms.
 // One block per column; fixed-order block tree, so the result is reproducible.
-__global__ void k_defl_d(const double2 *__restrict__ C, const double *__restrict__ inv_lambda, int k, int b,
-                         double2 *__restrict__ d, double2 *__restrict__ terms) {
+__global__ void k_defl_d(const double2 *__restrict__ C, const double2 *__restrict__ Cr,
+                         const double *__restrict__ inv_lambda, int k, int b, double2 *__restrict__ d,
+                         double2 *__restrict__ terms) {
   __shared__ double2 sh[128];
   const int j = blockIdx.x;
   double2 acc = make_double2(0.0, 0.0);
   for (int m = threadIdx.x; m < k; m += blockDim.x) {
-    const double2 a = C[(int64_t)j * k + m], g = C[(int64_t)(b + j) * k + m];
+    const double2 a = C[(int64_t)j * k + m], g = Cr[(int64_t)(b + j) * k + m];
     const double2 t = cscale(cjmul(a, g), inv_lambda[m]);
     if (terms) terms[(int64_t)j * k + m] = t;
     acc = cadd(acc, t);
@@ -112,8 +113,94 @@ __global__ void k_defl_d(const double2 *__restrict__ C, const double *__restrict
 
 void launch_defl_d(const double2 *C, const double *inv_lambda, int k, int b, double2 *d, double2 *terms,
                    cudaStream_t st) {
-  k_defl_d<<<b, 128, 0, st>>>(C, inv_lambda, k, b, d, terms);
+  k_defl_d<<<b, 128, 0, st>>>(C, C, inv_lambda, k, b, d, terms);
   count_launches(1);
+}
+
+void launch_defl_d2(const double2 *Cl, const double2 *Cr, const double *inv_lambda, int k, int b, double2 *d,
+                    cudaStream_t st) {
+  k_defl_d<<<b, 128, 0, st>>>(Cl, Cr, inv_lambda, k, b, d, nullptr);
+  count_launches(1);
+}
+
+// GZ[(x, t, c), j] = i^-phase[s] Z[(x, s, c), j] with perm[s] = t
+__global__ void k_gamma_h(GammaMono g, const double2 *__restrict__ Z, double2 *__restrict__ GZ, int64_t n, int b) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e % b);
+    const int64_t xa = e / b;
+    const int a = (int)(xa % 12);
+    const int64_t x = xa / 12;
+    const int s = a / 3, c = a % 3;
+    const double2 v = Z[(x * 12 + s * 3 + c) * b + j];
+    const int q = (4 - g.phase[s]) & 3;
+    double2 w = v;
+    if (q == 1) w = make_double2(-v.y, v.x);
+    if (q == 2) w = make_double2(-v.x, -v.y);
+    if (q == 3) w = make_double2(v.y, -v.x);
+    GZ[(x * 12 + g.perm[s] * 3 + c) * b + j] = w;
+  }
+}
+
+void launch_gamma_h(const GammaMono &g, const double2 *Z, double2 *GZ, int64_t V, int b, cudaStream_t st) {
+  const int64_t n = V * 12 * b;
+  unsigned grid = (unsigned)((n + 255) / 256);
+  if (grid > 65535u * 8) grid = 65535u * 8;
+  k_gamma_h<<<grid, 256, 0, st>>>(g, Z, GZ, n, b);
+  count_launches(1);
+}
+
+// per (chunk of sites, Gamma, m): sum over the chunk's sites and dofs of
+// conj(v[x, s, c]) g5(s) i^phase[s] v[x, perm[s], c]   (FP64)
+template <typename VC>
+__global__ void k_defl_tdg_partial(const VC *__restrict__ Vd, int k, int64_t nsite, int nchunks, GammaSet gs,
+                                   double2 *__restrict__ part) {
+  const int chunk = blockIdx.x;
+  const int64_t x0 = (nsite * chunk) / nchunks, x1 = (nsite * (chunk + 1)) / nchunks;
+  for (int m = threadIdx.x; m < k; m += blockDim.x) {
+    double2 acc[16];
+    for (int q = 0; q < gs.n; ++q) acc[q] = make_double2(0.0, 0.0);
+    for (int64_t x = x0; x < x1; ++x) {
+      double2 v[12];
+#pragma unroll
+      for (int a = 0; a < 12; ++a) {
+        const VC vv = Vd[(x * 12 + a) * k + m];
+        v[a] = make_double2(vv.x, vv.y);
+      }
+      for (int q = 0; q < gs.n; ++q) {
+        const GammaMono g = gs.g[q];
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) {
+          const double sgn = sp < 2 ? 1.0 : -1.0;
+          const int ph = g.phase[sp];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            double2 w = v[g.perm[sp] * 3 + c];  // i^ph w
+            if (ph == 1) w = make_double2(-w.y, w.x);
+            if (ph == 2) w = make_double2(-w.x, -w.y);
+            if (ph == 3) w = make_double2(w.y, -w.x);
+            const double2 u = v[sp * 3 + c];
+            acc[q].x += sgn * (u.x * w.x + u.y * w.y);
+            acc[q].y += sgn * (u.x * w.y - u.y * w.x);
+          }
+        }
+      }
+    }
+    for (int q = 0; q < gs.n; ++q) part[((int64_t)chunk * 16 + q) * k + m] = acc[q];
+  }
+}
+
+__global__ void k_defl_tdg_reduce(const double2 *__restrict__ part, const double *__restrict__ inv_lambda, int k,
+                                  int nchunks, int ng, double2 *__restrict__ td) {
+  // one thread per Gamma, fixed order: deterministic
+  const int q = threadIdx.x;
+  if (blockIdx.x != 0 || q >= ng) return;
+  double2 t = make_double2(0.0, 0.0);
+  for (int m = 0; m < k; ++m) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int ch = 0; ch < nchunks; ++ch) s = cadd(s, part[((int64_t)ch * 16 + q) * k + m]);
+    t = cadd(t, cscale(s, inv_lambda[m]));
+  }
+  td[q] = t;
 }
 
 // x0 (internal [site][12][b]) = V diag(1/lambda) C[:, b:2b]
@@ -249,6 +336,45 @@ int defl_trace_TD(dtr_defl_s *D, cudaStream_t st) {
   if (e != cudaSuccess) return cuda_fail(e, "T_D reduction");
   D->td[0] = h;
   D->td[1] = 0.0;
+  return DTR_OK;
+}
+
+int defl_trace_TD_gamma(dtr_defl_s *D, unsigned want, cudaStream_t st) {
+  GammaSet gs;
+  gs.n = 0;
+  int ids[16];
+  for (int n = 0; n < 16; ++n)
+    if (((want >> n) & 1u) && !((D->tdg_ok >> n) & 1u)) {
+      if (!gamma_monomial(n, &gs.g[gs.n])) return fail(DTR_EINVAL, "Gamma table is not monomial");
+      ids[gs.n++] = n;
+    }
+  if (gs.n == 0) return DTR_OK;
+  const int64_t nsite = D->lat.V;
+  const int k = D->k;
+  int nch = 4 * device_sms();
+  if (nch > nsite) nch = (int)nsite;
+  double2 *part = nullptr, *td = nullptr;
+  const size_t pbytes = (((size_t)nch * 16 * k * sizeof(double2) + 255) / 256) * 256;
+  DTR_CUDA(cudaMalloc((void **)&part, pbytes + 16 * sizeof(double2)));
+  td = (double2 *)((char *)part + pbytes);
+  if (D->prec == DTR_F64)
+    k_defl_tdg_partial<double2><<<nch, 128, 0, st>>>((const double2 *)D->V, k, nsite, nch, gs, part);
+  else
+    k_defl_tdg_partial<float2><<<nch, 128, 0, st>>>((const float2 *)D->V, k, nsite, nch, gs, part);
+  count_launches(1);
+  k_defl_tdg_reduce<<<1, 32, 0, st>>>(part, D->inv_lambda, k, nch, gs.n, td);
+  count_launches(1);
+  double2 h[16];
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, td, sizeof(double2) * gs.n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(part);
+  if (e != cudaSuccess) return cuda_fail(e, "T_D of Gamma");
+  for (int q = 0; q < gs.n; ++q) {
+    D->tdg[ids[q]][0] = h[q].x;
+    D->tdg[ids[q]][1] = h[q].y;
+    D->tdg_ok |= 1u << ids[q];
+  }
   return DTR_OK;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "dtr_internal.cuh"
+#include "gamma.cuh"
 
 namespace dtr {
 
@@ -18,14 +19,25 @@ int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 
 // d_j (and per-m terms, or NULL) from C (column-major k x 2b).
 void launch_defl_d(const double2 *C, const double *inv_lambda, int k, int b, double2 *d, double2 *terms,
                    cudaStream_t st);
+// d_j = sum_m conj(Cl[m, j]) Cr[m, b + j] / lambda_m (Cl, Cr column-major k x 2b).
+void launch_defl_d2(const double2 *Cl, const double2 *Cr, const double *inv_lambda, int k, int b, double2 *d,
+                    cudaStream_t st);
+// GZ = (Gamma^H (x) 1) Z on the internal layout [site][12][b].
+void launch_gamma_h(const GammaMono &g, const double2 *Z, double2 *GZ, int64_t V, int b, cudaStream_t st);
+// T_D of every Gamma_n in `want` (bit n) not yet cached in D: sum_m v_m^H g5 Gamma v_m / lambda_m.
+int defl_trace_TD_gamma(dtr_defl_s *D, unsigned want, cudaStream_t st);
 
 // Projection of an HP block (all columns share one z0 run; columns are
 // probing indices q0 .. q0+nrhs-1) from per-colour sums of V^H z0.
 // sites_by_colour: V site indices grouped by colour, V/ncolors per colour.
 size_t defl_hp_scratch_bytes(int64_t V, int k, int b, int ncolors, int sms);
+// xf (or NULL = identity) transforms the z0 codes of every site first, so the
+// projection is that of Gamma^H z (Gamma-insertion); d_dev may then be NULL
+// (no d_j); *C_out (or NULL) receives the address of C in `work`.
 int defl_project_hp(const dtr_defl_s *D, const int *sites_by_colour, int ncolors, uint64_t seed, int64_t run,
                     int64_t q0, int nrhs, int dilute12, int b, double2 *d_dev, double2 *terms_dev, void *work,
-                    size_t work_bytes, int sms, cudaStream_t st);
+                    size_t work_bytes, int sms, cudaStream_t st, const CodeXform *xf = nullptr,
+                    double2 **C_out = nullptr);
 
 // T_D = sum_m v_m^H g5 v_m / lambda_m from the stored V (FP64 accumulation).
 int defl_trace_TD(dtr_defl_s *D, cudaStream_t st);

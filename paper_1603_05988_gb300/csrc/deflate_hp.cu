@@ -31,7 +31,7 @@ constexpr int kHPEpt = 4;    // row elements (dof type a, vector m) per thread a
 template <typename VC>
 __global__ void __launch_bounds__(kHPMaxThreads)
     k_hp_partial(const VC *__restrict__ Vd, const int *__restrict__ sites, int per_colour, int nc, int nsplit, int k,
-                 uint64_t seed, int64_t run, double2 *__restrict__ partial) {
+                 uint64_t seed, int64_t run, CodeXform xf, double2 *__restrict__ partial) {
   __shared__ unsigned char codes[kHPTile * 12];
   __shared__ int tile_sites[kHPTile];
   const int c = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(kHPMaxThreads)
       uint64_t w[4];
       int64_t blk = i0 >> 7;
       philox4x64_10((uint64_t)blk, (uint64_t)run, 0ull, 0ull, seed, 0ull, w);
+      int raw[12];
 #pragma unroll
       for (int a = 0; a < 12; ++a) {
         const int64_t i = i0 + a;
@@ -67,8 +68,10 @@ __global__ void __launch_bounds__(kHPMaxThreads)
           blk = i >> 7;
           philox4x64_10((uint64_t)blk, (uint64_t)run, 0ull, 0ull, seed, 0ull, w);
         }
-        codes[tt * 12 + a] = (unsigned char)((w[(i >> 5) & 3] >> (2 * (i & 31))) & 3ull);
+        raw[a] = (int)((w[(i >> 5) & 3] >> (2 * (i & 31))) & 3ull);
       }
+#pragma unroll
+      for (int a = 0; a < 12; ++a) codes[tt * 12 + a] = (unsigned char)((raw[xf.src[a]] + xf.add[a]) & 3);
     }
     __syncthreads();
     auto add = [&](int j, const VC vv, int code) {
@@ -161,7 +164,7 @@ __global__ void k_hp_reduce(const double2 *__restrict__ partial, int nc, int nsp
 // C (column-major k x 2b) for block columns col < nrhs (probing index q0 + col):
 // C[col] = sum_c H[c, j] sum_{a in set} W_a[c],  C[b + col] = same with g5(a)
 __global__ void k_hp_finish(const double2 *__restrict__ W, int nc, int k, int b, int nrhs, int64_t q0, int dilute12,
-                            double2 *__restrict__ C) {
+                            CodeXform xf, double2 *__restrict__ C) {
   const int64_t n = (int64_t)k * b;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int m = (int)(e % k);
@@ -170,7 +173,7 @@ __global__ void k_hp_finish(const double2 *__restrict__ W, int nc, int k, int b,
     if (col < nrhs) {
       const int64_t q = q0 + col;
       const int64_t j = dilute12 ? q / 12 : q;
-      const int asel = dilute12 ? (int)(q % 12) : -1;
+      const int asel = dilute12 ? (int)xf.dst[q % 12] : -1;  // the column's dof type after the code transform
       constexpr int U = 8;  // colours in flight
       for (int c0 = 0; c0 < nc; c0 += U) {
         double2 up[U], lo[U];
@@ -237,7 +240,8 @@ size_t defl_hp_scratch_bytes(int64_t V, int k, int b, int ncolors, int sms) {
 
 int defl_project_hp(const dtr_defl_s *D, const int *sites_by_colour, int ncolors, uint64_t seed, int64_t run,
                     int64_t q0, int nrhs, int dilute12, int b, double2 *d_dev, double2 *terms_dev, void *work,
-                    size_t work_bytes, int sms, cudaStream_t st) {
+                    size_t work_bytes, int sms, cudaStream_t st, const CodeXform *xf, double2 **C_out) {
+  const CodeXform x = xf ? *xf : code_xform_identity();
   const int64_t V = D->lat.V;
   const int k = D->k;
   if (work_bytes < defl_hp_scratch_bytes(V, k, b, ncolors, sms)) return fail(DTR_ENOMEM, "HP deflation scratch too small");
@@ -253,19 +257,20 @@ int defl_project_hp(const dtr_defl_s *D, const int *sites_by_colour, int ncolors
   const int nthr = hp_threads(k);
   if (D->prec == DTR_F64)
     k_hp_partial<double2><<<grid, nthr, 0, st>>>((const double2 *)D->V, sites_by_colour, per, ncolors, ns, k,
-                                                        seed, run, partial);
+                                                  seed, run, x, partial);
   else
     k_hp_partial<float2><<<grid, nthr, 0, st>>>((const float2 *)D->V, sites_by_colour, per, ncolors, ns, k, seed,
-                                                       run, partial);
+                                                 run, x, partial);
   count_launches(1);
   const int64_t nw = (int64_t)ncolors * 12 * k;
   k_hp_reduce<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(partial, ncolors, ns, k, dilute12, W);
   count_launches(1);
   const int64_t nk = (int64_t)k * b;
-  k_hp_finish<<<(unsigned)((nk + 127) / 128), 128, 0, st>>>(W, ncolors, k, b, nrhs, q0, dilute12, C);
+  k_hp_finish<<<(unsigned)((nk + 127) / 128), 128, 0, st>>>(W, ncolors, k, b, nrhs, q0, dilute12, x, C);
   count_launches(1);
-  launch_defl_d(C, D->inv_lambda, k, b, d_dev, terms_dev, st);
+  if (d_dev) launch_defl_d(C, D->inv_lambda, k, b, d_dev, terms_dev, st);
   DTR_LAUNCH_CHECK("HP deflation projection");
+  if (C_out) *C_out = C;
   return DTR_OK;
 }
 

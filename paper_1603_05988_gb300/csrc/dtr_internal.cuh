@@ -141,6 +141,8 @@ struct dtr_defl_s {
   void *V;            // row-major [dof][k] complex, FP64 (double2) or FP32 (float2)
   double *inv_lambda; // device, k
   double td[2];
+  double tdg[16][2];  // T_D of Gamma_n (Gamma-insertion traces), valid where tdg_ok bit n is set
+  unsigned tdg_ok;
 };
 
 namespace dtr {

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "deflate.cuh"
+#include "gamma.cuh"
 #include "reduce.cuh"
 #include "solver.cuh"
 
@@ -49,13 +50,127 @@ __global__ void __launch_bounds__(kBlock) k_zdot(const double2 *__restrict__ Z, 
   }
 }
 
+// t^G_j = sum_x sum_(s,c) conj(z[x,s,c,j]) i^phase[s] y[x,perm[s],c,j] - dG_j for up to
+// four Gammas per launch (one thread per site and column; FP64, deterministic)
+template <int NG>
+__global__ void __launch_bounds__(kBlock) k_zdot_gamma(const double2 *__restrict__ Z, const double2 *__restrict__ Y,
+                                                       int64_t V, int b, int logb, GammaSet gs, int g0,
+                                                       const double2 *__restrict__ dg, double2 *__restrict__ out,
+                                                       Reduce red) {
+  __shared__ double2 tot[NG * 64];
+  double2 acc[NG];
+#pragma unroll
+  for (int q = 0; q < NG; ++q) acc[q] = make_double2(0.0, 0.0);
+  const int64_t n = V << logb;
+  const int j = threadIdx.x & (b - 1);
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n; it += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t base = (it >> logb) * 12 * b + j;
+    double2 z[12], y[12];
+#pragma unroll
+    for (int a = 0; a < 12; ++a) {
+      z[a] = __ldcs(Z + base + (int64_t)a * b);
+      y[a] = __ldcs(Y + base + (int64_t)a * b);
+    }
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
+      if (g0 + q >= gs.n) break;
+      const GammaMono g = gs.g[g0 + q];
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp) {
+        const int ph = g.phase[sp];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          double2 w = y[g.perm[sp] * 3 + c];
+          if (ph == 1) w = make_double2(-w.y, w.x);
+          if (ph == 2) w = make_double2(-w.x, -w.y);
+          if (ph == 3) w = make_double2(w.y, -w.x);
+          const double2 u = z[sp * 3 + c];
+          acc[q].x += u.x * w.x + u.y * w.y;
+          acc[q].y += u.x * w.y - u.y * w.x;
+        }
+      }
+    }
+  }
+  if (block_reduce<NG>(acc, b, red.partial, red.counter, tot)) {
+    if ((int)threadIdx.x < b) {
+      for (int q = 0; q < NG && g0 + q < gs.n; ++q) {
+        const double2 t = tot[q * b + threadIdx.x];
+        out[(g0 + q) * 64 + threadIdx.x] = dg ? csub(t, dg[(g0 + q) * 64 + threadIdx.x]) : t;
+      }
+    }
+  }
+}
+
 static size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+static int ilog2(int b) {
+  int l = 0;
+  while ((1 << l) < b) ++l;
+  return l;
+}
+
+// Run statistics of an (R x nvec) sample record (host, FP64, fixed order):
+// Trace_r = T_D + mean_j t_j, their mean, variance over runs, delete-1
+// jackknife error of the mean (Section 6.2), variance of the samples.
+struct RunStats {
+  double2 mean;
+  std::vector<double2> tr;
+  double var_runs, jk, var_s;
+};
+
+static RunStats run_stats(const double2 *samples, int R, int nvec, double td, double td_im) {
+  RunStats o;
+  o.tr.resize(R);
+  o.mean = make_double2(0.0, 0.0);
+  for (int r = 0; r < R; ++r) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int j = 0; j < nvec; ++j) s = cadd(s, samples[(size_t)r * nvec + j]);
+    o.tr[r] = make_double2(td + s.x / nvec, td_im + s.y / nvec);
+    o.mean = cadd(o.mean, o.tr[r]);
+  }
+  o.mean = cscale(o.mean, 1.0 / R);
+  o.var_runs = 0.0;
+  o.jk = 0.0;
+  if (R > 1) {
+    for (int r = 0; r < R; ++r) {
+      const double dx = o.tr[r].x - o.mean.x, dy = o.tr[r].y - o.mean.y;
+      o.var_runs += dx * dx + dy * dy;
+    }
+    o.var_runs /= (R - 1);
+    const double2 tot = cscale(o.mean, (double)R);
+    std::vector<double2> loo(R);
+    double2 lm = make_double2(0.0, 0.0);
+    for (int r = 0; r < R; ++r) {
+      loo[r] = cscale(csub(tot, o.tr[r]), 1.0 / (R - 1));
+      lm = cadd(lm, loo[r]);
+    }
+    lm = cscale(lm, 1.0 / R);
+    for (int r = 0; r < R; ++r) {
+      const double dx = loo[r].x - lm.x, dy = loo[r].y - lm.y;
+      o.jk += dx * dx + dy * dy;
+    }
+    o.jk = std::sqrt(o.jk * (R - 1) / R);
+  }
+  o.var_s = 0.0;
+  const size_t ns = (size_t)R * nvec;
+  if (ns > 1) {
+    double2 sm = make_double2(0.0, 0.0);
+    for (size_t i = 0; i < ns; ++i) sm = cadd(sm, samples[i]);
+    sm = cscale(sm, 1.0 / ns);
+    for (size_t i = 0; i < ns; ++i) {
+      const double dx = samples[i].x - sm.x, dy = samples[i].y - sm.y;
+      o.var_s += dx * dx + dy * dy;
+    }
+    o.var_s /= (ns - 1);
+  }
+  return o;
+}
 
 constexpr int kMaxLanes = 8;
 
 struct TraceLayout {
   int b, lanes;
-  size_t vec, zdot_red, solver, defl, hp, sites, small, lane, total;
+  size_t vec, zdot_red, solver, defl, hp, sites, small, gam, lane, total;
 };
 
 // Lanes actually used: concurrency needs a solver that can run without
@@ -81,7 +196,9 @@ static TraceLayout trace_layout(const dtr_gauge_s *g, const dtr_defl_s *D, const
   const int k = D ? D->k : 0;
   L.small = al(3 * 64 * sizeof(double2) + (size_t)k * 64 * sizeof(double2));
   L.lanes = trace_lanes(p);
-  L.lane = 2 * L.vec + L.zdot_red + L.solver + L.defl + L.hp + L.small;
+  // Gamma insertion: copy of the block's C (k x 2b), Gamma^H Z (generic projection), dG and tG (16 x 64)
+  L.gam = p->n_gamma > 0 ? al((size_t)k * 2 * 64 * sizeof(double2)) + L.vec + 2 * al(16 * 64 * sizeof(double2)) : 0;
+  L.lane = 2 * L.vec + L.zdot_red + L.solver + L.defl + L.hp + L.small + L.gam;
   L.total = 256 + L.sites + L.lanes * L.lane;
   return L;
 }
@@ -97,7 +214,8 @@ struct Lane {
   Reduce red;
   void *solver_work = nullptr, *defl_work = nullptr, *hp_work = nullptr;
   double2 *d_dev = nullptr, *t_dev = nullptr, *terms_dev = nullptr;
-  double2 *t_h = nullptr, *terms_h = nullptr;  // pinned
+  double2 *Cmain = nullptr, *GZ = nullptr, *dg = nullptr, *tg = nullptr;  // Gamma insertion
+  double2 *t_h = nullptr, *terms_h = nullptr, *tg_h = nullptr;  // pinned
   Scal *sc_h = nullptr;                         // pinned
   int *err_h = nullptr;                         // pinned
   size_t terms_cap = 0;
@@ -109,7 +227,7 @@ struct Lane {
 struct LanePool {
   cudaStream_t s[kMaxLanes] = {};
   cudaEvent_t start = nullptr;
-  double2 *t_h[kMaxLanes] = {}, *terms_h[kMaxLanes] = {};
+  double2 *t_h[kMaxLanes] = {}, *terms_h[kMaxLanes] = {}, *tg_h[kMaxLanes] = {};
   Scal *sc_h[kMaxLanes] = {};
   int *err_h[kMaxLanes] = {};
   size_t terms_cap[kMaxLanes] = {};
@@ -119,6 +237,7 @@ static thread_local LanePool t_pool;
 static int lane_host_buffers(int l, int k) {
   LanePool &P = t_pool;
   if (!P.t_h[l]) DTR_CUDA(cudaMallocHost((void **)&P.t_h[l], 64 * sizeof(double2)));
+  if (!P.tg_h[l]) DTR_CUDA(cudaMallocHost((void **)&P.tg_h[l], 16 * 64 * sizeof(double2)));
   if (!P.sc_h[l]) DTR_CUDA(cudaMallocHost((void **)&P.sc_h[l], sizeof(Scal)));
   if (!P.err_h[l]) DTR_CUDA(cudaMallocHost((void **)&P.err_h[l], 4 * sizeof(int)));
   const size_t need = (size_t)(k > 0 ? k : 1) * 64;
@@ -160,9 +279,17 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
     ln.d_dev = (double2 *)q;
     ln.t_dev = ln.d_dev + 64;
     ln.terms_dev = ln.d_dev + 192;
+    q += L.small;
+    if (L.gam) {
+      ln.Cmain = (double2 *)q;  q += al((size_t)k * 2 * 64 * sizeof(double2));
+      ln.GZ = (double2 *)q;     q += L.vec;
+      ln.dg = (double2 *)q;     q += al(16 * 64 * sizeof(double2));
+      ln.tg = (double2 *)q;
+    }
     int rc = lane_host_buffers(l, k);
     if (rc) return rc;
     ln.t_h = t_pool.t_h[l];
+    ln.tg_h = t_pool.tg_h[l];
     ln.terms_h = t_pool.terms_h[l];
     ln.sc_h = t_pool.sc_h[l];
     ln.err_h = t_pool.err_h[l];
@@ -216,6 +343,20 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
       DTR_CUDA(cudaMemcpyAsync(sites_dev, list.data(), sizeof(int) * g.V, cudaMemcpyHostToDevice, st));
     }
   }
+  // Gamma insertion: monomial tables, and T_D^G cached in the deflation handle
+  const int ng = p->n_gamma;
+  GammaSet gset;
+  gset.n = ng;
+  unsigned gmask = 0;
+  for (int q = 0; q < ng; ++q) {
+    if (!gamma_monomial(p->gamma[q], &gset.g[q])) return fail(DTR_EINVAL, "Gamma table is not monomial");
+    gmask |= 1u << p->gamma[q];
+  }
+  if (ng && D) {
+    int rc = defl_trace_TD_gamma(const_cast<dtr_defl_s *>(D), gmask, st);
+    if (rc) return rc;
+  }
+  std::vector<double2> gsamples((size_t)ng * R * p->nvec, make_double2(0.0, 0.0));
   // the lanes start after everything queued on the caller's stream
   if (nlanes > 1) {
     if (!t_pool.start) DTR_CUDA(cudaEventCreateWithFlags(&t_pool.start, cudaEventDisableTiming));
@@ -236,13 +377,32 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
     DTR_LAUNCH_CHECK("noise");
     if (D) {
       int rc;
-      if (hp_ok && one_run && !p->use_x0)
+      const bool hp_block = hp_ok && one_run && !p->use_x0;
+      double2 *Cm = nullptr;
+      if (hp_block)
         rc = defl_project_hp(D, sites_dev, p->ncolors, p->seed, p->z0_first + G0 / ncols, q0, nb, p->dilute12, b,
-                             ln.d_dev, res->replay ? ln.terms_dev : nullptr, ln.hp_work, L.hp, sms, s);
+                             ln.d_dev, res->replay ? ln.terms_dev : nullptr, ln.hp_work, L.hp, sms, s, nullptr, &Cm);
       else
         rc = defl_project_internal(D, ln.Z, b, ln.d_dev, res->replay ? ln.terms_dev : nullptr,
-                                   p->use_x0 ? ln.X : nullptr, nullptr, ln.defl_work, L.defl, sms, s);
+                                   p->use_x0 ? ln.X : nullptr, &Cm, ln.defl_work, L.defl, sms, s);
       if (rc) return rc;
+      if (ng) {
+        // d^G_j = (V^H Gamma^H z_j)^H Lambda^-1 (V^H g5 z_j): the g5 half of this block's C is kept
+        DTR_CUDA(cudaMemcpyAsync(ln.Cmain, Cm, sizeof(double2) * (size_t)k * 2 * b, cudaMemcpyDeviceToDevice, s));
+        for (int q = 0; q < ng; ++q) {
+          double2 *Cg = nullptr;
+          if (hp_block) {
+            const CodeXform xf = code_xform_gamma_h(gset.g[q]);
+            rc = defl_project_hp(D, sites_dev, p->ncolors, p->seed, p->z0_first + G0 / ncols, q0, nb, p->dilute12,
+                                 b, nullptr, nullptr, ln.hp_work, L.hp, sms, s, &xf, &Cg);
+          } else {
+            launch_gamma_h(gset.g[q], ln.Z, ln.GZ, g.V, b, s);
+            rc = defl_project_internal(D, ln.GZ, b, ln.tg, nullptr, nullptr, &Cg, ln.defl_work, L.defl, sms, s);
+          }
+          if (rc) return rc;
+          launch_defl_d2(Cg, ln.Cmain, D->inv_lambda, k, b, ln.dg + q * 64, s);
+        }
+      }
     }
     if (!D || !p->use_x0) DTR_CUDA(cudaMemsetAsync(ln.X, 0, (size_t)n * sizeof(double2), s));
     Scal *sc = nullptr;
@@ -252,6 +412,15 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
     k_zdot<<<reduce_grid(n, sms), kBlock, 0, s>>>(ln.Z, ln.X, n, b, D ? ln.d_dev : nullptr, ln.t_dev, ln.red);
     count_launches(1);
     DTR_LAUNCH_CHECK("z^H y reduction");
+    for (int q0g = 0; q0g < ng; q0g += 4) {
+      k_zdot_gamma<4><<<reduce_grid((int64_t)g.V * b, sms), kBlock, 0, s>>>(
+          ln.Z, ln.X, g.V, b, ilog2(b), gset, q0g, D ? ln.dg : nullptr, ln.tg, ln.red);
+      count_launches(1);
+    }
+    if (ng) {
+      DTR_LAUNCH_CHECK("z^H Gamma y reduction");
+      DTR_CUDA(cudaMemcpyAsync(ln.tg_h, ln.tg, sizeof(double2) * 64 * ng, cudaMemcpyDeviceToHost, s));
+    }
     DTR_CUDA(cudaMemcpyAsync(ln.t_h, ln.t_dev, sizeof(double2) * b, cudaMemcpyDeviceToHost, s));
     DTR_CUDA(cudaMemcpyAsync(ln.sc_h, sc, sizeof(Scal), cudaMemcpyDeviceToHost, s));
     if (D && res->replay)
@@ -276,6 +445,11 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
       if (rel > maxres || rel != rel) maxres = rel;
       if (!ln.sc_h->conv[jj]) all_conv = 0;
       if (ln.sc_h->flags[jj] & kFlagNaN) status = DTR_ENAN;
+      for (int q = 0; q < ng; ++q) {
+        double2 &gs_ = gsamples[((size_t)q * R + r) * p->nvec + jv];
+        gs_.x += ln.tg_h[q * 64 + jj].x;
+        gs_.y += ln.tg_h[q * 64 + jj].y;
+      }
       if (res->replay && D) {
         double *rp = res->replay + 2 * (((size_t)r * p->nvec + jv) * k);
         for (int m = 0; m < k; ++m) {
@@ -308,60 +482,19 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
   }
 
   // run statistics (host, FP64)
-  std::vector<double2> tr(R);
-  double2 mean = make_double2(0.0, 0.0);
-  for (int r = 0; r < R; ++r) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int j = 0; j < p->nvec; ++j) s = cadd(s, samples[(size_t)r * p->nvec + j]);
-    tr[r] = make_double2(td + s.x / p->nvec, td_im + s.y / p->nvec);
-    mean = cadd(mean, tr[r]);
-  }
-  mean = cscale(mean, 1.0 / R);
-  double var_runs = 0.0, jk = 0.0;
-  if (R > 1) {
-    for (int r = 0; r < R; ++r) {
-      const double dx = tr[r].x - mean.x, dy = tr[r].y - mean.y;
-      var_runs += dx * dx + dy * dy;
-    }
-    var_runs /= (R - 1);
-    // delete-1 jackknife of the mean
-    double2 tot = cscale(mean, (double)R);
-    std::vector<double2> loo(R);
-    double2 lm = make_double2(0.0, 0.0);
-    for (int r = 0; r < R; ++r) {
-      loo[r] = cscale(csub(tot, tr[r]), 1.0 / (R - 1));
-      lm = cadd(lm, loo[r]);
-    }
-    lm = cscale(lm, 1.0 / R);
-    for (int r = 0; r < R; ++r) {
-      const double dx = loo[r].x - lm.x, dy = loo[r].y - lm.y;
-      jk += dx * dx + dy * dy;
-    }
-    jk = std::sqrt(jk * (R - 1) / R);
-  }
-  double var_s = 0.0;
-  const size_t ns = samples.size();
-  if (ns > 1) {
-    double2 sm = make_double2(0.0, 0.0);
-    for (auto &s : samples) sm = cadd(sm, s);
-    sm = cscale(sm, 1.0 / ns);
-    for (auto &s : samples) {
-      const double dx = s.x - sm.x, dy = s.y - sm.y;
-      var_s += dx * dx + dy * dy;
-    }
-    var_s /= (ns - 1);
-  }
-  res->trace[0] = mean.x;
-  res->trace[1] = mean.y;
+  const RunStats st0 = run_stats(samples.data(), R, p->nvec, td, td_im);
+  res->trace[0] = st0.mean.x;
+  res->trace[1] = st0.mean.y;
   res->T_D[0] = td;
   res->T_D[1] = td_im;
-  res->var_runs = var_runs;
-  res->jk_err = jk;
-  res->var_samples = var_s;
+  res->var_runs = st0.var_runs;
+  res->jk_err = st0.jk;
+  res->var_samples = st0.var_s;
   res->n_solves = nsolves;
   res->iterations = iters;
   res->max_true_residual = maxres;
   res->all_converged = all_conv;
+  const size_t ns = samples.size();
   if (res->samples)
     for (size_t i = 0; i < ns; ++i) {
       res->samples[2 * i] = samples[i].x;
@@ -369,9 +502,25 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
     }
   if (res->trace_runs)
     for (int r = 0; r < R; ++r) {
-      res->trace_runs[2 * r] = tr[r].x;
-      res->trace_runs[2 * r + 1] = tr[r].y;
+      res->trace_runs[2 * r] = st0.tr[r].x;
+      res->trace_runs[2 * r + 1] = st0.tr[r].y;
     }
+  for (int q = 0; q < ng; ++q) {
+    const double gtd = D ? D->tdg[p->gamma[q]][0] : 0.0, gtd_im = D ? D->tdg[p->gamma[q]][1] : 0.0;
+    const double2 *gsq = gsamples.data() + (size_t)q * R * p->nvec;
+    const RunStats sg = run_stats(gsq, R, p->nvec, gtd, gtd_im);
+    res->gamma_trace[2 * q] = sg.mean.x;
+    res->gamma_trace[2 * q + 1] = sg.mean.y;
+    res->gamma_T_D[2 * q] = gtd;
+    res->gamma_T_D[2 * q + 1] = gtd_im;
+    res->gamma_var_runs[q] = sg.var_runs;
+    res->gamma_jk_err[q] = sg.jk;
+    if (res->gamma_samples)
+      for (size_t i = 0; i < (size_t)R * p->nvec; ++i) {
+        res->gamma_samples[2 * ((size_t)q * R * p->nvec + i)] = gsq[i].x;
+        res->gamma_samples[2 * ((size_t)q * R * p->nvec + i) + 1] = gsq[i].y;
+      }
+  }
   if (status == DTR_OK && !all_conv) return fail(DTR_ENOTCONV, "some right-hand sides did not reach tol");
   if (status == DTR_ENAN) return fail(DTR_ENAN, "NaN or Inf in a residual norm");
   return DTR_OK;

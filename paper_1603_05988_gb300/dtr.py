@@ -45,7 +45,7 @@ class TraceParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("z0_first", ctypes.c_int64), ("n_z0", ctypes.c_int),
                 ("ncolors", ctypes.c_int), ("nvec", ctypes.c_int), ("dilute12", ctypes.c_int),
                 ("block", ctypes.c_int), ("use_x0", ctypes.c_int), ("solve", SolveParams), ("lanes", ctypes.c_int),
-                ("pad_", ctypes.c_int)]
+                ("n_gamma", ctypes.c_int), ("gamma", ctypes.c_int * 16)]
 
 
 class TraceResult(ctypes.Structure):
@@ -54,7 +54,9 @@ class TraceResult(ctypes.Structure):
                 ("iterations", ctypes.c_int64), ("max_true_residual", ctypes.c_double),
                 ("all_converged", ctypes.c_int), ("pad_", ctypes.c_int),
                 ("samples", ctypes.POINTER(ctypes.c_double)), ("trace_runs", ctypes.POINTER(ctypes.c_double)),
-                ("replay", ctypes.POINTER(ctypes.c_double))]
+                ("replay", ctypes.POINTER(ctypes.c_double)), ("gamma_samples", ctypes.POINTER(ctypes.c_double)),
+                ("gamma_trace", ctypes.c_double * 32), ("gamma_T_D", ctypes.c_double * 32),
+                ("gamma_var_runs", ctypes.c_double * 16), ("gamma_jk_err", ctypes.c_double * 16)]
 
 
 class TuneResult(ctypes.Structure):
@@ -438,12 +440,18 @@ def deflate_project_static(defl, z, want_coeff=False):
 
 
 def trace_params(seed=0, z0_first=0, n_z0=1, ncolors=1, nvec=1, dilute12=False, block=16, use_x0=False,
-                 solve=None, lanes=1):
+                 solve=None, lanes=1, gammas=()):
     p = TraceParams()
     p.seed, p.z0_first, p.n_z0, p.ncolors, p.nvec = int(seed), int(z0_first), int(n_z0), int(ncolors), int(nvec)
     p.dilute12, p.block, p.use_x0 = int(bool(dilute12)), int(block), int(bool(use_x0))
     p.solve = solve if solve is not None else solve_params()
     p.lanes = int(lanes)
+    gammas = list(gammas)
+    if len(gammas) > 16:
+        raise ValueError("at most 16 Gamma matrices")
+    p.n_gamma = len(gammas)
+    for q, n in enumerate(gammas):
+        p.gamma[q] = int(n)
     return p
 
 
@@ -485,6 +493,9 @@ def trace_estimate(gauge, m0, defl, params, workspace=None, want_samples=True, w
     res.samples = samples.ctypes.data_as(dp) if samples is not None else None
     res.trace_runs = runs.ctypes.data_as(dp)
     res.replay = replay.ctypes.data_as(dp) if replay is not None else None
+    ng = params.n_gamma
+    gsamp = np.zeros(2 * ng * R * s) if (ng and want_samples) else None
+    res.gamma_samples = gsamp.ctypes.data_as(dp) if gsamp is not None else None
     rc = _lib.dtr_trace_estimate(gauge._h, float(m0), defl._h if defl is not None else None, ctypes.byref(params),
                                  _ptr(ws.buf), ws.nbytes, ctypes.byref(res), _stream())
     _check(rc, allow=(DTR_ENOTCONV,) if allow_notconv else ())
@@ -497,4 +508,15 @@ def trace_estimate(gauge, m0, defl, params, workspace=None, want_samples=True, w
         out["samples"] = (samples[0::2] + 1j * samples[1::2]).reshape(R, s)
     if replay is not None:
         out["replay"] = (replay[0::2] + 1j * replay[1::2]).reshape(R, s, k)
+    if ng:
+        gam = []
+        for q in range(ng):
+            d = dict(n=int(params.gamma[q]), trace=complex(res.gamma_trace[2 * q], res.gamma_trace[2 * q + 1]),
+                     T_D=complex(res.gamma_T_D[2 * q], res.gamma_T_D[2 * q + 1]),
+                     var_runs=res.gamma_var_runs[q], jk_err=res.gamma_jk_err[q])
+            if gsamp is not None:
+                g = gsamp[2 * q * R * s:2 * (q + 1) * R * s]
+                d["samples"] = (g[0::2] + 1j * g[1::2]).reshape(R, s)
+            gam.append(d)
+        out["gamma"] = gam
     return out
