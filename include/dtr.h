@@ -357,6 +357,10 @@ typedef struct {
   double gamma_T_D[32];
   double gamma_var_runs[16];
   double gamma_jk_err[16];
+  /* ||A^-1||_F^2 estimated as the mean over probing vectors of |A^-1 z|^2 (unbiased: E z z^H = 1),
+   * and its standard error: the total the variance model (Theorem 2) starts from */
+  double frob2;
+  double frob2_err;
 } dtr_trace_result;
 
 /* Algorithm 1 (deflatedHP) for R = n_z0 runs: for each run r and each block
@@ -368,6 +372,17 @@ typedef struct {
 size_t dtr_trace_workspace_bytes(dtr_gauge g, dtr_defl d, const dtr_trace_params *p);
 int dtr_trace_estimate(dtr_gauge g, double m0, dtr_defl d, const dtr_trace_params *p,
                        void *work, size_t work_bytes, dtr_trace_result *res, void *stream);
+
+/* ----------------------------------------------------------- diagnostics */
+/* W_d distance diagnostic (Section 6.2).  cols: device, canonical N x ns complex128 (column q =
+ * B e_(dofs[q]) for the matrix B under study, e.g. A^-1 or its deflated remainder; by
+ * g5-Hermiticity a column has the moduli of the row the definition names); dofs: host, the ns
+ * sampled dof indices; ncolors > 1 keeps only sites of the sampled site's probing colour (the mask
+ * of ncolors normalised hierarchical-probing vectors), 0 or 1 none.  W (host, maxd + 1) receives
+ * W_d = mean over q of (sum of |B_jq|^2 over dofs j != dofs[q] at sites of periodic Manhattan
+ * distance d) / (number of sites at distance d).  Synchronises `stream`. */
+int dtr_wd(dtr_lattice lat, const double *cols, const int64_t *dofs, int ns, int maxd, int ncolors, double *W,
+           void *stream);
 
 /* ------------------------------------------------------------- autotuner */
 typedef struct {

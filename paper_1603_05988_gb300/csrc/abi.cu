@@ -42,6 +42,8 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 size_t trace_workspace_bytes(const dtr_gauge_s *g, const dtr_defl_s *D, const dtr_trace_params *p);
 size_t tune_workspace_bytes(const dtr_gauge_s *g, const dtr_defl_s *D, const dtr_trace_params *p);
+int wd_diagnostic(const dtr_lattice_s *lat, const double2 *cols, const int64_t *dofs_host, int ns, int maxd,
+                  int ncolors, double *W, cudaStream_t st);
 int trace_autotune(const dtr_gauge_s *g, double m0, const dtr_defl_s *D, const dtr_trace_params *p, int reps,
                    int force, void *work, size_t work_bytes, dtr_tune_result *out, cudaStream_t st);
 int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, const dtr_trace_params *p, void *work,
@@ -650,6 +652,17 @@ int dtr_trace_estimate(dtr_gauge g, double m0, dtr_defl d, const dtr_trace_param
   int rc = check_trace_params(g, d, p);
   if (rc) return rc;
   return trace_estimate(g, m0, d, p, work, work_bytes, res, (cudaStream_t)stream);
+}
+
+int dtr_wd(dtr_lattice lat, const double *cols, const int64_t *dofs, int ns, int maxd, int ncolors, double *W,
+           void *stream) {
+  if (!lat || !cols || !dofs || !W) return fail(DTR_EINVAL, "null argument");
+  if (ns < 1 || maxd < 0 || maxd > 4096) return fail(DTR_EINVAL, "need ns >= 1 and 0 <= maxd <= 4096");
+  if (ncolors > 1) {
+    int rc = check_colouring(*lat, ncolors);
+    if (rc) return rc;
+  }
+  return wd_diagnostic(lat, (const double2 *)cols, dofs, ns, maxd, ncolors, W, (cudaStream_t)stream);
 }
 
 size_t dtr_trace_autotune_workspace_bytes(dtr_gauge g, dtr_defl d, const dtr_trace_params *p) {

@@ -21,9 +21,10 @@ namespace dtr {
 // out[j] = sum_i conj(Z_ij) Y_ij - d[j]   (FP64, deterministic)
 __global__ void __launch_bounds__(kBlock) k_zdot(const double2 *__restrict__ Z, const double2 *__restrict__ Y,
                                                  int64_t n, int b, const double2 *__restrict__ d,
-                                                 double2 *__restrict__ out, Reduce red) {
-  __shared__ double2 tot[64];
-  double2 acc[1] = {make_double2(0.0, 0.0)};
+                                                 double2 *__restrict__ out, double2 *__restrict__ ynorm,
+                                                 Reduce red) {
+  __shared__ double2 tot[2 * 64];
+  double2 acc[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};  // z^H y ; (|y|^2, 0)
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (; e + 3 * stride < n; e += 4 * stride) {  // four independent element pairs in flight
@@ -37,16 +38,21 @@ __global__ void __launch_bounds__(kBlock) k_zdot(const double2 *__restrict__ Z, 
     for (int u = 0; u < 4; ++u) {
       acc[0].x += z[u].x * y[u].x + z[u].y * y[u].y;
       acc[0].y += z[u].x * y[u].y - z[u].y * y[u].x;
+      acc[1].x += y[u].x * y[u].x + y[u].y * y[u].y;
     }
   }
   for (; e < n; e += stride) {
     const double2 z = Z[e], y = Y[e];
     acc[0].x += z.x * y.x + z.y * y.y;
     acc[0].y += z.x * y.y - z.y * y.x;
+    acc[1].x += y.x * y.x + y.y * y.y;
   }
-  if (block_reduce<1>(acc, b, red.partial, red.counter, tot)) {
+  if (block_reduce<2>(acc, b, red.partial, red.counter, tot)) {
     const int j = threadIdx.x;
-    if (j < b) out[j] = d ? csub(tot[j], d[j]) : tot[j];
+    if (j < b) {
+      out[j] = d ? csub(tot[j], d[j]) : tot[j];
+      ynorm[j] = tot[b + j];
+    }
   }
 }
 
@@ -213,7 +219,7 @@ struct Lane {
   double2 *Z = nullptr, *X = nullptr;
   Reduce red;
   void *solver_work = nullptr, *defl_work = nullptr, *hp_work = nullptr;
-  double2 *d_dev = nullptr, *t_dev = nullptr, *terms_dev = nullptr;
+  double2 *d_dev = nullptr, *t_dev = nullptr, *yn_dev = nullptr, *terms_dev = nullptr;
   double2 *Cmain = nullptr, *GZ = nullptr, *dg = nullptr, *tg = nullptr;  // Gamma insertion
   double2 *t_h = nullptr, *terms_h = nullptr, *tg_h = nullptr;  // pinned
   Scal *sc_h = nullptr;                         // pinned
@@ -236,7 +242,7 @@ static thread_local LanePool t_pool;
 
 static int lane_host_buffers(int l, int k) {
   LanePool &P = t_pool;
-  if (!P.t_h[l]) DTR_CUDA(cudaMallocHost((void **)&P.t_h[l], 64 * sizeof(double2)));
+  if (!P.t_h[l]) DTR_CUDA(cudaMallocHost((void **)&P.t_h[l], 128 * sizeof(double2)));
   if (!P.tg_h[l]) DTR_CUDA(cudaMallocHost((void **)&P.tg_h[l], 16 * 64 * sizeof(double2)));
   if (!P.sc_h[l]) DTR_CUDA(cudaMallocHost((void **)&P.sc_h[l], sizeof(Scal)));
   if (!P.err_h[l]) DTR_CUDA(cudaMallocHost((void **)&P.err_h[l], 4 * sizeof(int)));
@@ -278,6 +284,7 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
     ln.hp_work = q;       q += L.hp;
     ln.d_dev = (double2 *)q;
     ln.t_dev = ln.d_dev + 64;
+    ln.yn_dev = ln.d_dev + 128;
     ln.terms_dev = ln.d_dev + 192;
     q += L.small;
     if (L.gam) {
@@ -357,6 +364,7 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
     if (rc) return rc;
   }
   std::vector<double2> gsamples((size_t)ng * R * p->nvec, make_double2(0.0, 0.0));
+  std::vector<double> ynorm((size_t)R * p->nvec, 0.0);  // |A^-1 z|^2 per probing vector
   // the lanes start after everything queued on the caller's stream
   if (nlanes > 1) {
     if (!t_pool.start) DTR_CUDA(cudaEventCreateWithFlags(&t_pool.start, cudaEventDisableTiming));
@@ -409,7 +417,8 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
     int rc = solve_internal(gauge, m0, ln.X, ln.Z, b, &sp, ln.solver_work, L.solver, s, &sc, !D || !p->use_x0,
                             nlanes > 1);
     if (rc) return rc;
-    k_zdot<<<reduce_grid(n, sms), kBlock, 0, s>>>(ln.Z, ln.X, n, b, D ? ln.d_dev : nullptr, ln.t_dev, ln.red);
+    k_zdot<<<reduce_grid(n, sms), kBlock, 0, s>>>(ln.Z, ln.X, n, b, D ? ln.d_dev : nullptr, ln.t_dev, ln.yn_dev,
+                                                  ln.red);
     count_launches(1);
     DTR_LAUNCH_CHECK("z^H y reduction");
     for (int q0g = 0; q0g < ng; q0g += 4) {
@@ -421,7 +430,7 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
       DTR_LAUNCH_CHECK("z^H Gamma y reduction");
       DTR_CUDA(cudaMemcpyAsync(ln.tg_h, ln.tg, sizeof(double2) * 64 * ng, cudaMemcpyDeviceToHost, s));
     }
-    DTR_CUDA(cudaMemcpyAsync(ln.t_h, ln.t_dev, sizeof(double2) * b, cudaMemcpyDeviceToHost, s));
+    DTR_CUDA(cudaMemcpyAsync(ln.t_h, ln.t_dev, sizeof(double2) * 128, cudaMemcpyDeviceToHost, s));  // t, |y|^2
     DTR_CUDA(cudaMemcpyAsync(ln.sc_h, sc, sizeof(Scal), cudaMemcpyDeviceToHost, s));
     if (D && res->replay)
       DTR_CUDA(cudaMemcpyAsync(ln.terms_h, ln.terms_dev, sizeof(double2) * k * b, cudaMemcpyDeviceToHost, s));
@@ -440,6 +449,7 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
       double2 &sm = samples[(size_t)r * p->nvec + jv];
       sm.x += ln.t_h[jj].x;
       sm.y += ln.t_h[jj].y;
+      ynorm[(size_t)r * p->nvec + jv] += ln.t_h[64 + jj].x;
       iters += ln.sc_h->iters[jj];
       const double rel = ln.sc_h->bnorm2[jj] > 0 ? std::sqrt(ln.sc_h->rtrue2[jj] / ln.sc_h->bnorm2[jj]) : 0.0;
       if (rel > maxres || rel != rel) maxres = rel;
@@ -505,6 +515,16 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
       res->trace_runs[2 * r] = st0.tr[r].x;
       res->trace_runs[2 * r + 1] = st0.tr[r].y;
     }
+  {  // E |A^-1 z|^2 = ||A^-1||_F^2 for noise with E z z^H = 1 (Z4, probing, dilution groups summed)
+    const size_t nsmp = ynorm.size();
+    double m = 0.0;
+    for (double v : ynorm) m += v;
+    m /= (double)nsmp;
+    double v2 = 0.0;
+    for (double v : ynorm) v2 += (v - m) * (v - m);
+    res->frob2 = m;
+    res->frob2_err = nsmp > 1 ? std::sqrt(v2 / (double)(nsmp - 1) / (double)nsmp) : 0.0;
+  }
   for (int q = 0; q < ng; ++q) {
     const double gtd = D ? D->tdg[p->gamma[q]][0] : 0.0, gtd_im = D ? D->tdg[p->gamma[q]][1] : 0.0;
     const double2 *gsq = gsamples.data() + (size_t)q * R * p->nvec;

@@ -56,7 +56,8 @@ class TraceResult(ctypes.Structure):
                 ("samples", ctypes.POINTER(ctypes.c_double)), ("trace_runs", ctypes.POINTER(ctypes.c_double)),
                 ("replay", ctypes.POINTER(ctypes.c_double)), ("gamma_samples", ctypes.POINTER(ctypes.c_double)),
                 ("gamma_trace", ctypes.c_double * 32), ("gamma_T_D", ctypes.c_double * 32),
-                ("gamma_var_runs", ctypes.c_double * 16), ("gamma_jk_err", ctypes.c_double * 16)]
+                ("gamma_var_runs", ctypes.c_double * 16), ("gamma_jk_err", ctypes.c_double * 16),
+                ("frob2", ctypes.c_double), ("frob2_err", ctypes.c_double)]
 
 
 class TuneResult(ctypes.Structure):
@@ -117,6 +118,7 @@ _sig("dtr_net_train_step", _i, [_vp, _vp, _d, _vp, _vp, _i, _d, _i, ctypes.POINT
 _sig("dtr_trace_workspace_bytes", _sz, [_vp, _vp, ctypes.POINTER(TraceParams)])
 _sig("dtr_trace_estimate", _i, [_vp, _d, _vp, ctypes.POINTER(TraceParams), _vp, _sz,
                                 ctypes.POINTER(TraceResult), _vp])
+_sig("dtr_wd", _i, [_vp, _vp, _vp, _i, _i, _i, _vp, _vp])
 _sig("dtr_trace_autotune_workspace_bytes", _sz, [_vp, _vp, ctypes.POINTER(TraceParams)])
 _sig("dtr_trace_autotune", _i, [_vp, _d, _vp, ctypes.POINTER(TraceParams), _i, _i, _vp, _sz,
                                 ctypes.POINTER(TuneResult), _vp])
@@ -463,6 +465,19 @@ class TraceWorkspace:
         self.buf = _workspace(self.nbytes)
 
 
+def wd(lat, cols, dofs, maxd, ncolors=0):
+    """W_d (d = 0..maxd) of the matrix whose columns B e_i for the sampled dofs are
+    `cols` (device, shape (ns, N) complex128, row q = column of dofs[q])."""
+    cols = _field(cols, lat.N, "cols")
+    dofs = np.ascontiguousarray(dofs, dtype=np.int64)
+    if cols.shape[0] != dofs.shape[0]:
+        raise ValueError("one column per sampled dof")
+    W = np.zeros(int(maxd) + 1)
+    _check(_lib.dtr_wd(lat._h, _ptr(cols), dofs.ctypes.data_as(_vp), int(dofs.shape[0]), int(maxd), int(ncolors),
+                       W.ctypes.data_as(_vp), _stream()))
+    return W
+
+
 def trace_autotune(gauge, m0, defl, params, reps=3, force=False):
     """Time the candidate launch shapes (lanes; RHS block too if params.block <= 0)
     and return a dict with the fastest ("lanes", "block", "rhs_per_s") and the
@@ -503,7 +518,7 @@ def trace_estimate(gauge, m0, defl, params, workspace=None, want_samples=True, w
                var_runs=res.var_runs, jk_err=res.jk_err, var_samples=res.var_samples, n_solves=res.n_solves,
                iterations=res.iterations, max_true_residual=res.max_true_residual,
                all_converged=bool(res.all_converged), status=rc,
-               trace_runs=runs[0::2] + 1j * runs[1::2])
+               trace_runs=runs[0::2] + 1j * runs[1::2], frob2=res.frob2, frob2_err=res.frob2_err)
     if samples is not None:
         out["samples"] = (samples[0::2] + 1j * samples[1::2]).reshape(R, s)
     if replay is not None:
