@@ -44,7 +44,7 @@ L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--steps", type=int, default=128)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--solver", default="mixed_f32", choices=["mixed_f32", "f64"])
@@ -364,6 +364,9 @@ def main():
                     "frac": hb["achieved_gbs"] / hbm_peak, "traffic": None,
                     "kernel": "dslash BF16 storage (two-row links), FP32 math, 1 RHS, 32^3x64",
                     "avg_launch_ms": hb["avg_launch_ms"], "alg_bytes_per_launch": hb["alg_bytes_per_launch"],
+                    "alg_bytes_note": "240 B per site (48 + 48 B spinors, 144 B for four 3x3 BF16 links); the "
+                                      "kernel stores two rows per link and moves %d B per launch (%.0f GB/s)"
+                                      % (hb["stored_bytes_per_launch"], hb["moved_gbs"]),
                     "peak_note": "hbm_gbs of MEASURED_PEAKS.json (of measured)"}
         del g_big, lat_big
 
