@@ -80,3 +80,33 @@ def deflation_operator(AH, V, sigma):
     """Dense D = V Lambda^-1 V^H A^H (small N), the deflated part of A^-1."""
     AHd = AH.toarray() if hasattr(AH, "toarray") else np.asarray(AH)
     return (V / (sigma ** 2)[None, :]) @ (V.conj().T @ AHd)
+
+
+def bf16_round(V):
+    """Round complex128 values to bfloat16 (round to nearest even on the float32 bits), returned as complex128:
+    the copy a library keeps when it stores V in BF16."""
+    def r(x):
+        f = np.ascontiguousarray(x, dtype=np.float32)
+        u = f.view(np.uint32).astype(np.uint64)
+        u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+        return u.astype(np.uint32).view(np.float32).astype(np.float64)
+    return r(V.real) + 1j * r(V.imag)
+
+
+def galerkin(Adense, V):
+    """Galerkin deflation with a basis V that need not be orthonormal or exact (Section 5.2's
+    V Lambda^-1 V^H A^H with Lambda replaced by the k x k matrix it approximates):
+        G = V^H g5 A V,   D = V G^-1 V^H g5,   T_D = Tr(G^-1 V^H g5 V).
+    Returns (D, T_D, G).  For exact orthonormal eigenvectors of g5 A, G = Lambda (signed)."""
+    G5V = _wilson.gamma5_vec(V)
+    G = G5V.conj().T @ (Adense @ V)
+    Gi = np.linalg.inv(G)
+    D = V @ Gi @ G5V.conj().T
+    TD = complex(np.trace(Gi @ (V.conj().T @ G5V)))
+    return D, TD, G
+
+
+def galerkin_terms(Adense, V, Z):
+    """d_j = z_j^H D z_j of the Galerkin deflation for the columns of Z, and T_D."""
+    D, TD, _ = galerkin(Adense, V)
+    return np.einsum("ij,ij->j", np.conj(Z), D @ Z), TD

@@ -191,3 +191,39 @@ def test_gamma5_form_unbiased_for_any_deflation_space():
     t = np.einsum("ij,ij->j", np.conj(Z), Ainv @ Z) - deflation.quadrature_gamma5(V, lam, Z)
     est = deflation.T_D_gamma5(V, lam) + t.sum() / 256
     assert abs(est - tr) < 1e-11 * abs(tr)
+
+
+def test_galerkin_deflation_pins():
+    """Galerkin deflation D = V (V^H g5 A V)^-1 V^H g5: equals the literal Lambda form for exact
+    eigenvectors; for ANY basis (rounded to BF16, or a random one) D A is the identity on
+    span(V), and T_D = Tr(D)."""
+    from oracle import deflation, wilson
+    from paper_1603_05988_gb300 import synth
+    dims, m0 = (2, 2, 2, 4), -0.4
+    U = synth.random_su3_links(dims, 0.5, 44)
+    Ad = wilson.explicit(U, dims, m0).toarray()
+    AH = wilson.explicit_dagger(U, dims, m0)
+    V, lam, sig = deflation.smallest_triplets(Ad, 10)
+    D, TD, G = deflation.galerkin(Ad, V)
+    assert np.allclose(G, np.diag(lam), atol=1e-12)
+    assert abs(TD - deflation.T_D(AH, V, sig)) <= 1e-12 * abs(TD)
+    Z = np.eye(Ad.shape[0])[:, :7] * (1 + 1j)
+    d, _ = deflation.galerkin_terms(Ad, V, Z)
+    assert np.allclose(d, [deflation.quadrature(AH, V, sig, Z[:, j]) for j in range(7)], rtol=1e-11)
+    rng = np.random.default_rng(2)
+    for W in (deflation.bf16_round(V), V @ (rng.standard_normal((10, 10)) + 1j * rng.standard_normal((10, 10)))):
+        D, TD, _ = deflation.galerkin(Ad, W)
+        assert np.allclose(D @ (Ad @ W), W, atol=1e-9 * np.abs(W).max())
+        assert abs(TD - np.trace(D)) <= 1e-10 * abs(TD)
+
+
+def test_bf16_round_is_round_to_nearest_even():
+    from oracle import deflation
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, 1.0 + 2 ** -9, -3.14159265, 1e-3])
+    r = deflation.bf16_round(x + 0j).real
+    assert r[0] == 1.0
+    assert r[1] == 1.0                       # exactly half an ulp (2^-7 at 1): tie, to the even mantissa
+    assert r[3] == 1.0                       # a quarter ulp rounds down
+    assert r[2] == 1.0 + 2 ** -7             # three quarters of an ulp rounds up
+    assert abs(r[4] + 3.140625) < 1e-12      # 8-bit mantissa
+    assert np.all(np.abs(r - x) <= 2 ** -8 * np.abs(x))
