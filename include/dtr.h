@@ -226,12 +226,26 @@ int dtr_solve_batch(dtr_gauge g, double m0, const double *z, double *y, int nrhs
  *   z^H V Lambda_{A^HA}^-1 V^H A^H z  = z^H V diag(1/lambda) V^H gamma_5 z.
  * V: HOST, canonical N x k complex128 column-major; lambda: host, k doubles
  * (non-zero).  The library copies V to device memory in precision prec
- * (DTR_F64 or DTR_F32) and computes T_D in FP64 from the stored copy, so
- * the estimator stays unbiased for the rounded V. */
+ * (DTR_F64, DTR_F32, or DTR_BF16 rounded to nearest even: 4 bytes per
+ * complex value) and computes T_D in FP64 from the stored copy; every
+ * kernel widens the stored values exactly to FP64, so the estimator stays
+ * unbiased for the rounded V. */
 int dtr_defl_create(dtr_lattice lat, int k, dtr_prec prec, const double *V_host,
                     const double *lambda_host, dtr_defl *out);
 /* T_D (Algorithm 1, line 2) as (re, im) in td[2] (host). */
 int dtr_defl_trace(dtr_defl d, double td[2]);
+/* Galerkin (Gram) correction, computed in FP64 on the GPU: with G = V^H gamma_5 A V
+ * (k x k, A from gauge g at mass m0, V the stored copy widened exactly),
+ * the deflation operator becomes D = V G^-1 V^H gamma_5 in place of
+ * V Lambda^-1 V^H gamma_5: the same for exact eigenpairs, exact on span(V)
+ * (D A v = v) for any basis, which matters when V is inexact or rounded to
+ * FP32/BF16.  From then on T_D = Tr(G^-1 V^H gamma_5 V), d_j = c_j^H G^-1 g_j
+ * (c = V^H z, g = V^H gamma_5 z), x0 = V G^-1 g, and T_D of a Gamma is
+ * Tr(G^-1 V^H gamma_5 Gamma V); the per-m replay terms become conj(c_m)(G^-1 g)_m,
+ * whose prefixes are no longer the k' < k estimates.  Cost: k FP64 stencils
+ * plus two k x k x N FP64 contractions; G^-1 by Gauss-Jordan on the host.
+ * Synchronises `stream`.  DTR_EINVAL if G is singular. */
+int dtr_defl_gram(dtr_defl d, dtr_gauge g, double m0, void *stream);
 void dtr_destroy_defl(dtr_defl d);
 
 /* Deflation projection of a block of probing vectors (Algorithm 1, line 8,

@@ -3,6 +3,8 @@
 // kernels.  No exception or trap crosses the boundary; failures return a
 // status code and leave a message for dtr_last_error().
 #include <atomic>
+
+#include <cuda_bf16.h>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -42,12 +44,19 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 size_t trace_workspace_bytes(const dtr_gauge_s *g, const dtr_defl_s *D, const dtr_trace_params *p);
 size_t tune_workspace_bytes(const dtr_gauge_s *g, const dtr_defl_s *D, const dtr_trace_params *p);
+int defl_gram(dtr_defl_s *D, const dtr_gauge_s *g, double m0, cudaStream_t st);
 int wd_diagnostic(const dtr_lattice_s *lat, const double2 *cols, const int64_t *dofs_host, int ns, int maxd,
                   int ncolors, double *W, cudaStream_t st);
 int trace_autotune(const dtr_gauge_s *g, double m0, const dtr_defl_s *D, const dtr_trace_params *p, int reps,
                    int force, void *work, size_t work_bytes, dtr_tune_result *out, cudaStream_t st);
 int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, const dtr_trace_params *p, void *work,
                    size_t work_bytes, dtr_trace_result *res, cudaStream_t st);
+
+// round to nearest even, componentwise
+__global__ void k_to_bf16(const double2 *__restrict__ a, __nv_bfloat162 *__restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = __floats2bfloat162_rn((float)a[i].x, (float)a[i].y);
+}
 
 __global__ void k_to_f32(const double2 *__restrict__ a, float2 *__restrict__ b, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -401,7 +410,8 @@ int dtr_defl_create(dtr_lattice lat, int k, dtr_prec prec, const double *V_host,
                     dtr_defl *out) {
   if (!lat || !V_host || !lambda_host || !out) return fail(DTR_EINVAL, "null argument");
   if (k < 1) return fail(DTR_EINVAL, "k must be >= 1");
-  if (prec != DTR_F64 && prec != DTR_F32) return fail(DTR_EINVAL, "deflation storage must be DTR_F64 or DTR_F32");
+  if (prec != DTR_F64 && prec != DTR_F32 && prec != DTR_BF16)
+    return fail(DTR_EINVAL, "deflation storage must be DTR_F64, DTR_F32 or DTR_BF16");
   for (int m = 0; m < k; ++m)
     if (!(lambda_host[m] != 0.0) || !std::isfinite(lambda_host[m]))
       return fail(DTR_EINVAL, "lambda must be finite and non-zero");
@@ -417,7 +427,10 @@ int dtr_defl_create(dtr_lattice lat, int k, dtr_prec prec, const double *V_host,
   for (int m = 0; m < k; ++m)
     for (int64_t i = 0; i < N; ++i) rowmajor[(size_t)i * k + m] = src[(size_t)m * N + i];
   dtr_defl_s *D = new (std::nothrow) dtr_defl_s;
-  if (D) D->tdg_ok = 0u;
+  if (D) {
+    D->tdg_ok = 0u;
+    D->Ginv = nullptr;
+  }
   if (!D) return fail(DTR_ENOMEM, "host allocation failed");
   D->lat = *lat;
   D->k = k;
@@ -435,11 +448,15 @@ int dtr_defl_create(dtr_lattice lat, int k, dtr_prec prec, const double *V_host,
         e = cudaMemcpy(D->V, rowmajor.data(), (size_t)N * k * sizeof(double2), cudaMemcpyHostToDevice);
     } else {
       double2 *tmp = nullptr;
-      e = cudaMalloc(&D->V, (size_t)N * k * sizeof(float2));
+      e = cudaMalloc(&D->V, (size_t)N * k * (prec == DTR_F32 ? sizeof(float2) : sizeof(__nv_bfloat162)));
       if (e == cudaSuccess) e = cudaMalloc(&tmp, (size_t)N * k * sizeof(double2));
       if (e == cudaSuccess) e = cudaMemcpy(tmp, rowmajor.data(), (size_t)N * k * sizeof(double2), cudaMemcpyHostToDevice);
       if (e == cudaSuccess) {
-        k_to_f32<<<grid1d((int64_t)N * k), 256>>>(tmp, (float2 *)D->V, (int64_t)N * k); count_launches(1);
+        if (prec == DTR_F32)
+          k_to_f32<<<grid1d((int64_t)N * k), 256>>>(tmp, (float2 *)D->V, (int64_t)N * k);
+        else
+          k_to_bf16<<<grid1d((int64_t)N * k), 256>>>(tmp, (__nv_bfloat162 *)D->V, (int64_t)N * k);
+        count_launches(1);
         e = cudaGetLastError();
       }
       if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -474,7 +491,13 @@ void dtr_destroy_defl(dtr_defl d) {
   if (!d) return;
   cudaFree(d->V);
   cudaFree(d->inv_lambda);
+  cudaFree(d->Ginv);
   delete d;
+}
+
+int dtr_defl_gram(dtr_defl d, dtr_gauge g, double m0, void *stream) {
+  if (!d || !g) return fail(DTR_EINVAL, "null argument");
+  return defl_gram(d, g, m0, (cudaStream_t)stream);
 }
 
 size_t dtr_deflate_workspace_bytes(dtr_defl d, int nrhs) {

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kDeflBlock)
 #pragma unroll
       for (int q = 0; q < kMPT; ++q) {
         if (!ok[q]) continue;
-        const VC vv = Vd[i * k + m[q]];
+        const double2 vv = vload(Vd[i * k + m[q]]);
         const double vx = vv.x, vy = vv.y;
         // conj(v) * z
         const double re = vx * z.x + vy * z.y, im = vx * z.y - vy * z.x;
@@ -111,15 +111,60 @@ __global__ void k_defl_d(const double2 *__restrict__ C, const double2 *__restric
   if (threadIdx.x == 0) d[j] = sh[0];
 }
 
-void launch_defl_d(const double2 *C, const double *inv_lambda, int k, int b, double2 *d, double2 *terms,
-                   cudaStream_t st) {
-  k_defl_d<<<b, 128, 0, st>>>(C, C, inv_lambda, k, b, d, terms);
+// Galerkin form: y = G^-1 g_j (Cr[:, b + j]) per column, d_j = c_j^H y (fixed-order tree)
+__global__ void k_defl_d_gram(const double2 *__restrict__ C, const double2 *__restrict__ Cr,
+                              const double2 *__restrict__ Ginv, int k, int b, double2 *__restrict__ d,
+                              double2 *__restrict__ terms) {
+  __shared__ double2 sh[128];
+  const int j = blockIdx.x;
+  const double2 *g = Cr + (int64_t)(b + j) * k;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int m = threadIdx.x; m < k; m += blockDim.x) {
+    double2 y = make_double2(0.0, 0.0);
+    for (int n = 0; n < k; ++n) y = caxpy(Ginv[(int64_t)m * k + n], g[n], y);
+    const double2 t = cjmul(C[(int64_t)j * k + m], y);
+    if (terms) terms[(int64_t)j * k + m] = t;
+    acc = cadd(acc, t);
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int stride = 64; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride) sh[threadIdx.x] = cadd(sh[threadIdx.x], sh[threadIdx.x + stride]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d[j] = sh[0];
+}
+
+// expansion weights W[j][m] = (Lambda^-1 g_j)_m or (G^-1 g_j)_m, g_j = C[:, b + j]
+__global__ void k_defl_weights(const double2 *__restrict__ C, const double *__restrict__ inv_lambda,
+                               const double2 *__restrict__ Ginv, int k, int b, double2 *__restrict__ W) {
+  const int64_t n = (int64_t)k * b;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e % k), j = (int)(e / k);
+    const double2 *g = C + (int64_t)(b + j) * k;
+    double2 y = make_double2(0.0, 0.0);
+    if (Ginv) {
+      for (int q = 0; q < k; ++q) y = caxpy(Ginv[(int64_t)m * k + q], g[q], y);
+    } else {
+      y = cscale(g[m], inv_lambda[m]);
+    }
+    W[e] = y;
+  }
+}
+
+void launch_defl_d(const dtr_defl_s *D, const double2 *C, int b, double2 *d, double2 *terms, cudaStream_t st) {
+  if (D->Ginv)
+    k_defl_d_gram<<<b, 128, 0, st>>>(C, C, D->Ginv, D->k, b, d, terms);
+  else
+    k_defl_d<<<b, 128, 0, st>>>(C, C, D->inv_lambda, D->k, b, d, terms);
   count_launches(1);
 }
 
-void launch_defl_d2(const double2 *Cl, const double2 *Cr, const double *inv_lambda, int k, int b, double2 *d,
-                    cudaStream_t st) {
-  k_defl_d<<<b, 128, 0, st>>>(Cl, Cr, inv_lambda, k, b, d, nullptr);
+void launch_defl_d2(const dtr_defl_s *D, const double2 *Cl, const double2 *Cr, int b, double2 *d, cudaStream_t st) {
+  if (D->Ginv)
+    k_defl_d_gram<<<b, 128, 0, st>>>(Cl, Cr, D->Ginv, D->k, b, d, nullptr);
+  else
+    k_defl_d<<<b, 128, 0, st>>>(Cl, Cr, D->inv_lambda, D->k, b, d, nullptr);
   count_launches(1);
 }
 
@@ -163,8 +208,7 @@ __global__ void k_defl_tdg_partial(const VC *__restrict__ Vd, int k, int64_t nsi
       double2 v[12];
 #pragma unroll
       for (int a = 0; a < 12; ++a) {
-        const VC vv = Vd[(x * 12 + a) * k + m];
-        v[a] = make_double2(vv.x, vv.y);
+        v[a] = vload(Vd[(x * 12 + a) * k + m]);
       }
       for (int q = 0; q < gs.n; ++q) {
         const GammaMono g = gs.g[q];
@@ -205,17 +249,16 @@ __global__ void k_defl_tdg_reduce(const double2 *__restrict__ part, const double
 
 // x0 (internal [site][12][b]) = V diag(1/lambda) C[:, b:2b]
 template <typename VC>
-__global__ void k_defl_expand(const VC *__restrict__ Vd, const double2 *__restrict__ C,
-                              const double *__restrict__ inv_lambda, int k, int b, int64_t N, double2 *__restrict__ x) {
+__global__ void k_defl_expand(const VC *__restrict__ Vd, const double2 *__restrict__ W, int k, int b, int64_t N,
+                              double2 *__restrict__ x) {
   const int64_t n = N * b;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(e % b);
     const int64_t i = e / b;
     double2 acc = make_double2(0.0, 0.0);
     for (int m = 0; m < k; ++m) {
-      const VC vv = Vd[i * k + m];
-      const double2 w = cscale(C[(int64_t)(b + j) * k + m], inv_lambda[m]);
-      acc = caxpy(make_double2(vv.x, vv.y), w, acc);
+      const double2 vv = vload(Vd[i * k + m]);
+      acc = caxpy(vv, W[(int64_t)j * k + m], acc);
     }
     x[e] = acc;
   }
@@ -229,8 +272,8 @@ __global__ void k_defl_td_partial(const VC *__restrict__ Vd, int k, int64_t N, i
   for (int m = threadIdx.x; m < k; m += blockDim.x) {
     double acc = 0.0;
     for (int64_t i = i0; i < i1; ++i) {
-      const VC vv = Vd[i * k + m];
-      const double a2 = (double)vv.x * vv.x + (double)vv.y * vv.y;
+      const double2 vv = vload(Vd[i * k + m]);
+      const double a2 = vv.x * vv.x + vv.y * vv.y;
       acc += ((i % 12) < 6) ? a2 : -a2;
     }
     part[(int64_t)chunk * k + m] = acc;
@@ -269,8 +312,9 @@ size_t defl_scratch_bytes(int64_t V, int k, int b, int sms) {
   const int nch = defl_chunks(V, k, b, sms);
   size_t part = (size_t)nch * k * 2 * b * sizeof(double2);
   const size_t C = (size_t)k * 2 * b * sizeof(double2);
+  const size_t W = (size_t)k * b * sizeof(double2);
   const size_t d = 64 * sizeof(double2);
-  return ((part + 255) / 256 + (C + 255) / 256 + (d + 255) / 256 + 2) * 256;
+  return ((part + 255) / 256 + (C + 255) / 256 + (W + 255) / 256 + (d + 255) / 256 + 3) * 256;
 }
 
 int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 *d_dev, double2 *terms_dev,
@@ -287,26 +331,34 @@ int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 
   w += (((size_t)nch * k * 2 * b * sizeof(double2) + 255) / 256) * 256;
   double2 *C = (double2 *)w;
   w += (((size_t)k * 2 * b * sizeof(double2) + 255) / 256) * 256;
+  double2 *Wx = (double2 *)w;
+  w += (((size_t)k * b * sizeof(double2) + 255) / 256) * 256;
   const int logb = log2i(b);
   if (D->prec == DTR_F64)
     k_defl_partial<double2><<<nch * tiles, kDeflBlock, 0, st>>>((const double2 *)D->V, Z, k, b, logb, (int)V, nch,
                                                                 partial);
-  else
+  else if (D->prec == DTR_F32)
     k_defl_partial<float2><<<nch * tiles, kDeflBlock, 0, st>>>((const float2 *)D->V, Z, k, b, logb, (int)V, nch,
                                                                partial);
+  else
+    k_defl_partial<bfc2><<<nch * tiles, kDeflBlock, 0, st>>>((const bfc2 *)D->V, Z, k, b, logb, (int)V, nch,
+                                                             partial);
   count_launches(1);
   const int64_t nkb = (int64_t)k * b;
   k_defl_reduce<<<(unsigned)((nkb + 255) / 256), 256, 0, st>>>(partial, k, b, nch, C); count_launches(1);
-  launch_defl_d(C, D->inv_lambda, k, b, d_dev, terms_dev, st);
+  if (d_dev) launch_defl_d(D, C, b, d_dev, terms_dev, st);
   if (x0_internal) {
+    k_defl_weights<<<(unsigned)((nkb + 255) / 256), 256, 0, st>>>(C, D->inv_lambda, D->Ginv, k, b, Wx);
+    count_launches(1);
     const int64_t n = V * 12 * b;
     unsigned grid = (unsigned)((n + 255) / 256);
     if (grid > 65535u * 8) grid = 65535u * 8;
     if (D->prec == DTR_F64)
-      k_defl_expand<double2><<<grid, 256, 0, st>>>((const double2 *)D->V, C, D->inv_lambda, k, b, V * 12,
-                                                   x0_internal);
+      k_defl_expand<double2><<<grid, 256, 0, st>>>((const double2 *)D->V, Wx, k, b, V * 12, x0_internal);
+    else if (D->prec == DTR_F32)
+      k_defl_expand<float2><<<grid, 256, 0, st>>>((const float2 *)D->V, Wx, k, b, V * 12, x0_internal);
     else
-      k_defl_expand<float2><<<grid, 256, 0, st>>>((const float2 *)D->V, C, D->inv_lambda, k, b, V * 12, x0_internal);
+      k_defl_expand<bfc2><<<grid, 256, 0, st>>>((const bfc2 *)D->V, Wx, k, b, V * 12, x0_internal);
     count_launches(1);
   }
   DTR_LAUNCH_CHECK("deflation projection");
@@ -324,8 +376,10 @@ int defl_trace_TD(dtr_defl_s *D, cudaStream_t st) {
   td = (double *)((char *)part + (((size_t)nch * k * sizeof(double) + 127) / 128) * 128);
   if (D->prec == DTR_F64)
     k_defl_td_partial<double2><<<nch, 256, 0, st>>>((const double2 *)D->V, k, N, nch, part);
-  else
+  else if (D->prec == DTR_F32)
     k_defl_td_partial<float2><<<nch, 256, 0, st>>>((const float2 *)D->V, k, N, nch, part);
+  else
+    k_defl_td_partial<bfc2><<<nch, 256, 0, st>>>((const bfc2 *)D->V, k, N, nch, part);
   count_launches(1);
   k_defl_td_reduce<<<1, 1, 0, st>>>(part, D->inv_lambda, k, nch, td); count_launches(1);
   cudaError_t e = cudaGetLastError();
@@ -349,6 +403,17 @@ int defl_trace_TD_gamma(dtr_defl_s *D, unsigned want, cudaStream_t st) {
       ids[gs.n++] = n;
     }
   if (gs.n == 0) return DTR_OK;
+  if (D->Ginv) {
+    double2 h[16];
+    int rc = defl_tdg_gram(D, gs, h, st);
+    if (rc) return rc;
+    for (int q = 0; q < gs.n; ++q) {
+      D->tdg[ids[q]][0] = h[q].x;
+      D->tdg[ids[q]][1] = h[q].y;
+      D->tdg_ok |= 1u << ids[q];
+    }
+    return DTR_OK;
+  }
   const int64_t nsite = D->lat.V;
   const int k = D->k;
   int nch = 4 * device_sms();
@@ -359,8 +424,10 @@ int defl_trace_TD_gamma(dtr_defl_s *D, unsigned want, cudaStream_t st) {
   td = (double2 *)((char *)part + pbytes);
   if (D->prec == DTR_F64)
     k_defl_tdg_partial<double2><<<nch, 128, 0, st>>>((const double2 *)D->V, k, nsite, nch, gs, part);
-  else
+  else if (D->prec == DTR_F32)
     k_defl_tdg_partial<float2><<<nch, 128, 0, st>>>((const float2 *)D->V, k, nsite, nch, gs, part);
+  else
+    k_defl_tdg_partial<bfc2><<<nch, 128, 0, st>>>((const bfc2 *)D->V, k, nsite, nch, gs, part);
   count_launches(1);
   k_defl_tdg_reduce<<<1, 32, 0, st>>>(part, D->inv_lambda, k, nch, gs.n, td);
   count_launches(1);

@@ -1,13 +1,24 @@
 // Deflation-space kernels shared by the C-ABI entry points and the estimator.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "dtr_internal.cuh"
 #include "gamma.cuh"
 
 namespace dtr {
 
+// Storage types of the deflation space V (DTR_F64, DTR_F32, DTR_BF16), widened
+// exactly to FP64 where the kernels accumulate.
+typedef __nv_bfloat162 bfc2;
+__device__ __forceinline__ double2 vload(const double2 &v) { return v; }
+__device__ __forceinline__ double2 vload(const float2 &v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ double2 vload(const bfc2 &v) {
+  return make_double2(__bfloat162float(v.x), __bfloat162float(v.y));
+}
+
 // Scratch for one projection of a width-b block.
-size_t defl_scratch_bytes(int64_t V, int k, int b, int sms);
+size_t defl_scratch_bytes(int64_t V, int k, int b, int sms);  // includes k x b expansion weights
 
 // C = V^H [Z, g5 Z] (k x 2b, kept in scratch; *C_out points at it),
 // d_dev[j] = sum_m conj(C[m,j]) C[m,b+j] / lambda_m, terms_dev (k x b, or
@@ -16,12 +27,17 @@ int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 
                           double2 *x0_internal, double2 **C_out, void *work, size_t work_bytes, int sms,
                           cudaStream_t st);
 
-// d_j (and per-m terms, or NULL) from C (column-major k x 2b).
-void launch_defl_d(const double2 *C, const double *inv_lambda, int k, int b, double2 *d, double2 *terms,
-                   cudaStream_t st);
-// d_j = sum_m conj(Cl[m, j]) Cr[m, b + j] / lambda_m (Cl, Cr column-major k x 2b).
-void launch_defl_d2(const double2 *Cl, const double2 *Cr, const double *inv_lambda, int k, int b, double2 *d,
-                    cudaStream_t st);
+// d_j (and per-m terms, or NULL) from C (column-major k x 2b): with the
+// eigenvalue form sum_m conj(C[m, j]) C[m, b+j] / lambda_m, with the Galerkin
+// correction (D->Ginv) c_j^H G^-1 g_j, per-m terms conj(c_jm) (G^-1 g_j)_m.
+void launch_defl_d(const dtr_defl_s *D, const double2 *C, int b, double2 *d, double2 *terms, cudaStream_t st);
+// d_j from Cl[:, j] and Cr[:, b + j] (Gamma insertion: Cl = V^H Gamma^H Z).
+void launch_defl_d2(const dtr_defl_s *D, const double2 *Cl, const double2 *Cr, int b, double2 *d, cudaStream_t st);
+// Galerkin correction: G = V^H g5 A V from the stored V and the gauge field, G^-1
+// kept on the device, T_D = Tr(G^-1 V^H g5 V) (gram.cu).
+int defl_gram(dtr_defl_s *D, const dtr_gauge_s *g, double m0, cudaStream_t st);
+// T_D of the Gammas in gs in the Galerkin form, Tr(G^-1 V^H g5 Gamma V).
+int defl_tdg_gram(const dtr_defl_s *D, const GammaSet &gs, double2 *out, cudaStream_t st);
 // GZ = (Gamma^H (x) 1) Z on the internal layout [site][12][b].
 void launch_gamma_h(const GammaMono &g, const double2 *Z, double2 *GZ, int64_t V, int b, cudaStream_t st);
 // T_D of every Gamma_n in `want` (bit n) not yet cached in D: sum_m v_m^H g5 Gamma v_m / lambda_m.

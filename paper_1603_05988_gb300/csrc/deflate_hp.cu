@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(kHPMaxThreads)
       for (int a = 0; a < 12; ++a) codes[tt * 12 + a] = (unsigned char)((raw[xf.src[a]] + xf.add[a]) & 3);
     }
     __syncthreads();
-    auto add = [&](int j, const VC vv, int code) {
+    auto add = [&](int j, const VC vr, int code) {
+      const double2 vv = vload(vr);
       const double vx = vv.x, vy = vv.y;
       // conj(v) * i^code: 0 -> (vx, -vy), 1 -> (vy, vx), 2 -> (-vx, vy), 3 -> (-vy, -vx)
       double re = (code & 1) ? vy : vx;
@@ -258,9 +259,12 @@ int defl_project_hp(const dtr_defl_s *D, const int *sites_by_colour, int ncolors
   if (D->prec == DTR_F64)
     k_hp_partial<double2><<<grid, nthr, 0, st>>>((const double2 *)D->V, sites_by_colour, per, ncolors, ns, k,
                                                   seed, run, x, partial);
-  else
+  else if (D->prec == DTR_F32)
     k_hp_partial<float2><<<grid, nthr, 0, st>>>((const float2 *)D->V, sites_by_colour, per, ncolors, ns, k, seed,
                                                  run, x, partial);
+  else
+    k_hp_partial<bfc2><<<grid, nthr, 0, st>>>((const bfc2 *)D->V, sites_by_colour, per, ncolors, ns, k, seed, run,
+                                               x, partial);
   count_launches(1);
   const int64_t nw = (int64_t)ncolors * 12 * k;
   k_hp_reduce<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(partial, ncolors, ns, k, dilute12, W);
@@ -268,7 +272,7 @@ int defl_project_hp(const dtr_defl_s *D, const int *sites_by_colour, int ncolors
   const int64_t nk = (int64_t)k * b;
   k_hp_finish<<<(unsigned)((nk + 127) / 128), 128, 0, st>>>(W, ncolors, k, b, nrhs, q0, dilute12, x, C);
   count_launches(1);
-  if (d_dev) launch_defl_d(C, D->inv_lambda, k, b, d_dev, terms_dev, st);
+  if (d_dev) launch_defl_d(D, C, b, d_dev, terms_dev, st);
   DTR_LAUNCH_CHECK("HP deflation projection");
   if (C_out) *C_out = C;
   return DTR_OK;

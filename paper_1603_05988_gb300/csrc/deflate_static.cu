@@ -25,6 +25,7 @@
 // clearing between calls.
 #include <mutex>
 
+#include "deflate.cuh"
 #include "dtr_internal.cuh"
 
 namespace dtr {
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(kSBlock)
       for (int q = 0; q < kSMPT; ++q) {
         const int m = mt * tile + grp + q * G;
         if (m >= k) continue;
-        const VC vv = Vd[i * k + m];
+        const double2 vv = vload(Vd[i * k + m]);
         const double vx = vv.x, vy = vv.y;
         const double re = vx * zz.x + vy * zz.y, im = vx * zz.y - vy * zz.x;
         if (c < 6) {
@@ -130,6 +131,8 @@ using namespace dtr;
 
 extern "C" int dtr_deflate_project_static(dtr_defl d, const double *z, int nrhs, double *d_out, double *coeff_out,
                                           void *stream) {
+  if (d && d->Ginv) return dtr::fail(DTR_EINVAL, "the allocation-free projection supports the eigenvalue form only "
+                                               "(not a Galerkin-corrected deflation space)");
   if (!d || !z || !d_out) return fail(DTR_EINVAL, "null argument");
   if (nrhs < 1 || nrhs > DTR_STATIC_MAX_RHS)
     return fail(DTR_EINVAL, "dtr_deflate_project_static: nrhs must be in [1, DTR_STATIC_MAX_RHS = 16]");
@@ -152,9 +155,12 @@ extern "C" int dtr_deflate_project_static(dtr_defl d, const double *z, int nrhs,
   if (d->prec == DTR_F64)
     k_static_partial<double2><<<nch * tiles, kSBlock, 0, st>>>((const double2 *)d->V, (const double2 *)z, d->lat.N, k,
                                                                nrhs, b, logb, (int)V, nch, partial);
-  else
+  else if (d->prec == DTR_F32)
     k_static_partial<float2><<<nch * tiles, kSBlock, 0, st>>>((const float2 *)d->V, (const double2 *)z, d->lat.N, k,
                                                               nrhs, b, logb, (int)V, nch, partial);
+  else
+    k_static_partial<bfc2><<<nch * tiles, kSBlock, 0, st>>>((const bfc2 *)d->V, (const double2 *)z, d->lat.N, k,
+                                                            nrhs, b, logb, (int)V, nch, partial);
   count_launches(1);
   k_static_finish<<<1, 32, 0, st>>>(partial, d->inv_lambda, k, b, nch, C, dd);
   count_launches(1);

@@ -143,6 +143,7 @@ struct dtr_defl_s {
   double td[2];
   double tdg[16][2];  // T_D of Gamma_n (Gamma-insertion traces), valid where tdg_ok bit n is set
   unsigned tdg_ok;
+  double2 *Ginv;      // device k x k (row-major) inverse of G = V^H g5 A V once the Galerkin correction is on
 };
 
 namespace dtr {

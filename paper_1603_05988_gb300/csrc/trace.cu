@@ -408,7 +408,7 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
             rc = defl_project_internal(D, ln.GZ, b, ln.tg, nullptr, nullptr, &Cg, ln.defl_work, L.defl, sms, s);
           }
           if (rc) return rc;
-          launch_defl_d2(Cg, ln.Cmain, D->inv_lambda, k, b, ln.dg + q * 64, s);
+          launch_defl_d2(D, Cg, ln.Cmain, b, ln.dg + q * 64, s);
         }
       }
     }

@@ -119,6 +119,7 @@ _sig("dtr_trace_workspace_bytes", _sz, [_vp, _vp, ctypes.POINTER(TraceParams)])
 _sig("dtr_trace_estimate", _i, [_vp, _d, _vp, ctypes.POINTER(TraceParams), _vp, _sz,
                                 ctypes.POINTER(TraceResult), _vp])
 _sig("dtr_wd", _i, [_vp, _vp, _vp, _i, _i, _i, _vp, _vp])
+_sig("dtr_defl_gram", _i, [_vp, _vp, _d, _vp])
 _sig("dtr_trace_autotune_workspace_bytes", _sz, [_vp, _vp, ctypes.POINTER(TraceParams)])
 _sig("dtr_trace_autotune", _i, [_vp, _d, _vp, ctypes.POINTER(TraceParams), _i, _i, _vp, _sz,
                                 ctypes.POINTER(TuneResult), _vp])
@@ -392,6 +393,11 @@ class Deflation:
         self._h = h
         self.lat = lat
         self.k = k
+
+    def gram(self, gauge, m0):
+        """Switch to the Galerkin form D = V (V^H g5 A V)^-1 V^H g5 (computed on the GPU in FP64)."""
+        _check(_lib.dtr_defl_gram(self._h, gauge._h, float(m0), _stream()))
+        return self
 
     def T_D(self):
         td = (ctypes.c_double * 2)()
