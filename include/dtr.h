@@ -147,6 +147,11 @@ size_t dtr_dslash_workspace_bytes(dtr_lattice lat, int nrhs);
 int dtr_dslash(dtr_gauge g, double m0, const double *in, double *out, int nrhs, int dagger,
                dtr_prec prec, void *work, size_t work_bytes, void *stream);
 
+/* Rows per link stored for the half-precision stencils: 3 (default; 240 B per site and right-hand side
+ * in all) or 2 (environment DTR_HALF_LINKS=2 before the first gauge field: 192 B, the third row rebuilt
+ * in registers as conj(row0 x row1)). */
+int dtr_half_link_rows(void);
+
 /* Benchmark hook for the stencil of the operator above: launches the
  * library's internal dslash kernel (the one the solver's fused kernels share)
  * `reps` times back to back on internal-layout fields of width nrhs held in

@@ -268,6 +268,8 @@ int dtr_dslash(dtr_gauge g, double m0, const double *in, double *out, int nrhs, 
   return DTR_OK;
 }
 
+int dtr_half_link_rows(void) { return half_link_rows(); }
+
 int dtr_time_dslash(dtr_gauge g, double m0, int nrhs, dtr_prec prec, int reps, void *work, size_t work_bytes,
                     double *avg_ms, void *stream) {
   if (!g || !work || !avg_ms) return fail(DTR_EINVAL, "null argument");

@@ -6,14 +6,15 @@
 // AoSoA over items: word w of 32 consecutive items is one contiguous 512-byte
 // run, so every warp-wide 16-byte load touches four consecutive 128-byte lines
 // instead of the twelve a plain [item][12] record layout would (that layout
-// made the kernel L1-wavefront bound).  Links in "2-row" form: the first two
-// rows of each SU(3) matrix (6 complex, 24 bytes); the four links of a site
-// are 24 complex = six 16-byte words, AoSoA over sites, and link mu is read as
-// the two words holding complex slots 6mu..6mu+5.  The third row is rebuilt
-// in registers as conj(row0 x row1), exact for SU(3).  Arithmetic is FP32.
+// made the kernel L1-wavefront bound).  Links, AoSoA over sites: all three
+// rows (36 complex = nine 16-byte words per site; link mu is read from the
+// three words holding slots 9mu..9mu+8), or in "2-row" form the first two rows
+// (24 complex = six words), with the third rebuilt in registers as
+// conj(row0 x row1), exact for SU(3) (see half_link_rows).  Arithmetic is FP32.
 //
 // Algorithmic traffic per site and right-hand side: 48 B in + 48 B out, plus
-// 4 links x 24 B = 96 B per site shared by the b right-hand sides.  The
+// 4 links x 36 B = 144 B per site shared by the b right-hand sides (96 B with
+// two stored rows).  The
 // eight neighbour reads of each spinor are served by L1/L2 (a t-slab of the
 // lattice is a few MB), so DRAM traffic stays close to the algorithmic bytes.
 #include <cuda_bf16.h>
@@ -42,6 +43,9 @@ __host__ __device__ __forceinline__ int64_t spw(int64_t it, int w) { return (((i
 __host__ __device__ __forceinline__ int spw32(int it, int w) { return (((it >> 5) * 3 + w) << 5) + (it & 31); }
 __host__ __device__ __forceinline__ int64_t lkw(int64_t site, int w) { return (((site >> 5) * 6 + w) << 5) + (site & 31); }
 __host__ __device__ __forceinline__ int lkw32(int site, int w) { return (((site >> 5) * 6 + w) << 5) + (site & 31); }
+// links with all three rows stored: 36 complex (nine 16-byte words) per site
+__host__ __device__ __forceinline__ int64_t lkw3(int64_t site, int w) { return (((site >> 5) * 9 + w) << 5) + (site & 31); }
+__host__ __device__ __forceinline__ int lkw3_32(int site, int w) { return (((site >> 5) * 9 + w) << 5) + (site & 31); }
 
 // 12 complex values of item `it` = 3 x 16-byte words
 template <typename H> __device__ __forceinline__ void load12(const H *__restrict__ base, int it, float2 out[12]) {
@@ -69,6 +73,22 @@ template <typename H> __device__ __forceinline__ void store12(H *__restrict__ ba
       words[k] = *reinterpret_cast<const unsigned int *>(&h);
     }
     q[spw32(it, w)] = make_uint4(words[0], words[1], words[2], words[3]);
+  }
+}
+
+// link mu of a site stored with all three rows (complex slots 9mu..9mu+8 of the site's 36)
+template <int MU, typename H>
+__device__ __forceinline__ void load_link3(const H *__restrict__ U, int site, float2 m[3][3]) {
+  constexpr int w0 = (9 * MU) / 4, off = (9 * MU) % 4;
+  const uint4 *q = reinterpret_cast<const uint4 *>(U);
+  const uint4 u0 = __ldg(q + lkw3_32(site, w0)), u1 = __ldg(q + lkw3_32(site, w0 + 1)),
+              u2 = __ldg(q + lkw3_32(site, w0 + 2));
+  const unsigned int words[12] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w, u2.x, u2.y, u2.z, u2.w};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    H h;
+    *reinterpret_cast<unsigned int *>(&h) = words[off + k];
+    m[k / 3][k % 3] = HalfOps<H>::to_f2(h);
   }
 }
 
@@ -114,7 +134,7 @@ template <int MU> __device__ __forceinline__ float2 hBH(const float2 &w0, const 
   return row == 0 ? w0 : w1;
 }
 
-template <int MU, typename H>
+template <int MU, typename H, int ROWS>
 __device__ __forceinline__ void half_hop(const H *__restrict__ U, const H *__restrict__ in, const Geom &g,
                                          const int xc[4], const int str[4], int s, int b, int j, float2 Su[2][3],
                                          float2 Sl[2][3]) {
@@ -135,7 +155,8 @@ __device__ __forceinline__ void half_hop(const H *__restrict__ U, const H *__res
         h[r][a] = make_float2(v[r * 3 + a].x - bl.x, v[r * 3 + a].y - bl.y);
       }
     float2 m[3][3];
-    load_link<MU, H>(U, s, m);
+    if (ROWS == 3) load_link3<MU, H>(U, s, m);
+    else load_link<MU, H>(U, s, m);
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
@@ -161,7 +182,8 @@ __device__ __forceinline__ void half_hop(const H *__restrict__ U, const H *__res
         h[r][a] = make_float2(v[r * 3 + a].x + bl.x, v[r * 3 + a].y + bl.y);
       }
     float2 m[3][3];
-    load_link<MU, H>(U, sb, m);
+    if (ROWS == 3) load_link3<MU, H>(U, sb, m);
+    else load_link<MU, H>(U, sb, m);
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
@@ -191,7 +213,7 @@ __device__ __forceinline__ void half_hop(const H *__restrict__ U, const H *__res
 }
 
 // out = A in on half-precision AoSoA fields; thread per item (site, rhs), rhs fastest.
-template <typename H, int MINB>
+template <typename H, int MINB, int ROWS>
 __global__ void __launch_bounds__(256, MINB) k_dslash_half(const H *__restrict__ U, const H *__restrict__ in,
                                                            H *__restrict__ out, Geom g, int b, float diag) {
   const int n = g.V * b;
@@ -206,10 +228,10 @@ __global__ void __launch_bounds__(256, MINB) k_dslash_half(const H *__restrict__
     for (int r = 0; r < 2; ++r)
 #pragma unroll
       for (int a = 0; a < 3; ++a) Su[r][a] = Sl[r][a] = make_float2(0.f, 0.f);
-    half_hop<0, H>(U, in, g, xc, str, s, b, j, Su, Sl);
-    half_hop<1, H>(U, in, g, xc, str, s, b, j, Su, Sl);
-    half_hop<2, H>(U, in, g, xc, str, s, b, j, Su, Sl);
-    half_hop<3, H>(U, in, g, xc, str, s, b, j, Su, Sl);
+    half_hop<0, H, ROWS>(U, in, g, xc, str, s, b, j, Su, Sl);
+    half_hop<1, H, ROWS>(U, in, g, xc, str, s, b, j, Su, Sl);
+    half_hop<2, H, ROWS>(U, in, g, xc, str, s, b, j, Su, Sl);
+    half_hop<3, H, ROWS>(U, in, g, xc, str, s, b, j, Su, Sl);
     float2 self[12], o[12];
     load12<H>(in, it, self);
 #pragma unroll
@@ -256,6 +278,17 @@ __global__ void k_unpack_half(const H *__restrict__ in, double2 *__restrict__ ca
 
 // FP64 links [site][mu][3][3] -> two rows, half precision: the 24 complex
 // slots of a site (slot 6mu + k = row k/3, column k%3 of link mu), AoSoA over sites
+// all three rows: slot 9mu + k = row k/3, column k%3 of link mu
+template <typename H> __global__ void k_pack_links_half3(const double2 *__restrict__ U, H *__restrict__ out, int64_t V) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < V * 36; e += (int64_t)gridDim.x * blockDim.x) {
+    const int slot = (int)(e % 36);
+    const int64_t site = e / 36;
+    const int mu = slot / 9, k = slot % 9;
+    const double2 v = U[(site * 4 + mu) * 9 + k];
+    out[lkw3(site, slot >> 2) * 4 + (slot & 3)] = HalfOps<H>::from_f2(make_float2((float)v.x, (float)v.y));
+  }
+}
+
 template <typename H> __global__ void k_pack_links_half(const double2 *__restrict__ U, H *__restrict__ out, int64_t V) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < V * 24; e += (int64_t)gridDim.x * blockDim.x) {
     const int slot = (int)(e % 24);
@@ -277,13 +310,29 @@ static int half_occupancy() {
   return occ;
 }
 
+// Links of the half-precision stencil: all three rows stored (default), 144 B per
+// site, so a site and right-hand side moves exactly the algorithmic 240 B; or two
+// rows with the third rebuilt in registers as conj(row0 x row1) (96 B of links,
+// about 36 more FP32 instructions per hop).  DTR_HALF_LINKS=2 selects the
+// latter; read once per process, before the first gauge field is packed.
+int half_link_rows() {
+  static int v = 0;
+  if (!v) {
+    const char *e = getenv("DTR_HALF_LINKS");
+    v = (e && e[0] == '2') ? 2 : 3;
+  }
+  return v;
+}
+
 template <typename H>
 static void launch_half_kernel(const H *U, const H *in, H *out, const Geom &g, int b, float diag, unsigned grid,
                                cudaStream_t st) {
-  if (half_occupancy() == 3)
-    k_dslash_half<H, 3><<<grid, 256, 0, st>>>(U, in, out, g, b, diag);
+  if (half_link_rows() == 3)
+    k_dslash_half<H, 2, 3><<<grid, 256, 0, st>>>(U, in, out, g, b, diag);
+  else if (half_occupancy() == 3)
+    k_dslash_half<H, 3, 2><<<grid, 256, 0, st>>>(U, in, out, g, b, diag);
   else
-    k_dslash_half<H, 2><<<grid, 256, 0, st>>>(U, in, out, g, b, diag);
+    k_dslash_half<H, 2, 2><<<grid, 256, 0, st>>>(U, in, out, g, b, diag);
 }
 
 static unsigned g1(int64_t n) {
@@ -293,14 +342,22 @@ static unsigned g1(int64_t n) {
 }
 
 // sizes rounded up to whole groups of 32 items / sites
-size_t half_links_bytes(int64_t V) { return (size_t)((V + 31) / 32) * 32 * 24 * sizeof(__half2); }
+size_t half_links_bytes(int64_t V) {
+  return (size_t)((V + 31) / 32) * 32 * (half_link_rows() == 3 ? 36 : 24) * sizeof(__half2);
+}
 size_t half_field_bytes(int64_t V, int b) { return (size_t)((V * b + 31) / 32) * 32 * 12 * sizeof(__half2); }
 
 void launch_pack_links_half(const double2 *U64, void *out, int64_t V, int bf16, cudaStream_t st) {
-  if (bf16)
+  if (half_link_rows() == 3) {
+    if (bf16)
+      k_pack_links_half3<__nv_bfloat162><<<g1(V * 36), 256, 0, st>>>(U64, (__nv_bfloat162 *)out, V);
+    else
+      k_pack_links_half3<__half2><<<g1(V * 36), 256, 0, st>>>(U64, (__half2 *)out, V);
+  } else if (bf16) {
     k_pack_links_half<__nv_bfloat162><<<g1(V * 24), 256, 0, st>>>(U64, (__nv_bfloat162 *)out, V);
-  else
+  } else {
     k_pack_links_half<__half2><<<g1(V * 24), 256, 0, st>>>(U64, (__half2 *)out, V);
+  }
   count_launches(1);
 }
 

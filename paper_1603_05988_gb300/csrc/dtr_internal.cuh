@@ -130,7 +130,8 @@ struct dtr_gauge_s {
   dtr_lattice_s lat;
   double2 *U64;   // [site][mu][3][3], FP64
   float2 *U32;    // same layout, FP32
-  void *Ubf16;    // [site][mu][8] BF16 complex: two stored rows + 2 padding slots
+  void *Ubf16;    // BF16 links of the half-precision stencil, AoSoA over sites: three stored rows
+                  // (36 complex per site) or two (24), see half_link_rows()
   void *Uf16;     // same, FP16
 };
 
@@ -185,6 +186,7 @@ void launch_dslash(const typename cplx_t<R>::type *U, const typename cplx_t<R>::
 
 // half-precision-storage stencil (dslash_half.cu)
 size_t half_links_bytes(int64_t V);
+int half_link_rows();
 size_t half_field_bytes(int64_t V, int b);
 void launch_pack_links_half(const double2 *U64, void *out, int64_t V, int bf16, cudaStream_t st);
 void launch_dslash_half_canon(const void *Uh, const double2 *in, double2 *out, void *work, const Geom &g, int nrhs,

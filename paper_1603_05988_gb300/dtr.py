@@ -84,6 +84,7 @@ def _sig(name, res, args):
 _sig("dtr_last_error", ctypes.c_char_p, [])
 _sig("dtr_version", ctypes.c_char_p, [])
 _sig("dtr_kernel_launches", ctypes.c_uint64, [])
+_sig("dtr_half_link_rows", ctypes.c_int, [])
 _sig("dtr_graph_stats", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)])
 _sig("dtr_profile_persistent", _i, [_i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64),
                                     ctypes.POINTER(ctypes.c_double)])
@@ -255,6 +256,11 @@ def profile_persistent(enable=-1):
     w = ctypes.c_double()
     _check(_lib.dtr_profile_persistent(int(enable), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
     return {"ms": ms.value, "launches": n.value, "site_rhs_iterations": w.value}
+
+
+def half_link_rows():
+    """Rows per link the half-precision stencil stores (3, or 2 with the third rebuilt)."""
+    return int(_lib.dtr_half_link_rows())
 
 
 def kernel_launches():

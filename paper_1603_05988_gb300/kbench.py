@@ -21,11 +21,17 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # algorithmic bytes per site and right-hand side (in + out) and per site for the four 3x3 links, by
-# storage precision (each array touched once); the half-precision stencil stores two rows per link and
-# rebuilds the third, so it moves LINK_STORED_BYTES instead
+# storage precision (each array touched once); the half-precision stencil moves 96 B of links per site
+# instead of 144 when it stores two rows and rebuilds the third (dtr.half_link_rows() == 2)
 SPINOR_BYTES = {"f64": 2 * 192, "f32": 2 * 96, "bf16": 2 * 48, "f16": 2 * 48}
 LINK_BYTES = {"f64": 576, "f32": 288, "bf16": 144, "f16": 144}
-LINK_STORED_BYTES = {"f64": 576, "f32": 288, "bf16": 96, "f16": 96}
+
+
+def link_stored_bytes(prec):
+    from . import dtr
+    if prec in ("bf16", "f16"):
+        return 48 * dtr.half_link_rows()
+    return LINK_BYTES[prec]
 FLOPS_PER_SITE = 1368.0   # 1320 hopping (8 directions x (12 + 2 x 66 + 24) - 24) + 48 diagonal
 
 
@@ -49,9 +55,10 @@ def dslash_case(gauge, dims, prec, nrhs, reps, m0=-0.75):
     V = int(np.prod(dims))
     b = nrhs if prec in ("bf16", "f16") else dtr_pad(nrhs)
     alg_bytes = V * nrhs * SPINOR_BYTES[prec] + V * LINK_BYTES[prec]
-    moved = V * nrhs * SPINOR_BYTES[prec] + V * LINK_STORED_BYTES[prec]
+    moved = V * nrhs * SPINOR_BYTES[prec] + V * link_stored_bytes(prec)
     flops = V * nrhs * FLOPS_PER_SITE
     return {"kernel": "dslash", "lattice": list(dims), "prec": prec, "nrhs": nrhs, "padded_width": b,
+            "link_rows": dtr.half_link_rows() if prec in ("bf16", "f16") else 3,
             "avg_launch_ms": ms, "alg_bytes_per_launch": alg_bytes, "stored_bytes_per_launch": moved,
             "flops_per_launch": flops, "moved_gbs": moved / (ms * 1e-3) / 1e9,
             "achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9, "achieved_tflops": flops / (ms * 1e-3) / 1e12}
