@@ -105,3 +105,37 @@ def gamma5_vec(psi):
 def dense(U, dims, m0):
     """Dense A (small lattices only)."""
     return explicit(U, dims, m0).toarray()
+
+
+def apply_at(U, dims, m0, psi, sites):
+    """(A psi) at the listed sites only, written from the operator's definition one
+    direction at a time (a third coding, for lattices too large for the whole-field
+    forms): returns (len(sites), 12[, nrhs]) with rows 3 spin + colour."""
+    single = psi.ndim == 1
+    P = psi.reshape(12 * _lat.volume(dims), -1)
+    nr = P.shape[1]
+    sites = np.asarray(sites, dtype=np.int64)
+    c = _lat.coords(dims)[sites]                      # (S, 4) as (x, y, z, t)
+    g = _gamma.gammas()
+    eye4 = np.eye(4, dtype=np.complex128)
+
+    def spinor(s):                                    # (S, 4, 3, nr)
+        idx = (12 * s[:, None] + np.arange(12)[None, :])
+        return P[idx].reshape(len(s), 4, 3, nr)
+
+    out = (4.0 + m0) * spinor(sites)
+    for mu in range(4):
+        cf = c.copy()
+        cf[:, mu] = (cf[:, mu] + 1) % dims[mu]
+        cb = c.copy()
+        cb[:, mu] = (cb[:, mu] - 1) % dims[mu]
+        sf = _lat.site_index(cf, dims)
+        sb = _lat.site_index(cb, dims)
+        Uf = U[sites, mu]                             # U_mu(x)
+        Ub = U[sb, mu]                                # U_mu(x - mu)
+        hop_f = np.einsum("kab,ksbr->ksar", Uf, spinor(sf))
+        hop_b = np.einsum("kba,ksbr->ksar", np.conj(Ub), spinor(sb))
+        out = out - 0.5 * np.einsum("st,ktar->ksar", eye4 - g[mu], hop_f)
+        out = out - 0.5 * np.einsum("st,ktar->ksar", eye4 + g[mu], hop_b)
+    out = out.reshape(len(sites), 12, nr)
+    return out[:, :, 0] if single else out

@@ -52,6 +52,22 @@ def random_orthonormal(N, k, seed):
     return Q
 
 
+def disjoint_orthonormal(N, k, seed, support=256):
+    """N x k complex matrix with exactly orthonormal columns that is cheap at any N:
+    column m is supported on its own random set of `support` dofs with Z4 phases,
+    scaled by 1/sqrt(support).  Stands in for a deflation space where only the
+    projection arithmetic is under test (the estimator is unbiased for any V)."""
+    if k * support > N:
+        raise ValueError("k * support must not exceed N")
+    rng = np.random.Generator(np.random.Philox(key=int(seed) + 91))
+    idx = rng.choice(N, size=k * support, replace=False).reshape(k, support)
+    ph = np.array([1, 1j, -1, -1j])[rng.integers(0, 4, size=(k, support))]
+    V = np.zeros((N, k), dtype=np.complex128)
+    for m in range(k):
+        V[idx[m], m] = ph[m] / np.sqrt(support)
+    return V
+
+
 @dataclass
 class Workload:
     name: str

@@ -89,3 +89,23 @@ def test_dagger_is_conjugate_transpose_action():
     y = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
     # <y, A x> = <A^H y, x>
     assert abs(np.vdot(y, A @ x) - np.vdot(AH @ y, x)) < 1e-12 * np.linalg.norm(x) * np.linalg.norm(y)
+
+
+@pytest.mark.parametrize("dims,nr", [((4, 4, 4, 4), 1), ((4, 2, 4, 6), 3)])
+def test_apply_at_sites_matches_whole_field(dims, nr):
+    """The per-site coding of A (used at lattice sizes too large for the
+    whole-field forms) agrees with the matrix-free and explicit codings."""
+    from oracle import wilson
+    from paper_1603_05988_gb300 import synth
+    U = synth.random_su3_links(dims, 0.6, 19)
+    N = 12 * int(np.prod(dims))
+    rng = np.random.default_rng(3)
+    psi = rng.standard_normal((N, nr)) + 1j * rng.standard_normal((N, nr))
+    full = wilson.apply(U, dims, -0.3, psi)
+    sites = [0, 5, N // 12 - 1, 17]
+    at = wilson.apply_at(U, dims, -0.3, psi, sites)
+    for q, s in enumerate(sites):
+        assert np.allclose(at[q], full[12 * s:12 * s + 12], rtol=1e-13, atol=1e-13)
+    ex = wilson.explicit(U, dims, -0.3) @ psi[:, 0]
+    at1 = wilson.apply_at(U, dims, -0.3, psi[:, 0], sites)
+    assert np.allclose(at1, np.stack([ex[12 * s:12 * s + 12] for s in sites]), rtol=1e-13, atol=1e-13)
