@@ -392,6 +392,16 @@ size_t dtr_trace_workspace_bytes(dtr_gauge g, dtr_defl d, const dtr_trace_params
 int dtr_trace_estimate(dtr_gauge g, double m0, dtr_defl d, const dtr_trace_params *p,
                        void *work, size_t work_bytes, dtr_trace_result *res, void *stream);
 
+/* Deflation contraction C = V^H [Z, gamma_5 Z] of the estimator's probing blocks (entries 0, +-1, +-i)
+ * when V is stored in BF16: a BF16 GEMM on the tensor cores (tcgen05, FP32 accumulation in tensor
+ * memory per chunk of dofs, FP64 across chunks).  dtr_time_deflate times it (CUDA events on `stream`,
+ * average ms per contraction of an nrhs-column Z4 block, nrhs 1..64, reps >= 1; the FP64 CUDA-core
+ * contraction for other storage precisions); its workspace is dtr_time_deflate_workspace_bytes.
+ * dtr_tensor_core_contractions counts tensor-core contractions launched in this process. */
+size_t dtr_time_deflate_workspace_bytes(dtr_defl d, int nrhs);
+int dtr_time_deflate(dtr_defl d, int nrhs, int reps, void *work, size_t work_bytes, double *avg_ms, void *stream);
+uint64_t dtr_tensor_core_contractions(void);
+
 /* ----------------------------------------------------------- diagnostics */
 /* W_d distance diagnostic (Section 6.2).  cols: device, canonical N x ns complex128 (column q =
  * B e_(dofs[q]) for the matrix B under study, e.g. A^-1 or its deflated remainder; by

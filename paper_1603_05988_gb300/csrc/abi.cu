@@ -679,6 +679,51 @@ int dtr_trace_estimate(dtr_gauge g, double m0, dtr_defl d, const dtr_trace_param
   return trace_estimate(g, m0, d, p, work, work_bytes, res, (cudaStream_t)stream);
 }
 
+size_t dtr_time_deflate_workspace_bytes(dtr_defl d, int nrhs) {
+  if (!d || nrhs < 1 || nrhs > 64) return 0;
+  const int b = pad_rhs(nrhs);
+  return (((size_t)d->lat.V * 12 * b * sizeof(double2) + 255) / 256) * 256 + 64 * sizeof(double2) + 256 +
+         defl_scratch_bytes(d->lat.V, d->k, b, device_sms()) + 256;
+}
+
+int dtr_time_deflate(dtr_defl d, int nrhs, int reps, void *work, size_t work_bytes, double *avg_ms, void *stream) {
+  if (!d || !work || !avg_ms) return fail(DTR_EINVAL, "null argument");
+  if (nrhs < 1 || nrhs > 64 || reps < 1) return fail(DTR_EINVAL, "nrhs must be in [1, 64] and reps >= 1");
+  if (work_bytes < dtr_time_deflate_workspace_bytes(d, nrhs)) return fail(DTR_ENOMEM, "workspace too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int b = pad_rhs(nrhs);
+  const Geom geo = geom_of(d->lat);
+  char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+  double2 *Z = (double2 *)w;
+  w += (((size_t)d->lat.V * 12 * b * sizeof(double2) + 255) / 256) * 256;
+  double2 *dd = (double2 *)w;
+  w += 64 * sizeof(double2) + 256;
+  const size_t sb = defl_scratch_bytes(d->lat.V, d->k, b, device_sms());
+  launch_noise(Z, geo, 0x5EED, 0, 1, 0, 0, 1, nrhs, b, st);  // one Z4 vector per column
+  int rc = defl_project_internal(d, Z, b, dd, nullptr, nullptr, nullptr, w, sb, device_sms(), st, 1);  // warm
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  DTR_CUDA(cudaEventCreate(&e0));
+  DTR_CUDA(cudaEventCreate(&e1));
+  DTR_CUDA(cudaEventRecord(e0, st));
+  for (int r = 0; r < reps && rc == DTR_OK; ++r)
+    rc = defl_project_internal(d, Z, b, dd, nullptr, nullptr, nullptr, w, sb, device_sms(), st, 1);
+  DTR_CUDA(cudaEventRecord(e1, st));
+  DTR_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  DTR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  int herr = 0;
+  DTR_CUDA(cudaMemcpy(&herr, defl_error_word(w), sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) return fail(DTR_ETIMEOUT, "tensor-core deflation stage timed out");
+  *avg_ms = ms / reps;
+  return DTR_OK;
+}
+
+uint64_t dtr_tensor_core_contractions(void) { return (uint64_t)defl_tc_calls(); }
+
 int dtr_wd(dtr_lattice lat, const double *cols, const int64_t *dofs, int ns, int maxd, int ncolors, double *W,
            void *stream) {
   if (!lat || !cols || !dofs || !W) return fail(DTR_EINVAL, "null argument");

@@ -311,15 +311,20 @@ static int defl_chunks(int64_t V, int k, int b, int sms) {
 size_t defl_scratch_bytes(int64_t V, int k, int b, int sms) {
   const int nch = defl_chunks(V, k, b, sms);
   size_t part = (size_t)nch * k * 2 * b * sizeof(double2);
+  const size_t tc = defl_tc_scratch_bytes(V, k, b, sms);  // the tensor-core partials share this region
+  if (tc > part) part = tc;
   const size_t C = (size_t)k * 2 * b * sizeof(double2);
   const size_t W = (size_t)k * b * sizeof(double2);
   const size_t d = 64 * sizeof(double2);
-  return ((part + 255) / 256 + (C + 255) / 256 + (W + 255) / 256 + (d + 255) / 256 + 3) * 256;
+  return ((part + 255) / 256 + (C + 255) / 256 + (W + 255) / 256 + (d + 255) / 256 + 5) * 256;
 }
+
+// layout of the scratch: [status word, 256 B][partials][C][x0 weights]
+int *defl_error_word(void *work) { return (int *)(((uintptr_t)work + 255) & ~(uintptr_t)255); }
 
 int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 *d_dev, double2 *terms_dev,
                           double2 *x0_internal, double2 **C_out, void *work, size_t work_bytes, int sms,
-                          cudaStream_t st) {
+                          cudaStream_t st, int z4) {
   const int64_t V = D->lat.V;
   const int k = D->k;
   if (work_bytes < defl_scratch_bytes(V, k, b, sms)) return fail(DTR_ENOMEM, "deflation workspace too small");
@@ -327,13 +332,24 @@ int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 
   const int G = kDeflBlock / b;
   const int tiles = (k + G * kMPT - 1) / (G * kMPT);
   char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+  int *err = (int *)w;
+  w += 256;
   double2 *partial = (double2 *)w;
-  w += (((size_t)nch * k * 2 * b * sizeof(double2) + 255) / 256) * 256;
+  size_t partbytes = (size_t)nch * k * 2 * b * sizeof(double2);
+  const size_t tcbytes = defl_tc_scratch_bytes(V, k, b, sms);
+  if (tcbytes > partbytes) partbytes = tcbytes;
+  w += ((partbytes + 255) / 256) * 256;
   double2 *C = (double2 *)w;
   w += (((size_t)k * 2 * b * sizeof(double2) + 255) / 256) * 256;
   double2 *Wx = (double2 *)w;
   w += (((size_t)k * b * sizeof(double2) + 255) / 256) * 256;
   const int logb = log2i(b);
+  const int64_t nkb = (int64_t)k * b;
+  if (z4 && defl_tc_enabled(D, b)) {
+    DTR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    int rc = defl_contract_tc(D, Z, b, C, partial, partbytes, err, sms, st);
+    if (rc) return rc;
+  } else {
   if (D->prec == DTR_F64)
     k_defl_partial<double2><<<nch * tiles, kDeflBlock, 0, st>>>((const double2 *)D->V, Z, k, b, logb, (int)V, nch,
                                                                 partial);
@@ -344,8 +360,8 @@ int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 
     k_defl_partial<bfc2><<<nch * tiles, kDeflBlock, 0, st>>>((const bfc2 *)D->V, Z, k, b, logb, (int)V, nch,
                                                              partial);
   count_launches(1);
-  const int64_t nkb = (int64_t)k * b;
   k_defl_reduce<<<(unsigned)((nkb + 255) / 256), 256, 0, st>>>(partial, k, b, nch, C); count_launches(1);
+  }
   if (d_dev) launch_defl_d(D, C, b, d_dev, terms_dev, st);
   if (x0_internal) {
     k_defl_weights<<<(unsigned)((nkb + 255) / 256), 256, 0, st>>>(C, D->inv_lambda, D->Ginv, k, b, Wx);

@@ -371,7 +371,10 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
     DTR_CUDA(cudaEventRecord(t_pool.start, st));
     for (int l = 0; l < nlanes; ++l) DTR_CUDA(cudaStreamWaitEvent(lanes[l].s, t_pool.start, 0));
   }
-  for (int l = 0; l < nlanes; ++l) DTR_CUDA(cudaMemsetAsync(lanes[l].red.counter, 0, 256, lanes[l].s));
+  for (int l = 0; l < nlanes; ++l) {
+    DTR_CUDA(cudaMemsetAsync(lanes[l].red.counter, 0, 256, lanes[l].s));
+    if (D) DTR_CUDA(cudaMemsetAsync(defl_error_word(lanes[l].defl_work), 0, sizeof(int), lanes[l].s));
+  }
 
   // Enqueue the whole pipeline of one block of probing columns on its lane.
   auto enqueue_block = [&](Lane &ln, int64_t G0) -> int {
@@ -392,7 +395,7 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
                              ln.d_dev, res->replay ? ln.terms_dev : nullptr, ln.hp_work, L.hp, sms, s, nullptr, &Cm);
       else
         rc = defl_project_internal(D, ln.Z, b, ln.d_dev, res->replay ? ln.terms_dev : nullptr,
-                                   p->use_x0 ? ln.X : nullptr, &Cm, ln.defl_work, L.defl, sms, s);
+                                   p->use_x0 ? ln.X : nullptr, &Cm, ln.defl_work, L.defl, sms, s, 1);
       if (rc) return rc;
       if (ng) {
         // d^G_j = (V^H Gamma^H z_j)^H Lambda^-1 (V^H g5 z_j): the g5 half of this block's C is kept
@@ -405,7 +408,7 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
                                  b, nullptr, nullptr, ln.hp_work, L.hp, sms, s, &xf, &Cg);
           } else {
             launch_gamma_h(gset.g[q], ln.Z, ln.GZ, g.V, b, s);
-            rc = defl_project_internal(D, ln.GZ, b, ln.tg, nullptr, nullptr, &Cg, ln.defl_work, L.defl, sms, s);
+            rc = defl_project_internal(D, ln.GZ, b, ln.tg, nullptr, nullptr, &Cg, ln.defl_work, L.defl, sms, s, 1);
           }
           if (rc) return rc;
           launch_defl_d2(D, Cg, ln.Cmain, b, ln.dg + q * 64, s);
@@ -436,6 +439,7 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
       DTR_CUDA(cudaMemcpyAsync(ln.terms_h, ln.terms_dev, sizeof(double2) * k * b, cudaMemcpyDeviceToHost, s));
     if (nlanes > 1)
       DTR_CUDA(cudaMemcpyAsync(ln.err_h, solver_error_word(ln.solver_work), sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (D) DTR_CUDA(cudaMemcpyAsync(ln.err_h + 1, defl_error_word(ln.defl_work), sizeof(int), cudaMemcpyDeviceToHost, s));
     return DTR_OK;
   };
   // Fold one finished block into the host records (in block order: the
@@ -487,6 +491,7 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
     for (int l = 0; l < used; ++l) DTR_CUDA(cudaStreamSynchronize(lanes[l].s));
     for (int l = 0; l < used; ++l) {
       if (nlanes > 1 && *lanes[l].err_h) return fail(DTR_ETIMEOUT, "persistent solver barrier timed out");
+      if (D && lanes[l].err_h[1]) return fail(DTR_ETIMEOUT, "tensor-core deflation stage timed out");
       fold_block(lanes[l]);
     }
   }

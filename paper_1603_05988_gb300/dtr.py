@@ -85,6 +85,10 @@ _sig("dtr_last_error", ctypes.c_char_p, [])
 _sig("dtr_version", ctypes.c_char_p, [])
 _sig("dtr_kernel_launches", ctypes.c_uint64, [])
 _sig("dtr_half_link_rows", ctypes.c_int, [])
+_sig("dtr_tensor_core_contractions", ctypes.c_uint64, [])
+_sig("dtr_time_deflate_workspace_bytes", ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int])
+_sig("dtr_time_deflate", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.c_size_t, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p])
 _sig("dtr_graph_stats", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)])
 _sig("dtr_profile_persistent", _i, [_i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64),
                                     ctypes.POINTER(ctypes.c_double)])
@@ -256,6 +260,21 @@ def profile_persistent(enable=-1):
     w = ctypes.c_double()
     _check(_lib.dtr_profile_persistent(int(enable), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
     return {"ms": ms.value, "launches": n.value, "site_rhs_iterations": w.value}
+
+
+def tensor_core_contractions():
+    """Deflation contractions that ran on the tensor cores so far in this process."""
+    return int(_lib.dtr_tensor_core_contractions())
+
+
+def time_deflate(defl, nrhs, reps=20):
+    """Average duration (ms) of one deflation contraction of an nrhs-column Z4 block
+    (tensor cores for a BF16-stored deflation space), CUDA events on the current stream."""
+    nb = _lib.dtr_time_deflate_workspace_bytes(defl._h, int(nrhs))
+    w = _workspace(nb)
+    ms = ctypes.c_double()
+    _check(_lib.dtr_time_deflate(defl._h, int(nrhs), int(reps), _ptr(w), nb, ctypes.byref(ms), _stream()))
+    return ms.value
 
 
 def half_link_rows():

@@ -2,6 +2,7 @@
 
     python -m paper_1603_05988_gb300.kbench dslash --lattice 32,32,32,64 --prec bf16 --nrhs 1 --reps 20
     python -m paper_1603_05988_gb300.kbench solve --lattice 8,8,8,8 --nrhs 16 --reps 3 [--no-graph]
+    python -m paper_1603_05988_gb300.kbench deflate --lattice 16,16,16,32 --k 256 --prec bf16 --nrhs 16 --reps 20
 
 Large lattices take their links from the seeded 16^3x32 field repeated
 periodically (exact SU(3) matrices; the stencil's cost does not depend on
@@ -88,6 +89,25 @@ def solve_case(gauge, dims, nrhs, reps, m0, graph=True, grid=0):
             "persistent_ms_per_launch": prof["ms"] / max(prof["launches"], 1)}
 
 
+def deflate_case(dims, k, nrhs, reps, prec="bf16"):
+    """The deflation contraction C = V^H [Z, g5 Z] of an nrhs-column Z4 block with k
+    vectors stored in `prec` (tensor cores for BF16).  Algorithmic work: V read once
+    (N k x 4 B in BF16) plus the block (N x nrhs x 16 B); 8 N k (2 nrhs) real flops."""
+    from . import dtr, synth
+    lat = dtr.make_lattice(dims)
+    V = synth.disjoint_orthonormal(lat.N, k, 3, support=max(1, min(256, lat.N // k)))
+    lam = np.linspace(0.5, 1.5, k)
+    D = dtr.defl_create(lat, V, lam, prec=prec)
+    del V
+    ms = dtr.time_deflate(D, nrhs, reps)
+    vb = {"bf16": 4, "f32": 8, "f64": 16}[prec]
+    alg_bytes = lat.N * k * vb + lat.N * nrhs * 16
+    flops = 8.0 * lat.N * k * 2 * nrhs
+    return {"kernel": "deflation contraction", "lattice": list(dims), "k": k, "nrhs": nrhs, "prec": prec,
+            "avg_launch_ms": ms, "alg_bytes_per_launch": alg_bytes, "flops_per_launch": flops,
+            "achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9, "achieved_tflops": flops / (ms * 1e-3) / 1e12}
+
+
 def dtr_pad(n):
     b = 1
     while b < n:
@@ -97,7 +117,8 @@ def dtr_pad(n):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["dslash", "solve"])
+    ap.add_argument("what", choices=["dslash", "solve", "deflate"])
+    ap.add_argument("--k", type=int, default=256)
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--prec", default="bf16")
     ap.add_argument("--nrhs", default="1")
@@ -112,6 +133,11 @@ def main(argv=None):
         _b.build()
     from . import dtr
     dims = tuple(int(x) for x in a.lattice.split(","))
+    if a.what == "deflate":
+        for prec in a.prec.split(","):
+            for n in a.nrhs.split(","):
+                print(json.dumps(deflate_case(dims, a.k, int(n), a.reps, prec)), flush=True)
+        return
     lat = dtr.make_lattice(dims)
     if a.what == "solve":
         from . import synth

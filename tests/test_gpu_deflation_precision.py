@@ -86,3 +86,30 @@ def test_gram_matches_oracle_galerkin(dtr, c4, prec):
     G5 = gi.dense(gi.clifford(15), c["N"])
     td5 = np.trace(G5 @ Dg)
     assert abs(out["gamma"][0]["T_D"] - td5) <= 1e-9 * max(abs(td5), 1.0)
+
+
+@pytest.mark.parametrize("dims,k,b,R", [((4, 4, 4, 4), 32, 16, 32), ((8, 8, 8, 8), 200, 16, 16),
+                                        ((4, 4, 4, 8), 64, 3, 6)])
+def test_tensor_core_contraction_matches_oracle(dtr, dims, k, b, R):
+    """Plain Z4 blocks (one vector per run, blocks spanning runs) with a BF16
+    deflation space take the tensor-core contraction (BF16 operands, FP32
+    accumulation per dof chunk, FP64 across chunks): the per-sample deflation
+    terms match the oracle's gamma5 form for the same rounded V to FP32
+    accumulation accuracy, and T_D is exact."""
+    lat = dtr.make_lattice(dims)
+    U = synth.random_su3_links(dims, 0.5, 1000)
+    g = dtr.make_gauge(lat, U)
+    V = synth.random_orthonormal(lat.N, k, 7)
+    lam = np.where(np.arange(k) % 2 == 0, 1.0, -1.0) * np.linspace(0.7, 1.6, k)
+    D = dtr.defl_create(lat, V, lam, prec="bf16")
+    p = dtr.trace_params(seed=5, n_z0=R, ncolors=1, nvec=1, block=b,
+                         solve=dtr.solve_params(tol=1e-10, solver="mixed_f32"))
+    n0 = dtr.tensor_core_contractions()
+    out = dtr.trace_estimate(g, -0.4, D, p, want_replay=True)
+    assert dtr.tensor_core_contractions() - n0 == (R + b - 1) // b    # one per block
+    Vr = deflation.bf16_round(V)
+    Z = np.stack([noise.z0_vector(5, r, lat.N) for r in range(R)], axis=1)
+    d_ref = deflation.quadrature_gamma5(Vr, lam, Z)
+    d_gpu = out["replay"][:, 0, :].sum(axis=1)
+    assert np.abs(d_gpu - d_ref).max() <= 2e-5 * np.abs(d_ref).max()
+    assert abs(D.T_D() - deflation.T_D_gamma5(Vr, lam)) <= 1e-12 * np.sum(1 / np.abs(lam))
