@@ -3,50 +3,54 @@
 //
 // C = V^H [Z, g5 Z] (Section 5.2; Algorithm 1, line 8) is a tall-skinny
 // complex contraction over all N dofs.  With V in BF16 and Z in {0, +-1, +-i}
-// (exact in BF16) it is a real BF16 GEMM with FP32 accumulation:
-//     D[m, n] = sum_K A[m, K] B[n, K],   K = (dof i, re/im c),
-//     A[m, (i, c)] = (Re, Im) V[i][m]   -- V's stored BF16 pairs, as they lie
-//     B[4j + q, (i, c)]: q = 0 -> (Re z, Im z), q = 1 -> (Im z, -Re z),
-//                        q = 2, 3 -> the same times g5(i),  z = Z[i][j]
-// so that V^H z_j = D[m, 4j] + i D[m, 4j + 1] and V^H g5 z_j = D[m, 4j + 2] +
-// i D[m, 4j + 3].  Each CTA takes one 128-row tile of m and one chunk of dofs
-// (split K): its threads stage A and B in shared memory (two stages of 64 dofs,
-// eight MMAs of K = 16 each), one thread issues tcgen05.mma with the FP32
-// accumulator in tensor memory (TMEM), tcgen05.commit signals an mbarrier when
-// a stage's MMAs have read their operands, and the epilogue reads TMEM with
-// tcgen05.ld into FP64 partials.  The partials of all chunks are summed in FP64
-// in a fixed order (deterministic).
+// (exact in BF16) it is a real BF16 GEMM with FP32 accumulation over K = dof:
+//     D[r, n] = sum_i A[r, i] B[n, i]
+//     A[2m + c, i] = c-th part (Re, Im) of V[i][m]   -- V's stored row, as it lies
+//     B[4j + q, i] = Re z, Im z, g5 Re z, g5 Im z  (q = 0..3),  z = Z[i][j]
+// so that V^H z_j = (D[2m, 4j] + D[2m+1, 4j+1]) + i (D[2m, 4j+1] - D[2m+1, 4j])
+// and the same with columns 4j+2, 4j+3 for g5 z_j.
 //
-// Shared-memory operands are K-major without swizzle: 8 rows x 16 bytes core
-// matrices stored contiguously (128 B), the two core matrices of a K = 16 step
-// 128 B apart, consecutive 8-row groups 256 B apart.
+// A is MN-major in memory (r contiguous in a row of V), so the tensor memory
+// accelerator (TMA) moves it untouched: one thread issues, per stage of 64 dofs,
+// four 64 x 64 boxes with the 128-byte swizzle, which is the canonical MN-major
+// SWIZZLE_128B operand layout, several stages ahead of the MMAs.  B is built by
+// the threads from the FP64 probing values (loaded into registers one stage
+// ahead) in the K-major layout without swizzle.  Each CTA takes 256 rows r
+// (128 complex m: two M = 128 MMAs per K step, two accumulators in tensor
+// memory) and one chunk of dofs (split K), one CTA per SM.  tcgen05.commit
+// signals a stage's mbarrier once its MMAs have read their operands; the
+// epilogue reads tensor memory with tcgen05.ld into FP64 partials, which are
+// combined into C and summed over chunks in a fixed order (deterministic).
 //
-// Every wait is bounded: a stage whose MMAs do not complete within the budget
-// sets an error word (the host returns DTR_ETIMEOUT), waits once more, frees
-// the TMEM it holds and leaves.
+// Every wait is bounded: a copy or MMA that does not complete within the budget
+// sets an error word (the host returns DTR_ETIMEOUT); the CTA then waits once
+// more for what it has in flight, frees its tensor memory and leaves.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <atomic>
 #include <cstdlib>
+#include <mutex>
 
 #include "deflate.cuh"
 
 namespace dtr {
 
 constexpr int kTcThreads = 256;
-constexpr int kTcStageDofs = 64;   // dofs per pipeline stage (8 K-steps of 8 dofs = 16 BF16 values)
-constexpr int kTcM = 128;          // rows of m per CTA (MMA M)
-constexpr int kTcABytes = kTcM * kTcStageDofs * 2 * 2;  // 128 rows x 128 BF16 = 32 KB per stage
-constexpr long long kTcBudget = 2000000000LL;           // ~1 s at 2 GHz
+constexpr int kTcStageDofs = 64;  // dofs per pipeline stage (four K steps of 16)
+constexpr int kTcRows = 256;      // rows r = 2m + c per CTA (two MMAs of M = 128)
+constexpr int kTcBox = 64;        // TMA box: 64 BF16 (128 bytes, the swizzle span) x 64 dofs
+constexpr int kTcABytes = kTcRows * kTcStageDofs * 2;  // 32 KB per stage
+constexpr long long kTcBudget = 2000000000LL;          // ~1 s at 2 GHz
+constexpr size_t kTcMaxSmem = 232448;                  // opt-in shared memory per block
 
 struct TcArgs {
-  const bfc2 *V;       // row-major [dof][k]
   const double2 *Z;    // internal [site][12][b] (dof-major, b columns)
-  int k, b, logb, N;   // N = MMA N = max(16, 4b); logb = log2 b when b is a power of two, else -1
-  int vec4;            // rows of V 16-byte aligned (k % 4 == 0): four m per load
-  int64_t ndof;
-  int64_t chunk_dofs;  // multiple of kTcStageDofs
-  int nchunks, kpad;
+  int k, b, logb, N;   // N = MMA N = 4b rounded up to 16; logb = log2 b when b is a power of two, else -1
+  int ndof;            // dof indices fit 32 bits (checked on the host)
+  int chunk_dofs;      // multiple of kTcStageDofs
+  int kpad;            // rows r of the partials: 256 x row tiles
   double *part;        // [chunk][kpad][N]
   int *err;
 };
@@ -55,11 +59,19 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// shared-memory matrix descriptor: start >> 4, leading (K) byte offset >> 4,
-// stride (M/N) byte offset >> 4, descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t mma_desc(uint32_t saddr) {
+// K-major operand without swizzle: core matrices of 8 rows x 16 bytes, the two core
+// matrices of a K step 128 bytes apart (leading), 8-row groups 256 bytes apart (stride)
+__device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(256u >> 4) << 32) |
          (1ull << 46);
+}
+
+// MN-major operand with the 128-byte swizzle: atoms of 64 BF16 (MN) x 8 rows (K) of
+// 1 KB; the next 64 MN elements one TMA box (8 KB) further (leading), the next 8 K
+// rows 1 KB further (stride)
+__device__ __forceinline__ uint64_t desc_mn_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(8192u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, long long budget) {
@@ -76,46 +88,46 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, long l
   }
 }
 
-// thread 0 waits, every thread gets its verdict (the whole block takes the same path)
-__device__ __forceinline__ bool block_wait(uint32_t addr, uint32_t parity) {
-  int okv = 1;
-  if (threadIdx.x == 0) okv = mbar_wait(addr, parity, kTcBudget) ? 1 : 0;
-  return __syncthreads_and(okv) != 0;
-}
-
-// byte offset of operand element (row, kk) within one stage, kk in [0, 128) BF16 of the stage
-__device__ __forceinline__ uint32_t op_off(int row, int kk, int rows) {
-  const int ks = kk >> 4, kl = kk & 15;
-  return (uint32_t)(ks * rows * 32 + (row >> 3) * 256 + (kl >> 3) * 128 + (row & 7) * 16 + (kl & 7) * 2);
-}
-
-__device__ __forceinline__ uint32_t pick4(const uint4 &v, int g) {
-  return (g & 2) ? ((g & 1) ? v.w : v.z) : ((g & 1) ? v.y : v.x);
-}
-
 __device__ __forceinline__ uint32_t bf2_bits(float lo, float hi) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 2) k_defl_tc(TcArgs a) {
-  extern __shared__ __align__(1024) unsigned char smem[];
+// S stages of A, two of B; UNITS = (dof octet, column) pairs of B per thread = ceil(8 b / kTcThreads)
+template <int S, int UNITS>
+__global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  // the 128-byte swizzle repeats every 1 KB: operand buffers start on a 1 KB boundary
+  unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int N = a.N;
-  const uint32_t bbytes = (uint32_t)N * kTcStageDofs * 2 * 2;
-  const uint32_t stage_bytes = kTcABytes + bbytes;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+  const uint32_t bbytes = (uint32_t)N * kTcStageDofs * 2;
+  unsigned char *Abuf = smem;
+  unsigned char *Bbuf = smem + S * kTcABytes;
+  uint64_t *full = reinterpret_cast<uint64_t *>(Bbuf + 2 * bbytes);  // A of a stage has landed
+  uint64_t *done = full + S;                                          // MMAs of a stage have completed
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(done + S);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int mt = blockIdx.x, chunk = blockIdx.y;
-  const int m0 = mt * kTcM;
+  const int rt = blockIdx.x, chunk = blockIdx.y;
   uint32_t ncols = 32;
-  while ((int)ncols < N) ncols <<= 1;
+  while ((int)ncols < 2 * N) ncols <<= 1;
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[q])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done[q])) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (4 * a.b < N) {  // rows 4b .. N-1 of B are padding: zero once in both buffers
+    const int pad = N - 4 * a.b;
+    for (int idx = tid; idx < 2 * 8 * pad; idx += kTcThreads) {
+      const int bf = idx / (8 * pad), r = idx - bf * 8 * pad;
+      const int o = r / pad, n = 4 * a.b + r % pad;
+      *reinterpret_cast<uint4 *>(Bbuf + bf * bbytes + (o >> 1) * (N * 32) + (o & 1) * 128 + (n >> 3) * 256 +
+                                 (n & 7) * 16) = make_uint4(0u, 0u, 0u, 0u);
+    }
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -128,154 +140,160 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_defl_tc(TcArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
 
-  const int64_t c0 = (int64_t)chunk * a.chunk_dofs;
-  int64_t c1 = c0 + a.chunk_dofs;
-  if (c1 > a.ndof) c1 = a.ndof;
-  const int nst = c1 > c0 ? (int)((c1 - c0 + kTcStageDofs - 1) / kTcStageDofs) : 0;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
-  bool ok = true;
-  if (4 * a.b < N) {  // rows 4b .. N-1 of B (b < 4) are padding: zero once in both buffers
-    for (int idx = tid; idx < 2 * kTcStageDofs * (N - 4 * a.b); idx += kTcThreads) {
-      const int per = kTcStageDofs * (N - 4 * a.b);
-      const int bf = idx / per, r = idx - bf * per;
-      const int dl = r / (N - 4 * a.b), n = 4 * a.b + r % (N - 4 * a.b);
-      *reinterpret_cast<uint32_t *>(smem + bf * stage_bytes + kTcABytes + op_off(n, 2 * dl, N)) = 0u;
-    }
-  }
+  const int cbeg = chunk * a.chunk_dofs;
+  const int c1 = cbeg + a.chunk_dofs < a.ndof ? cbeg + a.chunk_dofs : a.ndof;
+  const int nst = c1 > cbeg ? (c1 - cbeg + kTcStageDofs - 1) / kTcStageDofs : 0;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(N >> 3) << 17) |
+                         ((uint32_t)(128 >> 4) << 24);
+  const int x0 = rt * kTcRows;  // first BF16 of the rows in a row of V
 
-  for (int s = 0; s < nst && ok; ++s) {
-    const int buf = s & 1;
-    if (s >= 2) {  // the MMAs of stage s - 2 have read this buffer
-      ok = block_wait(smem_u32(&mbar[buf]), (uint32_t)(((s - 2) >> 1) & 1));
-      if (!ok) {
-        if (tid == 0) atomicExch(a.err, 1);
-        break;
+  // thread 0: the four TMA boxes of stage st (rows x0 .. x0 + 255, dofs of the stage)
+  // boxes wholly past row 2k are not fetched (their accumulator rows are never read)
+  const int nbox = (2 * a.k - x0 + kTcBox - 1) / kTcBox < kTcRows / kTcBox ? (2 * a.k - x0 + kTcBox - 1) / kTcBox
+                                                                         : kTcRows / kTcBox;
+  auto issue_A = [&](int st) {
+    const uint32_t fb = smem_u32(&full[st % S]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                 "r"(nbox * kTcBox * kTcStageDofs * 2)
+                 : "memory");
+    const uint32_t dst = smem_u32(Abuf + (st % S) * kTcABytes);
+    const int y = cbeg + st * kTcStageDofs;
+    for (int bx = 0; bx < nbox; ++bx)
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+          "[%4];" ::"r"(dst + bx * (kTcBox * kTcStageDofs * 2)),
+          "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x0 + bx * kTcBox), "r"(y), "r"(fb)
+          : "memory");
+  };
+  auto load_Z = [&](int st, double2 (&zv)[UNITS][8]) {
+    const int d0 = cbeg + st * kTcStageDofs;
+#pragma unroll
+    for (int u = 0; u < UNITS; ++u) {
+      const int idx = tid + u * kTcThreads;
+      const int o = a.logb >= 0 ? idx >> a.logb : idx / a.b, j = idx - o * a.b;
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        const int i = d0 + 8 * o + g;
+        zv[u][g] = make_double2(0.0, 0.0);
+        if (idx < 8 * a.b && i < c1) zv[u][g] = __ldcs(a.Z + (int64_t)i * a.b + j);
       }
     }
-    unsigned char *A = smem + buf * stage_bytes;
-    unsigned char *B = A + kTcABytes;
-    const int64_t d0 = c0 + (int64_t)s * kTcStageDofs;
-    // A: unit (dof quad dq, m quad) -> four 16-byte loads (4 m of one dof each), a 4 x 4
-    // transpose in registers and four 16-byte stores (4 dofs of one m each: one row of a
-    // core matrix).  Lane l stores row 4l + ((f + l/2) mod 4) in its f-th store, so each
-    // quarter-warp writes eight distinct rows of a core matrix: no bank conflicts.
-    {
-      uint4 va[2][4];
+  };
+  // unit (dof octet o, column j) -> rows 4j + q, one 16-byte store each (8 dofs of one
+  // row: a row of a core matrix); rotating q by j/2 keeps a quarter-warp on eight
+  // distinct rows of a core matrix (no bank conflicts)
+  auto build_B = [&](int st, const double2 (&zv)[UNITS][8]) {
+    const int d0 = cbeg + st * kTcStageDofs;
+    const int r12 = d0 % 12;
+    unsigned char *B = Bbuf + (st & 1) * bbytes;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int dq = warp + 8 * h;
-        const int mm = m0 + 4 * lane;
+    for (int u = 0; u < UNITS; ++u) {
+      const int idx = tid + u * kTcThreads;
+      if (idx >= 8 * a.b) continue;
+      const int o = a.logb >= 0 ? idx >> a.logb : idx / a.b, j = idx - o * a.b;
+      unsigned char *Bq = B + (o >> 1) * (N * 32) + (o & 1) * 128;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int i = (int)(d0 + 4 * dq + e);
-          va[h][e] = make_uint4(0u, 0u, 0u, 0u);
-          if (i < c1) {
-            const bfc2 *src = a.V + (int64_t)i * a.k + mm;
-            if (a.vec4 && mm + 3 < a.k) {
-              va[h][e] = __ldcs(reinterpret_cast<const uint4 *>(src));
-            } else {
-              uint32_t w4[4] = {0u, 0u, 0u, 0u};
+      for (int f = 0; f < 4; ++f) {
+        const int q = (f + (j >> 1)) & 3;
+        const int n = 4 * j + q;
+        float x[8];
 #pragma unroll
-              for (int f = 0; f < 4; ++f)
-                if (mm + f < a.k) w4[f] = *reinterpret_cast<const uint32_t *>(src + f);
-              va[h][e] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-            }
-          }
+        for (int g = 0; g < 8; ++g) {
+          const float v = (q & 1) ? (float)zv[u][g].y : (float)zv[u][g].x;
+          x[g] = ((q & 2) && (r12 + 8 * o + g) % 12 >= 6) ? -v : v;
         }
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int dq = warp + 8 * h;
-        unsigned char *Aq = A + (dq >> 1) * (kTcM * 32) + (dq & 1) * 128;
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          const int g = (f + (lane >> 1)) & 3;
-          const int m = 4 * lane + g;
-          const uint4 w = make_uint4(pick4(va[h][0], g), pick4(va[h][1], g), pick4(va[h][2], g), pick4(va[h][3], g));
-          *reinterpret_cast<uint4 *>(Aq + (m >> 3) * 256 + (m & 7) * 16) = w;
-        }
+        *reinterpret_cast<uint4 *>(Bq + (n >> 3) * 256 + (n & 7) * 16) =
+            make_uint4(bf2_bits(x[0], x[1]), bf2_bits(x[2], x[3]), bf2_bits(x[4], x[5]), bf2_bits(x[6], x[7]));
       }
     }
-    // B: unit (dof quad dq, column j) -> four FP64 probing values, then the four operand
-    // rows 4j + q, each one 16-byte store (same rotation of q by j/2 as for A)
-    {
-      const int r12 = (int)(d0 % 12);
-      for (int idx = tid; idx < 16 * a.b; idx += kTcThreads) {
-        const int dq = a.logb >= 0 ? idx >> a.logb : idx / a.b, j = idx - dq * a.b;
-        double2 zv[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int i = (int)(d0 + 4 * dq + e);
-          zv[e] = make_double2(0.0, 0.0);
-          if (i < c1) zv[e] = __ldcs(a.Z + (int64_t)i * a.b + j);
-        }
-        unsigned char *Bq = B + (dq >> 1) * (N * 32) + (dq & 1) * 128;
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          const int q = (f + (j >> 1)) & 3;
-          const int n = 4 * j + q;
-          uint32_t w[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float zr = (float)zv[e].x, zi = (float)zv[e].y;
-            const float sg = ((q & 2) && (r12 + 4 * dq + e) % 12 >= 6) ? -1.f : 1.f;
-            w[e] = (q & 1) ? bf2_bits(sg * zi, -sg * zr) : bf2_bits(sg * zr, sg * zi);
-          }
-          *reinterpret_cast<uint4 *>(Bq + (n >> 3) * 256 + (n & 7) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-      }
+  };
+
+  bool ok = true;
+  bool t0ok = true;   // thread 0: every TMA stage it waited for has landed
+  int issued = -1;    // last stage whose MMAs were issued
+  int tma_next = 0;   // stages whose A copies were issued: 0 .. tma_next - 1
+  int consumed = 0;   // stages whose A copies thread 0 saw land
+  double2 zv[UNITS][8];
+  if (tid == 0)
+    for (; tma_next < S - 2 && tma_next < nst; ++tma_next) issue_A(tma_next);
+  if (nst > 0) load_Z(0, zv);
+  for (int s = 0; s < nst; ++s) {
+    // the MMAs of stage s - 2 have read A buffer (s - 2) % S and B buffer s % 2
+    int vote = 1;
+    if (tid == 0) {
+      vote = t0ok ? 1 : 0;
+      if (vote && s >= 2) vote = mbar_wait(smem_u32(&done[(s - 2) % S]), (uint32_t)(((s - 2) / S) & 1), kTcBudget);
     }
+    ok = __syncthreads_and(vote) != 0;
+    if (!ok) {
+      if (tid == 0) atomicExch(a.err, 1);
+      break;
+    }
+    if (tid == 0 && tma_next < nst) issue_A(tma_next++);
+    build_B(s, zv);
+    if (s + 1 < nst) load_Z(s + 1, zv);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = smem_u32(A), sb = smem_u32(B);
+      t0ok = mbar_wait(smem_u32(&full[s % S]), (uint32_t)((s / S) & 1), kTcBudget);
+      if (t0ok) {
+        consumed = s + 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = smem_u32(Abuf + (s % S) * kTcABytes), sb = smem_u32(Bbuf + (s & 1) * bbytes);
 #pragma unroll
-      for (int ks = 0; ks < kTcStageDofs / 8; ++ks) {
-        const uint64_t adesc = mma_desc(sa + (uint32_t)ks * kTcM * 32);
-        const uint64_t bdesc = mma_desc(sb + (uint32_t)ks * N * 32);
-        const uint32_t acc = (s > 0 || ks > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-            : "memory");
+        for (int ks = 0; ks < kTcStageDofs / 16; ++ks) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint64_t adesc = desc_mn_sw128(sa + (uint32_t)h * (2 * kTcBox * kTcStageDofs * 2) + (uint32_t)ks * 2048u);
+            const uint64_t bdesc = desc_kmajor(sb + (uint32_t)ks * N * 32);
+            const uint32_t acc = (s > 0 || ks > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(h * N)),
+                "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+                : "memory");
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&done[s % S]))
+                     : "memory");
+        issued = s;
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&mbar[buf]))
-                   : "memory");
     }
   }
-  if (ok && nst > 0) {  // all MMAs done (they complete in order)
-    const int L = nst - 1;
-    ok = block_wait(smem_u32(&mbar[L & 1]), (uint32_t)((L >> 1) & 1));
-    if (!ok && tid == 0) atomicExch(a.err, 1);
+  // drain: every issued copy lands and every issued MMA completes before the
+  // shared and tensor memory are given back
+  int vote = 1;
+  if (tid == 0) {
+    if (!t0ok) vote = 0;
+    for (int st = consumed; st < tma_next; ++st)
+      if (!mbar_wait(smem_u32(&full[st % S]), (uint32_t)((st / S) & 1), kTcBudget)) vote = 0;
+    if (issued >= 0 && !mbar_wait(smem_u32(&done[issued % S]), (uint32_t)((issued / S) & 1), kTcBudget)) vote = 0;
+    if (issued != nst - 1) vote = 0;
+    if (!vote) atomicExch(a.err, 1);
   }
-  if (!ok && nst > 0) {  // let anything still in flight drain before the TMEM is freed
-    const int L = nst - 1;
-    block_wait(smem_u32(&mbar[L & 1]), (uint32_t)((L >> 1) & 1));
-  }
+  ok = __syncthreads_and(vote) != 0;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows m) and half of the N columns
-  const int quad = warp & 3, half = warp >> 2;
-  const int m = quad * 32 + lane;
-  const int halfN = N >> 1;
-  double *out = a.part + ((int64_t)chunk * a.kpad + m0 + m) * N;
-  for (int col = half * halfN; col < (half + 1) * halfN; col += 8) {
-    uint32_t r[8];
+  // epilogue: warps 0-3 read the accumulator of rows 0-127 (columns 0 .. N-1), warps 4-7
+  // that of rows 128-255 (columns N .. 2N-1); warp w reads TMEM lanes 32 (w % 4) .. + 31
+  const int quad = warp & 3, h = warp >> 2;
+  const int r = h * 128 + quad * 32 + lane;
+  double *out = a.part + ((int64_t)chunk * a.kpad + x0 + r) * N;
+  for (int col = 0; col < N; col += 8) {
+    uint32_t v[8];
     if (ok && nst > 0) {
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
           "tcgen05.wait::ld.sync.aligned;\n"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-          : "r"(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col)
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+          : "r"(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(h * N + col))
           : "memory");
     } else {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) r[u] = 0u;
+      for (int u = 0; u < 8; ++u) v[u] = 0u;
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) out[col + u] = (double)__uint_as_float(r[u]);
+    for (int u = 0; u < 8; ++u) out[col + u] = (double)__uint_as_float(v[u]);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -284,7 +302,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_defl_tc(TcArgs a) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
-// C[col * k + m] from the chunk partials, fixed order over chunks
+// C[col * k + m] from the chunk partials (rows r = 2m + c), fixed order over chunks:
+// V^H z = (D[2m, re] + D[2m+1, im]) + i (D[2m, im] - D[2m+1, re])
 __global__ void k_defl_tc_reduce(const double *__restrict__ part, int nchunks, int k, int kpad, int b, int N,
                                  double2 *__restrict__ C) {
   const int64_t n = (int64_t)k * 2 * b;
@@ -295,24 +314,33 @@ __global__ void k_defl_tc_reduce(const double *__restrict__ part, int nchunks, i
     const int nre = 4 * j + (g5 ? 2 : 0);
     double re = 0.0, im = 0.0;
     for (int ch = 0; ch < nchunks; ++ch) {
-      const double *p = part + ((int64_t)ch * kpad + m) * N;
-      re += p[nre];
-      im += p[nre + 1];
+      const double *pr = part + ((int64_t)ch * kpad + 2 * m) * N;  // row 2m: Re V
+      const double *pi = pr + N;                                   // row 2m + 1: Im V
+      re += pr[nre] + pi[nre + 1];
+      im += pr[nre + 1] - pi[nre];
     }
     C[e] = make_double2(re, im);
   }
 }
 
-static void tc_shape(int64_t ndof, int k, int b, int sms, int *N, int *mtiles, int *nchunks, int64_t *chunk_dofs) {
-  *N = 4 * b < 16 ? 16 : 4 * b;
-  *mtiles = (k + kTcM - 1) / kTcM;
-  const int per_sm = *N <= 64 ? 2 : 1;  // CTAs that fit an SM's shared memory
-  int nc = (per_sm * sms + *mtiles - 1) / *mtiles;
+static void tc_shape(int64_t ndof, int k, int b, int sms, int *N, int *rtiles, int *nchunks, int *chunk_dofs) {
+  *N = (4 * b + 15) / 16 * 16;  // MMA N for M = 128: a multiple of 16 in [16, 256]
+  *rtiles = (2 * k + kTcRows - 1) / kTcRows;
+  int nc = (sms + *rtiles - 1) / *rtiles;  // one CTA per SM
   if (nc < 1) nc = 1;
   int64_t cd = (ndof + nc - 1) / nc;
   cd = (cd + kTcStageDofs - 1) / kTcStageDofs * kTcStageDofs;
-  *chunk_dofs = cd;
+  *chunk_dofs = (int)cd;
   *nchunks = (int)((ndof + cd - 1) / cd);
+}
+
+// stages of A that fit beside the two B buffers, the barriers and the 1 KB alignment slack
+static int tc_stages(int N, size_t *smem) {
+  const size_t fixed = 2 * (size_t)N * kTcStageDofs * 2 + 1024 + 256;
+  int S = (int)((kTcMaxSmem - fixed) / kTcABytes);
+  if (S > 6) S = 6;
+  *smem = (size_t)S * kTcABytes + fixed;
+  return S;
 }
 
 static std::atomic<unsigned long long> g_tc_calls{0};
@@ -324,27 +352,53 @@ bool defl_tc_enabled(const dtr_defl_s *D, int b) {
     const char *e = getenv("DTR_DEFL_TC");
     env = (e && e[0] == '0') ? 0 : 1;
   }
+  // rows of V are TMA-addressable when their byte length 4k is a multiple of 16;
   // dof indices are 32-bit inside the kernel
-  return env && D->prec == DTR_BF16 && b >= 1 && b <= 64 && D->lat.N < ((int64_t)1 << 31) - 2 * kTcStageDofs;
+  return env && D->prec == DTR_BF16 && b >= 1 && b <= 64 && D->k % 4 == 0 &&
+         D->lat.N < ((int64_t)1 << 31) - 2 * kTcStageDofs;
 }
 
 size_t defl_tc_scratch_bytes(int64_t V, int k, int b, int sms) {
-  int N, mt, nc;
-  int64_t cd;
-  tc_shape(V * 12, k, b, sms, &N, &mt, &nc, &cd);
-  return ((size_t)nc * mt * kTcM * N * sizeof(double) + 255) / 256 * 256 + 256;
+  int N, rt, nc, cd;
+  tc_shape(V * 12, k, b, sms, &N, &rt, &nc, &cd);
+  return ((size_t)nc * rt * kTcRows * N * sizeof(double) + 255) / 256 * 256 + 256;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  });
+  return fn;
 }
 
 int defl_contract_tc(const dtr_defl_s *D, const double2 *Z, int b, double2 *C, void *scratch, size_t scratch_bytes,
                      int *err_dev, int sms, cudaStream_t st) {
   const int k = D->k;
   const int64_t ndof = D->lat.N;
-  int N, mt, nc;
-  int64_t cd;
-  tc_shape(ndof, k, b, sms, &N, &mt, &nc, &cd);
+  int N, rt, nc, cd;
+  tc_shape(ndof, k, b, sms, &N, &rt, &nc, &cd);
   if (scratch_bytes < defl_tc_scratch_bytes(D->lat.V, k, b, sms)) return fail(DTR_ENOMEM, "tensor-core scratch too small");
+  if (k % 4 != 0 || ((uintptr_t)D->V & 15u)) return fail(DTR_EINVAL, "deflation rows not TMA-addressable");
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tmap_encoder();
+  if (!encode) return fail(DTR_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  // V as a 2D BF16 tensor: 2k values per row (contiguous), ndof rows 4k bytes apart
+  alignas(64) CUtensorMap tmap;
+  const cuuint64_t gdim[2] = {(cuuint64_t)2 * k, (cuuint64_t)ndof};
+  const cuuint64_t gstride[1] = {(cuuint64_t)k * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcBox, (cuuint32_t)kTcStageDofs};
+  const cuuint32_t estride[2] = {1, 1};
+  if (encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, D->V, gdim, gstride, box, estride,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return fail(DTR_ECUDA, "cuTensorMapEncodeTiled failed");
   TcArgs a;
-  a.V = (const bfc2 *)D->V;
   a.Z = Z;
   a.k = k;
   a.b = b;
@@ -352,16 +406,24 @@ int defl_contract_tc(const dtr_defl_s *D, const double2 *Z, int b, double2 *C, v
   while ((1 << a.logb) < b) ++a.logb;
   if ((1 << a.logb) != b) a.logb = -1;
   a.N = N;
-  a.vec4 = (k % 4) == 0;
-  a.ndof = ndof;
+  a.ndof = (int)ndof;
   a.chunk_dofs = cd;
-  a.nchunks = nc;
-  a.kpad = mt * kTcM;
+  a.kpad = rt * kTcRows;
   a.part = (double *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
   a.err = err_dev;
-  const size_t smem = 2 * ((size_t)kTcABytes + (size_t)N * kTcStageDofs * 4) + 64;
-  DTR_CUDA(cudaFuncSetAttribute(k_defl_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_defl_tc<<<dim3(mt, nc), kTcThreads, smem, st>>>(a);
+  size_t smem;
+  const int S = tc_stages(N, &smem);
+  const int units = (8 * b + kTcThreads - 1) / kTcThreads;
+  const dim3 grid(rt, nc);
+  if (S == 6 && units == 1) {
+    DTR_CUDA(cudaFuncSetAttribute(k_defl_tc<6, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_defl_tc<6, 1><<<grid, kTcThreads, smem, st>>>(tmap, a);
+  } else if (S == 5 && units == 2) {
+    DTR_CUDA(cudaFuncSetAttribute(k_defl_tc<5, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_defl_tc<5, 2><<<grid, kTcThreads, smem, st>>>(tmap, a);
+  } else {
+    return fail(DTR_EINVAL, "tensor-core contraction: no pipeline for this block width");
+  }
   count_launches(1);
   g_tc_calls.fetch_add(1, std::memory_order_relaxed);
   const int64_t n = (int64_t)k * 2 * b;

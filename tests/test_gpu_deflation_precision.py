@@ -89,7 +89,8 @@ def test_gram_matches_oracle_galerkin(dtr, c4, prec):
 
 
 @pytest.mark.parametrize("dims,k,b,R", [((4, 4, 4, 4), 32, 16, 32), ((8, 8, 8, 8), 200, 16, 16),
-                                        ((4, 4, 4, 8), 64, 3, 6)])
+                                        ((4, 4, 4, 8), 64, 3, 6), ((4, 4, 4, 8), 64, 5, 10),
+                                        ((4, 4, 4, 4), 100, 32, 32), ((4, 4, 4, 4), 32, 64, 64)])
 def test_tensor_core_contraction_matches_oracle(dtr, dims, k, b, R):
     """Plain Z4 blocks (one vector per run, blocks spanning runs) with a BF16
     deflation space take the tensor-core contraction (BF16 operands, FP32
