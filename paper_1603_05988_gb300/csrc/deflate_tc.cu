@@ -27,8 +27,6 @@
 // more for what it has in flight, frees its tensor memory and leaves.
 #include <cuda.h>
 #include <cudaTypedefs.h>
-#include <cuda_bf16.h>
-
 #include <atomic>
 #include <cstdlib>
 #include <mutex>
@@ -37,7 +35,7 @@
 
 namespace dtr {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 320;  // warp 0: TMA, warp 1: MMA, warps 2-9: B
 constexpr int kTcStageDofs = 64;  // dofs per pipeline stage (four K steps of 16)
 constexpr int kTcRows = 256;      // rows r = 2m + c per CTA (two MMAs of M = 128)
 constexpr int kTcBox = 64;        // TMA box: 64 BF16 (128 bytes, the swizzle span) x 64 dofs
@@ -51,7 +49,7 @@ struct TcArgs {
   int ndof;            // dof indices fit 32 bits (checked on the host)
   int chunk_dofs;      // multiple of kTcStageDofs
   int kpad;            // rows r of the partials: 256 x row tiles
-  double *part;        // [chunk][kpad][N]
+  float *part;         // [chunk][kpad][N], the FP32 accumulators of each chunk
   int *err;
 };
 
@@ -88,12 +86,42 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, long l
   }
 }
 
-__device__ __forceinline__ uint32_t bf2_bits(float lo, float hi) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t *>(&h);
+// BF16 bits of an FP64 value that BF16 holds exactly (zero, or a normal number with at
+// most 8 significant bits, such as the Z4 entries 0, +-1), from the high word of the
+// FP64 value alone: sign, exponent rebiased from 1023 to 127, top 7 fraction bits.
+// Integer operations only: FP64 instructions are scarce on this GPU.
+__device__ __forceinline__ uint32_t bf16_of_exact_f64(uint32_t hi) {
+  const uint32_t sign = (hi >> 16) & 0x8000u, mag = hi & 0x7FFFFFFFu;
+  const uint32_t bits = sign | ((((mag >> 20) - 1023u + 127u) & 0xFFu) << 7) | ((mag >> 13) & 0x7Fu);
+  return mag == 0u ? sign : bits;
 }
 
-// S stages of A, two of B; UNITS = (dof octet, column) pairs of B per thread = ceil(8 b / kTcThreads)
+// bounded wait that also gives up as soon as another role has given up (*abort)
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t addr, uint32_t parity, volatile int *abort) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > kTcBudget) {
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+constexpr int kTcBuilders = kTcThreads - 64;  // warps 2 .. 9 build B
+
+// Warp roles: lane 0 of warp 0 issues the TMA copies of A into an S-stage ring, lane 0
+// of warp 1 issues the MMAs, warps 2-9 build B (two buffers) from the probing values
+// they load into registers two stages ahead; full/empty mbarriers order the three, so
+// no block-wide barrier sits inside the stage loop.  Warps 0-7 run the epilogue.
+// UNITS = (dof octet, column) pairs of B per builder thread = ceil(8 b / 256).
 template <int S, int UNITS>
 __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
@@ -103,9 +131,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
   const uint32_t bbytes = (uint32_t)N * kTcStageDofs * 2;
   unsigned char *Abuf = smem;
   unsigned char *Bbuf = smem + S * kTcABytes;
-  uint64_t *full = reinterpret_cast<uint64_t *>(Bbuf + 2 * bbytes);  // A of a stage has landed
-  uint64_t *done = full + S;                                          // MMAs of a stage have completed
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(done + S);
+  uint64_t *afull = reinterpret_cast<uint64_t *>(Bbuf + 2 * bbytes);  // A of a stage has landed
+  uint64_t *aempty = afull + S;                                        // MMAs have read an A buffer
+  uint64_t *bfull = aempty + S;                                        // B of a stage is built
+  uint64_t *bempty = bfull + 2;                                        // MMAs have read a B buffer
+  uint64_t *accf = bempty + 2;                                         // every MMA has completed
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(accf + 1);
+  volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
+  int *consumed = reinterpret_cast<int *>(tslot + 2);  // A stages the MMA lane saw land
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rt = blockIdx.x, chunk = blockIdx.y;
   uint32_t ncols = 32;
@@ -114,9 +147,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
   if (tid == 0) {
 #pragma unroll
     for (int q = 0; q < S; ++q) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[q])) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done[q])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&afull[q])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&aempty[q])) : "memory");
     }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bfull[q])), "r"(kTcBuilders) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bempty[q])) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(accf)) : "memory");
+    *abort = 0;
+    *consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -128,6 +169,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
       *reinterpret_cast<uint4 *>(Bbuf + bf * bbytes + (o >> 1) * (N * 32) + (o & 1) * 128 + (n >> 3) * 256 +
                                  (n & 7) * 16) = make_uint4(0u, 0u, 0u, 0u);
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -143,108 +185,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
   const int cbeg = chunk * a.chunk_dofs;
   const int c1 = cbeg + a.chunk_dofs < a.ndof ? cbeg + a.chunk_dofs : a.ndof;
   const int nst = c1 > cbeg ? (c1 - cbeg + kTcStageDofs - 1) / kTcStageDofs : 0;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(N >> 3) << 17) |
-                         ((uint32_t)(128 >> 4) << 24);
   const int x0 = rt * kTcRows;  // first BF16 of the rows in a row of V
+  int tma_issued = 0;           // producer lane: stages whose copies were issued
+  int mma_issued = 0;           // MMA lane: stages whose MMAs were issued
 
-  // thread 0: the four TMA boxes of stage st (rows x0 .. x0 + 255, dofs of the stage)
-  // boxes wholly past row 2k are not fetched (their accumulator rows are never read)
-  const int nbox = (2 * a.k - x0 + kTcBox - 1) / kTcBox < kTcRows / kTcBox ? (2 * a.k - x0 + kTcBox - 1) / kTcBox
-                                                                         : kTcRows / kTcBox;
-  auto issue_A = [&](int st) {
-    const uint32_t fb = smem_u32(&full[st % S]);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
-                 "r"(nbox * kTcBox * kTcStageDofs * 2)
-                 : "memory");
-    const uint32_t dst = smem_u32(Abuf + (st % S) * kTcABytes);
-    const int y = cbeg + st * kTcStageDofs;
-    for (int bx = 0; bx < nbox; ++bx)
-      asm volatile(
-          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-          "[%4];" ::"r"(dst + bx * (kTcBox * kTcStageDofs * 2)),
-          "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x0 + bx * kTcBox), "r"(y), "r"(fb)
-          : "memory");
-  };
-  auto load_Z = [&](int st, double2 (&zv)[UNITS][8]) {
-    const int d0 = cbeg + st * kTcStageDofs;
-#pragma unroll
-    for (int u = 0; u < UNITS; ++u) {
-      const int idx = tid + u * kTcThreads;
-      const int o = a.logb >= 0 ? idx >> a.logb : idx / a.b, j = idx - o * a.b;
-#pragma unroll
-      for (int g = 0; g < 8; ++g) {
-        const int i = d0 + 8 * o + g;
-        zv[u][g] = make_double2(0.0, 0.0);
-        if (idx < 8 * a.b && i < c1) zv[u][g] = __ldcs(a.Z + (int64_t)i * a.b + j);
+  if (warp == 0) {
+    if (lane == 0) {
+      // boxes wholly past row 2k are not fetched (their accumulator rows are never read)
+      const int nbox = (2 * a.k - x0 + kTcBox - 1) / kTcBox < kTcRows / kTcBox
+                           ? (2 * a.k - x0 + kTcBox - 1) / kTcBox
+                           : kTcRows / kTcBox;
+      for (int st = 0; st < nst; ++st) {
+        const int q = st % S;
+        if (st >= S && !mbar_wait_ab(smem_u32(&aempty[q]), (uint32_t)((st / S - 1) & 1), abort)) break;
+        const uint32_t fb = smem_u32(&afull[q]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                     "r"(nbox * kTcBox * kTcStageDofs * 2)
+                     : "memory");
+        const uint32_t dst = smem_u32(Abuf + q * kTcABytes);
+        const int y = cbeg + st * kTcStageDofs;
+        for (int bx = 0; bx < nbox; ++bx)
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+              "%3}], [%4];" ::"r"(dst + bx * (kTcBox * kTcStageDofs * 2)),
+              "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x0 + bx * kTcBox), "r"(y), "r"(fb)
+              : "memory");
+        tma_issued = st + 1;
       }
     }
-  };
-  // unit (dof octet o, column j) -> rows 4j + q, one 16-byte store each (8 dofs of one
-  // row: a row of a core matrix); rotating q by j/2 keeps a quarter-warp on eight
-  // distinct rows of a core matrix (no bank conflicts)
-  auto build_B = [&](int st, const double2 (&zv)[UNITS][8]) {
-    const int d0 = cbeg + st * kTcStageDofs;
-    const int r12 = d0 % 12;
-    unsigned char *B = Bbuf + (st & 1) * bbytes;
-#pragma unroll
-    for (int u = 0; u < UNITS; ++u) {
-      const int idx = tid + u * kTcThreads;
-      if (idx >= 8 * a.b) continue;
-      const int o = a.logb >= 0 ? idx >> a.logb : idx / a.b, j = idx - o * a.b;
-      unsigned char *Bq = B + (o >> 1) * (N * 32) + (o & 1) * 128;
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const int q = (f + (j >> 1)) & 3;
-        const int n = 4 * j + q;
-        float x[8];
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-          const float v = (q & 1) ? (float)zv[u][g].y : (float)zv[u][g].x;
-          x[g] = ((q & 2) && (r12 + 8 * o + g) % 12 >= 6) ? -v : v;
-        }
-        *reinterpret_cast<uint4 *>(Bq + (n >> 3) * 256 + (n & 7) * 16) =
-            make_uint4(bf2_bits(x[0], x[1]), bf2_bits(x[2], x[3]), bf2_bits(x[4], x[5]), bf2_bits(x[6], x[7]));
-      }
-    }
-  };
-
-  bool ok = true;
-  bool t0ok = true;   // thread 0: every TMA stage it waited for has landed
-  int issued = -1;    // last stage whose MMAs were issued
-  int tma_next = 0;   // stages whose A copies were issued: 0 .. tma_next - 1
-  int consumed = 0;   // stages whose A copies thread 0 saw land
-  double2 zv[UNITS][8];
-  if (tid == 0)
-    for (; tma_next < S - 2 && tma_next < nst; ++tma_next) issue_A(tma_next);
-  if (nst > 0) load_Z(0, zv);
-  for (int s = 0; s < nst; ++s) {
-    // the MMAs of stage s - 2 have read A buffer (s - 2) % S and B buffer s % 2
-    int vote = 1;
-    if (tid == 0) {
-      vote = t0ok ? 1 : 0;
-      if (vote && s >= 2) vote = mbar_wait(smem_u32(&done[(s - 2) % S]), (uint32_t)(((s - 2) / S) & 1), kTcBudget);
-    }
-    ok = __syncthreads_and(vote) != 0;
-    if (!ok) {
-      if (tid == 0) atomicExch(a.err, 1);
-      break;
-    }
-    if (tid == 0 && tma_next < nst) issue_A(tma_next++);
-    build_B(s, zv);
-    if (s + 1 < nst) load_Z(s + 1, zv);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      t0ok = mbar_wait(smem_u32(&full[s % S]), (uint32_t)((s / S) & 1), kTcBudget);
-      if (t0ok) {
-        consumed = s + 1;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(N >> 3) << 17) |
+                             ((uint32_t)(128 >> 4) << 24);
+      for (int s = 0; s < nst; ++s) {
+        if (!mbar_wait_ab(smem_u32(&afull[s % S]), (uint32_t)((s / S) & 1), abort)) break;
+        *consumed = s + 1;
+        if (!mbar_wait_ab(smem_u32(&bfull[s & 1]), (uint32_t)((s >> 1) & 1), abort)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t sa = smem_u32(Abuf + (s % S) * kTcABytes), sb = smem_u32(Bbuf + (s & 1) * bbytes);
 #pragma unroll
         for (int ks = 0; ks < kTcStageDofs / 16; ++ks) {
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            const uint64_t adesc = desc_mn_sw128(sa + (uint32_t)h * (2 * kTcBox * kTcStageDofs * 2) + (uint32_t)ks * 2048u);
+            const uint64_t adesc =
+                desc_mn_sw128(sa + (uint32_t)h * (2 * kTcBox * kTcStageDofs * 2) + (uint32_t)ks * 2048u);
             const uint64_t bdesc = desc_kmajor(sb + (uint32_t)ks * N * 32);
             const uint32_t acc = (s > 0 || ks > 0) ? 1u : 0u;
             asm volatile(
@@ -255,31 +239,108 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
           }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&done[s % S]))
+                         smem_u32(&aempty[s % S]))
                      : "memory");
-        issued = s;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&bempty[s & 1]))
+                     : "memory");
+        mma_issued = s + 1;
       }
+      // one more commit: accf completes once every MMA issued above has completed
+      if (mma_issued > 0)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(accf))
+                     : "memory");
+    }
+  } else {
+    // builders: unit (dof octet o, column j) -> rows 4j + q of B, one 16-byte store each
+    // (8 dofs of one row: a row of a core matrix); rotating q by j/2 keeps a quarter-warp
+    // on eight distinct rows of a core matrix (no bank conflicts)
+    const int tb = tid - 64;
+    // two register sets of probing values (high words of Re z and Im z, all the BF16
+    // operand needs): the loads for stage s + 2 are issued right after stage s is built
+    uint2 za[UNITS][8], zb[UNITS][8];
+    auto load_Z = [&](int st, uint2 (&zv)[UNITS][8]) {
+      const int d0 = cbeg + st * kTcStageDofs;
+#pragma unroll
+      for (int u = 0; u < UNITS; ++u) {
+        const int idx = tb + u * kTcBuilders;
+        const int o = a.logb >= 0 ? idx >> a.logb : idx / a.b, j = idx - o * a.b;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+          const int i = d0 + 8 * o + g;
+          zv[u][g] = make_uint2(0u, 0u);
+          if (st < nst && idx < 8 * a.b && i < c1) {
+            const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(a.Z + (int64_t)i * a.b + j));
+            zv[u][g] = make_uint2(w.y, w.w);
+          }
+        }
+      }
+    };
+    // build B of stage s from zv, then reuse zv for the loads of stage s + 2
+    auto step = [&](int s, uint2 (&zv)[UNITS][8]) -> bool {
+      if (s >= 2 && !mbar_wait_ab(smem_u32(&bempty[s & 1]), (uint32_t)(((s >> 1) - 1) & 1), abort)) return false;
+      const int d0 = cbeg + s * kTcStageDofs;
+      const int r12 = d0 % 12;
+      unsigned char *B = Bbuf + (s & 1) * bbytes;
+#pragma unroll
+      for (int u = 0; u < UNITS; ++u) {
+        const int idx = tb + u * kTcBuilders;
+        if (idx >= 8 * a.b) continue;
+        const int o = a.logb >= 0 ? idx >> a.logb : idx / a.b, j = idx - o * a.b;
+        unsigned char *Bq = B + (o >> 1) * (N * 32) + (o & 1) * 128;
+        uint32_t re[8], im[8], g5[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+          re[g] = bf16_of_exact_f64(zv[u][g].x);
+          im[g] = bf16_of_exact_f64(zv[u][g].y);
+          g5[g] = (r12 + 8 * o + g) % 12 >= 6 ? 0x8000u : 0u;  // g5 = -1 on spins 2, 3
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const int q = (f + (j >> 1)) & 3;
+          const int n = 4 * j + q;
+          uint32_t x[8];
+#pragma unroll
+          for (int g = 0; g < 8; ++g) x[g] = ((q & 1) ? im[g] : re[g]) ^ ((q & 2) ? g5[g] : 0u);
+          *reinterpret_cast<uint4 *>(Bq + (n >> 3) * 256 + (n & 7) * 16) =
+              make_uint4(x[0] | (x[1] << 16), x[2] | (x[3] << 16), x[4] | (x[5] << 16), x[6] | (x[7] << 16));
+        }
+      }
+      load_Z(s + 2, zv);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bfull[s & 1])) : "memory");
+      return true;
+    };
+    load_Z(0, za);
+    load_Z(1, zb);
+    for (int s = 0; s < nst; s += 2) {
+      if (!step(s, za)) break;
+      if (s + 1 < nst && !step(s + 1, zb)) break;
     }
   }
-  // drain: every issued copy lands and every issued MMA completes before the
-  // shared and tensor memory are given back
+  __syncthreads();
+  // drain: every issued copy lands and every issued MMA completes before the shared
+  // and tensor memory are given back; any shortfall is an error
   int vote = 1;
   if (tid == 0) {
-    if (!t0ok) vote = 0;
-    for (int st = consumed; st < tma_next; ++st)
-      if (!mbar_wait(smem_u32(&full[st % S]), (uint32_t)((st / S) & 1), kTcBudget)) vote = 0;
-    if (issued >= 0 && !mbar_wait(smem_u32(&done[issued % S]), (uint32_t)((issued / S) & 1), kTcBudget)) vote = 0;
-    if (issued != nst - 1) vote = 0;
-    if (!vote) atomicExch(a.err, 1);
+    for (int st = *consumed; st < tma_issued; ++st)
+      if (!mbar_wait(smem_u32(&afull[st % S]), (uint32_t)((st / S) & 1), kTcBudget)) vote = 0;
   }
-  ok = __syncthreads_and(vote) != 0;
+  if (tid == 32) {
+    if (mma_issued > 0 && !mbar_wait(smem_u32(accf), 0u, kTcBudget)) vote = 0;
+    if (mma_issued != nst) vote = 0;
+  }
+  if (tid == 0 && *abort) vote = 0;
+  const bool ok = __syncthreads_and(vote) != 0;
+  if (!ok && tid == 0) atomicExch(a.err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // epilogue: warps 0-3 read the accumulator of rows 0-127 (columns 0 .. N-1), warps 4-7
   // that of rows 128-255 (columns N .. 2N-1); warp w reads TMEM lanes 32 (w % 4) .. + 31
   const int quad = warp & 3, h = warp >> 2;
   const int r = h * 128 + quad * 32 + lane;
-  double *out = a.part + ((int64_t)chunk * a.kpad + x0 + r) * N;
-  for (int col = 0; col < N; col += 8) {
+  float *out = a.part + ((int64_t)chunk * a.kpad + x0 + r) * N;
+  for (int col = 0; col < (warp < 8 ? N : 0); col += 8) {
     uint32_t v[8];
     if (ok && nst > 0) {
       asm volatile(
@@ -293,7 +354,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
       for (int u = 0; u < 8; ++u) v[u] = 0u;
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) out[col + u] = (double)__uint_as_float(v[u]);
+    for (int u = 0; u < 8; u += 2)
+      *reinterpret_cast<float2 *>(out + col + u) = make_float2(__uint_as_float(v[u]), __uint_as_float(v[u + 1]));
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -302,24 +364,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
-// C[col * k + m] from the chunk partials (rows r = 2m + c), fixed order over chunks:
-// V^H z = (D[2m, re] + D[2m+1, im]) + i (D[2m, im] - D[2m+1, re])
-__global__ void k_defl_tc_reduce(const double *__restrict__ part, int nchunks, int k, int kpad, int b, int N,
+// C[col * k + m] from the chunk partials (rows r = 2m + c):
+// V^H z = (D[2m, re] + D[2m+1, im]) + i (D[2m, im] - D[2m+1, re]), summed in FP64 over
+// the chunks by one warp per output: lane l takes chunks l, l + 32, ... in order, then a
+// fixed butterfly combines the lanes (the same order on every call: deterministic)
+__global__ void k_defl_tc_reduce(const float *__restrict__ part, int nchunks, int k, int kpad, int b, int N,
                                  double2 *__restrict__ C) {
   const int64_t n = (int64_t)k * 2 * b;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < n;
+       e += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int m = (int)(e % k);
     const int col = (int)(e / k);
     const int j = col % b, g5 = col >= b;
     const int nre = 4 * j + (g5 ? 2 : 0);
     double re = 0.0, im = 0.0;
-    for (int ch = 0; ch < nchunks; ++ch) {
-      const double *pr = part + ((int64_t)ch * kpad + 2 * m) * N;  // row 2m: Re V
-      const double *pi = pr + N;                                   // row 2m + 1: Im V
-      re += pr[nre] + pi[nre + 1];
-      im += pr[nre + 1] - pi[nre];
+    for (int ch = lane; ch < nchunks; ch += 32) {
+      const float2 pr = *reinterpret_cast<const float2 *>(part + ((int64_t)ch * kpad + 2 * m) * N + nre);
+      const float2 pi = *reinterpret_cast<const float2 *>(part + ((int64_t)ch * kpad + 2 * m + 1) * N + nre);
+      re += (double)pr.x + (double)pi.y;
+      im += (double)pr.y - (double)pi.x;
     }
-    C[e] = make_double2(re, im);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, off);
+      im += __shfl_xor_sync(0xffffffffu, im, off);
+    }
+    if (lane == 0) C[e] = make_double2(re, im);
   }
 }
 
@@ -361,7 +432,7 @@ bool defl_tc_enabled(const dtr_defl_s *D, int b) {
 size_t defl_tc_scratch_bytes(int64_t V, int k, int b, int sms) {
   int N, rt, nc, cd;
   tc_shape(V * 12, k, b, sms, &N, &rt, &nc, &cd);
-  return ((size_t)nc * rt * kTcRows * N * sizeof(double) + 255) / 256 * 256 + 256;
+  return ((size_t)nc * rt * kTcRows * N * sizeof(float) + 255) / 256 * 256 + 256;
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
@@ -409,25 +480,25 @@ int defl_contract_tc(const dtr_defl_s *D, const double2 *Z, int b, double2 *C, v
   a.ndof = (int)ndof;
   a.chunk_dofs = cd;
   a.kpad = rt * kTcRows;
-  a.part = (double *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
+  a.part = (float *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
   a.err = err_dev;
   size_t smem;
   const int S = tc_stages(N, &smem);
-  const int units = (8 * b + kTcThreads - 1) / kTcThreads;
+  const int units = (8 * b + kTcBuilders - 1) / kTcBuilders;
   const dim3 grid(rt, nc);
-  if (S == 6 && units == 1) {
-    DTR_CUDA(cudaFuncSetAttribute(k_defl_tc<6, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_defl_tc<6, 1><<<grid, kTcThreads, smem, st>>>(tmap, a);
-  } else if (S == 5 && units == 2) {
-    DTR_CUDA(cudaFuncSetAttribute(k_defl_tc<5, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_defl_tc<5, 2><<<grid, kTcThreads, smem, st>>>(tmap, a);
-  } else {
+#define DTR_TC_LAUNCH(SS, UU)                                                                                  \
+  if (S == SS && units == UU) {                                                                                \
+    DTR_CUDA(cudaFuncSetAttribute(k_defl_tc<SS, UU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    k_defl_tc<SS, UU><<<grid, kTcThreads, smem, st>>>(tmap, a);                                                \
+  } else
+  DTR_TC_LAUNCH(6, 1) DTR_TC_LAUNCH(5, 2) {
     return fail(DTR_EINVAL, "tensor-core contraction: no pipeline for this block width");
   }
+#undef DTR_TC_LAUNCH
   count_launches(1);
   g_tc_calls.fetch_add(1, std::memory_order_relaxed);
-  const int64_t n = (int64_t)k * 2 * b;
-  k_defl_tc_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.part, nc, k, a.kpad, b, N, C);
+  const int64_t n = (int64_t)k * 2 * b;  // one warp per output
+  k_defl_tc_reduce<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(a.part, nc, k, a.kpad, b, N, C);
   count_launches(1);
   DTR_LAUNCH_CHECK("tensor-core deflation contraction");
   return DTR_OK;
