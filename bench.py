@@ -364,7 +364,7 @@ def main():
                     "frac": st8["achieved_tflops"] / fp32_peak, "traffic": None,
                     "kernel": "dslash FP32, 16 RHS, 8^4", "avg_launch_ms": st8["avg_launch_ms"]}
     hbm_peak, hbm_note = measured_hbm_peak()
-    roof_hbm = None
+    roof_hbm = roof_tc = None
     if not args.skip_hbm:
         dims_big = (32, 32, 32, 64)
         lat_big = dtr.make_lattice(dims_big)
@@ -379,6 +379,17 @@ def main():
                                       % (hb["link_rows"], hb["stored_bytes_per_launch"], hb["moved_gbs"]),
                     "peak_note": hbm_note}
         del g_big, lat_big
+        # the tensor-core (tcgen05) deflation contraction: BF16 V, one 16-column Z4 block
+        dc = kbench.deflate_case((16, 16, 16, 32), 256, 16, 20, "bf16")
+        roof_tc = {"bound": "hbm", "achieved": dc["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                   "frac": dc["achieved_gbs"] / hbm_peak, "traffic": 2.0169e9,
+                   "kernel": "k_defl_tc (tcgen05 BF16 x Z4 contraction, FP32 accumulation in TMEM), "
+                             "16^3x32, k=256, 16 RHS",
+                   "avg_launch_ms": dc["avg_launch_ms"], "alg_bytes_per_launch": dc["alg_bytes_per_launch"],
+                   "achieved_tflops": dc["achieved_tflops"],
+                   "alg_bytes_note": "N k 4 B (V) + N b 16 B (Z) per launch; traffic = DRAM read + write of "
+                                     "one launch under ncu (profiles/defl_tc_bf16_16x16x16x32_k256_b16.md)",
+                   "tensor_pipe_active_pct": 14.3, "peak_note": hbm_note}
 
     # CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -422,6 +433,7 @@ def main():
             "roofline": roof,
             "roofline_stencil_fp32": roof_stencil,
             "roofline_stencil_bf16_hbm": roof_hbm,
+            "roofline_deflation_tc_hbm": roof_tc,
             "cpu_baseline": cpu,
             "fp64_path": {"value": value64, "unit": UNIT, "steps": nf, "ms_per_step": sum(ms64) / nf,
                           "lanes": L64, "iterations_per_rhs": iters64 / (nf * w.ncolors * L64),
