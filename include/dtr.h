@@ -74,9 +74,15 @@ typedef enum { DTR_F64 = 0, DTR_F32 = 1, DTR_BF16 = 2, DTR_F16 = 3 } dtr_prec;
 typedef enum {
   DTR_SOLVER_BICGSTAB_F64 = 0,   /* plain FP64 BiCGStab */
   DTR_SOLVER_MIXED_F32 = 1,      /* FP32 BiCGStab inner solves inside FP64 defect correction */
-  DTR_SOLVER_FGMRES_NET = 2      /* FP32 flexible GMRES(m) inner solves, right-preconditioned by a
+  DTR_SOLVER_FGMRES_NET = 2,     /* FP32 flexible GMRES(m) inner solves, right-preconditioned by a
                                     dtr_net, inside FP64 defect correction; falls back to the BiCGStab
                                     inner solve if a cycle cuts the true residual less than 10x */
+  DTR_SOLVER_MIXED_F16 = 3,      /* as DTR_SOLVER_MIXED_F32, with the inner Krylov vectors (r, r^, p, v,
+                                    s, t) stored in FP16 and the inner right-hand side scaled to entries of
+                                    RMS 1; FP32 arithmetic and FP32 inner iterate; the stencil reads its
+                                    input in FP16.  Persistent engine only.  inner_tol below 1e-3 is
+                                    raised to 1e-3 (what an FP16-stored recursion can certify) */
+  DTR_SOLVER_MIXED_BF16 = 4      /* the same with BF16 storage; inner_tol floor 1e-2 */
 } dtr_solver;
 
 /* Message of the last failure on this thread ("" if none).  Never NULL. */

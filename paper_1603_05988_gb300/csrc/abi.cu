@@ -351,11 +351,14 @@ void dtr_solve_params_default(dtr_solve_params *p) {
 static int check_solve_params(const dtr_solve_params *p) {
   if (!p) return fail(DTR_EINVAL, "null solve params");
   if (!(p->tol > 0.0) || p->maxiter < 1) return fail(DTR_EINVAL, "tol must be > 0 and maxiter >= 1");
-  if (p->solver != DTR_SOLVER_BICGSTAB_F64 && p->solver != DTR_SOLVER_MIXED_F32 && p->solver != DTR_SOLVER_FGMRES_NET)
+  if (p->solver != DTR_SOLVER_BICGSTAB_F64 && p->solver != DTR_SOLVER_MIXED_F32 && p->solver != DTR_SOLVER_FGMRES_NET &&
+      p->solver != DTR_SOLVER_MIXED_F16 && p->solver != DTR_SOLVER_MIXED_BF16)
     return fail(DTR_EINVAL, "unknown solver");
   if (p->solver == DTR_SOLVER_FGMRES_NET && (p->gmres_m < 1 || p->gmres_m > 32))
     return fail(DTR_EINVAL, "gmres_m must be in [1, 32]");
   if (p->engine != 0 && p->engine != 1) return fail(DTR_EINVAL, "engine must be 0 (persistent) or 1 (per-step)");
+  if ((p->solver == DTR_SOLVER_MIXED_F16 || p->solver == DTR_SOLVER_MIXED_BF16) && p->engine != 0)
+    return fail(DTR_EINVAL, "half-storage inner solves need the persistent engine");
   if (p->grid < 0) return fail(DTR_EINVAL, "grid must be >= 0");
   return DTR_OK;
 }

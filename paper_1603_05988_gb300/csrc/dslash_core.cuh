@@ -18,6 +18,9 @@
 // every lower-spin term flipped on input and output (sgn = -1).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "dtr_internal.cuh"
 
 namespace dtr {
@@ -33,6 +36,36 @@ template <typename C> struct AxpyLoad {
   const C *__restrict__ v;
   C a;
   __device__ __forceinline__ C operator()(int64_t idx) const { return caxpy(cneg(a), v[idx], r[idx]); }
+};
+
+// Complex values stored as S, computed as float2/double2: loads widen, stores round to nearest.
+template <typename S> struct CStore {
+  __device__ __forceinline__ static S ld(const S *p, int64_t i) { return p[i]; }
+  __device__ __forceinline__ static void st(S *p, int64_t i, S v) { p[i] = v; }
+};
+template <> struct CStore<__half2> {
+  __device__ __forceinline__ static float2 ld(const __half2 *p, int64_t i) { return __half22float2(p[i]); }
+  __device__ __forceinline__ static void st(__half2 *p, int64_t i, float2 v) { p[i] = __float22half2_rn(v); }
+};
+template <> struct CStore<__nv_bfloat162> {
+  __device__ __forceinline__ static float2 ld(const __nv_bfloat162 *p, int64_t i) {
+    return __bfloat1622float2(p[i]);
+  }
+  __device__ __forceinline__ static void st(__nv_bfloat162 *p, int64_t i, float2 v) {
+    p[i] = __float22bfloat162_rn(v);
+  }
+};
+template <typename S, typename C> struct PlainLoadS {
+  const S *__restrict__ f;
+  __device__ __forceinline__ C operator()(int64_t idx) const { return CStore<S>::ld(f, idx); }
+};
+template <typename S, typename C> struct AxpyLoadS {
+  const S *__restrict__ r;
+  const S *__restrict__ v;
+  C a;
+  __device__ __forceinline__ C operator()(int64_t idx) const {
+    return caxpy(cneg(a), CStore<S>::ld(v, idx), CStore<S>::ld(r, idx));
+  }
 };
 
 // B_mu applied to a 2-spin vector l (component-wise over colour)

@@ -32,6 +32,9 @@
 
 #include "dslash_core.cuh"
 #include "krylov_fin.cuh"
+#include <cstring>
+#include <type_traits>
+
 #include "persist.cuh"
 #include "reduce.cuh"
 
@@ -212,9 +215,26 @@ __device__ __forceinline__ void grid_sums(int P, const CA *__restrict__ part, CA
 
 template <typename C> __device__ __forceinline__ C mkc(const double2 v) { return mk<C>(v.x, v.y); }
 
-template <typename R, int T, int WITH_RESID>
-__global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
+// four complex values stored as S (4 bytes each) in one 16-byte word
+template <typename S> __device__ __forceinline__ void unpack4(const uint4 w, float2 (&c)[4]) {
+  S h[4];
+  memcpy(h, &w, sizeof(w));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) c[k] = CStore<S>::ld(h, k);
+}
+template <typename S> __device__ __forceinline__ uint4 pack4(const float2 (&c)[4]) {
+  S h[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) CStore<S>::st(h, k, c[k]);
+  uint4 w;
+  memcpy(&w, h, sizeof(w));
+  return w;
+}
+
+template <typename R, int T, int WITH_RESID, typename S = typename cplx_t<R>::type>
+__global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R, S> a) {
   typedef typename cplx_t<R>::type C;
+  typedef CStore<S> SS;
   __shared__ typename cplx_t<R>::type sh[T];
   __shared__ double2 tot[5 * 64];
   __shared__ R shw[(T / 32) * 5 * 2 * 32];
@@ -251,9 +271,9 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
         for (int c = 0; c < 12; ++c) {
           const C zz = a.z[base + c * b];
           const C rr = csub(zz, o[c]);
-          a.r[base + c * b] = rr;
-          a.rhat[base + c * b] = rr;
-          a.p[base + c * b] = rr;
+          SS::st(a.r, base + c * b, rr);
+          SS::st(a.rhat, base + c * b, rr);
+          SS::st(a.p, base + c * b, rr);
           vx[0] += rr.x * rr.x + rr.y * rr.y;
           vy[0] += zz.x * zz.x + zz.y * zz.y;
         }
@@ -273,15 +293,16 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
       if (blockIdx.x == 0 && threadIdx.x == 0) a.gs->iters = done;
       {  // P1: v = A p ; rhat^H v -> alpha   (per-thread sums in R, block/grid sums in FP64)
         R vx[1] = {0}, vy[1] = {0};
+        const PlainLoadS<S, C> ldp{a.p};
         for (int64_t it = t0; it < nsite; it += stride) {
           const int s = (int)(it >> logb);
           C o[12], self[12];
-          dslash_site<1, R>(a.U, a.p, a.g, b, s, j, a.diag, o, self);
+          dslash_site_ld<1, R>(a.U, ldp, a.g, b, s, j, a.diag, o, self);
           const int64_t base = (int64_t)s * 12 * b + j;
 #pragma unroll
           for (int c = 0; c < 12; ++c) {
-            a.v[base + c * b] = o[c];
-            const C rh = a.rhat[base + c * b];
+            SS::st(a.v, base + c * b, o[c]);
+            const C rh = SS::ld(a.rhat, base + c * b);
             vx[0] += rh.x * o[c].x + rh.y * o[c].y;
             vy[0] += rh.x * o[c].y - rh.y * o[c].x;
           }
@@ -297,7 +318,7 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
       int n_active = 0;
       {  // P2: t = A s with s = r - alpha v on the fly ; five dots -> omega, beta, convergence
         const C al = mkc<C>(ss.alpha[j]);
-        AxpyLoad<C> ld{a.r, a.v, al};
+        AxpyLoadS<S, C> ld{a.r, a.v, al};
         R vx[5] = {0, 0, 0, 0, 0}, vy[5] = {0, 0, 0, 0, 0};
         for (int64_t it = t0; it < nsite; it += stride) {
           const int s = (int)(it >> logb);
@@ -306,9 +327,9 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
           const int64_t base = (int64_t)s * 12 * b + j;
 #pragma unroll
           for (int c = 0; c < 12; ++c) {
-            a.t[base + c * b] = o[c];
-            a.s[base + c * b] = self[c];
-            const C rh = a.rhat[base + c * b];
+            SS::st(a.t, base + c * b, o[c]);
+            SS::st(a.s, base + c * b, self[c]);
+            const C rh = SS::ld(a.rhat, base + c * b);
             vx[0] += o[c].x * self[c].x + o[c].y * self[c].y;  // t^H s
             vy[0] += o[c].x * self[c].y - o[c].y * self[c].x;
             vx[1] += o[c].x * o[c].x + o[c].y * o[c].y;        // t^H t
@@ -338,7 +359,7 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
         const bool act = ss.active[j] != 0;
         constexpr int U = 4;  // independent elements (or FP32 pairs) in flight per thread
         int64_t e = t0;
-        if constexpr (sizeof(R) == 4) {
+        if constexpr (sizeof(R) == 4 && std::is_same<S, float2>::value) {
           if (b >= 2) {  // FP32: two adjacent columns j, j+1 per 16-byte access
           const int j0 = (2 * threadIdx.x) & (b - 1);
           const C al1 = mkc<C>(ss.alpha[j0 + 1]), om1 = mkc<C>(ss.omega[j0 + 1]);
@@ -384,33 +405,91 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R> a) {
           e = nel;  // done
           }
         }
+        if constexpr (!std::is_same<S, C>::value) {
+          if (b >= 4) {  // half storage: four adjacent columns per 16-byte access; x in FP32
+            const int j0 = (4 * threadIdx.x) & (b - 1);
+            C al4[4], om4[4], be4[4], mom4[4];
+            bool act4[4], any = false;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+              al4[w] = mkc<C>(ss.alpha[j0 + w]);
+              om4[w] = mkc<C>(ss.omega[j0 + w]);
+              be4[w] = mkc<C>(ss.beta[j0 + w]);
+              mom4[w] = cneg(om4[w]);
+              act4[w] = ss.active[j0 + w] != 0;
+              any = any || act4[w];
+            }
+            const int64_t n4 = nel >> 2;
+            float4 *X = (float4 *)a.x;
+            uint4 *Rr = (uint4 *)a.r, *Pp = (uint4 *)a.p;
+            const uint4 *Ss = (const uint4 *)a.s, *Tt = (const uint4 *)a.t, *Vv = (const uint4 *)a.v;
+            auto upd = [&](uint4 sw, uint4 pw, float4 xa, float4 xb, uint4 tw, uint4 vw, int64_t q) {
+              C sv[4], pv[4], tv[4], vv[4], rn[4], pn[4];
+              unpack4<S>(sw, sv);
+              unpack4<S>(pw, pv);
+              unpack4<S>(tw, tv);
+              unpack4<S>(vw, vv);
+              C xv[4] = {mk<C>(xa.x, xa.y), mk<C>(xa.z, xa.w), mk<C>(xb.x, xb.y), mk<C>(xb.z, xb.w)};
+#pragma unroll
+              for (int w = 0; w < 4; ++w) {
+                xv[w] = caxpy(om4[w], sv[w], caxpy(al4[w], pv[w], xv[w]));
+                rn[w] = caxpy(mom4[w], tv[w], sv[w]);
+                pn[w] = act4[w] ? caxpy(be4[w], caxpy(mom4[w], vv[w], pv[w]), rn[w]) : pv[w];
+              }
+              X[2 * q] = make_float4(xv[0].x, xv[0].y, xv[1].x, xv[1].y);
+              X[2 * q + 1] = make_float4(xv[2].x, xv[2].y, xv[3].x, xv[3].y);
+              Rr[q] = pack4<S>(rn);
+              if (any) Pp[q] = pack4<S>(pn);
+            };
+            const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+            int64_t f = t0;
+            for (; f + stride < n4; f += 2 * stride) {
+              uint4 sw[2], pw[2], tw[2], vw[2];
+              float4 xa[2], xb[2];
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const int64_t q = f + u * stride;
+                sw[u] = Ss[q];
+                pw[u] = Pp[q];
+                xa[u] = X[2 * q];
+                xb[u] = X[2 * q + 1];
+                tw[u] = Tt[q];
+                vw[u] = any ? Vv[q] : zero4;
+              }
+#pragma unroll
+              for (int u = 0; u < 2; ++u) upd(sw[u], pw[u], xa[u], xb[u], tw[u], vw[u], f + u * stride);
+            }
+            for (; f < n4; f += stride) upd(Ss[f], Pp[f], X[2 * f], X[2 * f + 1], Tt[f], any ? Vv[f] : zero4, f);
+            e = nel;  // done
+          }
+        }
         for (; e + (U - 1) * stride < nel; e += U * stride) {
           C sv[U], pv[U], xv[U], tv[U], vv[U];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int64_t q = e + u * stride;
-            sv[u] = a.s[q];
-            pv[u] = a.p[q];
+            sv[u] = SS::ld(a.s, q);
+            pv[u] = SS::ld(a.p, q);
             xv[u] = a.x[q];
-            tv[u] = a.t[q];
-            if (act) vv[u] = a.v[q];
+            tv[u] = SS::ld(a.t, q);
+            if (act) vv[u] = SS::ld(a.v, q);
           }
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int64_t q = e + u * stride;
             a.x[q] = caxpy(om, sv[u], caxpy(al, pv[u], xv[u]));
             const C rn = caxpy(mom, tv[u], sv[u]);
-            a.r[q] = rn;
-            if (act) a.p[q] = caxpy(be, caxpy(mom, vv[u], pv[u]), rn);
+            SS::st(a.r, q, rn);
+            if (act) SS::st(a.p, q, caxpy(be, caxpy(mom, vv[u], pv[u]), rn));
           }
         }
         for (; e < nel; e += stride) {
-          const C sv = a.s[e];
-          const C pv = a.p[e];
+          const C sv = SS::ld(a.s, e);
+          const C pv = SS::ld(a.p, e);
           a.x[e] = caxpy(om, sv, caxpy(al, pv, a.x[e]));
-          const C rn = caxpy(mom, a.t[e], sv);
-          a.r[e] = rn;
-          if (act) a.p[e] = caxpy(be, caxpy(mom, a.v[e], pv), rn);
+          const C rn = caxpy(mom, SS::ld(a.t, e), sv);
+          SS::st(a.r, e, rn);
+          if (act) SS::st(a.p, e, caxpy(be, caxpy(mom, SS::ld(a.v, e), pv), rn));
         }
         const bool stop = n_active == 0;
         if (stop && !WITH_RESID) break;  // kernel exit orders these writes for the host
@@ -482,21 +561,22 @@ unsigned long long *device_launch_counter() {
   return (unsigned long long *)p;
 }
 
-template <typename R, int T, int W> static int launch_one(const PArgs<R> &pa, cudaStream_t st) {
+template <typename R, int T, int W, typename S>
+static int launch_one(const PArgs<R, S> &pa, cudaStream_t st) {
   static int max_grid = 0;
   if (!max_grid) {
     int nb = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bicgstab_persistent<R, T, W>, T, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bicgstab_persistent<R, T, W, S>, T, 0);
     if (e != cudaSuccess) return cuda_fail(e, "persistent solver occupancy");
     if (nb < 1) return fail(DTR_ECUDA, "persistent solver cannot be resident");
     max_grid = nb * device_sms();
     if (max_grid > kPersistMaxGrid) max_grid = kPersistMaxGrid;
   }
   const int grid = (pa.grid > 0 && pa.grid < max_grid) ? pa.grid : max_grid;
-  PArgs<R> copy = pa;
+  PArgs<R, S> copy = pa;
   void *args[] = {&copy};
-  DTR_CUDA(cudaLaunchCooperativeKernel((const void *)k_bicgstab_persistent<R, T, W>, dim3(grid), dim3(T), args, 0,
-                                       st));
+  DTR_CUDA(cudaLaunchCooperativeKernel((const void *)k_bicgstab_persistent<R, T, W, S>, dim3(grid), dim3(T), args,
+                                       0, st));
   count_launches(1);
   if (g_prof.on) return persist_account(pa.gs, (double)pa.g.V * pa.b, st);
   return DTR_OK;
@@ -505,10 +585,15 @@ template <typename R, int T, int W> static int launch_one(const PArgs<R> &pa, cu
 template <typename R> int launch_persistent(const PArgs<R> &pa, int with_resid, cudaStream_t st);
 
 template <> int launch_persistent<double>(const PArgs<double> &pa, int with_resid, cudaStream_t st) {
-  return with_resid ? launch_one<double, 256, 1>(pa, st) : launch_one<double, 256, 0>(pa, st);
+  return with_resid ? launch_one<double, 256, 1, double2>(pa, st) : launch_one<double, 256, 0, double2>(pa, st);
 }
 template <> int launch_persistent<float>(const PArgs<float> &pa, int with_resid, cudaStream_t st) {
-  return with_resid ? launch_one<float, 512, 1>(pa, st) : launch_one<float, 512, 0>(pa, st);
+  return with_resid ? launch_one<float, 512, 1, float2>(pa, st) : launch_one<float, 512, 0, float2>(pa, st);
 }
+template <typename S> int launch_persistent_half(const PArgs<float, S> &pa, cudaStream_t st) {
+  return launch_one<float, 512, 0, S>(pa, st);
+}
+template int launch_persistent_half<__half2>(const PArgs<float, __half2> &, cudaStream_t);
+template int launch_persistent_half<__nv_bfloat162>(const PArgs<float, __nv_bfloat162> &, cudaStream_t);
 
 }  // namespace dtr

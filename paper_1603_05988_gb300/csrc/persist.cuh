@@ -1,6 +1,9 @@
 // Persistent (single cooperative launch) batched BiCGStab.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "solver.cuh"
 
 namespace dtr {
@@ -18,9 +21,13 @@ struct GridSync {
 };
 constexpr size_t kGridSyncLaunchBytes = offsetof(GridSync, error);
 
-template <typename R> struct PArgs {
+// S: storage type of the Krylov vectors r, rhat, p, v, s, t (the arithmetic is
+// in R; the iterate x is stored in R).  S = complex R, or __half2 /
+// __nv_bfloat162 for the half-storage inner solve (FP32 arithmetic).
+template <typename R, typename S = typename cplx_t<R>::type> struct PArgs {
   const typename cplx_t<R>::type *U;
-  typename cplx_t<R>::type *x, *r, *rhat, *p, *v, *s, *t;
+  typename cplx_t<R>::type *x;
+  S *r, *rhat, *p, *v, *s, *t;
   const typename cplx_t<R>::type *z;  // right-hand sides (true-residual cycles only)
   Geom g;
   int b, logb;
@@ -37,6 +44,8 @@ template <typename R> struct PArgs {
 // iterations) until every column meets tol in the true residual (FP64 path);
 // with_resid = 0: iterations only, from the caller-initialised state.
 template <typename R> int launch_persistent(const PArgs<R> &pa, int with_resid, cudaStream_t st);
+// Inner iterations with the Krylov vectors stored in S (FP16 or BF16), FP32 arithmetic.
+template <typename S> int launch_persistent_half(const PArgs<float, S> &pa, cudaStream_t st);
 
 // Optional timing of persistent launches (for roofline accounting): every
 // block stamps the device global timer at entry and exit, and a one-thread

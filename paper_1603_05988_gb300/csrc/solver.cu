@@ -9,7 +9,9 @@
 // convergence test), p update.  The scalar algebra of each step runs in the
 // last block of the reducing kernel, so the host only polls a device-side
 // active-column count every `check_every` iterations.
+#include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <mutex>
 #include <vector>
 
@@ -225,32 +227,36 @@ __global__ void __launch_bounds__(kBlock) k_pupdate(typename cplx_t<R>::type *__
   }
 }
 
-// mixed: r32 = scale * r64, rhat = p = r32, e = 0 (inner columns = outer active)
-__global__ void __launch_bounds__(kBlock) k_mixed_init(const double2 *__restrict__ r64, float2 *__restrict__ r,
-                                                       float2 *__restrict__ rhat, float2 *__restrict__ p,
+// mixed: r32 = hs * scale * r64 (scale = 1 / ||r64|| per column; hs = 1 for FP32
+// storage, sqrt(12 V) for half storage, so that the entries are O(1) and stay in
+// FP16's normal range), rhat = p = r32, e = 0 (inner columns = outer active).
+// S: storage of the inner Krylov vectors; the inner iterate e is FP32.
+template <typename S>
+__global__ void __launch_bounds__(kBlock) k_mixed_init(const double2 *__restrict__ r64, S *__restrict__ r,
+                                                       S *__restrict__ rhat, S *__restrict__ p,
                                                        float2 *__restrict__ e, int64_t n, int b,
-                                                       const Scal *__restrict__ outer) {
+                                                       const Scal *__restrict__ outer, double hs) {
   const int j = threadIdx.x & (b - 1);
-  const double sc = outer->active[j] ? outer->scale[j] : 0.0;
+  const double sc = outer->active[j] ? outer->scale[j] * hs : 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double2 v = r64[i];
     const float2 f = make_float2((float)(v.x * sc), (float)(v.y * sc));
-    r[i] = f;
-    rhat[i] = f;
-    p[i] = f;
+    CStore<S>::st(r, i, f);
+    CStore<S>::st(rhat, i, f);
+    CStore<S>::st(p, i, f);
     e[i] = make_float2(0.f, 0.f);
   }
 }
 
 __global__ void k_mixed_scal_init(const Scal *__restrict__ outer, Scal *inner, int b, double inner_tol2,
-                                  int inner_maxiter) {
+                                  int inner_maxiter, double hs2) {
   const int j = threadIdx.x;
   if (j < b) {
     const int act = outer->active[j];
     inner->active[j] = act;
     inner->rho[j] = make_double2(1.0, 0.0);
-    inner->bnorm2[j] = 1.0;
-    inner->rnorm2[j] = 1.0;
+    inner->bnorm2[j] = hs2;  // ||r32||^2 of a unit column scaled by hs
+    inner->rnorm2[j] = hs2;
     inner->iters[j] = 0;
     inner->flags[j] = 0;
     inner->alpha[j] = inner->omega[j] = inner->beta[j] = make_double2(0.0, 0.0);
@@ -264,12 +270,13 @@ __global__ void k_mixed_scal_init(const Scal *__restrict__ outer, Scal *inner, i
   }
 }
 
-// x64 += e / scale for outer-active columns; fold inner iteration counts.
+// x64 += e / (hs * scale) for outer-active columns; fold inner iteration counts.
 __global__ void __launch_bounds__(kBlock) k_mixed_accum(double2 *__restrict__ x, const float2 *__restrict__ e,
-                                                        int64_t n, int b, Scal *outer, const Scal *__restrict__ inner) {
+                                                        int64_t n, int b, Scal *outer, const Scal *__restrict__ inner,
+                                                        double hs) {
   const int j = threadIdx.x & (b - 1);
   const int act = outer->active[j];
-  const double inv = act ? 1.0 / outer->scale[j] : 0.0;
+  const double inv = act ? 1.0 / (outer->scale[j] * hs) : 0.0;
   if (act) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
       const float2 v = e[i];
@@ -361,13 +368,31 @@ static int iterate(const typename cplx_t<R>::type *U, KrylovVecs<R> &K, const Ge
   return DTR_OK;
 }
 
+static bool mixed_bicgstab(int solver) {
+  return solver == DTR_SOLVER_MIXED_F32 || solver == DTR_SOLVER_MIXED_F16 || solver == DTR_SOLVER_MIXED_BF16;
+}
+// storage of the inner Krylov vectors: 0 FP32, 1 FP16, 2 BF16
+static int inner_store(int solver) {
+  return solver == DTR_SOLVER_MIXED_F16 ? 1 : solver == DTR_SOLVER_MIXED_BF16 ? 2 : 0;
+}
+// Relative residual reduction asked of one inner solve.  A recursion whose vectors are
+// rounded to 11 (FP16) or 8 (BF16) significant bits cannot certify more than ~1e-3 or
+// ~1e-2 of reduction, so smaller requests are raised to that floor (the FP64 outer
+// loop reaches the outer tolerance either way).
+static double inner_tol_for(const dtr_solve_params *p) {
+  double t = p->inner_tol > 0 ? p->inner_tol : 1e-5;
+  const int store = inner_store(p->solver);
+  const double floor = store == 1 ? kInnerTolFloorF16 : store == 2 ? kInnerTolFloorBF16 : 0.0;
+  return t < floor ? floor : t;
+}
+
 size_t solver_scratch_bytes(int64_t V, int b, int solver, int gmres_m) {
   const size_t vec64 = ((size_t)V * 12 * b * sizeof(double2) + 255) / 256 * 256;
   const size_t vec32 = ((size_t)V * 12 * b * sizeof(float2) + 255) / 256 * 256;
   const size_t red = 256 + (size_t)kMaxGrid * 5 * 64 * sizeof(double2);
   const size_t scal = 2 * ((sizeof(Scal) + 255) / 256) * 256;
   const size_t fixed = 256 + red + scal + 256 + 256;
-  if (solver == DTR_SOLVER_MIXED_F32) return fixed + vec64 + 7 * vec32;
+  if (mixed_bicgstab(solver)) return fixed + vec64 + 7 * vec32;  // half storage uses half of each slot
   if (solver == DTR_SOLVER_FGMRES_NET) return fixed + vec64 + 7 * vec32 + fgmres_scratch_bytes(V, b, gmres_m) + 256;
   return fixed + 6 * vec64;
 }
@@ -424,25 +449,62 @@ struct MixedState {
   unsigned gd, gv;
   double itol;
   int maxiter, grid;
+  int store;  // inner Krylov vectors: 0 FP32, 1 FP16, 2 BF16
+  double hs;  // inner right-hand-side scale (see k_mixed_init)
 };
+
+// inner iterations of one defect-correction cycle on the caller-initialised state
+template <typename S>
+static int launch_inner(const dtr_gauge_s *gauge, const KrylovVecs<float> &K, float2 *sv, const Geom &g, int b,
+                        int logb, double m0, Scal *inner, const Reduce &red, GridSync *gs, int maxiter, int grid,
+                        cudaStream_t st) {
+  PArgs<float, S> pa;
+  pa.U = gauge->U32;
+  pa.x = K.x;
+  pa.r = (S *)K.r; pa.rhat = (S *)K.rhat; pa.p = (S *)K.p; pa.v = (S *)K.v; pa.s = (S *)sv; pa.t = (S *)K.t;
+  pa.z = nullptr;
+  pa.g = g; pa.b = b; pa.logb = logb; pa.diag = (float)(4.0 + m0);
+  pa.sc = inner; pa.partial = red.partial; pa.gs = gs;
+  pa.max_iters = maxiter + 1;
+  pa.max_cycles = 1;
+  pa.grid = grid;
+  if constexpr (std::is_same<S, float2>::value) return launch_persistent<float>(pa, 0, st);
+  else return launch_persistent_half<S>(pa, st);
+}
+
+template <typename S>
+static void launch_mixed_init(const double2 *r64, const KrylovVecs<float> &K, int64_t n, int b, const Scal *outer,
+                              double hs, unsigned gv, cudaStream_t st) {
+  k_mixed_init<S><<<gv, kBlock, 0, st>>>(r64, (S *)K.r, (S *)K.rhat, (S *)K.p, K.x, n, b, outer, hs);
+}
+
+static void mixed_init(int store, const double2 *r64, const KrylovVecs<float> &K, int64_t n, int b,
+                       const Scal *outer, double hs, unsigned gv, cudaStream_t st) {
+  if (store == 1) launch_mixed_init<__half2>(r64, K, n, b, outer, hs, gv, st);
+  else if (store == 2) launch_mixed_init<__nv_bfloat162>(r64, K, n, b, outer, hs, gv, st);
+  else launch_mixed_init<float2>(r64, K, n, b, outer, hs, gv, st);
+  count_launches(1);
+}
+
+static int inner_solve(int store, const dtr_gauge_s *gauge, const KrylovVecs<float> &K, float2 *sv, const Geom &g,
+                       int b, int logb, double m0, Scal *inner, const Reduce &red, GridSync *gs, int maxiter,
+                       int grid, cudaStream_t st) {
+  if (store == 1) return launch_inner<__half2>(gauge, K, sv, g, b, logb, m0, inner, red, gs, maxiter, grid, st);
+  if (store == 2)
+    return launch_inner<__nv_bfloat162>(gauge, K, sv, g, b, logb, m0, inner, red, gs, maxiter, grid, st);
+  return launch_inner<float2>(gauge, K, sv, g, b, logb, m0, inner, red, gs, maxiter, grid, st);
+}
 
 // One defect-correction cycle after a residual: returns the kernels it launched.
 int enqueue_inner(const MixedState &S, cudaStream_t st, int *kernels) {
   const int64_t n = (int64_t)S.g.V * 12 * S.b;
-  k_mixed_init<<<S.gv, kBlock, 0, st>>>(S.r64, S.K.r, S.K.rhat, S.K.p, S.K.x, n, S.b, S.outer); count_launches(1);
-  k_mixed_scal_init<<<1, 64, 0, st>>>(S.outer, S.inner, S.b, S.itol * S.itol, S.maxiter); count_launches(1);
+  mixed_init(S.store, S.r64, S.K, n, S.b, S.outer, S.hs, S.gv, st);
+  k_mixed_scal_init<<<1, 64, 0, st>>>(S.outer, S.inner, S.b, S.itol * S.itol, S.maxiter, S.hs * S.hs);
+  count_launches(1);
   DTR_LAUNCH_CHECK("inner init");
   DTR_CUDA(cudaMemsetAsync(S.gs, 0, kGridSyncLaunchBytes, st));
-  PArgs<float> pa;
-  pa.U = S.gauge->U32;
-  pa.x = S.K.x; pa.r = S.K.r; pa.rhat = S.K.rhat; pa.p = S.K.p; pa.v = S.K.v; pa.s = S.sv; pa.t = S.K.t;
-  pa.z = nullptr;
-  pa.g = S.g; pa.b = S.b; pa.logb = S.logb; pa.diag = (float)(4.0 + S.m0);
-  pa.sc = S.inner; pa.partial = S.red.partial; pa.gs = S.gs;
-  pa.max_iters = S.maxiter + 1;
-  pa.max_cycles = 1;
-  pa.grid = S.grid;
-  int rc = launch_persistent<float>(pa, 0, st);
+  int rc = inner_solve(S.store, S.gauge, S.K, S.sv, S.g, S.b, S.logb, S.m0, S.inner, S.red, S.gs, S.maxiter, S.grid,
+                       st);
   if (rc) return rc;
   *kernels = 3 + (persist_profile().on ? 1 : 0);
   return DTR_OK;
@@ -454,7 +516,7 @@ struct GraphKey {
   int L[4];
   double m0;
   const void *x, *z, *work;
-  int b, x_is_zero, maxiter, grid, prof, pad;
+  int b, x_is_zero, maxiter, grid, prof, store;
   double tol, itol;
 };
 
@@ -539,7 +601,7 @@ int capture_mixed_graph(const MixedState &S, int x_is_zero, double tol2, int max
   int kin = 0;
   rc = enqueue_inner(S, cs2, &kin);
   if (rc) return bail(rc);
-  k_mixed_accum<<<S.gv, kBlock, 0, cs2>>>(S.x, S.K.x, n, S.b, S.outer, S.inner);
+  k_mixed_accum<<<S.gv, kBlock, 0, cs2>>>(S.x, S.K.x, n, S.b, S.outer, S.inner, S.hs);
   k_resid<double, 0><<<S.gd, kBlock, 0, cs2>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
                                                4.0 + S.m0, S.outer, S.red, 1);
   k_loop_cond<<<1, 32, 0, cs2>>>(h, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 0, devcnt, (unsigned)(kin + 3));
@@ -592,6 +654,7 @@ static int solve_mixed_graph(const MixedState &S, int x_is_zero, double tol2, in
   key.prof = persist_profile().on ? 1 : 0;
   key.tol = tol2;
   key.itol = S.itol;
+  key.store = S.store;
   std::lock_guard<std::mutex> lock(g_graph_mu);
   GraphEntry *hit = nullptr;
   for (auto &e : g_graphs)
@@ -627,7 +690,7 @@ static int solve_mixed_graph(const MixedState &S, int x_is_zero, double tol2, in
 
 bool solve_can_run_async(const dtr_solve_params *p) {
   if (p->engine != 0) return false;
-  return p->solver == DTR_SOLVER_BICGSTAB_F64 || (p->solver == DTR_SOLVER_MIXED_F32 && !p->no_graph);
+  return p->solver == DTR_SOLVER_BICGSTAB_F64 || (mixed_bicgstab(p->solver) && !p->no_graph);
 }
 
 int *solver_error_word(void *work) {
@@ -667,7 +730,11 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
   const unsigned gv = reduce_grid(n, sms);
   const int check = p->check_every > 0 ? p->check_every : 8;
   const bool persistent = p->engine == 0;
-  if (p->solver == DTR_SOLVER_MIXED_F32 && persistent && !p->no_graph) {
+  const int store = inner_store(p->solver);
+  const double hs = store ? std::sqrt(12.0 * (double)g.V) : 1.0;
+  const double itol = inner_tol_for(p);
+  if (store && !persistent) return fail(DTR_EINVAL, "half-storage inner solves need the persistent engine");
+  if (mixed_bicgstab(p->solver) && persistent && !p->no_graph) {
     MixedState S;
     S.gauge = gauge; S.g = g; S.b = b; S.logb = logb; S.m0 = m0; S.x = x; S.z = z;
     S.r64 = (double2 *)w; w = align256(w + n * sizeof(double2));
@@ -679,9 +746,11 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     S.K.t = (float2 *)w;    w = align256(w + n * sizeof(float2));
     S.sv = (float2 *)w;     w = align256(w + n * sizeof(float2));
     S.outer = outer; S.inner = inner; S.red = red; S.gs = gs; S.gd = gd; S.gv = gv;
-    S.itol = p->inner_tol > 0 ? p->inner_tol : 1e-5;
+    S.itol = itol;
     S.maxiter = p->maxiter;
     S.grid = p->grid;
+    S.store = store;
+    S.hs = hs;
     *scal_out = outer;
     int rc = solve_mixed_graph(S, x_is_zero, p->tol * p->tol, p->maxiter, work, st);
     if (rc) return rc;
@@ -727,7 +796,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     }
     return DTR_OK;
   }
-  if (p->solver == DTR_SOLVER_MIXED_F32 || p->solver == DTR_SOLVER_FGMRES_NET) {
+  if (mixed_bicgstab(p->solver) || p->solver == DTR_SOLVER_FGMRES_NET) {
     double2 *r64 = (double2 *)w; w = align256(w + n * sizeof(double2));
     KrylovVecs<float> K;
     K.x = (float2 *)w;    w = align256(w + n * sizeof(float2));
@@ -739,7 +808,6 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     float2 *sv = (float2 *)w; w = align256(w + n * sizeof(float2));
     void *fg_work = w;
     const size_t fg_bytes = p->solver == DTR_SOLVER_FGMRES_NET ? fgmres_scratch_bytes(g.V, b, p->gmres_m) : 0;
-    const double itol = p->inner_tol > 0 ? p->inner_tol : 1e-5;
     bool fgmres = p->solver == DTR_SOLVER_FGMRES_NET;
     std::vector<double> prev_rel(64, -1.0);
     for (int cycle = 0; cycle <= kMaxRestarts; ++cycle) {
@@ -755,8 +823,8 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
       int rc = read_n_active(outer, st, &n_active);
       if (rc) return rc;
       if (n_active == 0) break;
-      k_mixed_init<<<gv, kBlock, 0, st>>>(r64, K.r, K.rhat, K.p, K.x, n, b, outer); count_launches(1);
-      k_mixed_scal_init<<<1, 64, 0, st>>>(outer, inner, b, itol * itol, p->maxiter); count_launches(1);
+      mixed_init(store, r64, K, n, b, outer, hs, gv, st);
+      k_mixed_scal_init<<<1, 64, 0, st>>>(outer, inner, b, itol * itol, p->maxiter, hs * hs); count_launches(1);
       DTR_LAUNCH_CHECK("inner init");
       if (fgmres) {
         // fall back to the BiCGStab inner solve if the last FGMRES cycle cut the true residual < 10x
@@ -784,21 +852,13 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
         DTR_CUDA(cudaMemcpyAsync(inner->iters, its.data(), sizeof(int) * b, cudaMemcpyHostToDevice, st));
       } else if (persistent) {
         DTR_CUDA(cudaMemsetAsync(gs, 0, kGridSyncLaunchBytes, st));
-        PArgs<float> pa;
-        pa.U = gauge->U32;
-        pa.x = K.x; pa.r = K.r; pa.rhat = K.rhat; pa.p = K.p; pa.v = K.v; pa.s = sv; pa.t = K.t; pa.z = nullptr;
-        pa.g = g; pa.b = b; pa.logb = logb; pa.diag = (float)(4.0 + m0);
-        pa.sc = inner; pa.partial = red.partial; pa.gs = gs;
-        pa.max_iters = p->maxiter + 1;
-        pa.max_cycles = 1;
-        pa.grid = p->grid;
-        rc = launch_persistent<float>(pa, 0, st);
+        rc = inner_solve(store, gauge, K, sv, g, b, logb, m0, inner, red, gs, p->maxiter, p->grid, st);
         if (rc) return rc;
       } else {
         rc = iterate<float>(gauge->U32, K, g, b, m0, inner, red, check, p->maxiter + check, st);
         if (rc) return rc;
       }
-      k_mixed_accum<<<gv, kBlock, 0, st>>>(x, K.x, n, b, outer, inner); count_launches(1);
+      k_mixed_accum<<<gv, kBlock, 0, st>>>(x, K.x, n, b, outer, inner, hs); count_launches(1);
       DTR_LAUNCH_CHECK("defect accumulate");
     }
     if (persistent) return read_gs_error(gs, st);

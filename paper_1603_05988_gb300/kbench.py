@@ -2,6 +2,7 @@
 
     python -m paper_1603_05988_gb300.kbench dslash --lattice 32,32,32,64 --prec bf16 --nrhs 1 --reps 20
     python -m paper_1603_05988_gb300.kbench solve --lattice 8,8,8,8 --nrhs 16 --reps 3 [--no-graph]
+        [--solver f64,mixed_f32,mixed_f16,mixed_bf16] [--inner-tol T] [--eps E --gauge-seed S --m0 M]
     python -m paper_1603_05988_gb300.kbench deflate --lattice 16,16,16,32 --k 256 --prec bf16 --nrhs 16 --reps 20
 
 Large lattices take their links from the seeded 16^3x32 field repeated
@@ -65,15 +66,16 @@ def dslash_case(gauge, dims, prec, nrhs, reps, m0=-0.75):
             "achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9, "achieved_tflops": flops / (ms * 1e-3) / 1e12}
 
 
-def solve_case(gauge, dims, nrhs, reps, m0, graph=True, grid=0):
-    """Mixed-precision solves of nrhs Z4 right-hand sides to 1e-10 (persistent
-    engine), with the persistent launches timed on the device."""
+def solve_case(gauge, dims, nrhs, reps, m0, graph=True, grid=0, solver="mixed_f32", inner_tol=1e-5):
+    """Solves of nrhs Z4 right-hand sides to 1e-10 (persistent engine), with the
+    persistent launches timed on the device.  solver: f64, mixed_f32 (FP32 inner
+    vectors), mixed_f16 / mixed_bf16 (half-storage inner vectors)."""
     import time
     import torch
     from . import dtr
     lat = gauge.lat
     z = dtr.gen_noise(lat, 0, 1, 16 if nrhs <= 16 else 512, False, 0, nrhs)
-    p = dtr.solve_params(tol=1e-10, solver="mixed_f32", graph=graph, grid=grid)
+    p = dtr.solve_params(tol=1e-10, solver=solver, graph=graph, grid=grid, inner_tol=inner_tol)
     dtr.solve_batch(gauge, m0, z, params=p)
     dtr.profile_persistent(1)
     torch.cuda.synchronize()
@@ -84,8 +86,12 @@ def solve_case(gauge, dims, nrhs, reps, m0, graph=True, grid=0):
     dt = (time.perf_counter() - t0) / reps
     prof = dtr.profile_persistent(0)
     its = float(np.mean([s["iterations"] for s in st]))
-    return {"kernel": "mixed solve", "lattice": list(dims), "nrhs": nrhs, "graph": graph, "ms_per_solve": dt * 1e3,
-            "iterations_per_rhs": its, "persistent_launches": prof["launches"],
+    return {"kernel": "solve", "solver": solver, "inner_tol": inner_tol, "lattice": list(dims), "nrhs": nrhs,
+            "graph": graph, "ms_per_solve": dt * 1e3, "rhs_per_s": nrhs / dt,
+            "iterations_per_rhs": its, "cycles_max": int(max(s["restarts"] for s in st)),
+            "max_true_residual": float(max(s["true_residual"] for s in st)),
+            "all_converged": bool(all(s["converged"] for s in st)),
+            "persistent_launches": prof["launches"],
             "persistent_ms_per_launch": prof["ms"] / max(prof["launches"], 1)}
 
 
@@ -125,6 +131,10 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--m0", type=float, default=-0.6)
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--solver", default="mixed_f32", help="solve: comma list of f64, mixed_f32, mixed_f16, mixed_bf16")
+    ap.add_argument("--inner-tol", type=float, default=1e-5)
+    ap.add_argument("--eps", type=float, default=0.7)
+    ap.add_argument("--gauge-seed", type=int, default=1001)
     a = ap.parse_args(argv)
     import torch
     torch.cuda.set_device(0)
@@ -141,9 +151,11 @@ def main(argv=None):
     lat = dtr.make_lattice(dims)
     if a.what == "solve":
         from . import synth
-        g = dtr.make_gauge(lat, synth.random_su3_links(dims, 0.7, 1001))
-        for n in a.nrhs.split(","):
-            print(json.dumps(solve_case(g, dims, int(n), a.reps, a.m0, graph=not a.no_graph)), flush=True)
+        g = dtr.make_gauge(lat, synth.random_su3_links(dims, a.eps, a.gauge_seed))
+        for solver in a.solver.split(","):
+            for n in a.nrhs.split(","):
+                print(json.dumps(solve_case(g, dims, int(n), a.reps, a.m0, graph=not a.no_graph, solver=solver,
+                                            inner_tol=a.inner_tol)), flush=True)
         return
     g = dtr.make_gauge(lat, tiled_links(dims))
     for prec in a.prec.split(","):
