@@ -58,6 +58,15 @@ __global__ void k_to_bf16(const double2 *__restrict__ a, __nv_bfloat162 *__restr
     b[i] = __floats2bfloat162_rn((float)a[i].x, (float)a[i].y);
 }
 
+// FP64 links as FP32 hi + lo pairs (hi = nearest FP32, lo = nearest FP32 to the remainder)
+__global__ void k_split_links(const double2 *__restrict__ a, float4 *__restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = a[i];
+    const float hx = (float)v.x, hy = (float)v.y;
+    b[i] = make_float4(hx, (float)(v.x - (double)hx), hy, (float)(v.y - (double)hy));
+  }
+}
+
 __global__ void k_to_f32(const double2 *__restrict__ a, float2 *__restrict__ b, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = make_float2((float)a[i].x, (float)a[i].y);
@@ -187,14 +196,17 @@ int dtr_make_gauge(dtr_lattice lat, const double *links_host, dtr_gauge *out) {
   g->U32 = nullptr;
   g->Ubf16 = nullptr;
   g->Uf16 = nullptr;
+  g->Udf = nullptr;
   const int64_t n = lat->V * 4 * 9;
   cudaError_t e = cudaMalloc((void **)&g->U64, n * sizeof(double2));
   if (e == cudaSuccess) e = cudaMalloc((void **)&g->U32, n * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&g->Udf, n * sizeof(float4));
   if (e == cudaSuccess) e = cudaMalloc(&g->Ubf16, half_links_bytes(lat->V));
   if (e == cudaSuccess) e = cudaMalloc(&g->Uf16, half_links_bytes(lat->V));
   if (e == cudaSuccess) e = cudaMemcpy(g->U64, links_host, n * sizeof(double2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
     k_to_f32<<<grid1d(n), 256>>>(g->U64, g->U32, n); count_launches(1);
+    k_split_links<<<grid1d(n), 256>>>(g->U64, (float4 *)g->Udf, n); count_launches(1);
     launch_pack_links_half(g->U64, g->Ubf16, lat->V, 1, 0);
     launch_pack_links_half(g->U64, g->Uf16, lat->V, 0, 0);
     e = cudaGetLastError();
@@ -205,6 +217,7 @@ int dtr_make_gauge(dtr_lattice lat, const double *links_host, dtr_gauge *out) {
     cudaFree(g->U32);
     cudaFree(g->Ubf16);
     cudaFree(g->Uf16);
+    cudaFree(g->Udf);
     delete g;
     return cuda_fail(e, "gauge upload");
   }
@@ -224,6 +237,7 @@ void dtr_destroy_gauge(dtr_gauge g) {
   cudaFree(g->U32);
   cudaFree(g->Ubf16);
   cudaFree(g->Uf16);
+  cudaFree(g->Udf);
   delete g;
 }
 

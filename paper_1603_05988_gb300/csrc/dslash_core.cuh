@@ -180,6 +180,13 @@ __device__ __forceinline__ void hop_dir(const typename cplx_t<R>::type *__restri
   }
 }
 
+template <typename C, typename R> __device__ __forceinline__ C mk_r(R re, R im) {
+  C c;
+  c.x = re;
+  c.y = im;
+  return c;
+}
+
 // out[c] (c = 3*spin + colour) = (A psi)(s) for right-hand side j; self = psi(s).
 template <int SGN, typename R, class LD>
 __device__ __forceinline__ void dslash_site_ld(const typename cplx_t<R>::type *__restrict__ U, const LD &in,
@@ -210,9 +217,9 @@ __device__ __forceinline__ void dslash_site_ld(const typename cplx_t<R>::type *_
     for (int a = 0; a < 3; ++a) {
       const C su = Su[r][a], sl = Sl[r][a];
       const C pu = self[r * 3 + a], pl = self[(r + 2) * 3 + a];
-      out[r * 3 + a] = mk<C>(diag * pu.x - half * su.x, diag * pu.y - half * su.y);
-      out[(r + 2) * 3 + a] = SGN > 0 ? mk<C>(diag * pl.x + half * sl.x, diag * pl.y + half * sl.y)
-                                     : mk<C>(diag * pl.x - half * sl.x, diag * pl.y - half * sl.y);
+      out[r * 3 + a] = mk_r<C, R>(diag * pu.x - half * su.x, diag * pu.y - half * su.y);
+      out[(r + 2) * 3 + a] = SGN > 0 ? mk_r<C, R>(diag * pl.x + half * sl.x, diag * pl.y + half * sl.y)
+                                     : mk_r<C, R>(diag * pl.x - half * sl.x, diag * pl.y - half * sl.y);
     }
 }
 

@@ -133,6 +133,8 @@ struct dtr_gauge_s {
   void *Ubf16;    // BF16 links of the half-precision stencil, AoSoA over sites: three stored rows
                   // (36 complex per site) or two (24), see half_link_rows()
   void *Uf16;     // same, FP16
+  void *Udf;      // [site][mu][3][3] FP64 links split into FP32 hi + lo (16 B per complex: Re hi, Re lo,
+                  // Im hi, Im lo) for the double-float residual update of the mixed solvers
 };
 
 struct dtr_defl_s {

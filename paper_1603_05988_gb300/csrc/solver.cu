@@ -10,11 +10,13 @@
 // last block of the reducing kernel, so the host only polls a device-side
 // active-column count every `check_every` iterations.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <type_traits>
 #include <mutex>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "dslash_core.cuh"
 #include "reduce.cuh"
 #include "solver.cuh"
@@ -106,6 +108,66 @@ __global__ void __launch_bounds__(kBlock) k_resid_zero(const double2 *__restrict
     __syncthreads();
     if (threadIdx.x == 0) count_active(sc, b);
   }
+}
+
+// Residual after a defect-correction cycle without an FP64 stencil: the cycle added
+// e / (hs * scale) to x (k_mixed_accum), so r -= A e / (hs * scale), with A e
+// evaluated in double-float arithmetic (links split into FP32 hi + lo, e exact in
+// FP32): relative error ~2^-46 of |A| |e|, so r stays the true residual of x to
+// ~1e-14 kappa |z| over all cycles.  tot = (||r||^2, ||z||^2 as stored).  An FP64
+// residual (k_resid) confirms convergence before the solve reports it.
+__global__ void __launch_bounds__(kBlock) k_resid_update(const cdf *__restrict__ Udf, const float2 *__restrict__ e,
+                                                         double2 *__restrict__ r, Geom g, int b, int logb, dff diag,
+                                                         double hs, Scal *sc, Reduce red) {
+  __shared__ double2 tot[64];
+  double2 acc[1] = {make_double2(0.0, 0.0)};
+  const int64_t n = (int64_t)g.V << logb;
+  const int j = threadIdx.x & (b - 1);
+  const double inv = sc->active[j] ? 1.0 / (sc->scale[j] * hs) : 0.0;
+  const F32AsDf ld{e};
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n; it += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(it >> logb);
+    const int64_t base = (int64_t)s * 12 * b + j;
+    if (inv != 0.0) {
+      cdf o[12], self[12];
+      dslash_site_ld<1, dff>(Udf, ld, g, b, s, j, diag, o, self);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        double2 rr = r[base + c * b];
+        rr.x = fma(-inv, (double)o[c].x.hi + (double)o[c].x.lo, rr.x);
+        rr.y = fma(-inv, (double)o[c].y.hi + (double)o[c].y.lo, rr.y);
+        r[base + c * b] = rr;
+        acc[0].x += rr.x * rr.x + rr.y * rr.y;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        const double2 rr = r[base + c * b];
+        acc[0].x += rr.x * rr.x + rr.y * rr.y;
+      }
+    }
+  }
+  if (block_reduce<1>(acc, b, red.partial, red.counter, tot)) {
+    if (threadIdx.x < b) fin_resid(sc, threadIdx.x, make_double2(tot[threadIdx.x].x, sc->bnorm2[threadIdx.x]), 1);
+    __syncthreads();
+    if (threadIdx.x == 0) count_active(sc, b);
+  }
+}
+
+// The double-float residual update is on unless DTR_RESID_UPDATE=0 (every cycle then
+// ends with the FP64 residual).
+static bool resid_update_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = getenv("DTR_RESID_UPDATE");
+    v = (e && e[0] == '0') ? 0 : 1;
+  }
+  return v != 0;
+}
+
+static dff split_df(double v) {
+  const float h = (float)v;
+  return dff(h, (float)(v - (double)h));
 }
 
 // v = A p; sigma = rhat^H v -> alpha
@@ -420,8 +482,10 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, const Scal *__restrict
                             unsigned int max_cycles, int first, unsigned long long *dev_launches,
                             unsigned int body_kernels) {
   if (threadIdx.x == 0) {
-    if (first) {
+    if (first == 1) {
       gs->cycles = 0;
+    } else if (first == 2) {
+      // entry of the FP64-residual loop after the verification: cycles keep counting
     } else {
       gs->cycles += 1;
       if (dev_launches) atomicAdd(dev_launches, (unsigned long long)body_kernels);
@@ -451,6 +515,7 @@ struct MixedState {
   int maxiter, grid;
   int store;  // inner Krylov vectors: 0 FP32, 1 FP16, 2 BF16
   double hs;  // inner right-hand-side scale (see k_mixed_init)
+  int upd;    // cycles end with the double-float residual update (then one FP64 verification)
 };
 
 // inner iterations of one defect-correction cycle on the caller-initialised state
@@ -516,7 +581,7 @@ struct GraphKey {
   int L[4];
   double m0;
   const void *x, *z, *work;
-  int b, x_is_zero, maxiter, grid, prof, store;
+  int b, x_is_zero, maxiter, grid, prof, store, upd, pad2;
   double tol, itol;
 };
 
@@ -602,13 +667,47 @@ int capture_mixed_graph(const MixedState &S, int x_is_zero, double tol2, int max
   rc = enqueue_inner(S, cs2, &kin);
   if (rc) return bail(rc);
   k_mixed_accum<<<S.gv, kBlock, 0, cs2>>>(S.x, S.K.x, n, S.b, S.outer, S.inner, S.hs);
-  k_resid<double, 0><<<S.gd, kBlock, 0, cs2>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
-                                               4.0 + S.m0, S.outer, S.red, 1);
+  if (S.upd)
+    k_resid_update<<<S.gd, kBlock, 0, cs2>>>((const cdf *)S.gauge->Udf, S.K.x, S.r64, S.g, S.b, S.logb,
+                                             split_df(4.0 + S.m0), S.hs, S.outer, S.red);
+  else
+    k_resid<double, 0><<<S.gd, kBlock, 0, cs2>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
+                                                 4.0 + S.m0, S.outer, S.red, 1);
   k_loop_cond<<<1, 32, 0, cs2>>>(h, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 0, devcnt, (unsigned)(kin + 3));
   CAP_CHECK(cudaGetLastError());
   cudaGraph_t tmp = nullptr;
   CAP_CHECK(cudaStreamEndCapture(cs2, &tmp));
   open = 1;
+  if (S.upd) {
+    // verification: the FP64 residual of x decides; columns it finds short of tol
+    // continue in a second loop whose cycles end with the FP64 residual
+    k_resid<double, 0><<<S.gd, kBlock, 0, cs>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
+                                                4.0 + S.m0, S.outer, S.red, 1);
+    cudaGraphConditionalHandle h2;
+    CAP_CHECK(cudaGraphConditionalHandleCreate(&h2, graph, 0, 0));
+    k_loop_cond<<<1, 32, 0, cs>>>(h2, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 2, devcnt, 0);
+    CAP_CHECK(cudaGetLastError());
+    CAP_CHECK(cudaStreamGetCaptureInfo(cs, &stc, nullptr, &capg, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp2 = {cudaGraphNodeTypeConditional};
+    cp2.conditional.handle = h2;
+    cp2.conditional.type = cudaGraphCondTypeWhile;
+    cp2.conditional.size = 1;
+    cudaGraphNode_t cnode2;
+    CAP_CHECK(cudaGraphAddNode(&cnode2, capg, deps, nullptr, nd, &cp2));
+    cudaGraph_t body2 = cp2.conditional.phGraph_out[0];
+    CAP_CHECK(cudaStreamUpdateCaptureDependencies(cs, &cnode2, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CAP_CHECK(cudaStreamBeginCaptureToGraph(cs2, body2, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    open = 2;
+    rc = enqueue_inner(S, cs2, &kin);
+    if (rc) return bail(rc);
+    k_mixed_accum<<<S.gv, kBlock, 0, cs2>>>(S.x, S.K.x, n, S.b, S.outer, S.inner, S.hs);
+    k_resid<double, 0><<<S.gd, kBlock, 0, cs2>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
+                                                 4.0 + S.m0, S.outer, S.red, 1);
+    k_loop_cond<<<1, 32, 0, cs2>>>(h2, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 0, devcnt, (unsigned)(kin + 3));
+    CAP_CHECK(cudaGetLastError());
+    CAP_CHECK(cudaStreamEndCapture(cs2, &tmp));
+    open = 1;
+  }
   CAP_CHECK(cudaStreamEndCapture(cs, &tmp));
   open = 0;
 #undef CAP_CHECK
@@ -655,6 +754,7 @@ static int solve_mixed_graph(const MixedState &S, int x_is_zero, double tol2, in
   key.tol = tol2;
   key.itol = S.itol;
   key.store = S.store;
+  key.upd = S.upd;
   std::lock_guard<std::mutex> lock(g_graph_mu);
   GraphEntry *hit = nullptr;
   for (auto &e : g_graphs)
@@ -683,7 +783,9 @@ static int solve_mixed_graph(const MixedState &S, int x_is_zero, double tol2, in
   }
   hit->last_use = ++g_graph_tick;
   DTR_CUDA(cudaGraphLaunch(hit->exec, st));
-  count_launches(3);  // k_scal_init, first residual, k_loop_cond (the body counts itself on the device)
+  // k_scal_init, first residual, k_loop_cond (+ FP64 verification and its k_loop_cond);
+  // the loop bodies count themselves on the device
+  count_launches(S.upd ? 5 : 3);
   ++g_graph_launches;
   return DTR_OK;
 }
@@ -751,6 +853,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     S.grid = p->grid;
     S.store = store;
     S.hs = hs;
+    S.upd = resid_update_enabled() ? 1 : 0;
     *scal_out = outer;
     int rc = solve_mixed_graph(S, x_is_zero, p->tol * p->tol, p->maxiter, work, st);
     if (rc) return rc;
@@ -810,10 +913,18 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     const size_t fg_bytes = p->solver == DTR_SOLVER_FGMRES_NET ? fgmres_scratch_bytes(g.V, b, p->gmres_m) : 0;
     bool fgmres = p->solver == DTR_SOLVER_FGMRES_NET;
     std::vector<double> prev_rel(64, -1.0);
+    // cycles end with the double-float residual update until it reports convergence;
+    // the FP64 residual then verifies, and any further cycles end with the FP64
+    // residual (the same kernel sequence as the graph-driven loop)
+    bool fp64_resid = !resid_update_enabled();
     for (int cycle = 0; cycle <= kMaxRestarts; ++cycle) {
       const int restart = cycle < kMaxRestarts;
+      const bool update = cycle > 0 && !fp64_resid;
       if (cycle == 0 && x_is_zero)
         k_resid_zero<<<gv, kBlock, 0, st>>>(z, r64, n, b, outer, red);
+      else if (update)
+        k_resid_update<<<gd, kBlock, 0, st>>>((const cdf *)gauge->Udf, K.x, r64, g, b, logb, split_df(4.0 + m0), hs,
+                                              outer, red);
       else
         k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0,
                                                    outer, red, restart);
@@ -822,6 +933,15 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
       int n_active = 0;
       int rc = read_n_active(outer, st, &n_active);
       if (rc) return rc;
+      if (n_active == 0 && update) {  // verify in FP64
+        k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0,
+                                                   outer, red, restart);
+        count_launches(1);
+        DTR_LAUNCH_CHECK("FP64 verification residual");
+        fp64_resid = true;
+        rc = read_n_active(outer, st, &n_active);
+        if (rc) return rc;
+      }
       if (n_active == 0) break;
       mixed_init(store, r64, K, n, b, outer, hs, gv, st);
       k_mixed_scal_init<<<1, 64, 0, st>>>(outer, inner, b, itol * itol, p->maxiter, hs * hs); count_launches(1);
