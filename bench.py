@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--eig-iters", type=int, default=150,
                     help="cap on setup eigensolver iterations (deflation-space quality; untimed)")
     ap.add_argument("--skip-hbm", action="store_true", help="skip the 32^3x64 half-precision stencil measurement")
-    ap.add_argument("--cpu-sample-rhs", type=int, default=1, help="RHS in the CPU-oracle baseline sample")
+    ap.add_argument("--cpu-sample-rhs", type=int, default=16,
+                    help="RHS in the CPU-oracle baseline sample (16: about 13 s of one Grace core)")
     ap.add_argument("--lanes", type=int, default=0, help="z0 runs in flight per step (0 = autotune)")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven solver cycles instead of the CUDA graph (same kernels and results; lets a "
@@ -394,7 +395,7 @@ def main():
     # CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1:
-        r = cpu_oracle_sample(args.cpu_sample_rhs, 2)
+        r = cpu_oracle_sample(args.cpu_sample_rhs, 1)
         tcpu = r["times"][-1]
         cpu = {"value": args.cpu_sample_rhs / tcpu, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d RHS of the 8^4 workload: CGNR to 1e-10 (%d iters) + deflation quadrature, "

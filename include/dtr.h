@@ -68,7 +68,15 @@ typedef struct dtr_defl_s *dtr_defl;
 typedef struct dtr_net_s *dtr_net;
 
 /* Storage precision of a field or of the deflation space. */
-typedef enum { DTR_F64 = 0, DTR_F32 = 1, DTR_BF16 = 2, DTR_F16 = 3 } dtr_prec;
+typedef enum {
+  DTR_F64 = 0,
+  DTR_F32 = 1,
+  DTR_BF16 = 2,
+  DTR_F16 = 3,
+  DTR_DF32 = 4  /* dtr_dslash only: input rounded to FP32, arithmetic in double-float (pairs of FP32
+                   numbers with exact products and sums, ~2^-46 relative per operation) on links split
+                   into FP32 hi + lo: the stencil of the mixed solvers' outer-residual update */
+} dtr_prec;
 
 /* Krylov solver for A y = z (Algorithm 1, line 7; the paper does not name one). */
 typedef enum {

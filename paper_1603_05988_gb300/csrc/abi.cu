@@ -251,8 +251,9 @@ int dtr_dslash(dtr_gauge g, double m0, const double *in, double *out, int nrhs, 
                void *work, size_t work_bytes, void *stream) {
   if (!g || !in || !out || !work) return fail(DTR_EINVAL, "null argument");
   if (nrhs < 1 || nrhs > 64) return fail(DTR_EINVAL, "nrhs must be in [1, 64]");
-  if (prec != DTR_F64 && prec != DTR_F32 && prec != DTR_BF16 && prec != DTR_F16)
+  if (prec != DTR_F64 && prec != DTR_F32 && prec != DTR_BF16 && prec != DTR_F16 && prec != DTR_DF32)
     return fail(DTR_EINVAL, "unknown dslash precision");
+  if (prec == DTR_DF32 && dagger) return fail(DTR_EINVAL, "double-float dslash supports dagger = 0 only");
   if ((prec == DTR_BF16 || prec == DTR_F16) && dagger)
     return fail(DTR_EINVAL, "half-precision storage dslash supports dagger = 0 only");
   if ((prec == DTR_BF16 || prec == DTR_F16) && g->lat.V * nrhs * 3 >= (1LL << 31))
@@ -267,6 +268,12 @@ int dtr_dslash(dtr_gauge g, double m0, const double *in, double *out, int nrhs, 
     const int bf = prec == DTR_BF16;
     launch_dslash_half_canon(bf ? g->Ubf16 : g->Uf16, (const double2 *)in, (double2 *)out, w, geo, nrhs, nrhs, m0,
                              bf, st);
+  } else if (prec == DTR_DF32) {
+    float2 *a = (float2 *)w;
+    double2 *o = (double2 *)(w + vb);
+    launch_pack<float>((const double2 *)in, a, g->lat.V, nrhs, b, st);
+    launch_dslash_df(g->Udf, a, o, geo, b, m0, st);
+    launch_unpack<double>(o, (double2 *)out, g->lat.V, nrhs, b, st);
   } else if (prec == DTR_F64) {
     double2 *a = (double2 *)w, *o = (double2 *)(w + vb);
     launch_pack<double>((const double2 *)in, a, g->lat.V, nrhs, b, st);

@@ -185,6 +185,9 @@ void launch_unpack(const typename cplx_t<R>::type *internal, double2 *canon, int
 template <typename R>
 void launch_dslash(const typename cplx_t<R>::type *U, const typename cplx_t<R>::type *in,
                    typename cplx_t<R>::type *out, const Geom &g, int b, double m0, int dagger, cudaStream_t st);
+// out = A in on the internal layout, in FP32, arithmetic in double-float on the split links Udf
+void launch_dslash_df(const void *Udf, const float2 *in, double2 *out, const Geom &g, int b, double m0,
+                      cudaStream_t st);
 
 // half-precision-storage stencil (dslash_half.cu)
 size_t half_links_bytes(int64_t V);

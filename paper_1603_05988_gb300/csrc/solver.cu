@@ -154,20 +154,48 @@ __global__ void __launch_bounds__(kBlock) k_resid_update(const cdf *__restrict__
   }
 }
 
-// The double-float residual update is on unless DTR_RESID_UPDATE=0 (every cycle then
-// ends with the FP64 residual).
-static bool resid_update_enabled() {
-  static int v = -1;
-  if (v < 0) {
+// Whether cycles end with the double-float residual update.  It replaces one FP64
+// residual per cycle but costs about half of one, so it pays when a solve runs more
+// than two cycles: by default on for the half-storage inner solves (store != 0), off
+// for the FP32 one; DTR_RESID_UPDATE=1 turns it on for every mixed solver, =0 off.
+static bool resid_update_enabled(int store) {
+  static int v = -2;
+  if (v == -2) {
     const char *e = getenv("DTR_RESID_UPDATE");
-    v = (e && e[0] == '0') ? 0 : 1;
+    v = (e && e[0] == '0') ? 0 : (e && e[0] == '1') ? 1 : -1;
   }
-  return v != 0;
+  return v == 1 || (v == -1 && store != 0);
 }
 
 static dff split_df(double v) {
   const float h = (float)v;
   return dff(h, (float)(v - (double)h));
+}
+
+__global__ void __launch_bounds__(kBlock) k_dslash_df(const cdf *__restrict__ Udf, const float2 *__restrict__ in,
+                                                      double2 *__restrict__ out, Geom g, int b, int logb, dff diag) {
+  const int64_t n = (int64_t)g.V << logb;
+  const int j = threadIdx.x & (b - 1);
+  const F32AsDf ld{in};
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n; it += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(it >> logb);
+    const int64_t base = (int64_t)s * 12 * b + j;
+    cdf o[12], self[12];
+    dslash_site_ld<1, dff>(Udf, ld, g, b, s, j, diag, o, self);
+#pragma unroll
+    for (int c = 0; c < 12; ++c)
+      out[base + c * b] = make_double2((double)o[c].x.hi + (double)o[c].x.lo, (double)o[c].y.hi + (double)o[c].y.lo);
+  }
+}
+
+void launch_dslash_df(const void *Udf, const float2 *in, double2 *out, const Geom &g, int b, double m0,
+                      cudaStream_t st) {
+  const int64_t n = (int64_t)g.V * b;
+  int logb = 0;
+  while ((1 << logb) < b) ++logb;
+  k_dslash_df<<<reduce_grid(n, device_sms()), kBlock, 0, st>>>((const cdf *)Udf, in, out, g, b, logb,
+                                                               split_df(4.0 + m0));
+  count_launches(1);
 }
 
 // v = A p; sigma = rhat^H v -> alpha
@@ -853,7 +881,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     S.grid = p->grid;
     S.store = store;
     S.hs = hs;
-    S.upd = resid_update_enabled() ? 1 : 0;
+    S.upd = resid_update_enabled(store) ? 1 : 0;
     *scal_out = outer;
     int rc = solve_mixed_graph(S, x_is_zero, p->tol * p->tol, p->maxiter, work, st);
     if (rc) return rc;
@@ -916,7 +944,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     // cycles end with the double-float residual update until it reports convergence;
     // the FP64 residual then verifies, and any further cycles end with the FP64
     // residual (the same kernel sequence as the graph-driven loop)
-    bool fp64_resid = !resid_update_enabled();
+    bool fp64_resid = !resid_update_enabled(store);
     for (int cycle = 0; cycle <= kMaxRestarts; ++cycle) {
       const int restart = cycle < kMaxRestarts;
       const bool update = cycle > 0 && !fp64_resid;

@@ -24,9 +24,9 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 # ---------------------------------------------------------------- C structs
 DTR_OK, DTR_EINVAL, DTR_ENOMEM, DTR_ECUDA, DTR_ENOTCONV, DTR_ENAN, DTR_ETIMEOUT = range(7)
-DTR_F64, DTR_F32, DTR_BF16, DTR_F16 = range(4)
+DTR_F64, DTR_F32, DTR_BF16, DTR_F16, DTR_DF32 = range(5)
 SOLVER_F64, SOLVER_MIXED_F32, SOLVER_FGMRES_NET, SOLVER_MIXED_F16, SOLVER_MIXED_BF16 = 0, 1, 2, 3, 4
-_PREC = {"f64": DTR_F64, "f32": DTR_F32, "bf16": DTR_BF16, "f16": DTR_F16}
+_PREC = {"f64": DTR_F64, "f32": DTR_F32, "bf16": DTR_BF16, "f16": DTR_F16, "df32": DTR_DF32}
 _SOLVER = {"f64": SOLVER_F64, "mixed_f32": SOLVER_MIXED_F32, "fgmres_net": SOLVER_FGMRES_NET,
            "mixed_f16": SOLVER_MIXED_F16, "mixed_bf16": SOLVER_MIXED_BF16}
 
