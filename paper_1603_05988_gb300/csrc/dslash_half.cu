@@ -217,9 +217,10 @@ template <typename H, int MINB, int ROWS>
 __global__ void __launch_bounds__(256, MINB) k_dslash_half(const H *__restrict__ U, const H *__restrict__ in,
                                                            H *__restrict__ out, Geom g, int b, float diag) {
   const int n = g.V * b;
+  const int lb = (b & (b - 1)) == 0 ? __ffs(b) - 1 : -1;  // log2 b for a power-of-two width
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
-    const int j = it % b;
-    const int s = it / b;
+    const int j = lb >= 0 ? it & (b - 1) : it % b;
+    const int s = lb >= 0 ? it >> lb : it / b;
     int xc[4];
     site_coords(g, s, xc);
     const int str[4] = {1, g.L[0], g.L[0] * g.L[1], g.L[0] * g.L[1] * g.L[2]};

@@ -86,15 +86,22 @@ __host__ __device__ __forceinline__ float2 cmuli(float2 a) { return make_float2(
 struct Geom {
   int L[4];
   int V;
+  unsigned mg[3];  // division by L[0..2] as (umulhi(n, mg) + n) >> sh, exact for n < 2^31
+  int sh[3];       // (a runtime integer division costs ~20 instructions, this three)
 };
 
+__device__ __forceinline__ int div_by(int n, unsigned m, int sh) {
+  return (int)((__umulhi((unsigned)n, m) + (unsigned)n) >> sh);
+}
+
 __device__ __forceinline__ void site_coords(const Geom &g, int s, int c[4]) {
-  c[0] = s % g.L[0];
-  int r = s / g.L[0];
-  c[1] = r % g.L[1];
-  r /= g.L[1];
-  c[2] = r % g.L[2];
-  c[3] = r / g.L[2];
+  const int r0 = div_by(s, g.mg[0], g.sh[0]);
+  c[0] = s - r0 * g.L[0];
+  const int r1 = div_by(r0, g.mg[1], g.sh[1]);
+  c[1] = r0 - r1 * g.L[1];
+  const int r2 = div_by(r1, g.mg[2], g.sh[2]);
+  c[2] = r1 - r2 * g.L[2];
+  c[3] = r2;
 }
 __device__ __forceinline__ int site_of(const Geom &g, const int c[4]) {
   return c[0] + g.L[0] * (c[1] + g.L[1] * (c[2] + g.L[2] * c[3]));
@@ -151,9 +158,19 @@ struct dtr_defl_s {
 
 namespace dtr {
 
+// Multiplier and shift for exact unsigned division by d >= 1 of any n < 2^31 (division
+// by an invariant integer with an add step): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1.
+inline void div_magic(int d, unsigned *m, int *l) {
+  int k = 0;
+  while ((1LL << k) < d) ++k;
+  *l = k;
+  *m = (unsigned)((((1ULL << 32) * (unsigned long long)((1LL << k) - d)) / (unsigned long long)d) + 1ULL);
+}
+
 inline Geom geom_of(const dtr_lattice_s &l) {
   Geom g;
   for (int i = 0; i < 4; ++i) g.L[i] = l.dims[i];
+  for (int i = 0; i < 3; ++i) div_magic(g.L[i], &g.mg[i], &g.sh[i]);
   g.V = (int)l.V;
   return g;
 }
