@@ -47,6 +47,22 @@ def z0_codes(seed, run, N):
     return ((words[blk, w] >> sh) & np.uint64(3)).astype(np.uint8)
 
 
+def z0_codes_at(seed, run, idx):
+    """z0 codes at the listed dof indices only (the same counter-based stream as
+    z0_codes, evaluating just the 128-dof blocks that hold them): for fields too
+    large to draw whole."""
+    idx = np.asarray(idx, dtype=np.int64)
+    blocks, inv = np.unique(idx // 128, return_inverse=True)
+    ctr = np.zeros((len(blocks), 4), dtype=np.uint64)
+    ctr[:, 0] = blocks.astype(np.uint64)
+    ctr[:, 1] = np.uint64(run)
+    key = np.array([seed, 0], dtype=np.uint64)
+    words = _philox.philox4x64_10(ctr, key)
+    w = (idx % 128) // 32
+    sh = (2 * (idx % 32)).astype(np.uint64)
+    return ((words[inv, w] >> sh) & np.uint64(3)).astype(np.uint8)
+
+
 def z0_vector(seed, run, N):
     """z0 = exp(i*pi*q/2) written exactly as 1, i, -1, -i (Algorithm 1, line 3)."""
     return Z4_VALUES[z0_codes(seed, run, N)]

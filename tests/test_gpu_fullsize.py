@@ -96,3 +96,32 @@ def test_solve_and_trace_samples(dtr, big):
     zy = np.einsum("ij,ij->j", np.conj(Z), Y)
     t_ref = zy - deflation.quadrature_gamma5(Vs, lam, Z)
     assert np.abs(out["samples"][0] - t_ref).max() <= 1e-8 * np.abs(t_ref).max()
+
+
+def test_tensor_core_deflation_full_size(dtr, big):
+    """A block of 16 plain Z4 vectors (one per run) at the full lattice size takes
+    the tensor-core contraction (BF16 V); its per-sample deflation terms match the
+    oracle's gamma5 form for the same rounded V.  V is zero outside the 12 dofs
+    of the sites its columns touch, so the oracle evaluates the quadrature on
+    those rows only (exact, not a sample), with z0 drawn there by the same stream."""
+    c = big
+    if c["prec"] != "bf16":
+        pytest.skip("the tensor-core contraction serves BF16 deflation spaces")
+    k, R = c["k"], 16
+    lam = np.where(np.arange(k) % 2 == 0, 1.0, -1.0) * np.linspace(0.8, 1.5, k)
+    V = synth.disjoint_orthonormal(c["N"], k, 6)
+    D = dtr.defl_create(c["lat"], V, lam, prec="bf16")
+    sites = np.unique(np.nonzero(np.any(V != 0, axis=1))[0] // 12)
+    rows = (12 * sites[:, None] + np.arange(12)[None, :]).reshape(-1)
+    Vr = deflation.bf16_round(V[rows])
+    del V
+    p = dtr.trace_params(seed=5, n_z0=R, ncolors=1, nvec=1, block=R,
+                         solve=dtr.solve_params(tol=1e-10, solver="mixed_f32"))
+    n0 = dtr.tensor_core_contractions()
+    out = dtr.trace_estimate(c["g"], c["m0"], D, p, want_replay=True)
+    assert dtr.tensor_core_contractions() - n0 == 1
+    assert out["all_converged"]
+    Z = np.stack([noise.Z4_VALUES[noise.z0_codes_at(5, r, rows)] for r in range(R)], axis=1)
+    d_ref = deflation.quadrature_gamma5(Vr, lam, Z)
+    d_gpu = out["replay"][:, 0, :].sum(axis=1)
+    assert np.abs(d_gpu - d_ref).max() <= 2e-5 * np.abs(d_ref).max()

@@ -104,3 +104,12 @@ def test_probing_vector_structure():
     assert np.allclose(G, N * np.eye(16))
     Zd = noise.noise_vectors(dims, 3, 2, 2, True, 0, 24)
     assert np.count_nonzero(Zd) == N * 24 // 12
+
+
+@pytest.mark.parametrize("N,seed,run", [(3072, 0, 0), (49152, 2**63 + 5, 17), (1 << 20, 9, 3)])
+def test_z0_codes_at_matches_whole_field(N, seed, run):
+    """The restricted evaluation draws the same codes as the whole-field one at
+    any index set (including repeats, block edges and the last dof)."""
+    rng = np.random.default_rng(N)
+    idx = np.concatenate([rng.integers(0, N, size=500), [0, 127, 128, N - 1, N - 1, 31, 32]])
+    assert np.array_equal(noise.z0_codes_at(seed, run, idx), noise.z0_codes(seed, run, N)[idx])
