@@ -3,6 +3,8 @@
     python -m paper_1603_05988_gb300.kbench dslash --lattice 32,32,32,64 --prec bf16 --nrhs 1 --reps 20
     python -m paper_1603_05988_gb300.kbench solve --lattice 8,8,8,8 --nrhs 16 --reps 3 [--no-graph]
         [--solver f64,mixed_f32,mixed_f16,mixed_bf16] [--inner-tol T] [--eps E --gauge-seed S --m0 M]
+    python -m paper_1603_05988_gb300.kbench learned --lattice 16,16,16,32 --eval-lattice 24,24,24,48 \
+        --eps 0.8 --m0 -0.75 --gauge-seed 1002 --nrhs 8 [--steps 200 --batch 8 --pool 16]
     python -m paper_1603_05988_gb300.kbench deflate --lattice 16,16,16,32 --k 256 --prec bf16 --nrhs 16 --reps 20
 
 Large lattices take their links from the seeded 16^3x32 field repeated
@@ -95,6 +97,55 @@ def solve_case(gauge, dims, nrhs, reps, m0, graph=True, grid=0, solver="mixed_f3
             "persistent_ms_per_launch": prof["ms"] / max(prof["launches"], 1)}
 
 
+def learned_case(train_dims, eval_dims, eps, m0, seed, steps, batch, pool, nrhs, gmres_m=16):
+    """The learned preconditioner at the sizes of its workload: the network is
+    trained at train_dims on pool x batch (residual, error) pairs from the
+    library's own solves (residual loss, Adam, all on the GPU), then FGMRES(m)
+    with the trained network, FGMRES(m) without it and the mixed FP32 BiCGStab
+    solve held-out Z4 right-hand sides to 1e-10 at train_dims and at eval_dims
+    (the same weights: the network is a translation-invariant stencil)."""
+    import time
+    import torch
+    from . import dtr, learned, synth
+
+    def gauge_at(dims, gseed):
+        lat = dtr.make_lattice(dims)
+        return dtr.make_gauge(lat, synth.random_su3_links(dims, eps, gseed))
+
+    g = gauge_at(train_dims, seed)
+    net = dtr.Net(g.lat, act=0, init_scale=1.0 / (4.0 + m0), noise=1e-3, seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = learned.train(net, g, m0, steps=steps, batch=batch, lr=3e-4, pool=pool)
+    torch.cuda.synchronize()
+    out = {"kernel": "learned preconditioner", "train_lattice": list(train_dims), "eps": eps, "m0": m0,
+           "pairs": pool * batch, "steps": steps, "train_s": time.perf_counter() - t0,
+           "loss_first": float(np.mean(hist[:5])), "loss_last": float(np.mean(hist[-10:])), "eval": []}
+    W = net.weights()
+    for dims in (train_dims, eval_dims):
+        if tuple(dims) == tuple(train_dims):
+            gg, nn = g, net
+        else:
+            gg = gauge_at(dims, seed + 1)
+            nn = dtr.Net(gg.lat, act=0, weights=W)
+        z = torch.cat([dtr.gen_noise(gg.lat, 4242, k, 1, False, 0, 1) for k in range(nrhs)])
+        row = {"lattice": list(dims)}
+        for name, p in (("fgmres_plain", dtr.solve_params(tol=1e-10, solver="fgmres_net", net=None, gmres_m=gmres_m)),
+                        ("fgmres_learned", dtr.solve_params(tol=1e-10, solver="fgmres_net", net=nn, gmres_m=gmres_m)),
+                        ("bicgstab_mixed_f32", dtr.solve_params(tol=1e-10, solver="mixed_f32"))):
+            dtr.solve_batch(gg, m0, z, params=p, allow_notconv=True)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            y, st = dtr.solve_batch(gg, m0, z, params=p, allow_notconv=True)
+            torch.cuda.synchronize()
+            row[name] = {"ms": (time.perf_counter() - t1) * 1e3,
+                         "iterations_per_rhs": float(np.mean([s["iterations"] for s in st])),
+                         "converged": bool(all(s["converged"] for s in st)),
+                         "max_true_residual": float(max(s["true_residual"] for s in st))}
+        out["eval"].append(row)
+    return out
+
+
 def deflate_case(dims, k, nrhs, reps, prec="bf16"):
     """The deflation contraction C = V^H [Z, g5 Z] of an nrhs-column Z4 block with k
     vectors stored in `prec` (tensor cores for BF16).  Algorithmic work: V read once
@@ -123,7 +174,7 @@ def dtr_pad(n):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["dslash", "solve", "deflate"])
+    ap.add_argument("what", choices=["dslash", "solve", "deflate", "learned"])
     ap.add_argument("--k", type=int, default=256)
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--prec", default="bf16")
@@ -135,6 +186,10 @@ def main(argv=None):
     ap.add_argument("--inner-tol", type=float, default=1e-5)
     ap.add_argument("--eps", type=float, default=0.7)
     ap.add_argument("--gauge-seed", type=int, default=1001)
+    ap.add_argument("--eval-lattice", default="24,24,24,48", help="learned: evaluation lattice")
+    ap.add_argument("--steps", type=int, default=200, help="learned: Adam steps")
+    ap.add_argument("--batch", type=int, default=8, help="learned: pairs per step")
+    ap.add_argument("--pool", type=int, default=16, help="learned: batches of independent pairs")
     a = ap.parse_args(argv)
     import torch
     torch.cuda.set_device(0)
@@ -143,6 +198,11 @@ def main(argv=None):
         _b.build()
     from . import dtr
     dims = tuple(int(x) for x in a.lattice.split(","))
+    if a.what == "learned":
+        ev = tuple(int(v) for v in a.eval_lattice.split(","))
+        print(json.dumps(learned_case(dims, ev, a.eps, a.m0, a.gauge_seed, a.steps, a.batch, a.pool,
+                                      int(a.nrhs.split(",")[0]))), flush=True)
+        return
     if a.what == "deflate":
         for prec in a.prec.split(","):
             for n in a.nrhs.split(","):
