@@ -347,8 +347,10 @@ def main():
     share = grid / sms
     agg = prof["site_rhs_iterations"] * flop_per_unit / (total_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak * share, "unit": "TFLOP/s",
-            "frac": achieved / (fp32_peak * share), "traffic": None,
-            "kernel": "k_bicgstab_persistent<float,512> (FP32 inner solve, 16 RHS, 8^4, L2-resident)",
+            "frac": achieved / (fp32_peak * share), "traffic": 2.978e7,
+            "traffic_note": "DRAM read + write of one launch under ncu (26.47 + 3.32 MB), same kernel and problem "
+                            "(8^4, 16 RHS) on 152 CTAs: profiles/persistent_bicgstab_f32_8x8x8x8_b16.md",
+            "kernel": "k_bicgstab_persistent<float,512,0,float2> (FP32 inner solve, 16 RHS, 8^4, L2-resident)",
             "avg_launch_ms": pms, "launches": prof["launches"], "flops_per_launch": pflops,
             "ctas_per_launch": grid, "concurrent_launches": L,
             "peak_note": "FP32 peak = %d SMs x 128 lanes x 2 flop x 2.07 GHz (of nominal clocks) = %.1f TFLOP/s, "
@@ -372,7 +374,10 @@ def main():
         g_big = dtr.make_gauge(lat_big, kbench.tiled_links(dims_big))
         hb = kbench.dslash_case(g_big, dims_big, "bf16", 1, 30)
         roof_hbm = {"bound": "hbm", "achieved": hb["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                    "frac": hb["achieved_gbs"] / hbm_peak, "traffic": None,
+                    "frac": hb["achieved_gbs"] / hbm_peak,
+                    "traffic": 4.946e8 if hb["link_rows"] == 3 else None,
+                    "traffic_note": "DRAM read + write of one launch under ncu (407.4 + 87.2 MB): "
+                                    "profiles/dslash_half_bf16_32x32x32x64.md",
                     "kernel": "dslash BF16 storage, FP32 math, 1 RHS, 32^3x64",
                     "avg_launch_ms": hb["avg_launch_ms"], "alg_bytes_per_launch": hb["alg_bytes_per_launch"],
                     "alg_bytes_note": "240 B per site (48 + 48 B spinors, 144 B for four 3x3 BF16 links); the "
