@@ -11,20 +11,25 @@
 // and the same with columns 4j+2, 4j+3 for g5 z_j.
 //
 // A is MN-major in memory (r contiguous in a row of V), so the tensor memory
-// accelerator (TMA) moves it untouched: one thread issues, per stage of 64 dofs,
-// four 64 x 64 boxes with the 128-byte swizzle, which is the canonical MN-major
-// SWIZZLE_128B operand layout, several stages ahead of the MMAs.  B is built by
-// the threads from the FP64 probing values (loaded into registers one stage
-// ahead) in the K-major layout without swizzle.  Each CTA takes 256 rows r
+// accelerator (TMA) moves it untouched: per stage of 64 dofs, four 64 x 64 boxes
+// with the 128-byte swizzle, which is the canonical MN-major SWIZZLE_128B operand
+// layout.  B is built in the K-major layout without swizzle from the FP64 probing
+// values, with integer operations on their high words (exact for values BF16
+// holds; FP64 instructions are scarce on this GPU).  Each CTA takes 256 rows r
 // (128 complex m: two M = 128 MMAs per K step, two accumulators in tensor
-// memory) and one chunk of dofs (split K), one CTA per SM.  tcgen05.commit
-// signals a stage's mbarrier once its MMAs have read their operands; the
-// epilogue reads tensor memory with tcgen05.ld into FP64 partials, which are
-// combined into C and summed over chunks in a fixed order (deterministic).
+// memory) and one chunk of dofs (split K), one CTA per SM, with warp roles: a
+// lane of warp 0 streams A through a 5-6 stage ring, a lane of warp 1 issues the
+// MMAs, warps 2-9 build B into two buffers from probing values loaded two
+// stages ahead; full/empty mbarriers order them (tcgen05.commit arrives on a
+// stage's empty barrier once its MMAs have read their operands).  The epilogue
+// reads tensor memory with tcgen05.ld into FP32 partials, which a warp per
+// output combines into C and sums over chunks in FP64 in a fixed order
+// (deterministic).
 //
-// Every wait is bounded: a copy or MMA that does not complete within the budget
-// sets an error word (the host returns DTR_ETIMEOUT); the CTA then waits once
-// more for what it has in flight, frees its tensor memory and leaves.
+// Every wait is bounded: a role whose wait exceeds the budget sets a shared
+// abort flag that ends the other roles' waits and an error word (the host
+// returns DTR_ETIMEOUT); the CTA then waits once more for what it has in
+// flight, frees its tensor memory and leaves.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <atomic>
