@@ -3,6 +3,8 @@
     python -m paper_1603_05988_gb300.kbench dslash --lattice 32,32,32,64 --prec bf16 --nrhs 1 --reps 20
     python -m paper_1603_05988_gb300.kbench solve --lattice 8,8,8,8 --nrhs 16 --reps 3 [--no-graph]
         [--solver f64,mixed_f32,mixed_f16,mixed_bf16] [--inner-tol T] [--eps E --gauge-seed S --m0 M]
+    python -m paper_1603_05988_gb300.kbench trace --lattice 16,16,16,32 --eps 0.8 --m0 -0.75 --gauge-seed 1002 \
+        --k 200 --prec f32 --ncolors 512 --nvec 512 --block 32 --solver f64,mixed_f32,mixed_f16,mixed_bf16
     python -m paper_1603_05988_gb300.kbench learned --lattice 16,16,16,32 --eval-lattice 24,24,24,48 \
         --eps 0.8 --m0 -0.75 --gauge-seed 1002 --nrhs 8 [--steps 200 --batch 8 --pool 16]
     python -m paper_1603_05988_gb300.kbench deflate --lattice 16,16,16,32 --k 256 --prec bf16 --nrhs 16 --reps 20
@@ -97,6 +99,39 @@ def solve_case(gauge, dims, nrhs, reps, m0, graph=True, grid=0, solver="mixed_f3
             "persistent_ms_per_launch": prof["ms"] / max(prof["launches"], 1)}
 
 
+def trace_case(dims, eps, m0, seed, k, defl_prec, ncolors, nvec, block, solvers):
+    """The whole estimator (noise + HP mask, deflation projection, batched solves
+    to 1e-10, reductions) for one z0 run of nvec probing vectors in blocks of
+    `block` columns, with a k-vector deflation space stored in defl_prec (columns
+    with disjoint supports: the projection's cost does not depend on the values);
+    wall-clock RHS/s per solver after one warm-up run."""
+    import time
+    import torch
+    from . import dtr, synth
+    lat = dtr.make_lattice(dims)
+    g = dtr.make_gauge(lat, synth.random_su3_links(dims, eps, seed))
+    V = synth.disjoint_orthonormal(lat.N, k, 4)
+    lam = np.where(np.arange(k) % 2 == 0, 1.0, -1.0) * np.linspace(0.8, 1.5, k)
+    D = dtr.defl_create(lat, V, lam, prec=defl_prec)
+    del V
+    rows = []
+    for solver in solvers:
+        sp = dtr.solve_params(tol=1e-10, solver=solver)
+        warm = dtr.trace_params(seed=0, z0_first=100, n_z0=1, ncolors=ncolors, nvec=nvec, block=block, solve=sp)
+        dtr.trace_estimate(g, m0, D, warm)
+        p = dtr.trace_params(seed=0, z0_first=0, n_z0=1, ncolors=ncolors, nvec=nvec, block=block, solve=sp)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = dtr.trace_estimate(g, m0, D, p)
+        dt = time.perf_counter() - t0
+        rows.append({"kernel": "trace estimate", "lattice": list(dims), "k": k, "defl_prec": defl_prec,
+                     "ncolors": ncolors, "nvec": nvec, "block": block, "solver": solver, "s": dt,
+                     "rhs_per_s": nvec / dt, "iterations_per_rhs": out["iterations"] / max(out["n_solves"], 1),
+                     "all_converged": bool(out["all_converged"]), "max_true_residual": out["max_true_residual"],
+                     "trace": [out["trace"].real, out["trace"].imag]})
+    return rows
+
+
 def learned_case(train_dims, eval_dims, eps, m0, seed, steps, batch, pool, nrhs, gmres_m=16):
     """The learned preconditioner at the sizes of its workload: the network is
     trained at train_dims on pool x batch (residual, error) pairs from the
@@ -174,7 +209,7 @@ def dtr_pad(n):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["dslash", "solve", "deflate", "learned"])
+    ap.add_argument("what", choices=["dslash", "solve", "deflate", "learned", "trace"])
     ap.add_argument("--k", type=int, default=256)
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--prec", default="bf16")
@@ -187,6 +222,9 @@ def main(argv=None):
     ap.add_argument("--eps", type=float, default=0.7)
     ap.add_argument("--gauge-seed", type=int, default=1001)
     ap.add_argument("--eval-lattice", default="24,24,24,48", help="learned: evaluation lattice")
+    ap.add_argument("--ncolors", type=int, default=512, help="trace: probing colours")
+    ap.add_argument("--nvec", type=int, default=512, help="trace: probing vectors of the z0 run")
+    ap.add_argument("--block", type=int, default=32, help="trace: right-hand sides per block")
     ap.add_argument("--steps", type=int, default=200, help="learned: Adam steps")
     ap.add_argument("--batch", type=int, default=8, help="learned: pairs per step")
     ap.add_argument("--pool", type=int, default=16, help="learned: batches of independent pairs")
@@ -198,6 +236,11 @@ def main(argv=None):
         _b.build()
     from . import dtr
     dims = tuple(int(x) for x in a.lattice.split(","))
+    if a.what == "trace":
+        for row in trace_case(dims, a.eps, a.m0, a.gauge_seed, a.k, a.prec, a.ncolors, a.nvec, a.block,
+                              a.solver.split(",")):
+            print(json.dumps(row), flush=True)
+        return
     if a.what == "learned":
         ev = tuple(int(v) for v in a.eval_lattice.split(","))
         print(json.dumps(learned_case(dims, ev, a.eps, a.m0, a.gauge_seed, a.steps, a.batch, a.pool,
