@@ -70,7 +70,8 @@ def dslash_case(gauge, dims, prec, nrhs, reps, m0=-0.75):
             "achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9, "achieved_tflops": flops / (ms * 1e-3) / 1e12}
 
 
-def solve_case(gauge, dims, nrhs, reps, m0, graph=True, grid=0, solver="mixed_f32", inner_tol=1e-5):
+def solve_case(gauge, dims, nrhs, reps, m0, graph=True, grid=0, solver="mixed_f32", inner_tol=1e-5,
+               engine="persistent"):
     """Solves of nrhs Z4 right-hand sides to 1e-10 (persistent engine), with the
     persistent launches timed on the device.  solver: f64, mixed_f32 (FP32 inner
     vectors), mixed_f16 / mixed_bf16 (half-storage inner vectors)."""
@@ -79,7 +80,7 @@ def solve_case(gauge, dims, nrhs, reps, m0, graph=True, grid=0, solver="mixed_f3
     from . import dtr
     lat = gauge.lat
     z = dtr.gen_noise(lat, 0, 1, 16 if nrhs <= 16 else 512, False, 0, nrhs)
-    p = dtr.solve_params(tol=1e-10, solver=solver, graph=graph, grid=grid, inner_tol=inner_tol)
+    p = dtr.solve_params(tol=1e-10, solver=solver, graph=graph, grid=grid, inner_tol=inner_tol, engine=engine)
     dtr.solve_batch(gauge, m0, z, params=p)
     dtr.profile_persistent(1)
     torch.cuda.synchronize()
@@ -90,7 +91,8 @@ def solve_case(gauge, dims, nrhs, reps, m0, graph=True, grid=0, solver="mixed_f3
     dt = (time.perf_counter() - t0) / reps
     prof = dtr.profile_persistent(0)
     its = float(np.mean([s["iterations"] for s in st]))
-    return {"kernel": "solve", "solver": solver, "inner_tol": inner_tol, "lattice": list(dims), "nrhs": nrhs,
+    return {"kernel": "solve", "solver": solver, "engine": engine, "inner_tol": inner_tol, "lattice": list(dims),
+            "nrhs": nrhs,
             "graph": graph, "ms_per_solve": dt * 1e3, "rhs_per_s": nrhs / dt,
             "iterations_per_rhs": its, "cycles_max": int(max(s["restarts"] for s in st)),
             "max_true_residual": float(max(s["true_residual"] for s in st)),
@@ -219,6 +221,8 @@ def main(argv=None):
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--solver", default="mixed_f32", help="solve: comma list of f64, mixed_f32, mixed_f16, mixed_bf16")
     ap.add_argument("--inner-tol", type=float, default=1e-5)
+    ap.add_argument("--engine", default="persistent", choices=["persistent", "kernels"],
+                    help="solve: one persistent launch per (inner) solve, or one kernel per BiCGStab step")
     ap.add_argument("--eps", type=float, default=0.7)
     ap.add_argument("--gauge-seed", type=int, default=1001)
     ap.add_argument("--eval-lattice", default="24,24,24,48", help="learned: evaluation lattice")
@@ -258,7 +262,7 @@ def main(argv=None):
         for solver in a.solver.split(","):
             for n in a.nrhs.split(","):
                 print(json.dumps(solve_case(g, dims, int(n), a.reps, a.m0, graph=not a.no_graph, solver=solver,
-                                            inner_tol=a.inner_tol)), flush=True)
+                                            inner_tol=a.inner_tol, engine=a.engine)), flush=True)
         return
     g = dtr.make_gauge(lat, tiled_links(dims))
     for prec in a.prec.split(","):
