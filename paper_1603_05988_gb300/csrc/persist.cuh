@@ -18,6 +18,8 @@ struct GridSync {
   unsigned long long t1;    // latest block exit (ns)
   int error;                // sticky: a barrier wait gave up
   unsigned int cycles;      // defect-correction cycles run by the graph-driven loop
+  int sel;                  // mixed solver: the next residual is the double-float update (1) or FP64 (0)
+  int last_upd;             // mixed solver: the last residual computed was the double-float update
 };
 constexpr size_t kGridSyncLaunchBytes = offsetof(GridSync, error);
 

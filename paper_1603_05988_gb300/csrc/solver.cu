@@ -60,9 +60,11 @@ __global__ void __launch_bounds__(kBlock) k_resid(const typename cplx_t<R>::type
                                                   typename cplx_t<R>::type *__restrict__ r,
                                                   typename cplx_t<R>::type *__restrict__ rhat,
                                                   typename cplx_t<R>::type *__restrict__ p, Geom g, int b, int logb,
-                                                  R diag, Scal *sc, Reduce red, int restart) {
+                                                  R diag, Scal *sc, Reduce red, int restart,
+                                                  const int *run_flag, int run_if, int *mark) {
   typedef typename cplx_t<R>::type C;
   __shared__ double2 tot[64];
+  if (run_flag && *(volatile const int *)run_flag != run_if) return;  // not selected (uniform over the grid)
   double2 acc[1] = {make_double2(0.0, 0.0)};
   const int64_t n = (int64_t)g.V << logb;
   const int j = threadIdx.x & (b - 1);
@@ -87,7 +89,10 @@ __global__ void __launch_bounds__(kBlock) k_resid(const typename cplx_t<R>::type
   if (block_reduce<1>(acc, b, red.partial, red.counter, tot)) {
     if (threadIdx.x < b) fin_resid(sc, threadIdx.x, tot[threadIdx.x], restart);
     __syncthreads();
-    if (threadIdx.x == 0) count_active(sc, b);
+    if (threadIdx.x == 0) {
+      count_active(sc, b);
+      if (mark) *mark = 0;
+    }
   }
 }
 
@@ -118,8 +123,10 @@ __global__ void __launch_bounds__(kBlock) k_resid_zero(const double2 *__restrict
 // residual (k_resid) confirms convergence before the solve reports it.
 __global__ void __launch_bounds__(kBlock) k_resid_update(const cdf *__restrict__ Udf, const float2 *__restrict__ e,
                                                          double2 *__restrict__ r, Geom g, int b, int logb, dff diag,
-                                                         double hs, Scal *sc, Reduce red) {
+                                                         double hs, Scal *sc, Reduce red, const int *run_flag,
+                                                         int run_if, int *mark) {
   __shared__ double2 tot[64];
+  if (run_flag && *(volatile const int *)run_flag != run_if) return;  // not selected (uniform over the grid)
   double2 acc[1] = {make_double2(0.0, 0.0)};
   const int64_t n = (int64_t)g.V << logb;
   const int j = threadIdx.x & (b - 1);
@@ -150,21 +157,25 @@ __global__ void __launch_bounds__(kBlock) k_resid_update(const cdf *__restrict__
   if (block_reduce<1>(acc, b, red.partial, red.counter, tot)) {
     if (threadIdx.x < b) fin_resid(sc, threadIdx.x, make_double2(tot[threadIdx.x].x, sc->bnorm2[threadIdx.x]), 1);
     __syncthreads();
-    if (threadIdx.x == 0) count_active(sc, b);
+    if (threadIdx.x == 0) {
+      count_active(sc, b);
+      if (mark) *mark = 1;
+    }
   }
 }
 
-// Whether cycles end with the double-float residual update.  It replaces one FP64
-// residual per cycle but costs about half of one, so it pays when a solve runs more
-// than two cycles: by default on for the half-storage inner solves (store != 0), off
-// for the FP32 one; DTR_RESID_UPDATE=1 turns it on for every mixed solver, =0 off.
-static bool resid_update_enabled(int store) {
-  static int v = -2;
-  if (v == -2) {
+// Whether cycles may end with the double-float residual update (costing about half an
+// FP64 residual): k_mixed_accum then takes it for cycles predicted to stay well above
+// tol and the FP64 residual for the cycle predicted to converge, which also certifies
+// the result, so a solve of c cycles runs c - 1 updates and one FP64 residual.  On
+// unless DTR_RESID_UPDATE=0 (every cycle ends with the FP64 residual).
+static bool resid_update_enabled(int /*store*/) {
+  static int v = -1;
+  if (v < 0) {
     const char *e = getenv("DTR_RESID_UPDATE");
-    v = (e && e[0] == '0') ? 0 : (e && e[0] == '1') ? 1 : -1;
+    v = (e && e[0] == '0') ? 0 : 1;
   }
-  return v == 1 || (v == -1 && store != 0);
+  return v != 0;
 }
 
 static dff split_df(double v) {
@@ -361,9 +372,22 @@ __global__ void k_mixed_scal_init(const Scal *__restrict__ outer, Scal *inner, i
 }
 
 // x64 += e / (hs * scale) for outer-active columns; fold inner iteration counts.
+// With gs: choose the residual that ends this cycle (gs->sel): the double-float
+// update if allowed and some active column is predicted (its last residual times the
+// inner solve's achieved reduction) to stay more than 10x above tol, else the FP64
+// residual, which then also certifies convergence.
 __global__ void __launch_bounds__(kBlock) k_mixed_accum(double2 *__restrict__ x, const float2 *__restrict__ e,
                                                         int64_t n, int b, Scal *outer, const Scal *__restrict__ inner,
-                                                        double hs) {
+                                                        double hs, GridSync *gs, int allow_update) {
+  if (gs && blockIdx.x == 0 && threadIdx.x == 0) {
+    int far = 0;
+    for (int q = 0; q < b; ++q) {
+      if (!outer->active[q]) continue;
+      const double red2 = inner->bnorm2[q] > 0.0 ? inner->rnorm2[q] / inner->bnorm2[q] : 1.0;
+      if (outer->rtrue2[q] * red2 > 100.0 * outer->tol2 * outer->bnorm2[q]) far = 1;
+    }
+    gs->sel = (allow_update && far) ? 1 : 0;
+  }
   const int j = threadIdx.x & (b - 1);
   const int act = outer->active[j];
   const double inv = act ? 1.0 / (outer->scale[j] * hs) : 0.0;
@@ -673,7 +697,7 @@ int capture_mixed_graph(const MixedState &S, int x_is_zero, double tol2, int max
     k_resid_zero<<<S.gv, kBlock, 0, cs>>>(S.z, S.r64, n, S.b, S.outer, S.red);
   else
     k_resid<double, 0><<<S.gd, kBlock, 0, cs>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
-                                                4.0 + S.m0, S.outer, S.red, 1);
+                                                4.0 + S.m0, S.outer, S.red, 1, nullptr, 0, &S.gs->last_upd);
   unsigned long long *devcnt = device_launch_counter();
   k_loop_cond<<<1, 32, 0, cs>>>(h, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 1, devcnt, 0);
   CAP_CHECK(cudaGetLastError());
@@ -695,23 +719,27 @@ int capture_mixed_graph(const MixedState &S, int x_is_zero, double tol2, int max
   int kin = 0;
   rc = enqueue_inner(S, cs2, &kin);
   if (rc) return bail(rc);
-  k_mixed_accum<<<S.gv, kBlock, 0, cs2>>>(S.x, S.K.x, n, S.b, S.outer, S.inner, S.hs);
-  if (S.upd)
+  k_mixed_accum<<<S.gv, kBlock, 0, cs2>>>(S.x, S.K.x, n, S.b, S.outer, S.inner, S.hs, S.gs, S.upd);
+  if (S.upd)  // one of the two runs, as k_mixed_accum chose
     k_resid_update<<<S.gd, kBlock, 0, cs2>>>((const cdf *)S.gauge->Udf, S.K.x, S.r64, S.g, S.b, S.logb,
-                                             split_df(4.0 + S.m0), S.hs, S.outer, S.red);
-  else
-    k_resid<double, 0><<<S.gd, kBlock, 0, cs2>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
-                                                 4.0 + S.m0, S.outer, S.red, 1);
-  k_loop_cond<<<1, 32, 0, cs2>>>(h, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 0, devcnt, (unsigned)(kin + 3));
+                                             split_df(4.0 + S.m0), S.hs, S.outer, S.red, &S.gs->sel, 1,
+                                             &S.gs->last_upd);
+  k_resid<double, 0><<<S.gd, kBlock, 0, cs2>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
+                                               4.0 + S.m0, S.outer, S.red, 1, S.upd ? &S.gs->sel : nullptr, 0,
+                                               &S.gs->last_upd);
+  k_loop_cond<<<1, 32, 0, cs2>>>(h, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 0, devcnt,
+                                 (unsigned)(kin + (S.upd ? 4 : 3)));
   CAP_CHECK(cudaGetLastError());
   cudaGraph_t tmp = nullptr;
   CAP_CHECK(cudaStreamEndCapture(cs2, &tmp));
   open = 1;
   if (S.upd) {
-    // verification: the FP64 residual of x decides; columns it finds short of tol
-    // continue in a second loop whose cycles end with the FP64 residual
+    // verification (when the loop ended on a double-float update): the FP64 residual
+    // of x decides; columns it finds short of tol continue in a second loop whose
+    // cycles end with the FP64 residual
     k_resid<double, 0><<<S.gd, kBlock, 0, cs>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
-                                                4.0 + S.m0, S.outer, S.red, 1);
+                                                4.0 + S.m0, S.outer, S.red, 1, &S.gs->last_upd, 1,
+                                                &S.gs->last_upd);
     cudaGraphConditionalHandle h2;
     CAP_CHECK(cudaGraphConditionalHandleCreate(&h2, graph, 0, 0));
     k_loop_cond<<<1, 32, 0, cs>>>(h2, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 2, devcnt, 0);
@@ -729,9 +757,9 @@ int capture_mixed_graph(const MixedState &S, int x_is_zero, double tol2, int max
     open = 2;
     rc = enqueue_inner(S, cs2, &kin);
     if (rc) return bail(rc);
-    k_mixed_accum<<<S.gv, kBlock, 0, cs2>>>(S.x, S.K.x, n, S.b, S.outer, S.inner, S.hs);
+    k_mixed_accum<<<S.gv, kBlock, 0, cs2>>>(S.x, S.K.x, n, S.b, S.outer, S.inner, S.hs, nullptr, 0);
     k_resid<double, 0><<<S.gd, kBlock, 0, cs2>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
-                                                 4.0 + S.m0, S.outer, S.red, 1);
+                                                 4.0 + S.m0, S.outer, S.red, 1, nullptr, 0, &S.gs->last_upd);
     k_loop_cond<<<1, 32, 0, cs2>>>(h2, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 0, devcnt, (unsigned)(kin + 3));
     CAP_CHECK(cudaGetLastError());
     CAP_CHECK(cudaStreamEndCapture(cs2, &tmp));
@@ -917,7 +945,7 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     }
     for (int cycle = 0; cycle <= kMaxRestarts; ++cycle) {
       k_resid<double, 1><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, K.r, K.rhat, K.p, g, b, logb, 4.0 + m0, outer, red,
-                                                 cycle < kMaxRestarts); count_launches(1);
+                                                 cycle < kMaxRestarts, nullptr, 0, nullptr); count_launches(1);
       DTR_LAUNCH_CHECK("residual");
       int n_active = 0;
       int rc = read_n_active(outer, st, &n_active);
@@ -942,32 +970,38 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     const size_t fg_bytes = p->solver == DTR_SOLVER_FGMRES_NET ? fgmres_scratch_bytes(g.V, b, p->gmres_m) : 0;
     bool fgmres = p->solver == DTR_SOLVER_FGMRES_NET;
     std::vector<double> prev_rel(64, -1.0);
-    // cycles end with the double-float residual update until it reports convergence;
-    // the FP64 residual then verifies, and any further cycles end with the FP64
-    // residual (the same kernel sequence as the graph-driven loop)
-    bool fp64_resid = !resid_update_enabled(store);
+    // phase 1: each cycle ends with the residual k_mixed_accum chose (the double-float
+    // update or the FP64 residual; the other kernel exits at entry); when no column is
+    // left active, an FP64 residual verifies unless the last one already was FP64;
+    // phase 2: any further cycles end with the FP64 residual (the same kernel
+    // sequence as the graph-driven loop)
+    bool upd_phase = resid_update_enabled(store);
     for (int cycle = 0; cycle <= kMaxRestarts; ++cycle) {
       const int restart = cycle < kMaxRestarts;
-      const bool update = cycle > 0 && !fp64_resid;
-      if (cycle == 0 && x_is_zero)
+      if (cycle == 0 && x_is_zero) {
         k_resid_zero<<<gv, kBlock, 0, st>>>(z, r64, n, b, outer, red);
-      else if (update)
+        count_launches(1);
+      } else if (cycle > 0 && upd_phase) {
         k_resid_update<<<gd, kBlock, 0, st>>>((const cdf *)gauge->Udf, K.x, r64, g, b, logb, split_df(4.0 + m0), hs,
-                                              outer, red);
-      else
+                                              outer, red, &gs->sel, 1, &gs->last_upd);
         k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0,
-                                                   outer, red, restart);
-      count_launches(1);
+                                                   outer, red, restart, &gs->sel, 0, &gs->last_upd);
+        count_launches(2);
+      } else {
+        k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0,
+                                                   outer, red, restart, nullptr, 0, &gs->last_upd);
+        count_launches(1);
+      }
       DTR_LAUNCH_CHECK("outer residual");
       int n_active = 0;
       int rc = read_n_active(outer, st, &n_active);
       if (rc) return rc;
-      if (n_active == 0 && update) {  // verify in FP64
+      if (n_active == 0 && cycle > 0 && upd_phase) {  // verify in FP64 if the last residual was the update
         k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0,
-                                                   outer, red, restart);
+                                                   outer, red, restart, &gs->last_upd, 1, &gs->last_upd);
         count_launches(1);
         DTR_LAUNCH_CHECK("FP64 verification residual");
-        fp64_resid = true;
+        upd_phase = false;
         rc = read_n_active(outer, st, &n_active);
         if (rc) return rc;
       }
@@ -1007,7 +1041,8 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
         rc = iterate<float>(gauge->U32, K, g, b, m0, inner, red, check, p->maxiter + check, st);
         if (rc) return rc;
       }
-      k_mixed_accum<<<gv, kBlock, 0, st>>>(x, K.x, n, b, outer, inner, hs); count_launches(1);
+      k_mixed_accum<<<gv, kBlock, 0, st>>>(x, K.x, n, b, outer, inner, hs, upd_phase ? gs : nullptr, upd_phase ? 1 : 0);
+      count_launches(1);
       DTR_LAUNCH_CHECK("defect accumulate");
     }
     if (persistent) return read_gs_error(gs, st);
