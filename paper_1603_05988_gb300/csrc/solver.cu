@@ -379,14 +379,15 @@ __global__ void k_mixed_scal_init(const Scal *__restrict__ outer, Scal *inner, i
 __global__ void __launch_bounds__(kBlock) k_mixed_accum(double2 *__restrict__ x, const float2 *__restrict__ e,
                                                         int64_t n, int b, Scal *outer, const Scal *__restrict__ inner,
                                                         double hs, GridSync *gs, int allow_update) {
-  if (gs && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (gs && blockIdx.x == 0) {  // one column per thread of block 0
+    const int q = threadIdx.x;
     int far = 0;
-    for (int q = 0; q < b; ++q) {
-      if (!outer->active[q]) continue;
+    if (q < b && outer->active[q]) {
       const double red2 = inner->bnorm2[q] > 0.0 ? inner->rnorm2[q] / inner->bnorm2[q] : 1.0;
-      if (outer->rtrue2[q] * red2 > 100.0 * outer->tol2 * outer->bnorm2[q]) far = 1;
+      far = outer->rtrue2[q] * red2 > 100.0 * outer->tol2 * outer->bnorm2[q];
     }
-    gs->sel = (allow_update && far) ? 1 : 0;
+    far = __syncthreads_or(far);
+    if (q == 0) gs->sel = (allow_update && far) ? 1 : 0;
   }
   const int j = threadIdx.x & (b - 1);
   const int act = outer->active[j];
