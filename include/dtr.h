@@ -408,10 +408,15 @@ int dtr_trace_estimate(dtr_gauge g, double m0, dtr_defl d, const dtr_trace_param
                        void *work, size_t work_bytes, dtr_trace_result *res, void *stream);
 
 /* Deflation contraction C = V^H [Z, gamma_5 Z] of the estimator's probing blocks (entries 0, +-1, +-i)
- * when V is stored in BF16: a BF16 GEMM on the tensor cores (tcgen05, FP32 accumulation in tensor
- * memory per chunk of dofs, FP64 across chunks).  dtr_time_deflate times it (CUDA events on `stream`,
- * average ms per contraction of an nrhs-column Z4 block, nrhs 1..64, reps >= 1; the FP64 CUDA-core
- * contraction for other storage precisions); its workspace is dtr_time_deflate_workspace_bytes.
+ * when V is stored in BF16 and k is a multiple of 4 (rows of V TMA-addressable): a BF16 GEMM on the
+ * tensor cores (tcgen05, A moved by TMA, FP32 accumulation in tensor memory per chunk of dofs, FP64
+ * across chunks in a fixed order).  dtr_trace_estimate uses it for every such block that is not a
+ * hierarchical-probing block of one z0 run (those take the per-colour addition pass).
+ * dtr_time_deflate times it: CUDA events on `stream`, average ms per contraction of an nrhs-column Z4
+ * block (nrhs 1..64, reps >= 1), after one warm-up; for other storage precisions it times the CUDA-core
+ * contraction.  work: device, at least dtr_time_deflate_workspace_bytes(d, nrhs) bytes, caller-owned.
+ * Returns DTR_EINVAL (bad arguments), DTR_ENOMEM (workspace too small), DTR_ETIMEOUT (a tensor-core
+ * stage wait gave up; the kernel returned without faulting) or DTR_ECUDA.  Synchronises `stream`.
  * dtr_tensor_core_contractions counts tensor-core contractions launched in this process. */
 size_t dtr_time_deflate_workspace_bytes(dtr_defl d, int nrhs);
 int dtr_time_deflate(dtr_defl d, int nrhs, int reps, void *work, size_t work_bytes, double *avg_ms, void *stream);
