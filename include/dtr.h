@@ -78,7 +78,7 @@ typedef enum {
                    into FP32 hi + lo: the stencil of the mixed solvers' outer-residual update */
 } dtr_prec;
 
-/* Krylov solver for A y = z (Algorithm 1, line 7; the paper does not name one). */
+/* Krylov solver for A y = z (the solve step of Algorithm 1; the paper does not name one). */
 typedef enum {
   DTR_SOLVER_BICGSTAB_F64 = 0,   /* plain FP64 BiCGStab */
   DTR_SOLVER_MIXED_F32 = 1,      /* FP32 BiCGStab inner solves inside FP64 defect correction */
@@ -150,7 +150,7 @@ void dtr_destroy_gauge(dtr_gauge g);
 /* ------------------------------------------------------------------- dslash */
 /* out = A in (dagger = 0) or out = A^H in (dagger = 1), for nrhs fields.
  * Operator definition above (the matrix of Algorithm 1; A^H is the product
- * of Algorithm 1, lines 2 and 8).  in, out: device, canonical N x nrhs
+ * of Algorithm 1's deflated part and deflation term).  in, out: device, canonical N x nrhs
  * complex128, must not overlap.  prec selects the arithmetic: DTR_F64;
  * DTR_F32 (fields rounded to FP32, FP32 math, result widened to FP64);
  * DTR_BF16 / DTR_F16 (half-precision storage of the fields and of the links,
@@ -178,7 +178,7 @@ int dtr_time_dslash(dtr_gauge g, double m0, int nrhs, dtr_prec prec, int reps, v
                     double *avg_ms, void *stream);
 
 /* -------------------------------------------------------------------- noise */
-/* Probing vectors z = z0 .* z_h (Algorithm 1, lines 3-6; Section 5.2).
+/* Probing vectors z = z0 .* z_h (Algorithm 1; Section 5.2).
  *   z0(i)  = i^q(i), q(i) in {0,1,2,3} the 2-bit code of dof i taken from
  *            Philox4x64-10 (Salmon et al., SC'11) with key {seed, 0} and
  *            counter {i / 128, z0_index, 0, 0}: output word (i % 128) / 32,
@@ -227,7 +227,7 @@ typedef struct {
  * inner_tol 1e-5, persistent engine. */
 void dtr_solve_params_default(dtr_solve_params *p);
 
-/* Solve A y = z for nrhs right-hand sides at once (Algorithm 1, line 7).
+/* Solve A y = z for nrhs right-hand sides at once (the solve step of Algorithm 1).
  * z: device, canonical N x nrhs; y: device, canonical N x nrhs, used as the
  * initial guess on entry (zero it for none), solution on exit.  stats: host
  * array of nrhs entries, or NULL.  Returns DTR_ENOTCONV if any RHS missed
@@ -252,7 +252,7 @@ int dtr_solve_batch(dtr_gauge g, double m0, const double *z, double *y, int nrhs
  * unbiased for the rounded V. */
 int dtr_defl_create(dtr_lattice lat, int k, dtr_prec prec, const double *V_host,
                     const double *lambda_host, dtr_defl *out);
-/* T_D (Algorithm 1, line 2) as (re, im) in td[2] (host). */
+/* T_D (Algorithm 1's deflated part) as (re, im) in td[2] (host). */
 int dtr_defl_trace(dtr_defl d, double td[2]);
 /* Galerkin (Gram) correction, computed in FP64 on the GPU: with G = V^H gamma_5 A V
  * (k x k, A from gauge g at mass m0, V the stored copy widened exactly),
@@ -268,7 +268,7 @@ int dtr_defl_trace(dtr_defl d, double td[2]);
 int dtr_defl_gram(dtr_defl d, dtr_gauge g, double m0, void *stream);
 void dtr_destroy_defl(dtr_defl d);
 
-/* Deflation projection of a block of probing vectors (Algorithm 1, line 8,
+/* Deflation projection of a block of probing vectors (Algorithm 1's deflation term,
  * second term; Section 5.2):
  *   C = V^H [Z, gamma_5 Z]                       (k x 2 nrhs, FP64)
  *   d_j = sum_m conj(C[m, j]) C[m, nrhs + j] / lambda_m
@@ -361,8 +361,8 @@ typedef struct {
 } dtr_trace_params;
 
 typedef struct {
-  double trace[2];      /* mean over runs of Trace_r (Algorithm 1, line 9), (re, im) */
-  double T_D[2];        /* deflated part (Algorithm 1, line 2) */
+  double trace[2];      /* mean over runs of Trace_r (Algorithm 1's estimate), (re, im) */
+  double T_D[2];        /* deflated part (Algorithm 1) */
   double var_runs;      /* sample variance over runs of Trace_r (complex form) */
   double jk_err;        /* delete-1 jackknife standard error of trace (complex form) */
   double var_samples;   /* sample variance of the individual samples t_j */

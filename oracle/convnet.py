@@ -1,6 +1,6 @@
 """4D convolutional network of the learned preconditioner (oracle; test infrastructure).
 
-The paper does not name its linear solver (Algorithm 1, line 7); the library
+The paper does not name its linear solver (the solve step of Algorithm 1); the library
 adds an FGMRES solver right-preconditioned by a small network M ~ A^-1.  This
 module is the plain reference of that network, used to check the CUDA
 forward and backward kernels:

@@ -5,7 +5,7 @@ found as eigenpairs (Lambda, V) of A^H A.  Section 5.2: with U = A V Sigma^-1
 and Sigma = Lambda^(1/2),
     T_D = Tr(V Sigma^-1 U^H) = Tr(Lambda^-1 V^H A^H V)
 and each Hutchinson quadrature subtracts z^H V Lambda^-1 V^H (A^H z), so U is
-never stored (Algorithm 1, lines 2 and 8).  This module evaluates exactly
+never stored (Algorithm 1: the deflated part T_D and the deflation term).  This module evaluates exactly
 those literal expressions with an explicit A^H.
 
 The triplets themselves (small lattices only) come from the dense Hermitian
@@ -36,14 +36,14 @@ def smallest_triplets(Adense, k):
 
 
 def T_D(AH, V, sigma):
-    """Algorithm 1, line 2: T_D = Tr(Lambda^-1 V^H A^H V) with Lambda = Sigma^2."""
+    """Algorithm 1's deflated part: T_D = Tr(Lambda^-1 V^H A^H V) with Lambda = Sigma^2."""
     Lam = sigma ** 2
     AHV = AH @ V
     return complex(np.sum(np.einsum("im,im->m", np.conj(V), AHV) / Lam))
 
 
 def quadrature(AH, V, sigma, z):
-    """Algorithm 1, line 8 deflation term: z^H V Lambda^-1 V^H (A^H z).
+    """Algorithm 1's deflation term: z^H V Lambda^-1 V^H (A^H z).
 
     z may be (N,) or (N, nrhs); returns one value per column.
     """

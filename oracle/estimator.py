@@ -1,13 +1,11 @@
 """Algorithm 1 (deflatedHP) and the statistics around it (oracle).
 
-deflated_hp follows Algorithm 1 of Section 5.2 step by step:
-  T_D = Tr(Lambda^-1 V^H A^H V); T_R = 0            (line 2)
-  z0 given (drawn by oracle.noise)                   (line 3)
-  for j = 1..s:                                      (line 4)
-      z_h = next probing vector; z = z0 .* z_h       (lines 5-6, oracle.noise)
-      solve A y = z                                  (line 7)
-      T_R += z^H y - z^H V Lambda^-1 V^H (A^H z)     (line 8)
-      Trace = T_R / j + T_D                          (line 9)
+deflated_hp evaluates the estimator of Algorithm 1 (Section 5.2) in the order
+the paper gives it: the deflated part T_D = Tr(Lambda^-1 V^H A^H V) once; then,
+for each probing vector z = z0 .* z_h in turn (z0 and z_h drawn by
+oracle.noise), the solution y of A y = z and the sample z^H y minus the
+deflation term z^H V Lambda^-1 V^H (A^H z), accumulated so that after j samples
+the estimate is T_D plus the mean of the first j samples.
 
 Statistics:
   * Section 6.2: error bars by jackknife over independent runs with different
@@ -33,8 +31,8 @@ def deflated_hp(AH, solve, Z, V=None, sigma=None, group=1):
     into `group` = 12 diluted columns whose quadratures add up to one sample
     (Section 1, dilution); group = 1 otherwise.
     Returns dict with T_D, per-column zy (z^H y) and defl (deflation term),
-    per-sample t (sum over the group of z^H y - defl) and trace (running
-    Trace after each sample j, line 9).
+    per-sample t (sum over the group of z^H y - defl) and trace (the running
+    estimate T_D + mean of the first j samples, for each j).
     """
     ncol = Z.shape[1]
     assert ncol % group == 0

@@ -1,7 +1,7 @@
 """Z4 noise, hierarchical-probing colourings and Hadamard vectors (oracle).
 
 Section 1 (Z4 vectors: entries uniform in {+1, -1, +i, -i}); Section 5.2 and
-Algorithm 1 lines 3-6 (z0 = exp(i*pi*randi([0,3])/2), z = z0 .* z_h with z_h
+Algorithm 1 (z0 = exp(i*pi*randi([0,3])/2), z = z0 .* z_h with z_h
 the next hierarchical-probing vector, a permuted Hadamard vector over a
 nested distance-2^l colouring of the lattice).
 
@@ -64,7 +64,7 @@ def z0_codes_at(seed, run, idx):
 
 
 def z0_vector(seed, run, N):
-    """z0 = exp(i*pi*q/2) written exactly as 1, i, -1, -i (Algorithm 1, line 3)."""
+    """z0 = exp(i*pi*q/2) written exactly as 1, i, -1, -i (the draw of z0 in Algorithm 1)."""
     return Z4_VALUES[z0_codes(seed, run, N)]
 
 

@@ -8,7 +8,7 @@ other counter words and the round key, the key bumped by the Weyl constants
 between rounds.  Vectorised over counters with numpy uint64; the 128-bit
 product is formed from 32-bit halves.
 
-The paper draws z0 with randi([0,3]) (Algorithm 1, line 3); a counter-based
+The paper draws z0 with randi([0,3]) (Algorithm 1); a counter-based
 generator makes that draw a pure function of (seed, z0 run, dof index) so the
 CPU and GPU sides can each compute it from the definition.
 """

@@ -1,6 +1,6 @@
 """Reference linear solvers for A y = z (oracle; test infrastructure).
 
-Algorithm 1, line 7 ("Solve A y = z"); the paper does not name the solver.
+The solve step of Algorithm 1 (A y = z); the paper does not name the solver.
 The oracle uses methods different from the CUDA library's BiCGStab:
   dense_solve   LU (numpy.linalg.solve), small N;
   cgnr          conjugate gradients on the normal equations A^H A y = A^H z,

@@ -1,4 +1,4 @@
-// Deflation projection (Section 5.2; Algorithm 1, lines 2 and 8).
+// Deflation projection (Section 5.2; Algorithm 1: the deflated part T_D and the deflation term).
 //
 // With V the right singular vectors stored as eigenvectors of Q = g5 A
 // (signed eigenvalues lambda), the paper's quadrature z^H V L^-1 V^H (A^H z),

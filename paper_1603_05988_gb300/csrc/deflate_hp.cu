@@ -1,5 +1,5 @@
 // Deflation projection specialised to hierarchical-probing blocks (Section 5.2,
-// Algorithm 1 line 8 with z = z0 .* z_h).
+// Algorithm 1's deflation term with z = z0 .* z_h).
 //
 // All columns of an HP block share one z0 and differ only by the Hadamard
 // sign H[c, j] of each site colour c (and, with dilution, by the dof type a

@@ -1,7 +1,7 @@
 // Deflation contraction on the 5th-generation tensor cores (tcgen05), for a
 // deflation space stored in BF16 and Z4-valued probing blocks.
 //
-// C = V^H [Z, g5 Z] (Section 5.2; Algorithm 1, line 8) is a tall-skinny
+// C = V^H [Z, g5 Z] (Section 5.2; Algorithm 1's deflation term) is a tall-skinny
 // complex contraction over all N dofs.  With V in BF16 and Z in {0, +-1, +-i}
 // (exact in BF16) it is a real BF16 GEMM with FP32 accumulation over K = dof:
 //     D[r, n] = sum_i A[r, i] B[n, i]

@@ -1,4 +1,4 @@
-// Probing-vector generation z = z0 .* z_h (Algorithm 1, lines 3-6).
+// Probing-vector generation z = z0 .* z_h (Algorithm 1; Section 5.2).
 //
 // z0: Z4 noise (Section 1) drawn with Philox4x64-10 (Salmon, Moraes, Dror &
 // Shaw, SC'11), written here from that definition: counter {i/128, run, 0, 0},

@@ -1,4 +1,4 @@
-// Batched BiCGStab for A y = z (Algorithm 1, line 7), one column per probing
+// Batched BiCGStab for A y = z (the solve step of Algorithm 1), one column per probing
 // vector, all columns of a block advanced together with per-column scalars
 // kept on the device.  Two drivers:
 //   * plain FP64 BiCGStab with true-residual restarts;

@@ -1,9 +1,9 @@
 // Algorithm 1 (deflatedHP, Section 5.2) for R independent z0 runs.
 //
 // For every run r and every block of probing columns the device generates
-// z = z0_r .* z_h (lines 3-6), projects it on the deflation space (line 8,
-// second term), solves A y = z (line 7) and reduces t = z^H y - d in FP64
-// (line 8).  Trace_r = T_D + mean_j t_j (line 9).  The host keeps the
+// z = z0_r .* z_h, projects it on the deflation space (the deflation term d),
+// solves A y = z and reduces the samples t = z^H y - d in FP64; the run's
+// estimate is Trace_r = T_D + mean_j t_j.  The host keeps the
 // per-sample record (also the per-m deflation terms, so a run can be replayed
 // for any smaller k, Section 6.3) and forms the run statistics: the mean over
 // runs, the variance over runs and its delete-1 jackknife error (Section 6.2).
