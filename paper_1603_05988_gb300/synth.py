@@ -13,8 +13,9 @@ in for them:
 so U = exp(i eps H) is exactly unitary with det U = exp(i eps Tr H) = 1 up to
 rounding.  Layout: U[site, mu, a, b], site = x + Lx*(y + Ly*(z + Lz*t)).
 
-Named workloads (lattice, eps, m0, noise, deflation) follow the five
-configurations the build is measured on.
+Named workloads (lattice, eps, m0, noise, deflation) follow the five workload
+configurations of the estimator: 4^4, 8^4, 16^3x32 and 32^3x64 (the fifth, the
+learned preconditioner, reuses the 16^3x32 one).
 """
 from dataclasses import dataclass, field
 
