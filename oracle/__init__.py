@@ -25,8 +25,8 @@ Modules
   solve      dense LU and CGNR reference solvers
   deflation  k smallest singular triplets via dense eig of gamma5*A; T_D and
              the deflation quadrature in the paper's literal A^H form
-  estimator  Algorithm 1 (deflatedHP), jackknife over z0 runs, R_s, the
-             time-to-relative-error figure of merit
+  estimator  Algorithm 1 (deflatedHP), sample variance and the jackknife of
+             the mean over z0 runs
 """
 
 # submodules are imported explicitly by callers (from oracle import wilson, ...)

@@ -7,15 +7,10 @@ oracle.noise), the solution y of A y = z and the sample z^H y minus the
 deflation term z^H V Lambda^-1 V^H (A^H z), accumulated so that after j samples
 the estimate is T_D plus the mean of the first j samples.
 
-Statistics:
-  * Section 6.2: error bars by jackknife over independent runs with different
-    z0 (40 runs in the paper; delete-1 jackknife is the reading taken here).
-  * Section 6.2: speedup R_s = V_stoc / (V_hp(s) * s).
-  * Figure of merit used to compare implementations: the wall time to reach
-    a relative standard error eps on the trace, t(s) Var_T(s) / (eps |Tr|)^2,
-    where Var_T(s) is the variance of one run's estimate after s vectors and
-    t(s) the time one run takes.
-Variances use the complex form E|t - E t|^2, the form eq. (1.2) evaluates.
+Statistics: error bars by the delete-1 jackknife of the mean over independent
+runs with different z0 (Section 6.2; delete-1 is the reading taken here), and
+the sample variance.  Variances use the complex form E|t - E t|^2, the form
+eq. (1.2) evaluates.
 """
 import numpy as np
 
@@ -68,23 +63,3 @@ def jackknife_mean(x):
     loo = (x.sum() - x) / (n - 1)
     var = (n - 1) / n * np.sum(np.abs(loo - loo.mean()) ** 2)
     return x.mean(), float(var)
-
-
-def jackknife_variance(x):
-    """Delete-1 jackknife of the sample variance: (variance, its standard error)."""
-    x = np.asarray(x)
-    n = len(x)
-    full = sample_variance(x)
-    loo = np.array([sample_variance(np.delete(x, i)) for i in range(n)])
-    err = np.sqrt((n - 1) / n * np.sum((loo - loo.mean()) ** 2))
-    return full, float(err)
-
-
-def speedup_Rs(V_stoc, V_hp_s, s):
-    """Section 6.2: R_s = V_stoc / (V_hp(s) * s)."""
-    return V_stoc / (V_hp_s * s)
-
-
-def time_to_rel_error(t_run, var_T, trace, eps=1e-3):
-    """Wall time for the mean of repeated runs to reach standard error eps*|Tr|."""
-    return t_run * var_T / (eps * abs(trace)) ** 2
