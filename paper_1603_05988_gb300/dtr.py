@@ -320,6 +320,13 @@ _ENGINE = {"persistent": 0, "kernels": 1}
 
 def solve_params(tol=1e-10, maxiter=5000, solver="f64", check_every=8, inner_tol=1e-5, engine="persistent",
                  grid=0, net=None, gmres_m=16, graph=True):
+    """dtr_solve_params.  solver: "f64" (plain FP64 BiCGStab), "mixed_f32",
+    "mixed_f16", "mixed_bf16" (inner BiCGStab with FP32, FP16 or BF16 Krylov
+    vectors in FP64 defect correction; the half-storage ones need the
+    persistent engine) or "fgmres_net" (FGMRES(gmres_m) with the network `net`,
+    None = unpreconditioned).  engine: "persistent" (one cooperative launch per
+    (inner) solve) or "kernels" (one kernel per BiCGStab step).  graph: run the
+    mixed defect-correction loop as one CUDA graph (persistent engine)."""
     p = SolveParams()
     _lib.dtr_solve_params_default(ctypes.byref(p))
     p.tol, p.maxiter, p.solver, p.check_every, p.inner_tol = tol, maxiter, _SOLVER[solver], check_every, inner_tol
