@@ -212,7 +212,7 @@ def main():
     w = synth.WORKLOADS[WORKLOAD]
     U = synth.random_su3_links(w.dims, w.eps, w.gauge_seed)
     lat = dtr.make_lattice(w.dims)
-    gauge = dtr.make_gauge(lat, U)
+    gauge = dtr.gauge_from_host(lat, U)
     t0 = time.perf_counter()
     V, lam, eres, eit = eigensolver.smallest_gamma5_eigpairs(gauge, w.m0, w.k, iters=args.eig_iters, tol=1e-2,
                                                                      seed=rank)
@@ -293,7 +293,7 @@ def main():
     V_host, lam_host = np.asarray(V), np.asarray(lam)         # the eigensolver returns host arrays
     barrier()
     t0 = time.perf_counter()
-    gauge_e = dtr.make_gauge(lat, U)
+    gauge_e = dtr.gauge_from_host(lat, U)
     defl_e = dtr.defl_create(lat, V_host, lam_host, prec=w.defl_prec)
     t_up = time.perf_counter() - t0
     for i in range(args.steps):
@@ -371,7 +371,7 @@ def main():
     if not args.skip_hbm:
         dims_big = (32, 32, 32, 64)
         lat_big = dtr.make_lattice(dims_big)
-        g_big = dtr.make_gauge(lat_big, kbench.tiled_links(dims_big))
+        g_big = dtr.gauge_from_host(lat_big, kbench.tiled_links(dims_big))
         hb = kbench.dslash_case(g_big, dims_big, "bf16", 1, 30)
         roof_hbm = {"bound": "hbm", "achieved": hb["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
                     "frac": hb["achieved_gbs"] / hbm_peak,

@@ -139,10 +139,24 @@ void dtr_destroy_lattice(dtr_lattice lat);
 int dtr_lattice_info(dtr_lattice lat, int dims[4], int64_t *volume, int64_t *ndof);
 
 /* -------------------------------------------------------------------- gauge */
+/* Random SU(3) gauge field generated on the device: the coefficient field of
+ * the Dirac matrix of Section 6 (whose gauge ensembles are not available, so a
+ * seeded random field stands in).  Every link is a pure function of
+ * (seed, site, mu): U_mu(x) = exp(i eps H) with H = (G + G^H)/2 - Tr/3, G a
+ * 3 x 3 matrix of complex Gaussians (real and imaginary parts N(0, 1)) drawn by
+ * Philox4x64-10 (Salmon et al., SC'11) with key {seed, 1} and counters
+ * {site, mu, c, 0}, c = 0..4, through Box-Muller on 53-bit uniforms
+ * u = ((w >> 11) + 1/2) 2^-53: normal 4c + 2p and 4c + 2p + 1 are
+ * sqrt(-2 ln u_2p) (cos, sin)(2 pi u_2p+1) of output words 2p, 2p + 1 of
+ * counter c, and G_ab = n_2(3a+b) + i n_2(3a+b)+1.  The exponential is exact to
+ * FP64 rounding (unitary, det 1).  eps in [0, 100] (eps = 0: the free field).
+ * Builds the same internal copies as dtr_gauge_from_host.  Synchronous.
+ * DTR_EINVAL (bad argument), DTR_ECUDA (allocation or launch failed). */
+int dtr_make_gauge(dtr_lattice lat, double eps, uint64_t seed, dtr_gauge *out);
 /* Upload SU(3) links (host pointer, canonical layout above, 4*V*9 complex128)
- * and build the library's internal copies (FP64 and FP32).  The gauge field
- * is the coefficient field of the Dirac matrix of Section 6.  Synchronous. */
-int dtr_make_gauge(dtr_lattice lat, const double *links_host, dtr_gauge *out);
+ * and build the library's internal copies (FP64, FP32, double-float split and
+ * half precision).  Synchronous. */
+int dtr_gauge_from_host(dtr_lattice lat, const double *links_host, dtr_gauge *out);
 /* Copy the FP64 links back to a host buffer in the canonical layout. */
 int dtr_gauge_to_host(dtr_gauge g, double *links_host);
 void dtr_destroy_gauge(dtr_gauge g);
@@ -154,9 +168,9 @@ void dtr_destroy_gauge(dtr_gauge g);
  * complex128, must not overlap.  prec selects the arithmetic: DTR_F64;
  * DTR_F32 (fields rounded to FP32, FP32 math, result widened to FP64);
  * DTR_BF16 / DTR_F16 (half-precision storage of the fields and of the links,
- * which are kept as their first two rows -- the third row of an SU(3) matrix
- * is the conjugated cross product of the first two -- FP32 math; dagger = 0
- * only).
+ * all three rows by default, or the first two rows with the third rebuilt as
+ * the conjugated cross product of the first two when dtr_half_link_rows()
+ * returns 2; FP32 math; dagger = 0 only).
  * work: device workspace of dtr_dslash_workspace_bytes(lat, nrhs) bytes. */
 size_t dtr_dslash_workspace_bytes(dtr_lattice lat, int nrhs);
 int dtr_dslash(dtr_gauge g, double m0, const double *in, double *out, int nrhs, int dagger,
@@ -291,10 +305,15 @@ int dtr_deflate_project(dtr_defl d, const double *z, int nrhs, double *d_out, do
  * every GPU that loads the library until the process exits.  It calls no
  * cudaMalloc, cudaFree or other allocating routine.
  * Limits: nrhs <= DTR_STATIC_MAX_RHS and k <= DTR_STATIC_MAX_K, else
- * DTR_EINVAL.  The first call on a device (with that device current) looks up
- * the array's device address; make that first call before any stream capture.
- * All calls share the array: calls whose GPU work overlaps (other streams or
- * host threads) race, so serialise them. */
+ * DTR_EINVAL.  The first call in each CUDA context (with that context's device
+ * current) looks up the array's device address, which is then cached under the
+ * context's unique id, so a context created after a reset never reuses a stale
+ * address; make that first call before any stream capture.  All calls share
+ * the array: calls whose GPU work overlaps (other streams or host threads)
+ * race, so serialise them.  It supports the eigenvalue form only
+ * (DTR_EINVAL after dtr_defl_gram).  Cost: its partial kernel runs at most
+ * 128 blocks, each walking V / 64 sites in turn, so at large lattices it is
+ * far slower than dtr_deflate_project (it is meant for modest problems). */
 #define DTR_STATIC_MAX_K 128
 #define DTR_STATIC_MAX_RHS 16
 int dtr_deflate_project_static(dtr_defl d, const double *z, int nrhs, double *d_out, double *coeff_out,
@@ -358,6 +377,10 @@ typedef struct {
   int gamma[16];       /* their Clifford indices n (0..15): Gamma_n = g1^n0 g2^n1 g3^n2 g4^n3 for the
                           bits n0..n3 of n (Gamma_0 = 1, Gamma_15 = g5), chiral basis.  The same noise,
                           solves and deflation space serve every Gamma (end of Section 5.2). */
+  int64_t vec_first;   /* first probing vector of each run: the call uses Hadamard columns vec_first ..
+                          vec_first + nvec - 1 (<= ncolors; 0 for plain Z4 noise), so a run of Algorithm 1
+                          can be split over several calls whose samples add up; trace_runs then averages
+                          this call's vectors only.  0 = from the first vector. */
 } dtr_trace_params;
 
 typedef struct {

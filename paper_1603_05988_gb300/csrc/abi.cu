@@ -187,8 +187,10 @@ int dtr_lattice_info(dtr_lattice lat, int dims[4], int64_t *volume, int64_t *ndo
   return DTR_OK;
 }
 
-int dtr_make_gauge(dtr_lattice lat, const double *links_host, dtr_gauge *out) {
-  if (!lat || !links_host || !out) return fail(DTR_EINVAL, "null argument");
+// Allocate a gauge handle and fill its FP64 links from host memory (links_host
+// != NULL) or with the device generator (eps, seed), then derive the FP32,
+// double-float split and half-precision copies the kernels read.
+static int gauge_create(dtr_lattice lat, const double *links_host, double eps, uint64_t seed, dtr_gauge *out) {
   dtr_gauge_s *g = new (std::nothrow) dtr_gauge_s;
   if (!g) return fail(DTR_ENOMEM, "host allocation failed");
   g->lat = *lat;
@@ -203,7 +205,14 @@ int dtr_make_gauge(dtr_lattice lat, const double *links_host, dtr_gauge *out) {
   if (e == cudaSuccess) e = cudaMalloc(&g->Udf, n * sizeof(float4));
   if (e == cudaSuccess) e = cudaMalloc(&g->Ubf16, half_links_bytes(lat->V));
   if (e == cudaSuccess) e = cudaMalloc(&g->Uf16, half_links_bytes(lat->V));
-  if (e == cudaSuccess) e = cudaMemcpy(g->U64, links_host, n * sizeof(double2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    if (links_host) {
+      e = cudaMemcpy(g->U64, links_host, n * sizeof(double2), cudaMemcpyHostToDevice);
+    } else {
+      launch_make_links(g->U64, lat->V, eps, seed, 0);
+      e = cudaGetLastError();
+    }
+  }
   if (e == cudaSuccess) {
     k_to_f32<<<grid1d(n), 256>>>(g->U64, g->U32, n); count_launches(1);
     k_split_links<<<grid1d(n), 256>>>(g->U64, (float4 *)g->Udf, n); count_launches(1);
@@ -219,10 +228,21 @@ int dtr_make_gauge(dtr_lattice lat, const double *links_host, dtr_gauge *out) {
     cudaFree(g->Uf16);
     cudaFree(g->Udf);
     delete g;
-    return cuda_fail(e, "gauge upload");
+    return cuda_fail(e, links_host ? "gauge upload" : "gauge generation");
   }
   *out = g;
   return DTR_OK;
+}
+
+int dtr_gauge_from_host(dtr_lattice lat, const double *links_host, dtr_gauge *out) {
+  if (!lat || !links_host || !out) return fail(DTR_EINVAL, "null argument");
+  return gauge_create(lat, links_host, 0.0, 0, out);
+}
+
+int dtr_make_gauge(dtr_lattice lat, double eps, uint64_t seed, dtr_gauge *out) {
+  if (!lat || !out) return fail(DTR_EINVAL, "null argument");
+  if (!(eps >= 0.0) || !(eps <= 100.0)) return fail(DTR_EINVAL, "eps must be in [0, 100]");
+  return gauge_create(lat, nullptr, eps, seed, out);
 }
 
 int dtr_gauge_to_host(dtr_gauge g, double *links_host) {
@@ -683,6 +703,9 @@ static int check_trace_params(const dtr_gauge_s *g, const dtr_defl_s *D, const d
   if (rc) return rc;
   if (p->ncolors > 1 && p->nvec > p->ncolors) return fail(DTR_EINVAL, "nvec must be <= ncolors");
   if (p->ncolors == 1 && p->nvec != 1) return fail(DTR_EINVAL, "plain Z4 noise (ncolors = 1) has nvec = 1");
+  if (p->vec_first < 0 || (p->ncolors == 1 && p->vec_first != 0) ||
+      (p->ncolors > 1 && p->vec_first + p->nvec > p->ncolors))
+    return fail(DTR_EINVAL, "vec_first + nvec must be <= ncolors (vec_first = 0 for plain Z4 noise)");
   if (D && (D->lat.V != g->lat.V)) return fail(DTR_EINVAL, "deflation space built for another lattice");
   if (p->n_gamma < 0 || p->n_gamma > 16) return fail(DTR_EINVAL, "n_gamma must be in [0, 16]");
   for (int q = 0; q < p->n_gamma; ++q)

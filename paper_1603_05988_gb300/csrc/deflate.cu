@@ -264,33 +264,54 @@ __global__ void k_defl_expand(const VC *__restrict__ Vd, const double2 *__restri
   }
 }
 
-// T_D partials: sum_i sign(i) |V[i][m]|^2 over a chunk of dofs
+// T_D partials: part[chunk][m] = sum over the chunk's sites x and dof types a
+// of g5(a) |V[12x + a][m]|^2.  Thread m of block (chunk, m-tile) walks the
+// chunk's sites; a site's twelve rows are independent loads (12 in flight per
+// thread), consecutive threads read consecutive m (coalesced).
+constexpr int kTdThreads = 256;
 template <typename VC>
-__global__ void k_defl_td_partial(const VC *__restrict__ Vd, int k, int64_t N, int nchunks, double *__restrict__ part) {
+__global__ void __launch_bounds__(kTdThreads)
+    k_defl_td_partial(const VC *__restrict__ Vd, int k, int64_t nsite, int nchunks, double *__restrict__ part) {
   const int chunk = blockIdx.x;
-  const int64_t i0 = (N * chunk) / nchunks, i1 = (N * (chunk + 1)) / nchunks;
-  for (int m = threadIdx.x; m < k; m += blockDim.x) {
-    double acc = 0.0;
-    for (int64_t i = i0; i < i1; ++i) {
-      const double2 vv = vload(Vd[i * k + m]);
+  const int m = blockIdx.y * kTdThreads + threadIdx.x;
+  if (m >= k) return;
+  const int64_t x0 = (nsite * chunk) / nchunks, x1 = (nsite * (chunk + 1)) / nchunks;
+  double acc = 0.0;
+  for (int64_t x = x0; x < x1; ++x) {
+    const VC *row = Vd + x * 12 * k + m;
+    VC v[12];
+#pragma unroll
+    for (int a = 0; a < 12; ++a) v[a] = __ldcs(row + (int64_t)a * k);
+#pragma unroll
+    for (int a = 0; a < 12; ++a) {
+      const double2 vv = vload(v[a]);
       const double a2 = vv.x * vv.x + vv.y * vv.y;
-      acc += ((i % 12) < 6) ? a2 : -a2;
+      acc += a < 6 ? a2 : -a2;
     }
-    part[(int64_t)chunk * k + m] = acc;
   }
+  part[(int64_t)chunk * k + m] = acc;
 }
 
-__global__ void k_defl_td_reduce(const double *__restrict__ part, const double *__restrict__ inv_lambda, int k,
-                                 int nchunks, double *__restrict__ td) {
-  // single thread, fixed order: deterministic
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+// T_D = sum_m (sum_chunk part[chunk][m]) / lambda_m: thread t sums m = t, t + T, ...
+// (chunks in order), then a fixed shared-memory tree over the threads.
+// Deterministic for a given (k, nchunks).
+__global__ void __launch_bounds__(kTdThreads)
+    k_defl_td_reduce(const double *__restrict__ part, const double *__restrict__ inv_lambda, int k, int nchunks,
+                     double *__restrict__ td) {
+  __shared__ double sh[kTdThreads];
   double t = 0.0;
-  for (int m = 0; m < k; ++m) {
+  for (int m = threadIdx.x; m < k; m += kTdThreads) {
     double s = 0.0;
     for (int ch = 0; ch < nchunks; ++ch) s += part[(int64_t)ch * k + m];
     t += s * inv_lambda[m];
   }
-  *td = t;
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int w = kTdThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *td = sh[0];
 }
 
 static int log2i(int b) {
@@ -383,21 +404,24 @@ int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 
 }
 
 int defl_trace_TD(dtr_defl_s *D, cudaStream_t st) {
-  const int64_t N = D->lat.N;
+  const int64_t nsite = D->lat.V;
   const int k = D->k;
-  int nch = 256;
-  if (nch > N) nch = (int)N;
+  const int mt = (k + kTdThreads - 1) / kTdThreads;
+  int64_t nch64 = (8LL * device_sms() + mt - 1) / mt;  // about eight blocks per SM
+  if (nch64 > nsite) nch64 = nsite;
+  const int nch = (int)nch64;
   double *part = nullptr, *td = nullptr;
   DTR_CUDA(cudaMalloc((void **)&part, (size_t)nch * k * sizeof(double) + 256));
   td = (double *)((char *)part + (((size_t)nch * k * sizeof(double) + 127) / 128) * 128);
+  const dim3 grid(nch, mt);
   if (D->prec == DTR_F64)
-    k_defl_td_partial<double2><<<nch, 256, 0, st>>>((const double2 *)D->V, k, N, nch, part);
+    k_defl_td_partial<double2><<<grid, kTdThreads, 0, st>>>((const double2 *)D->V, k, nsite, nch, part);
   else if (D->prec == DTR_F32)
-    k_defl_td_partial<float2><<<nch, 256, 0, st>>>((const float2 *)D->V, k, N, nch, part);
+    k_defl_td_partial<float2><<<grid, kTdThreads, 0, st>>>((const float2 *)D->V, k, nsite, nch, part);
   else
-    k_defl_td_partial<bfc2><<<nch, 256, 0, st>>>((const bfc2 *)D->V, k, N, nch, part);
+    k_defl_td_partial<bfc2><<<grid, kTdThreads, 0, st>>>((const bfc2 *)D->V, k, nsite, nch, part);
   count_launches(1);
-  k_defl_td_reduce<<<1, 1, 0, st>>>(part, D->inv_lambda, k, nch, td); count_launches(1);
+  k_defl_td_reduce<<<1, kTdThreads, 0, st>>>(part, D->inv_lambda, k, nch, td); count_launches(1);
   cudaError_t e = cudaGetLastError();
   double h = 0.0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, td, sizeof(double), cudaMemcpyDeviceToHost, st);

@@ -60,10 +60,12 @@ size_t defl_hp_scratch_bytes(int64_t V, int k, int b, int ncolors, int sms);
 // xf (or NULL = identity) transforms the z0 codes of every site first, so the
 // projection is that of Gamma^H z (Gamma-insertion); d_dev may then be NULL
 // (no d_j); *C_out (or NULL) receives the address of C in `work`.
+// reuse_w: W in `work` already holds this run's per-colour sums (same D, seed,
+// run, dilution, identity transform): only the per-column finish runs.
 int defl_project_hp(const dtr_defl_s *D, const int *sites_by_colour, int ncolors, uint64_t seed, int64_t run,
                     int64_t q0, int nrhs, int dilute12, int b, double2 *d_dev, double2 *terms_dev, void *work,
                     size_t work_bytes, int sms, cudaStream_t st, const CodeXform *xf = nullptr,
-                    double2 **C_out = nullptr);
+                    double2 **C_out = nullptr, bool reuse_w = false);
 
 // T_D = sum_m v_m^H g5 v_m / lambda_m from the stored V (FP64 accumulation).
 int defl_trace_TD(dtr_defl_s *D, cudaStream_t st);

@@ -13,6 +13,17 @@
 // 2 N k additions per run rather than 8 N k b flops per block.  On GB300, where
 // FP64 runs at 1/61 of the FP32 rate, this is the difference between the
 // projection costing as much as the solves and costing almost nothing.
+//
+// With V stored in FP32 or BF16 the additions of one 64-site tile run in FP32
+// with compensation: every term is an exactly widened stored value with its
+// sign flipped or its parts swapped, and each addition is an error-free
+// transformation (Knuth's TwoSum: s + t = fl(s + t) + e exactly), the error
+// words summed apart, so the tile's sum is carried as a pair (s, c) accurate
+// to about 64 * 2^-48 relative; each tile's pair is added into FP64
+// accumulators in a fixed order.  The pass stays on the FP32 pipe (six FP32
+// additions per term instead of one FP64 addition, 64x cheaper on GB300) and is
+// bound by the V stream; FP64 V keeps plain FP64 additions.  W of a run is
+// computed once and reused by every block of that run (reuse_w).
 #include "deflate.cuh"
 #include "philox.cuh"
 
@@ -28,10 +39,49 @@ constexpr int kHPEpt = 4;    // row elements (dof type a, vector m) per thread a
 // each with a fixed dof type a = e / k, and accumulates conj(V) z0 over the
 // block's sites of one colour (two sites in flight).  blockIdx.y picks the
 // chunk e0 of the run when 12 k > T kHPEpt.  partial[(split*nc + c) * 12k + e].
+// Tile accumulator: FP32 TwoSum pairs for FP32 / BF16 V, plain FP64 for FP64 V.
+struct HPAccF {
+  float2 s, c;  // running sum and the sum of the rounding errors
+  __device__ __forceinline__ void zero() { s = c = make_float2(0.f, 0.f); }
+  __device__ __forceinline__ static void two_sum(float &s, float &c, float x) {
+    const float t = __fadd_rn(s, x);
+    const float bp = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    s = t;
+    c = __fadd_rn(c, e);
+  }
+  __device__ __forceinline__ void add(float re, float im) {
+    two_sum(s.x, c.x, re);
+    two_sum(s.y, c.y, im);
+  }
+  __device__ __forceinline__ void flush(double2 &acc) const {
+    acc.x += (double)s.x + (double)c.x;
+    acc.y += (double)s.y + (double)c.y;
+  }
+};
+struct HPAccD {
+  double2 s;
+  __device__ __forceinline__ void zero() { s = make_double2(0.0, 0.0); }
+  __device__ __forceinline__ void add(double re, double im) {
+    s.x += re;
+    s.y += im;
+  }
+  __device__ __forceinline__ void flush(double2 &acc) const {
+    acc.x += s.x;
+    acc.y += s.y;
+  }
+};
+template <typename VC> struct HPAcc { typedef HPAccF type; };
+template <> struct HPAcc<double2> { typedef HPAccD type; };
+__device__ __forceinline__ float2 hp_widen(const float2 &v) { return v; }
+__device__ __forceinline__ float2 hp_widen(const bfc2 &v) { return __bfloat1622float2(v); }
+__device__ __forceinline__ double2 hp_widen(const double2 &v) { return v; }
+
 template <typename VC>
 __global__ void __launch_bounds__(kHPMaxThreads)
     k_hp_partial(const VC *__restrict__ Vd, const int *__restrict__ sites, int per_colour, int nc, int nsplit, int k,
                  uint64_t seed, int64_t run, CodeXform xf, double2 *__restrict__ partial) {
+  typedef typename HPAcc<VC>::type AC;
   __shared__ unsigned char codes[kHPTile * 12];
   __shared__ int tile_sites[kHPTile];
   const int c = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
@@ -74,18 +124,19 @@ __global__ void __launch_bounds__(kHPMaxThreads)
       for (int a = 0; a < 12; ++a) codes[tt * 12 + a] = (unsigned char)((raw[xf.src[a]] + xf.add[a]) & 3);
     }
     __syncthreads();
+    AC tacc[kHPEpt];  // this tile's sums
+#pragma unroll
+    for (int j = 0; j < kHPEpt; ++j) tacc[j].zero();
     auto add = [&](int j, const VC vr, int code) {
-      const double2 vv = vload(vr);
-      const double vx = vv.x, vy = vv.y;
+      const auto vv = hp_widen(vr);
       // conj(v) * i^code: 0 -> (vx, -vy), 1 -> (vy, vx), 2 -> (-vx, vy), 3 -> (-vy, -vx)
-      double re = (code & 1) ? vy : vx;
-      double im = (code & 1) ? vx : -vy;
+      auto re = (code & 1) ? vv.y : vv.x;
+      auto im = (code & 1) ? vv.x : -vv.y;
       if (code & 2) {
         re = -re;
         im = -im;
       }
-      acc[j].x += re;
-      acc[j].y += im;
+      tacc[j].add(re, im);
     };
     int u = 0;
     for (; u + 1 < nt; u += 2) {
@@ -113,6 +164,8 @@ __global__ void __launch_bounds__(kHPMaxThreads)
       for (int j = 0; j < kHPEpt; ++j)
         if (aj[j] >= 0) add(j, __ldcs(r0 + e0 + j * T), codes[u * 12 + aj[j]]);
     }
+#pragma unroll
+    for (int j = 0; j < kHPEpt; ++j) tacc[j].flush(acc[j]);
   }
   double2 *out = partial + ((int64_t)split * nc + c) * L;
 #pragma unroll
@@ -241,7 +294,8 @@ size_t defl_hp_scratch_bytes(int64_t V, int k, int b, int ncolors, int sms) {
 
 int defl_project_hp(const dtr_defl_s *D, const int *sites_by_colour, int ncolors, uint64_t seed, int64_t run,
                     int64_t q0, int nrhs, int dilute12, int b, double2 *d_dev, double2 *terms_dev, void *work,
-                    size_t work_bytes, int sms, cudaStream_t st, const CodeXform *xf, double2 **C_out) {
+                    size_t work_bytes, int sms, cudaStream_t st, const CodeXform *xf, double2 **C_out,
+                    bool reuse_w) {
   const CodeXform x = xf ? *xf : code_xform_identity();
   const int64_t V = D->lat.V;
   const int k = D->k;
@@ -256,7 +310,9 @@ int defl_project_hp(const dtr_defl_s *D, const int *sites_by_colour, int ncolors
   double2 *C = (double2 *)w;
   dim3 grid(ncolors * ns, hp_rowchunks(k));
   const int nthr = hp_threads(k);
-  if (D->prec == DTR_F64)
+  if (reuse_w) {
+    // W of this run is already in the workspace
+  } else if (D->prec == DTR_F64)
     k_hp_partial<double2><<<grid, nthr, 0, st>>>((const double2 *)D->V, sites_by_colour, per, ncolors, ns, k,
                                                   seed, run, x, partial);
   else if (D->prec == DTR_F32)
@@ -265,10 +321,12 @@ int defl_project_hp(const dtr_defl_s *D, const int *sites_by_colour, int ncolors
   else
     k_hp_partial<bfc2><<<grid, nthr, 0, st>>>((const bfc2 *)D->V, sites_by_colour, per, ncolors, ns, k, seed, run,
                                                x, partial);
-  count_launches(1);
-  const int64_t nw = (int64_t)ncolors * 12 * k;
-  k_hp_reduce<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(partial, ncolors, ns, k, dilute12, W);
-  count_launches(1);
+  if (!reuse_w) {
+    count_launches(1);
+    const int64_t nw = (int64_t)ncolors * 12 * k;
+    k_hp_reduce<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(partial, ncolors, ns, k, dilute12, W);
+    count_launches(1);
+  }
   const int64_t nk = (int64_t)k * b;
   k_hp_finish<<<(unsigned)((nk + 127) / 128), 128, 0, st>>>(W, ncolors, k, b, nrhs, q0, dilute12, x, C);
   count_launches(1);

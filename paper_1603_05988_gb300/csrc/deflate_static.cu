@@ -16,14 +16,28 @@
 // every GPU that loads the library holds it until the process exits.
 //
 // Host code must not pass the array's name to a kernel: on the host that name
-// is only a stand-in, not a device address.  The device address is looked up
-// once per device with cudaGetSymbolAddress, on the first call made while
-// that device is current.  That first call should therefore come before any
-// stream capture.  All calls share the one array, so calls whose work
+// is only a stand-in, not a device address.  The device address belongs to
+// the copy of the module loaded in one CUDA context, and a new context (after
+// cudaDeviceReset, or a primary context released and created again) may load
+// it elsewhere.  So the address is looked up with cudaGetSymbolAddress on the
+// first call made in each context (with that context's device current) and
+// cached under the context's unique id (cuCtxGetId), never under the device
+// ordinal alone.  That first call in a context should therefore come before
+// any stream capture.  All calls share the one array, so calls whose work
 // overlaps on the GPU (different streams, different host threads) race; every
 // slot a call reads was written earlier in that same call, so nothing needs
 // clearing between calls.
+//
+// Cost: the partial kernel runs 64 site chunks x ceil(k / (4 * 256 / b))
+// blocks (at most 128 blocks), each walking V / 64 sites one after another,
+// so it uses a fraction of the GPU and is far slower than
+// dtr_deflate_project at large lattices (roughly the time to stream V once
+// per block row of m values at a few hundred GB/s): it is meant for modest
+// problems, within its k <= 128, nrhs <= 16 limits.
+#include <cudaTypedefs.h>
+
 #include <mutex>
+#include <unordered_map>
 
 #include "deflate.cuh"
 #include "dtr_internal.cuh"
@@ -108,20 +122,59 @@ __global__ void k_static_finish(const double2 *__restrict__ partial, const doubl
 }
 
 static std::mutex g_static_mu;
-static double2 *g_static_ptr[64];
+static std::unordered_map<unsigned long long, double2 *> g_static_ptr;  // context id -> array address
 
-// Device address of g_static_scratch on the current device (looked up once).
+struct CtxEntryPoints {
+  PFN_cuCtxGetCurrent_v4000 current = nullptr;
+  PFN_cuCtxGetId_v12000 id = nullptr;
+};
+
+static const CtxEntryPoints &ctx_entry_points() {
+  static CtxEntryPoints ep;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      ep.current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      ep.id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+  });
+  return ep;
+}
+
+// Device address of g_static_scratch in the current context, looked up once
+// per context (keyed by the context's unique id, so a context created after a
+// reset never reuses an address from the old one).
 static int static_scratch(double2 **out) {
-  int dev = 0;
-  DTR_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return fail(DTR_EINVAL, "device index above 63");
-  std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_ptr[dev]) {
+  const CtxEntryPoints &ep = ctx_entry_points();
+  if (!ep.current || !ep.id) {  // no way to name the context: look the address up every call
     void *p = nullptr;
     DTR_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
-    g_static_ptr[dev] = (double2 *)p;
+    *out = (double2 *)p;
+    return DTR_OK;
   }
-  *out = g_static_ptr[dev];
+  CUcontext ctx = nullptr;
+  if (ep.current(&ctx) != CUDA_SUCCESS || !ctx) {
+    // no context bound to this thread yet: the runtime binds the current
+    // device's primary context on its first call that needs one
+    void *p = nullptr;
+    DTR_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+    if (ep.current(&ctx) != CUDA_SUCCESS || !ctx) return fail(DTR_ECUDA, "no current CUDA context");
+  }
+  unsigned long long id = 0;
+  if (ep.id(ctx, &id) != CUDA_SUCCESS) return fail(DTR_ECUDA, "cuCtxGetId failed");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  auto it = g_static_ptr.find(id);
+  if (it == g_static_ptr.end()) {
+    void *p = nullptr;
+    DTR_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+    it = g_static_ptr.emplace(id, (double2 *)p).first;
+  }
+  *out = it->second;
   return DTR_OK;
 }
 

@@ -211,6 +211,8 @@ size_t half_links_bytes(int64_t V);
 int half_link_rows();
 size_t half_field_bytes(int64_t V, int b);
 void launch_pack_links_half(const double2 *U64, void *out, int64_t V, int bf16, cudaStream_t st);
+// random SU(3) links U = exp(i eps H) generated on the device from (seed, site, mu) (gauge.cu)
+void launch_make_links(double2 *U64, int64_t V, double eps, uint64_t seed, cudaStream_t st);
 void launch_dslash_half_canon(const void *Uh, const double2 *in, double2 *out, void *work, const Geom &g, int nrhs,
                               int b, double m0, int bf16, cudaStream_t st);
 void launch_dslash_half_raw(const void *Uh, void *work, const Geom &g, int b, double m0, int bf16, int reps,
@@ -218,9 +220,10 @@ void launch_dslash_half_raw(const void *Uh, void *work, const Geom &g, int b, do
 
 // noise into internal FP64 layout of width b: block column k is global column
 // g0 + k of the run-major sequence (ncols probing columns per run, runs from
-// run0); columns nrhs..b-1 are zero padding
+// run0), probing column qoff + (g0 + k) % ncols of its run; columns nrhs..b-1
+// are zero padding
 void launch_noise(double2 *out, const Geom &g, uint64_t seed, int64_t run0, int ncolors, int dilute12, int64_t g0,
-                  int64_t ncols, int nrhs, int b, cudaStream_t st);
+                  int64_t ncols, int nrhs, int b, cudaStream_t st, int64_t qoff = 0);
 // noise into canonical layout
 void launch_noise_canon(double2 *out, const Geom &g, uint64_t seed, int64_t z0_index, int ncolors,
                         int dilute12, int64_t q0, int nrhs, cudaStream_t st);

@@ -13,9 +13,9 @@ namespace dtr {
 
 // Internal layout [site][12][b]; one thread per (site, column).  Column k of
 // the block is global column G = g0 + k of the run-major sequence
-// (run = run0 + G / ncols, probing index q = G % ncols).
+// (run = run0 + G / ncols, probing index q = qoff + G % ncols).
 __global__ void noise_internal_kernel(double2 *out, Geom g, uint64_t seed, int64_t run0, int ncolors, int dilute12,
-                                      int64_t g0, int64_t ncols, int nrhs, int b) {
+                                      int64_t g0, int64_t ncols, int64_t qoff, int nrhs, int b) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (int64_t)g.V * b) return;
   const int j = (int)(tid % b);
@@ -31,7 +31,7 @@ __global__ void noise_internal_kernel(double2 *out, Geom g, uint64_t seed, int64
   const int colour = hp_colour(xc, ncolors);
   const int64_t G = g0 + j;
   const int64_t run = run0 + G / ncols;
-  const int64_t q = G % ncols;
+  const int64_t q = qoff + G % ncols;
   const int64_t hcol = dilute12 ? q / 12 : q;
   const int keep = dilute12 ? (int)(q % 12) : -1;
   const int sign = (__popcll((unsigned long long)(colour & hcol)) & 1) ? -1 : 1;
@@ -73,11 +73,11 @@ __global__ void noise_canon_kernel(double2 *out, Geom g, uint64_t seed, int64_t 
 }
 
 void launch_noise(double2 *out, const Geom &g, uint64_t seed, int64_t run0, int ncolors, int dilute12, int64_t g0,
-                  int64_t ncols, int nrhs, int b, cudaStream_t st) {
+                  int64_t ncols, int nrhs, int b, cudaStream_t st, int64_t qoff) {
   const int64_t n = (int64_t)g.V * b;
   const int T = 256;
   noise_internal_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(out, g, seed, run0, ncolors, dilute12, g0, ncols,
-                                                                    nrhs, b); count_launches(1);
+                                                                    qoff, nrhs, b); count_launches(1);
 }
 
 void launch_noise_canon(double2 *out, const Geom &g, uint64_t seed, int64_t z0_index, int ncolors, int dilute12,

@@ -227,6 +227,7 @@ struct Lane {
   size_t terms_cap = 0;
   int64_t G0 = 0;
   int nb = 0;
+  int64_t hp_run = -1;   // z0 run whose per-colour sums W are in hp_work (-1: none)
 };
 
 // Library-owned streams and pinned staging of the extra lanes (per host thread).
@@ -315,6 +316,7 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
   };
 
   const int ncols = p->nvec * (p->dilute12 ? 12 : 1);
+  const int64_t qoff = p->vec_first * (p->dilute12 ? 12 : 1);  // first probing column of each run
   const int R = p->n_z0;
   const double td = D ? D->td[0] : 0.0;
   const double td_im = D ? D->td[1] : 0.0;
@@ -384,16 +386,22 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
     ln.nb = nb;
     const int64_t q0 = G0 % ncols;
     const bool one_run = q0 + nb <= ncols;
-    launch_noise(ln.Z, g, p->seed, p->z0_first, p->ncolors, p->dilute12, G0, ncols, nb, b, s);
+    launch_noise(ln.Z, g, p->seed, p->z0_first, p->ncolors, p->dilute12, G0, ncols, nb, b, s, qoff);
     DTR_LAUNCH_CHECK("noise");
     if (D) {
       int rc;
       const bool hp_block = hp_ok && one_run && !p->use_x0;
       double2 *Cm = nullptr;
-      if (hp_block)
-        rc = defl_project_hp(D, sites_dev, p->ncolors, p->seed, p->z0_first + G0 / ncols, q0, nb, p->dilute12, b,
-                             ln.d_dev, res->replay ? ln.terms_dev : nullptr, ln.hp_work, L.hp, sms, s, nullptr, &Cm);
-      else
+      if (hp_block) {
+        // the per-colour sums W of a z0 run serve every block of that run: they are
+        // recomputed only when this lane moves to another run (or a Gamma pass
+        // overwrote them)
+        const int64_t run = p->z0_first + G0 / ncols;
+        rc = defl_project_hp(D, sites_dev, p->ncolors, p->seed, run, qoff + q0, nb, p->dilute12, b, ln.d_dev,
+                             res->replay ? ln.terms_dev : nullptr, ln.hp_work, L.hp, sms, s, nullptr, &Cm,
+                             ln.hp_run == run);
+        ln.hp_run = run;
+      } else
         rc = defl_project_internal(D, ln.Z, b, ln.d_dev, res->replay ? ln.terms_dev : nullptr,
                                    p->use_x0 ? ln.X : nullptr, &Cm, ln.defl_work, L.defl, sms, s, 1);
       if (rc) return rc;
@@ -404,8 +412,9 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
           double2 *Cg = nullptr;
           if (hp_block) {
             const CodeXform xf = code_xform_gamma_h(gset.g[q]);
-            rc = defl_project_hp(D, sites_dev, p->ncolors, p->seed, p->z0_first + G0 / ncols, q0, nb, p->dilute12,
-                                 b, nullptr, nullptr, ln.hp_work, L.hp, sms, s, &xf, &Cg);
+            rc = defl_project_hp(D, sites_dev, p->ncolors, p->seed, p->z0_first + G0 / ncols, qoff + q0, nb,
+                                 p->dilute12, b, nullptr, nullptr, ln.hp_work, L.hp, sms, s, &xf, &Cg);
+            ln.hp_run = -1;
           } else {
             launch_gamma_h(gset.g[q], ln.Z, ln.GZ, g.V, b, s);
             rc = defl_project_internal(D, ln.GZ, b, ln.tg, nullptr, nullptr, &Cg, ln.defl_work, L.defl, sms, s, 1);

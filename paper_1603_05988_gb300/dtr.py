@@ -46,7 +46,7 @@ class TraceParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("z0_first", ctypes.c_int64), ("n_z0", ctypes.c_int),
                 ("ncolors", ctypes.c_int), ("nvec", ctypes.c_int), ("dilute12", ctypes.c_int),
                 ("block", ctypes.c_int), ("use_x0", ctypes.c_int), ("solve", SolveParams), ("lanes", ctypes.c_int),
-                ("n_gamma", ctypes.c_int), ("gamma", ctypes.c_int * 16)]
+                ("n_gamma", ctypes.c_int), ("gamma", ctypes.c_int * 16), ("vec_first", ctypes.c_int64)]
 
 
 class TraceResult(ctypes.Structure):
@@ -98,7 +98,8 @@ _sig("dtr_selftest_barrier", _i, [_i64, ctypes.POINTER(ctypes.c_int), ctypes.POI
 _sig("dtr_make_lattice", _i, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_vp)])
 _sig("dtr_destroy_lattice", None, [_vp])
 _sig("dtr_lattice_info", _i, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64), ctypes.POINTER(_i64)])
-_sig("dtr_make_gauge", _i, [_vp, _vp, ctypes.POINTER(_vp)])
+_sig("dtr_make_gauge", _i, [_vp, _d, _u64, ctypes.POINTER(_vp)])
+_sig("dtr_gauge_from_host", _i, [_vp, _vp, ctypes.POINTER(_vp)])
 _sig("dtr_gauge_to_host", _i, [_vp, _vp])
 _sig("dtr_destroy_gauge", None, [_vp])
 _sig("dtr_dslash_workspace_bytes", _sz, [_vp, _i])
@@ -198,12 +199,18 @@ def make_lattice(dims):
 
 
 class Gauge:
-    def __init__(self, lat, links):
-        links = np.ascontiguousarray(links, dtype=np.complex128)
-        if links.shape != (lat.V, 4, 3, 3):
-            raise ValueError("links must have shape (V, 4, 3, 3)")
+    """Gauge field handle: links uploaded from host (`links`, shape (V, 4, 3, 3)
+    complex128) or generated on the device from (eps, seed)."""
+
+    def __init__(self, lat, links=None, eps=None, seed=None):
         h = _vp()
-        _check(_lib.dtr_make_gauge(lat._h, links.ctypes.data_as(_vp), ctypes.byref(h)))
+        if links is not None:
+            links = np.ascontiguousarray(links, dtype=np.complex128)
+            if links.shape != (lat.V, 4, 3, 3):
+                raise ValueError("links must have shape (V, 4, 3, 3)")
+            _check(_lib.dtr_gauge_from_host(lat._h, links.ctypes.data_as(_vp), ctypes.byref(h)))
+        else:
+            _check(_lib.dtr_make_gauge(lat._h, float(eps), int(seed), ctypes.byref(h)))
         self._h = h
         self.lat = lat
 
@@ -218,8 +225,14 @@ class Gauge:
             self._h = None
 
 
-def make_gauge(lat, links):
-    return Gauge(lat, links)
+def make_gauge(lat, eps, seed):
+    """Random SU(3) field U = exp(i eps H) generated on the device (dtr_make_gauge)."""
+    return Gauge(lat, eps=eps, seed=seed)
+
+
+def gauge_from_host(lat, links):
+    """Gauge field uploaded from host links of shape (V, 4, 3, 3) (dtr_gauge_from_host)."""
+    return Gauge(lat, links=links)
 
 
 def dslash(gauge, m0, x, dagger=False, prec="f64"):
@@ -481,8 +494,10 @@ def deflate_project_static(defl, z, want_coeff=False):
 
 
 def trace_params(seed=0, z0_first=0, n_z0=1, ncolors=1, nvec=1, dilute12=False, block=16, use_x0=False,
-                 solve=None, lanes=1, gammas=()):
+                 solve=None, lanes=1, gammas=(), vec_first=0):
+    """dtr_trace_params; vec_first: first probing (Hadamard) vector of each run used by this call."""
     p = TraceParams()
+    p.vec_first = int(vec_first)
     p.seed, p.z0_first, p.n_z0, p.ncolors, p.nvec = int(seed), int(z0_first), int(n_z0), int(ncolors), int(nvec)
     p.dilute12, p.block, p.use_x0 = int(bool(dilute12)), int(block), int(bool(use_x0))
     p.solve = solve if solve is not None else solve_params()

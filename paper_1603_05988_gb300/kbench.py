@@ -111,7 +111,7 @@ def trace_case(dims, eps, m0, seed, k, defl_prec, ncolors, nvec, block, solvers)
     import torch
     from . import dtr, synth
     lat = dtr.make_lattice(dims)
-    g = dtr.make_gauge(lat, synth.random_su3_links(dims, eps, seed))
+    g = dtr.gauge_from_host(lat, synth.random_su3_links(dims, eps, seed))
     V = synth.disjoint_orthonormal(lat.N, k, 4)
     lam = np.where(np.arange(k) % 2 == 0, 1.0, -1.0) * np.linspace(0.8, 1.5, k)
     D = dtr.defl_create(lat, V, lam, prec=defl_prec)
@@ -147,7 +147,7 @@ def learned_case(train_dims, eval_dims, eps, m0, seed, steps, batch, pool, nrhs,
 
     def gauge_at(dims, gseed):
         lat = dtr.make_lattice(dims)
-        return dtr.make_gauge(lat, synth.random_su3_links(dims, eps, gseed))
+        return dtr.gauge_from_host(lat, synth.random_su3_links(dims, eps, gseed))
 
     g = gauge_at(train_dims, seed)
     net = dtr.Net(g.lat, act=0, init_scale=1.0 / (4.0 + m0), noise=1e-3, seed=1)
@@ -258,13 +258,13 @@ def main(argv=None):
     lat = dtr.make_lattice(dims)
     if a.what == "solve":
         from . import synth
-        g = dtr.make_gauge(lat, synth.random_su3_links(dims, a.eps, a.gauge_seed))
+        g = dtr.gauge_from_host(lat, synth.random_su3_links(dims, a.eps, a.gauge_seed))
         for solver in a.solver.split(","):
             for n in a.nrhs.split(","):
                 print(json.dumps(solve_case(g, dims, int(n), a.reps, a.m0, graph=not a.no_graph, solver=solver,
                                             inner_tol=a.inner_tol, engine=a.engine)), flush=True)
         return
-    g = dtr.make_gauge(lat, tiled_links(dims))
+    g = dtr.gauge_from_host(lat, tiled_links(dims))
     for prec in a.prec.split(","):
         for n in a.nrhs.split(","):
             print(json.dumps(dslash_case(g, dims, prec, int(n), a.reps)), flush=True)

@@ -28,7 +28,7 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for required in ["dtr_make_lattice", "dtr_make_gauge", "dtr_dslash", "dtr_gen_noise", "dtr_solve_batch",
+    for required in ["dtr_make_lattice", "dtr_make_gauge", "dtr_gauge_from_host", "dtr_dslash", "dtr_gen_noise", "dtr_solve_batch",
                      "dtr_deflate_project", "dtr_trace_estimate", "dtr_defl_create", "dtr_last_error"]:
         assert required in names
 
@@ -60,7 +60,7 @@ def test_binding_mirrors_the_abi():
     if not os.path.exists(build.LIB):
         build.build()
     from paper_1603_05988_gb300 import dtr
-    for name in ["make_lattice", "make_gauge", "dslash", "gen_noise", "solve_batch", "defl_create",
+    for name in ["make_lattice", "make_gauge", "gauge_from_host", "dslash", "gen_noise", "solve_batch", "defl_create",
                  "deflate_project", "trace_estimate"]:
         assert callable(getattr(dtr, name))
     assert "sm_103a" in dtr.version()

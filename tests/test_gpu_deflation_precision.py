@@ -27,7 +27,7 @@ def c4(dtr):
     lat = dtr.make_lattice(dims)
     N = Ad.shape[0]
     g5 = np.tile(np.array([1.0] * 6 + [-1.0] * 6), N // 12)
-    return dict(dims=dims, m0=m0, Ad=Ad, Ainv=Ainv, V=V, lam=lam, lat=lat, g=dtr.make_gauge(lat, U), N=N, g5=g5)
+    return dict(dims=dims, m0=m0, Ad=Ad, Ainv=Ainv, V=V, lam=lam, lat=lat, g=dtr.gauge_from_host(lat, U), N=N, g5=g5)
 
 
 def _zblock(c, seed, n):
@@ -99,7 +99,7 @@ def test_tensor_core_contraction_matches_oracle(dtr, dims, k, b, R):
     accumulation accuracy, and T_D is exact."""
     lat = dtr.make_lattice(dims)
     U = synth.random_su3_links(dims, 0.5, 1000)
-    g = dtr.make_gauge(lat, U)
+    g = dtr.gauge_from_host(lat, U)
     V = synth.random_orthonormal(lat.N, k, 7)
     lam = np.where(np.arange(k) % 2 == 0, 1.0, -1.0) * np.linspace(0.7, 1.6, k)
     D = dtr.defl_create(lat, V, lam, prec="bf16")

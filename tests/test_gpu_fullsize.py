@@ -41,7 +41,7 @@ def big(request, dtr):
     dims = c["dims"]
     U = kbench.tiled_links(dims) if c["tiled"] else synth.random_su3_links(dims, 0.8, 1002)
     lat = dtr.make_lattice(dims)
-    g = dtr.make_gauge(lat, U)
+    g = dtr.gauge_from_host(lat, U)
     rng = np.random.default_rng(11)
     c.update(U=U, lat=lat, g=g, N=lat.N, sites=np.sort(rng.choice(lat.V, size=48, replace=False)))
     yield c

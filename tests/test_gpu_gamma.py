@@ -29,7 +29,7 @@ def c4(dtr):
     V, lam, sig = deflation.smallest_triplets(Ad, 32)
     lat = dtr.make_lattice(dims)
     return dict(dims=dims, m0=m0, AH=wilson.explicit_dagger(U, dims, m0), Ad=Ad, Ainv=Ainv, V=V, lam=lam, sig=sig,
-                lat=lat, g=dtr.make_gauge(lat, U), N=Ad.shape[0])
+                lat=lat, g=dtr.gauge_from_host(lat, U), N=Ad.shape[0])
 
 
 def _check(out, refs, tol_t=1e-8):

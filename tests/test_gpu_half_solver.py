@@ -29,7 +29,7 @@ def dtr():
 def _setup(dtr, dims, eps, m0, seed):
     U = synth.random_su3_links(dims, eps, seed)
     lat = dtr.make_lattice(dims)
-    g = dtr.make_gauge(lat, U)
+    g = dtr.gauge_from_host(lat, U)
     return U, lat, g
 
 

@@ -50,7 +50,7 @@ def test_net_gradient_matches_oracle(dtr, act, residual):
     dims = (2, 2, 2, 4)
     lat = dtr.make_lattice(dims)
     U = synth.random_su3_links(dims, 0.5, 21)
-    g = dtr.make_gauge(lat, U)
+    g = dtr.gauge_from_host(lat, U)
     net = dtr.Net(lat, act=act, init_scale=0.5, noise=0.05, seed=4)
     rng = np.random.default_rng(6)
     X = _c64(rng.standard_normal((lat.N, 2)) + 1j * rng.standard_normal((lat.N, 2)))
@@ -79,7 +79,7 @@ def trained(dtr):
     dims, m0 = (4, 4, 4, 4), -0.15
     U = synth.random_su3_links(dims, 0.2, 1000)
     lat = dtr.make_lattice(dims)
-    g = dtr.make_gauge(lat, U)
+    g = dtr.gauge_from_host(lat, U)
     net = dtr.Net(lat, act=0, init_scale=1.0 / (4.0 + m0), noise=1e-3, seed=1)
     hist = learned.train(net, g, m0, steps=200, batch=8, lr=3e-4, pool=16)
     return dict(dims=dims, m0=m0, U=U, lat=lat, g=g, net=net, hist=hist)

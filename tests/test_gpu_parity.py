@@ -32,7 +32,7 @@ def _cpu(t):
 def _setup(dtr, dims, eps, m0, seed):
     U = synth.random_su3_links(dims, eps, seed)
     lat = dtr.make_lattice(dims)
-    g = dtr.make_gauge(lat, U)
+    g = dtr.gauge_from_host(lat, U)
     return U, lat, g
 
 
@@ -206,7 +206,7 @@ def cfg1(dtr):
     tr, Ainv = exact.trace_inverse_lu(Ad)
     V, lam, sig = deflation.smallest_triplets(Ad, 32)
     lat = dtr.make_lattice(dims)
-    g = dtr.make_gauge(lat, U)
+    g = dtr.gauge_from_host(lat, U)
     return dict(dims=dims, m0=m0, U=U, A=A, AH=AH, Ad=Ad, tr=tr, Ainv=Ainv, V=V, lam=lam, sig=sig, lat=lat, g=g)
 
 
@@ -418,7 +418,7 @@ def test_trace_8x8x8x8_hp16_sampled(dtr, solver):
     dims, m0 = (8, 8, 8, 8), -0.6
     U = synth.random_su3_links(dims, 0.7, 1001)
     lat = dtr.make_lattice(dims)
-    g = dtr.make_gauge(lat, U)
+    g = dtr.gauge_from_host(lat, U)
     V = synth.random_orthonormal(lat.N, 100, 5)
     lam = np.where(np.arange(100) % 2 == 0, 1.0, -1.0) * np.linspace(0.9, 1.4, 100)
     D = dtr.defl_create(lat, V, lam)

@@ -24,7 +24,7 @@ def c4(dtr):
     tr, Ainv = exact.trace_inverse_lu(Ad)
     V, lam, sig = deflation.smallest_triplets(Ad, 32)
     lat = dtr.make_lattice(dims)
-    return dict(dims=dims, m0=m0, Ad=Ad, Ainv=Ainv, V=V, lam=lam, lat=lat, g=dtr.make_gauge(lat, U), N=Ad.shape[0])
+    return dict(dims=dims, m0=m0, Ad=Ad, Ainv=Ainv, V=V, lam=lam, lat=lat, g=dtr.gauge_from_host(lat, U), N=Ad.shape[0])
 
 
 DOFS = [0, 37, 400, 1111, 2047, 3071]
