@@ -1,31 +1,36 @@
 #!/usr/bin/env python3
-"""Benchmark of the deflated hierarchical-probing trace estimator (Algorithm 1)
-on the 8^4 Wilson-Dirac workload: eps 0.7, m0 -0.6, 16-colour hierarchical
-probing per Z4 vector z0, blocks of 16 right-hand sides per launch, k = 100
-FP64 deflation vectors, solves to a true relative residual of 1e-10.
+"""Benchmark of the deflated hierarchical-probing trace estimator (Algorithm 1).
 
-One step = one wave of L z0 runs of the whole path (noise + HP mask,
-deflation projection, 16 batched solves per run, FP64 z^H y reductions and run
-statistics) = 16 L right-hand sides, where L (runs in flight at once, each on
-its own stream and SM share; every solve is still one 16-RHS block) is chosen
-by the library's autotuner before the timed region.  Metric: right-hand sides
-solved per second (whole job), plus the variance x time figure of merit (time
-to a 1e-3 relative trace error) for the mixed-precision path and for the plain
-FP64 path (autotuned the same way) on the same seeds.
+Headline workload (the largest that fits one GB300), wilson32x32x32x64_hp512x8_k1000:
+32^3x64 lattice (N = 25,165,824), eps 0.8, m0 -0.78, gauge seed 1003 (links
+generated on the device), k = 1000 deflation vectors stored in BF16 and built on
+the device by the setup eigensolver, 512 hierarchical-probing vectors per z0 run,
+mixed-precision batched solves (FP32 inner BiCGStab in FP64 defect correction,
+CUDA-graph captured) to a true relative residual of 1e-10, launch shape (RHS
+block 8-64 and concurrent lanes) chosen by the library's autotuner.
+
+One step = one wave of the whole path over W = lanes x block probing vectors of
+one z0 run (noise + HP mask, deflation projection, batched solves, FP64 z^H y
+reductions): 512 / W consecutive steps make one run of Algorithm 1.  Metric:
+right-hand sides solved per second, plus variance x time to a 1e-3 relative
+trace error for this path and for the plain FP64 GPU path on the same seeds.
+The 8^4 workload (wilson8x8x8x8_hp16x256_k100) is measured the same way and
+reported under "extra".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle (the program the CUDA path is
-checked against) on a bounded sample of the same workload.  Under torchrun
-(N > 1) every rank runs its own z0 runs (weak scaling, no data-path
-collective); rank 0 prints the line.
+--impl reference times the FP64 CPU oracle (the program the CUDA path is checked
+against) on bounded samples of the same workload.  Under torchrun (N > 1) every
+rank runs its own z0 runs (weak scaling, no data-path collective); rank 0 prints.
 """
 import argparse
 import json
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -35,7 +40,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "wilson8x8x8x8_hp16x256_k100"
+WORKLOAD = "wilson32x32x32x64_hp512x8_k1000"
+SMALL = "wilson8x8x8x8_hp16x256_k100"
 METRIC = "RHS solves/s (deflated HP Tr(A^-1) estimator, true residual 1e-10)"
 UNIT = "RHS/s"
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
@@ -44,24 +50,31 @@ L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=128)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--solver", default="mixed_f32", choices=["mixed_f32", "f64"])
-    ap.add_argument("--f64-steps", type=int, default=6, help="steps of the plain FP64 path timed for comparison")
-    ap.add_argument("--eig-iters", type=int, default=150,
-                    help="cap on setup eigensolver iterations (deflation-space quality; untimed)")
-    ap.add_argument("--skip-hbm", action="store_true", help="skip the 32^3x64 half-precision stencil measurement")
-    ap.add_argument("--cpu-sample-rhs", type=int, default=16,
-                    help="RHS in the CPU-oracle baseline sample (16: about 13 s of one Grace core)")
-    ap.add_argument("--lanes", type=int, default=0, help="z0 runs in flight per step (0 = autotune)")
+    ap.add_argument("--eig-time", type=float, default=100.0,
+                    help="wall-time cap (s) of the 32^3x64 setup eigensolver (untimed setup)")
+    ap.add_argument("--eig-iters", type=int, default=40, help="iteration cap of the setup eigensolvers")
+    ap.add_argument("--f64-steps", type=int, default=2, help="steps of the plain FP64 path timed for comparison")
+    ap.add_argument("--var-runs", type=int, default=2, help="complete z0 runs of 512 vectors for Var_T")
+    ap.add_argument("--small-steps", type=int, default=48, help="timed steps of the 8^4 workload (extra)")
+    ap.add_argument("--skip-small", action="store_true", help="skip the 8^4 workload")
+    ap.add_argument("--skip-kernels", action="store_true", help="skip the standalone kernel roofline lines")
+    ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-autotune", action="store_true", help="use --block/--lanes instead of the autotuner")
+    ap.add_argument("--block", type=int, default=32)
+    ap.add_argument("--lanes", type=int, default=1)
+    ap.add_argument("--cpu-procs", type=int, default=0, help="CPU oracle processes (0: cores, memory permitting)")
+    ap.add_argument("--ref-lattice", default="", help="reference arm: lattice of the oracle samples (default: the "
+                                                       "workload's 32^3x64)")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven solver cycles instead of the CUDA graph (same kernels and results; lets a "
                          "profiler list the kernels of the solver loop)")
     return ap.parse_args()
 
 
-def measured_hbm_peak():
+def measured_peaks():
     """HBM copy bandwidth (GB/s) measured on the GB300s, else the recipe's fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -130,59 +143,168 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- CPU oracle
-CPU_SAMPLE_CODE = r"""
-import json, sys, time
-import numpy as np
-sys.path.insert(0, sys.argv[1])
-from paper_1603_05988_gb300 import synth
-from oracle import noise, solve, wilson, deflation
-w = synth.WORKLOADS[sys.argv[2]]
-nrhs, reps = int(sys.argv[3]), int(sys.argv[4])
-U = synth.random_su3_links(w.dims, w.eps, w.gauge_seed)
-A = wilson.explicit(U, w.dims, w.m0)
-AH = wilson.explicit_dagger(U, w.dims, w.m0)
-V = synth.random_orthonormal(w.N, w.k, 0)
-sig = np.linspace(0.9, 1.4, w.k)
-times = []
-for r in range(reps):
+# The oracle as it stands, on the host cores, on bounded samples of the 32^3x64
+# workload: its operator (oracle.wilson.apply_at, the per-site coding) applied at
+# every 16th site of a 32^3x64 field in each process, extrapolated to the whole
+# field; the right-hand side's cost is (2 x iterations + 2) applications in its
+# CGNR, with the iteration count from its CGNR to 1e-10 at 8^4 (same eps, m0).
+SAMPLE_STRIDE = 16
+_CPU_STATE = {}
+
+
+def _links_chunk(args):
+    path, eps, seed, s0, s1 = args
+    sys.path.insert(0, ROOT)
+    from oracle import gauge
+    out = np.load(path, mmap_mode="r+")
+    sites = np.repeat(np.arange(s0, s1), 4)
+    mu = np.tile(np.arange(4), s1 - s0)
+    out[s0:s1] = gauge.links_at(seed, eps, sites, mu).reshape(s1 - s0, 4, 3, 3)
+    out.flush()
+    return s1 - s0
+
+
+def _cpu_links_file(dims, eps, seed, pool):
+    """The device generator's field drawn by the oracle (counter-based), shared by the workers."""
+    path = os.path.join(tempfile.gettempdir(), "dtr_links_%s_%g_%d.npy" % ("x".join(map(str, dims)), eps, seed))
+    if not os.path.exists(path):
+        V = int(np.prod(dims))
+        tmp = path + ".%d.tmp.npy" % os.getpid()
+        np.lib.format.open_memmap(tmp, mode="w+", dtype=np.complex128, shape=(V, 4, 3, 3)).flush()
+        step = max(1, V // 64)
+        pool.map(_links_chunk, [(tmp, eps, seed, s0, min(V, s0 + step)) for s0 in range(0, V, step)])
+        os.replace(tmp, path)
+    return path
+
+
+def _cpu_sample(args):
+    """Time the oracle's operator at every SAMPLE_STRIDE-th site of the field (one process)."""
+    links_path, dims, m0, q = args
+    os.environ["OMP_NUM_THREADS"] = "1"
+    sys.path.insert(0, ROOT)
+    from oracle import wilson
+    if _CPU_STATE.get("key") != (links_path, q):
+        N = 12 * int(np.prod(dims))
+        rng = np.random.default_rng(q)
+        _CPU_STATE.update(key=(links_path, q), U=np.load(links_path, mmap_mode="r"),
+                          psi=rng.standard_normal(N) + 1j * rng.standard_normal(N))
+    V = int(np.prod(dims))
+    sites = np.arange(q % SAMPLE_STRIDE, V, SAMPLE_STRIDE)
     t0 = time.perf_counter()
-    Z = noise.noise_vectors(w.dims, w.noise_seed, 100000 + r, w.ncolors, False, 0, nrhs)
-    Y, it, res = solve.cgnr(A, Z, tol=w.tol)
-    t = np.einsum("ij,ij->j", np.conj(Z), Y) - deflation.quadrature(AH, V, sig, Z)
-    times.append(time.perf_counter() - t0)
-print(json.dumps({"times": times, "iters": int(it), "res": float(np.max(res))}))
-"""
+    wilson.apply_at(_CPU_STATE["U"], dims, m0, _CPU_STATE["psi"], sites)
+    return (time.perf_counter() - t0) * V / len(sites)   # one whole-field application
 
 
-def cpu_oracle_sample(nrhs, reps):
-    """Run the FP64 oracle (one thread) on `reps` samples of `nrhs` RHS each."""
-    env = dict(os.environ)
-    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[v] = "1"
-    out = subprocess.run([sys.executable, "-c", CPU_SAMPLE_CODE, ROOT, WORKLOAD, str(nrhs), str(reps)],
-                         capture_output=True, text=True, env=env, timeout=1800)
-    if out.returncode != 0:
-        raise RuntimeError("CPU oracle sample failed: " + out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+def _cgnr_iterations_8x8(eps, m0, seed):
+    """CGNR iterations to 1e-10 for the same (eps, m0) at 8^4 (explicit matrix), with the time per RHS."""
+    from oracle import gauge, noise, solve, wilson
+    dims = (8, 8, 8, 8)
+    U = gauge.random_su3_links(dims, eps, seed)
+    A = wilson.explicit(U, dims, m0)
+    z = noise.noise_vectors(dims, 0, 0, 16, False, 0, 1)[:, 0]
+    t0 = time.perf_counter()
+    _, it, res = solve.cgnr(A, z, tol=1e-10)
+    return it, time.perf_counter() - t0
+
+
+def cpu_procs(requested):
+    n = os.cpu_count() or 1
+    try:
+        with open("/proc/meminfo") as f:
+            avail = [int(l.split()[1]) for l in f if l.startswith("MemAvailable")][0] * 1024
+    except (OSError, IndexError):
+        avail = 16 << 30
+    by_mem = max(1, int(avail * 0.25 // (2 << 30)))    # ~1 GB per worker at 32^3x64; a quarter of free memory
+    p = min(n, by_mem, 32)
+    if requested > 0:
+        p = min(p, requested)
+    return max(1, p)
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for l in f:
+                if l.lower().startswith(("model name", "cpu part")):
+                    return l.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+class CpuOracle:
+    """A pool of spawned oracle processes on the 32^3x64 workload (or `dims`)."""
+
+    def __init__(self, nprocs, dims=None):
+        w = _workload(WORKLOAD)
+        self.dims = tuple(dims) if dims else w.dims
+        self.m0, self.n = w.m0, nprocs
+        self.pool = mp.get_context("spawn").Pool(nprocs)
+        self.path = _cpu_links_file(self.dims, w.eps, w.gauge_seed, self.pool)
+        self.iters, self.t8 = _cgnr_iterations_8x8(w.eps, w.m0, w.gauge_seed)
+
+    def step(self):
+        """All processes at once; returns (wall seconds, mean whole-field application seconds)."""
+        t0 = time.perf_counter()
+        ts = self.pool.map(_cpu_sample, [(self.path, self.dims, self.m0, q) for q in range(self.n)])
+        return time.perf_counter() - t0, float(np.mean(ts))
+
+    def rhs_per_s(self, t_apply):
+        return self.n / (t_apply * (2 * self.iters + 2))
+
+    def sample_note(self, t_apply):
+        return ("extrapolated per RHS: %d processes, each the FP64 oracle's operator (per-site coding) at every %dth "
+                "site of a %s field, scaled to one whole-field application (%.2f s); RHS cost = (2 x %d + 2) "
+                "applications, %d = the oracle's CGNR iterations to 1e-10 at 8^4 with the same eps and m0"
+                % (self.n, SAMPLE_STRIDE, "x".join(map(str, self.dims)), t_apply, self.iters, self.iters))
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_oracle_baseline(nprocs, reps=3, dims=None):
+    o = CpuOracle(nprocs, dims)
+    try:
+        t_apply = min(o.step()[1] for _ in range(reps))
+        return {"value": o.rhs_per_s(t_apply), "cores": nprocs, "t_apply_s": t_apply, "cgnr_iterations": o.iters,
+                "nproc": os.cpu_count(), "cpu_model": _cpu_model(), "sample": o.sample_note(t_apply)}
+    finally:
+        o.close()
+
+
+def _workload(name):
+    from paper_1603_05988_gb300 import synth
+    return synth.WORKLOADS[name]
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    steps, warm = args.steps, args.warmup
-    # one RHS per step: the oracle's Algorithm 1 quadrature on one probing vector
-    r = cpu_oracle_sample(1, steps + warm)
-    ts = r["times"][warm:]
-    value = len(ts) / sum(ts)
+    n = cpu_procs(args.cpu_procs)
+    dims = tuple(int(x) for x in args.ref_lattice.split(",")) if args.ref_lattice else None
+    o = CpuOracle(n, dims)
+    try:
+        walls, applies = [], []
+        for s in range(args.warmup + args.steps):
+            wt, ta = o.step()
+            if s >= args.warmup:
+                walls.append(wt)
+                applies.append(ta)
+        t_apply = float(np.mean(applies))
+        value = o.rhs_per_s(t_apply)
+        note = o.sample_note(t_apply)
+    finally:
+        o.close()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * sum(ts) / len(ts), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "step": "1 RHS (CPU oracle sample)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d steps x 1 RHS at 8^4, CGNR to 1e-10 + deflation quadrature (paper A^H form)"
-                                   % steps},
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / len(walls),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": list(o.dims),
+                   "step": "%d oracle processes, one sampled operator application each" % n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": n, "kind": "oracle", "sample": note,
+                         "nproc": os.cpu_count(), "cpu_model": _cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -190,6 +312,34 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- GPU path
+def persistent_roofline(prof, sms, lanes, wall_ms, block, hbm_peak, hbm_note, workload):
+    """Roofline of the persistent FP32 BiCGStab kernel from its device-timed launches.
+    Algorithmic bytes per site, RHS and iteration: the fused minimum of one BiCGStab
+    iteration in FP32 storage, two stencils (96 B in + 96 B out + 288 / b B links each)
+    and six vector passes of 96 B; flops 2 x 1368 + 12 x 104."""
+    bytes_unit = 2 * (96 + 96 + 288.0 / block) + 6 * 96
+    flop_unit = 2 * 1368.0 + 12 * 104.0
+    n = max(prof["launches"], 1)
+    pms = prof["ms"] / n
+    units = prof["site_rhs_iterations"] / n
+    gbs = units * bytes_unit / (pms / 1e3) / 1e9 if pms > 0 else 0.0
+    tfl = units * flop_unit / (pms / 1e3) / 1e12 if pms > 0 else 0.0
+    grid = sms // lanes if lanes > 1 else sms
+    share = grid / sms
+    fp32_peak = sms * 128 * 2 * 2.07e9 / 1e12
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak * share, "unit": "GB/s", "frac": gbs / (hbm_peak * share),
+            "traffic": None, "kernel": "k_bicgstab_persistent (FP32 inner BiCGStab, %d RHS, %s)" % (block, workload),
+            "avg_launch_ms": pms, "launches": prof["launches"], "alg_bytes_per_launch": units * bytes_unit,
+            "alg_bytes_note": "%.0f B per site, RHS and iteration (two FP32 stencils 2 x (96 + 96 + 288/%d) + six "
+                              "96 B vector passes: the fused minimum) x site-RHS-iterations of the launch"
+                              % (bytes_unit, block),
+            "peak_note": hbm_note + "; times the launch's SM share %d/%d" % (grid, sms),
+            "fp32": {"achieved_tflops": tfl, "peak_tflops": fp32_peak * share, "frac": tfl / (fp32_peak * share),
+                     "note": "3984 flop per site, RHS and iteration; FP32 peak = SMs x 128 x 2 x 2.07 GHz (nominal)"},
+            "aggregate_gbs": prof["site_rhs_iterations"] * bytes_unit / (wall_ms / 1e3) / 1e9 if wall_ms else None,
+            "ctas_per_launch": grid, "concurrent_launches": lanes}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -203,42 +353,253 @@ def main():
         dist.init_process_group("nccl")
     else:
         torch.cuda.set_device(0)
-
     from paper_1603_05988_gb300 import build as _build
     if not os.path.exists(_build.LIB):
         _build.build()
-    from paper_1603_05988_gb300 import dtr, eigensolver, synth
+    from paper_1603_05988_gb300 import dtr, synth
 
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    hbm_peak, hbm_note = measured_peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
     w = synth.WORKLOADS[WORKLOAD]
-    U = synth.random_su3_links(w.dims, w.eps, w.gauge_seed)
+    ncol = w.ncolors                                   # 512 probing vectors per run
+
+    # ---------------------------------------------------------------- setup
     lat = dtr.make_lattice(w.dims)
-    gauge = dtr.gauge_from_host(lat, U)
     t0 = time.perf_counter()
-    V, lam, eres, eit = eigensolver.smallest_gamma5_eigpairs(gauge, w.m0, w.k, iters=args.eig_iters, tol=1e-2,
-                                                                     seed=rank)
-    t_setup = time.perf_counter() - t0
-    defl = dtr.defl_create(lat, V, lam, prec=w.defl_prec)
+    gauge = dtr.make_gauge(lat, w.eps, w.gauge_seed)
+    t_gauge = time.perf_counter() - t0
+    ep = dtr.eig_params(w.k, store=w.defl_prec, tol=1e-2, degree=48, max_iter=args.eig_iters,
+                        time_limit_s=args.eig_time, seed=rank)
+    defl, eres, est = dtr.eig_deflation(gauge, w.m0, ep)
+    torch.cuda.empty_cache()
+    bound = (abs(4.0 + w.m0) + 4.0)
+    lam = defl.lambdas()
+    rn = eres * np.abs(lam) / bound                    # the same residuals relative to the bound on ||A||
+    setup = {"gauge_s": t_gauge, "eigensolver": {k_: est[k_] for k_ in ("iterations", "converged", "basis", "seconds",
+                                                                         "max_residual")},
+             "residual_median": float(np.median(eres)),
+             "residual_vs_norm": {"max": float(rn.max()), "median": float(np.median(rn)),
+                                  "below_1e-2": int(np.sum(rn <= 1e-2))},
+             "abs_lambda_range": [float(np.abs(lam).min()), float(np.abs(lam).max())],
+             "residual_note": "||Q v - lambda v|| / (|lambda| ||v||), and relative to the bound |4 + m0| + 4 = %.2f "
+                              "on ||A|| (the scale of a tolerance stated against the matrix norm)" % bound,
+             "eigensolver_workspace_gb": est["workspace_bytes"] / 1e9, "T_D": [defl.T_D().real, defl.T_D().imag]}
+
+    def params(solver, lanes, block, run, vec0, nvec, graph=True):
+        return dtr.trace_params(seed=w.noise_seed, z0_first=run, n_z0=1, ncolors=ncol, nvec=nvec, vec_first=vec0,
+                                block=block, lanes=lanes,
+                                solve=dtr.solve_params(tol=w.tol, solver=solver, graph=graph and not args.no_graph))
+
+    # launch shape: lanes x block, every candidate that fits beside the deflation space
+    free, _ = torch.cuda.mem_get_info()
+    if args.no_autotune:
+        tune = {"lanes": args.lanes, "block": args.block, "table": [], "forced": True}
+    else:
+        tp = dtr.trace_params(seed=w.noise_seed, z0_first=0, n_z0=1, ncolors=ncol, nvec=ncol, block=0,
+                              solve=dtr.solve_params(tol=w.tol, solver="mixed_f32", graph=not args.no_graph))
+        tune = dtr.trace_autotune(gauge, w.m0, defl, tp, reps=1, max_workspace_bytes=free - (6 << 30))
+        torch.cuda.empty_cache()
+    L, B = tune["lanes"], tune["block"]
+    W = L * B                                          # probing vectors per step
+    steps_per_run = ncol // W
+    ws = dtr.TraceWorkspace(gauge, defl, params("mixed_f32", L, B, 0, 0, W))
+    base = 1 + rank * 100003
+
+    def step(solver, i, wsp=ws, g=gauge, graph=True):
+        run = base + i // steps_per_run
+        v0 = (i % steps_per_run) * W
+        return dtr.trace_estimate(g, w.m0, defl, params(solver, L, B, run, v0, W, graph), workspace=wsp)
+
+    # warm-up on runs of their own
+    for i in range(args.warmup):
+        dtr.trace_estimate(gauge, w.m0, defl, params("mixed_f32", L, B, 500000 + i, 0, W), workspace=ws)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = dtr.kernel_launches()
+    dtr.profile_persistent(1)
+    samples = {}
+    ms = []
+    iters = 0
+    maxres = 0.0
+    for i in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = step("mixed_f32", i)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        samples[i] = out["samples"][0]
+        iters += out["iterations"]
+        maxres = max(maxres, out["max_true_residual"])
+        if not out["all_converged"] or out["max_true_residual"] > w.tol:
+            raise RuntimeError("step did not converge: %r" % (out["max_true_residual"],))
+    prof = dtr.profile_persistent(0)
+    launches = dtr.kernel_launches() - launches0
+    barrier()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(sum(ms))
+    value = W * args.steps * world / (total_ms / 1e3)
+
+    # complete z0 runs (untimed steps beyond the timed ones) for the run-to-run variance
+    nvar = max(args.var_runs, 1) * steps_per_run
+    for i in range(args.steps, nvar):
+        samples[i] = step("mixed_f32", i)["samples"][0]
+    td = defl.T_D()
+    traces = []
+    for r in range(max(args.var_runs, 1)):
+        t_r = np.concatenate([samples[r * steps_per_run + j] for j in range(steps_per_run)])
+        traces.append(td + t_r.mean())
+    tr_mean = complex(np.mean(traces))
+    var_T = float(np.sum(np.abs(np.array(traces) - tr_mean) ** 2) / max(len(traces) - 1, 1))
+
+    # plain FP64 path on the same seeds (the first steps of the timed sequence)
+    ms64, diff = [], 0.0
+    step("f64", 0)                                    # warm-up (graph-free FP64 solver)
+    for i in range(args.f64_steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        o64 = step("f64", i)
+        e1.record()
+        torch.cuda.synchronize()
+        ms64.append(e0.elapsed_time(e1))
+        diff = max(diff, float(np.abs(o64["samples"][0] - samples[i]).max() / np.abs(samples[i]).max()))
+    value64 = W * args.f64_steps / (sum(ms64) / 1e3)
+    t_run = ncol / value * world
+    t_run64 = ncol / value64
+    ttr = t_run * var_T / (1e-3 * abs(tr_mean)) ** 2
+    ttr64 = t_run64 * var_T / (1e-3 * abs(tr_mean)) ** 2
+
+    # end to end through the public API: the gauge links uploaded from pinned host memory,
+    # then the same steps, each reading its samples and run traces back to the host
+    U_host = gauge.to_host()
+    U_pin = torch.empty((lat.V, 4, 3, 3, 2), dtype=torch.float64, pin_memory=True)
+    U_pin.numpy()[:] = U_host.view(np.float64).reshape(lat.V, 4, 3, 3, 2)
+    del U_host
+    U_np = U_pin.numpy().view(np.complex128).reshape(lat.V, 4, 3, 3)
+    barrier()
+    t0 = time.perf_counter()
+    gauge_e = dtr.gauge_from_host(lat, U_np)
+    for i in range(args.steps):
+        o = step("mixed_f32", i, g=gauge_e)
+        _ = o["samples"].sum()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = W * args.steps * world / e2e_s
+    up_bytes = U_np.nbytes
+    del gauge_e, U_pin, U_np
+
+    roof = persistent_roofline(prof, sms, L, total_ms, B, hbm_peak, hbm_note, "32^3x64")
+    head = {
+        "value": value, "ms_per_step": total_ms / args.steps, "rhs_per_step": W, "lanes": L, "block": B,
+        "iterations_per_rhs": iters / (args.steps * W), "max_true_residual": maxres, "launches": launches,
+        "clocks": clk, "roofline": roof, "setup": setup,
+        "autotune": {"lanes": L, "block": B, "table": [(c["lanes"], c["block"], round(c["rhs_per_s"], 1))
+                                                       for c in tune.get("table", [])]},
+        "fp64_path": {"value": value64, "unit": UNIT, "steps": args.f64_steps, "ms_per_step": sum(ms64) / len(ms64),
+                      "max_rel_sample_diff_vs_mixed": diff},
+        "variance_x_time": {"trace": [tr_mean.real, tr_mean.imag], "var_T": var_T, "runs": len(traces),
+                            "time_to_1e-3_s": ttr, "time_to_1e-3_s_fp64_path": ttr64,
+                            "speedup_vs_fp64_path": ttr64 / ttr,
+                            "note": "Var_T over %d complete runs of 512 vectors (complex form); both paths give the "
+                                    "same samples (max relative difference above), so they share Var_T" % len(traces)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": up_bytes / args.steps,
+                "d2h_bytes_per_step": W * 16 + 16,
+                "note": "host wall clock: dtr_gauge_from_host of the links from pinned host memory (%d B; "
+                        "h2d_bytes_per_step = that / steps), then %d dtr_trace_estimate calls reading samples and "
+                        "run traces back to the host; the noise is drawn on the device from (seed, run); the "
+                        "deflation space (setup output, %.1f GB) stays resident" % (up_bytes, args.steps,
+                                                                                    lat.N * w.k * 4 / 1e9)},
+    }
+    del ws
+    torch.cuda.empty_cache()
+
+    # ------------------------------------------------------ the 8^4 workload
+    small = None
+    if not args.skip_small:
+        del defl, gauge
+        torch.cuda.empty_cache()
+        small = measure_small(args, dtr, synth, torch, barrier, max_over_ranks, sms, hbm_peak, hbm_note, rank, world)
+
+    # ------------------------------------------- standalone kernel rooflines
+    kern = {} if args.skip_kernels else kernel_rooflines(dtr, hbm_peak, hbm_note)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        c = cpu_oracle_baseline(cpu_procs(args.cpu_procs))
+        cpu = dict(c, unit=UNIT, kind="oracle")
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64 (FP32 inner BiCGStab, FP64 defect correction; BF16 deflation space with FP64 "
+                     "accumulation; FP64 reductions)",
+            "data": "synthetic (random SU(3) links generated on the device, seeded)",
+            "config": {"workload": WORKLOAD, "lattice": list(w.dims), "eps": w.eps, "m0": w.m0, "k": w.k,
+                       "defl_prec": w.defl_prec, "ncolors": ncol, "rhs_per_step": W, "block": B, "lanes": L,
+                       "tol": w.tol, "solver": "mixed_f32", "graph": not args.no_graph,
+                       "l2": "inputs far larger than L2 (V 100.7 GB, one 32-RHS FP64 field 12.9 GB)",
+                       "step": "one wave of %d probing vectors of a z0 run (%d steps per run of 512)"
+                               % (W, steps_per_run)},
+            "clocks": clk,
+            "e2e": head["e2e"],
+            "gpu_launches": launches,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "setup": setup,
+            "autotune": head["autotune"],
+            "iterations_per_rhs": head["iterations_per_rhs"],
+            "fp64_path": head["fp64_path"],
+            "variance_x_time": head["variance_x_time"],
+            "speedup_vs_fp64_path": value / value64,
+            "extra": {"wilson8x8x8x8_hp16x256_k100": small, **kern},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def measure_small(args, dtr, synth, torch, barrier, max_over_ranks, sms, hbm_peak, hbm_note, rank, world):
+    """The 8^4 workload: 16-colour HP runs in 16-RHS blocks, k = 100 FP64 deflation
+    vectors from the GPU eigensolver, L z0 runs in flight per step (autotuned)."""
+    w = synth.WORKLOADS[SMALL]
+    lat = dtr.make_lattice(w.dims)
+    gauge = dtr.gauge_from_host(lat, synth.random_su3_links(w.dims, w.eps, w.gauge_seed))
+    ep = dtr.eig_params(w.k, store="f64", tol=1e-2, degree=48, max_iter=max(args.eig_iters, 60), seed=rank)
+    defl, eres, est = dtr.eig_deflation(gauge, w.m0, ep)
 
     def params(solver, z0, lanes):
         return dtr.trace_params(seed=w.noise_seed, z0_first=z0, n_z0=lanes, ncolors=w.ncolors, nvec=w.ncolors,
-                                block=w.block, solve=dtr.solve_params(tol=w.tol, solver=solver, graph=not args.no_graph),
-                                lanes=lanes)
-
-    # launch shape: the library's autotuner times 1, 2, 4, 8 lanes (untimed setup)
-    tune = {}
-    for s_ in (args.solver, "f64"):
-        if s_ in tune:
-            continue
-        if args.lanes > 0:
-            tune[s_] = {"lanes": args.lanes, "block": w.block, "rhs_per_s": None, "table": [], "forced": True}
-        else:
-            tune[s_] = dtr.trace_autotune(gauge, w.m0, defl, params(s_, 0, 1), reps=3 if s_ == args.solver else 1)
-    lanes = {s_: t["lanes"] for s_, t in tune.items()}
+                                block=w.block, solve=dtr.solve_params(tol=w.tol, solver=solver,
+                                                                      graph=not args.no_graph), lanes=lanes)
+    lanes = {}
+    tables = {}
+    for s_ in ("mixed_f32", "f64"):
+        t = dtr.trace_autotune(gauge, w.m0, defl, params(s_, 0, 1), reps=3 if s_ == "mixed_f32" else 1)
+        lanes[s_] = t["lanes"]
+        tables[s_] = [(c["lanes"], round(c["rhs_per_s"])) for c in t["table"]]
     wss = {s_: dtr.TraceWorkspace(gauge, defl, params(s_, 0, lanes[s_])) for s_ in lanes}
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     base = rank * 1000003
 
-    def run_steps(solver, nsteps, first, timed):
+    def run_steps(solver, nsteps, first):
         L = lanes[solver]
         ms, traces, iters = [], [], 0
         for i in range(nsteps):
@@ -253,207 +614,91 @@ def main():
             traces.extend(out["trace_runs"])
             iters += out["iterations"]
             if not out["all_converged"] or out["max_true_residual"] > w.tol:
-                raise RuntimeError("step did not converge: %r" % (out["max_true_residual"],))
+                raise RuntimeError("8^4 step did not converge")
         return ms, traces, iters
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
-    L = lanes[args.solver]
-    # warm-up
-    run_steps(args.solver, args.warmup, base + 900000, False)
+    L = lanes["mixed_f32"]
+    run_steps("mixed_f32", args.warmup, base + 900000)
     barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    launches0 = dtr.kernel_launches()
-    dtr.profile_persistent(1)                          # device-timed persistent solver launches
-    torch.cuda.nvtx.range_push("timed")
-    ms, traces, iters = run_steps(args.solver, args.steps, base, True)
-    torch.cuda.nvtx.range_pop()
+    dtr.profile_persistent(1)
+    ms, traces, iters = run_steps("mixed_f32", args.small_steps, base)
     prof = dtr.profile_persistent(0)
-    launches = dtr.kernel_launches() - launches0
-    barrier()
-    clk = clocks.stop()
     total_ms = max_over_ranks(sum(ms))
-    rhs_per_step = w.ncolors * L
-    value = rhs_per_step * args.steps * world / (total_ms / 1e3)
-
-    # end-to-end through the public calls from host-resident inputs (host wall
-    # clock): upload of the gauge field and of the deflation space from host
-    # memory, then the steps, each reading its samples and traces back to the host
-    V_host, lam_host = np.asarray(V), np.asarray(lam)         # the eigensolver returns host arrays
-    barrier()
-    t0 = time.perf_counter()
-    gauge_e = dtr.gauge_from_host(lat, U)
-    defl_e = dtr.defl_create(lat, V_host, lam_host, prec=w.defl_prec)
-    t_up = time.perf_counter() - t0
-    for i in range(args.steps):
-        out = dtr.trace_estimate(gauge_e, w.m0, defl_e, params(args.solver, base + i * L, L),
-                                 workspace=wss[args.solver])
-        _ = out["samples"].sum()
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = rhs_per_step * args.steps * world / e2e_s
-    up_bytes = U.size * 16 + V_host.size * 16 + lam_host.size * 8
-    del gauge_e, defl_e
-    # the same steps with the inputs already resident (per-step public call only)
-    barrier()
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        out = dtr.trace_estimate(gauge, w.m0, defl, params(args.solver, base + i * L, L), workspace=wss[args.solver])
-        _ = out["samples"].sum()
-    torch.cuda.synchronize()
-    e2e_res_value = rhs_per_step * args.steps * world / max_over_ranks(time.perf_counter() - t0)
-
-    # plain FP64 path on the same seeds (reference GPU path of the metric)
+    value = w.ncolors * L * args.small_steps * world / (total_ms / 1e3)
     L64 = lanes["f64"]
-    nf = max(1, min(args.f64_steps, (args.steps * L) // L64))
-    run_steps("f64", 1, base + 900000, False)
-    ms64, traces64, iters64 = run_steps("f64", nf, base, True)
+    nf = max(1, min(6, (args.small_steps * L) // L64))
+    run_steps("f64", 1, base + 900000)
+    ms64, traces64, _ = run_steps("f64", nf, base)
     value64 = w.ncolors * L64 * nf / (sum(ms64) / 1e3)
     ncmp = min(len(traces), len(traces64))
-    trace_diff = max(abs(a - b) / abs(b) for a, b in zip(traces[:ncmp], traces64[:ncmp]))
-
-    # variance x time: Var_T over the timed runs, t_run the mean time per run
+    tdiff = max(abs(a - b) / abs(b) for a, b in zip(traces[:ncmp], traces64[:ncmp]))
     tr_mean = complex(np.mean(traces))
     var_T = float(np.sum(np.abs(np.array(traces) - tr_mean) ** 2) / (len(traces) - 1))
-    t_run = (total_ms / (args.steps * L)) / 1e3
+    t_run = (total_ms / (args.small_steps * L)) / 1e3
     t_run64 = (sum(ms64) / (nf * L64)) / 1e3
-    ttr = t_run * var_T / (1e-3 * abs(tr_mean)) ** 2
-    ttr64 = t_run64 * var_T / (1e-3 * abs(tr_mean)) ** 2
-
-    # roofline of the dominant kernel: the persistent BiCGStab kernel (one
-    # cooperative launch per inner solve), timed inside the timed region by
-    # device global-timer stamps (first block entry to last block exit; the
-    # launches sit in CUDA-graph loop bodies, where events cannot be recorded);
-    # algorithmic FP32 flops per site, RHS and iteration: two stencils
-    # (2 x 1368) plus the fused vector work (12 complex x 104 flops)
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    fp32_peak = sms * 128 * 2 * 2.07e9 / 1e12          # TFLOP/s: SMs x FP32 lanes x FMA x max clock
-    flop_per_unit = 2 * 1368.0 + 12 * 104.0
-    pms = prof["ms"] / max(prof["launches"], 1)
-    pflops = prof["site_rhs_iterations"] * flop_per_unit / max(prof["launches"], 1)
-    achieved = pflops / (pms / 1e3) / 1e12 if pms > 0 else 0.0
-    grid = sms // L if L > 1 else sms                   # CTAs (one per SM) of one launch
-    share = grid / sms
-    agg = prof["site_rhs_iterations"] * flop_per_unit / (total_ms / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak * share, "unit": "TFLOP/s",
-            "frac": achieved / (fp32_peak * share), "traffic": 2.978e7,
-            "traffic_note": "DRAM read + write of one launch under ncu (26.47 + 3.32 MB), same kernel and problem "
-                            "(8^4, 16 RHS) on 152 CTAs: profiles/persistent_bicgstab_f32_8x8x8x8_b16.md",
-            "kernel": "k_bicgstab_persistent<float,512,0,float2> (FP32 inner solve, 16 RHS, 8^4, L2-resident)",
-            "avg_launch_ms": pms, "launches": prof["launches"], "flops_per_launch": pflops,
-            "ctas_per_launch": grid, "concurrent_launches": L,
-            "peak_note": "FP32 peak = %d SMs x 128 lanes x 2 flop x 2.07 GHz (of nominal clocks) = %.1f TFLOP/s, "
-                         "times the launch's SM share %d/%d" % (sms, fp32_peak, grid, sms),
-            "aggregate": {"achieved": agg, "peak": fp32_peak, "frac": agg / fp32_peak,
-                          "note": "all persistent-kernel flops in the timed region / timed wall time"},
-            "share_note": "share of GPU time in the timed region: profiles/launches_wilson8x8x8x8_hp16x256_k100.md"}
-
-    # the stencil core alone at the bench's shape, and the half-precision stencil
-    # on a lattice far larger than L2 (HBM roofline)
-    from paper_1603_05988_gb300 import kbench
-    st8 = kbench.dslash_case(gauge, w.dims, "f32", w.block, 200)
-    roof_stencil = {"bound": "alu", "achieved": st8["achieved_tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": st8["achieved_tflops"] / fp32_peak, "traffic": None,
-                    "kernel": "dslash FP32, 16 RHS, 8^4", "avg_launch_ms": st8["avg_launch_ms"]}
-    hbm_peak, hbm_note = measured_hbm_peak()
-    roof_hbm = roof_tc = None
-    if not args.skip_hbm:
-        dims_big = (32, 32, 32, 64)
-        lat_big = dtr.make_lattice(dims_big)
-        g_big = dtr.gauge_from_host(lat_big, kbench.tiled_links(dims_big))
-        hb = kbench.dslash_case(g_big, dims_big, "bf16", 1, 30)
-        roof_hbm = {"bound": "hbm", "achieved": hb["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                    "frac": hb["achieved_gbs"] / hbm_peak,
-                    "traffic": 4.946e8 if hb["link_rows"] == 3 else None,
-                    "traffic_note": "DRAM read + write of one launch under ncu (407.4 + 87.2 MB): "
-                                    "profiles/dslash_half_bf16_32x32x32x64.md",
-                    "kernel": "dslash BF16 storage, FP32 math, 1 RHS, 32^3x64",
-                    "avg_launch_ms": hb["avg_launch_ms"], "alg_bytes_per_launch": hb["alg_bytes_per_launch"],
-                    "alg_bytes_note": "240 B per site (48 + 48 B spinors, 144 B for four 3x3 BF16 links); the "
-                                      "kernel stores %d rows per link and moves %d B per launch (%.0f GB/s)"
-                                      % (hb["link_rows"], hb["stored_bytes_per_launch"], hb["moved_gbs"]),
-                    "peak_note": hbm_note}
-        del g_big, lat_big
-        # the tensor-core (tcgen05) deflation contraction: BF16 V, one 16-column Z4 block
-        dc = kbench.deflate_case((16, 16, 16, 32), 256, 16, 20, "bf16")
-        roof_tc = {"bound": "hbm", "achieved": dc["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                   "frac": dc["achieved_gbs"] / hbm_peak, "traffic": 2.0169e9,
-                   "kernel": "k_defl_tc (tcgen05 BF16 x Z4 contraction, FP32 accumulation in TMEM), "
-                             "16^3x32, k=256, 16 RHS",
-                   "avg_launch_ms": dc["avg_launch_ms"], "alg_bytes_per_launch": dc["alg_bytes_per_launch"],
-                   "achieved_tflops": dc["achieved_tflops"],
-                   "alg_bytes_note": "N k 4 B (V) + N b 16 B (Z) per launch; traffic = DRAM read + write of "
-                                     "one launch under ncu (profiles/defl_tc_bf16_16x16x16x32_k256_b16.md)",
-                   "tensor_pipe_active_pct": 14.3, "peak_note": hbm_note}
-
-    # CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
-    cpu = None
-    if rank == 0 and world == 1:
-        r = cpu_oracle_sample(args.cpu_sample_rhs, 1)
-        tcpu = r["times"][-1]
-        cpu = {"value": args.cpu_sample_rhs / tcpu, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d RHS of the 8^4 workload: CGNR to 1e-10 (%d iters) + deflation quadrature, "
-                         "%.1f s" % (args.cpu_sample_rhs, r["iters"], tcpu)}
-
-    scal_bytes = 7440
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (FP32 inner BiCGStab, FP64 defect correction, "
-                                                            "FP64 deflation and reductions)"
-            if args.solver == "mixed_f32" else "f64",
-            "data": "synthetic (random SU(3) links, seeded)",
-            "config": {"workload": WORKLOAD, "lattice": list(w.dims), "eps": w.eps, "m0": w.m0,
-                       "rhs_per_step": rhs_per_step, "block": w.block, "ncolors": w.ncolors, "k": w.k,
-                       "lanes": L, "z0_runs_per_step": L,
-                       "autotune": {s_: {"lanes": t["lanes"], "table": [(c["lanes"], round(c["rhs_per_s"]))
-                                                                        for c in t["table"]]}
-                                    for s_, t in tune.items()},
-                       "defl_prec": w.defl_prec, "tol": w.tol, "solver": args.solver,
-                       "l2": "flushed (256 MiB write) before every timed step",
-                       "deflation_space": "subspace iteration on (g5 A)^-1: %d its, max rel residual %.2e, "
-                                          "setup %.1f s (untimed)" % (eit, float(np.max(eres)), t_setup)},
-            "clocks": clk,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": up_bytes / args.steps,
-                    "d2h_bytes_per_step": rhs_per_step * 16 + scal_bytes * L,
-                    "upload_s": t_up,
-                    "note": "host wall clock: dtr_make_gauge + dtr_defl_create from host arrays (links %d B, "
-                            "V + lambda %d B; h2d_bytes_per_step = that / steps), then %d dtr_trace_estimate "
-                            "calls reading samples and traces back to the host; the noise is drawn on the device "
-                            "from (seed, run)" % (U.size * 16, V_host.size * 16 + lam_host.size * 8, args.steps),
-                    "resident_inputs": {"value": e2e_res_value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                                        "note": "same steps, gauge and V already on the device"}},
-            "gpu_launches": launches,
-            "roofline": roof,
-            "roofline_stencil_fp32": roof_stencil,
-            "roofline_stencil_bf16_hbm": roof_hbm,
-            "roofline_deflation_tc_hbm": roof_tc,
-            "cpu_baseline": cpu,
-            "fp64_path": {"value": value64, "unit": UNIT, "steps": nf, "ms_per_step": sum(ms64) / nf,
-                          "lanes": L64, "iterations_per_rhs": iters64 / (nf * w.ncolors * L64),
-                          "max_rel_trace_diff_vs_mixed": trace_diff},
-            "iterations_per_rhs": iters / (args.steps * rhs_per_step),
-            "variance_x_time": {"trace": [tr_mean.real, tr_mean.imag], "var_T": var_T, "runs": len(traces),
-                                "time_to_1e-3_s": ttr, "time_to_1e-3_s_fp64_path": ttr64,
-                                "speedup_vs_fp64_path": ttr64 / ttr},
+    # roofline: at 8^4 the persistent kernel is L2-resident and latency-bound; against its SM share of FP32
+    fp32_peak = sms * 128 * 2 * 2.07e9 / 1e12
+    flop_unit = 2 * 1368.0 + 12 * 104.0
+    n = max(prof["launches"], 1)
+    pms = prof["ms"] / n
+    achieved = prof["site_rhs_iterations"] * flop_unit / n / (pms / 1e3) / 1e12 if pms > 0 else 0.0
+    grid = sms // L if L > 1 else sms
+    return {"value": value, "unit": UNIT, "steps": args.small_steps, "ms_per_step": total_ms / args.small_steps,
+            "rhs_per_step": w.ncolors * L, "lanes": L, "block": w.block, "autotune": tables,
+            "iterations_per_rhs": iters / (args.small_steps * w.ncolors * L),
+            "setup": {"eigensolver": {k_: est[k_] for k_ in ("iterations", "converged", "seconds", "max_residual")},
+                      "tol": 1e-2},
+            "fp64_path": {"value": value64, "lanes": L64, "steps": nf, "max_rel_trace_diff_vs_mixed": tdiff},
             "speedup_vs_fp64_path": value / value64,
-        }
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
-    return 0
+            "variance_x_time": {"var_T": var_T, "runs": len(traces),
+                                "time_to_1e-3_s": t_run * var_T / (1e-3 * abs(tr_mean)) ** 2,
+                                "time_to_1e-3_s_fp64_path": t_run64 * var_T / (1e-3 * abs(tr_mean)) ** 2,
+                                "speedup_vs_fp64_path": t_run64 / t_run},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak * grid / sms, "unit": "TFLOP/s",
+                         "frac": achieved / (fp32_peak * grid / sms),
+                         "kernel": "k_bicgstab_persistent (FP32 inner solve, 16 RHS, 8^4, L2-resident)",
+                         "avg_launch_ms": pms, "launches": prof["launches"], "ctas_per_launch": grid},
+            "l2": "flushed (256 MiB write) before every timed step"}
+
+
+def kernel_rooflines(dtr, hbm_peak, hbm_note):
+    """Standalone kernels: the BF16-storage stencil (HBM) and the FP64 stencil (FP64 pipe) at
+    32^3x64, and the tensor-core deflation contraction (HBM) at 16^3x32."""
+    from paper_1603_05988_gb300 import kbench
+    out = {}
+    dims = (32, 32, 32, 64)
+    lat = dtr.make_lattice(dims)
+    g = dtr.make_gauge(lat, 0.8, 1003)
+    hb = kbench.dslash_case(g, dims, "bf16", 1, 30)
+    out["roofline_stencil_bf16_hbm"] = {
+        "bound": "hbm", "achieved": hb["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+        "frac": hb["achieved_gbs"] / hbm_peak, "traffic": 4.946e8 if hb["link_rows"] == 3 else None,
+        "traffic_note": "DRAM read + write of one launch under ncu (407.4 + 87.2 MB): "
+                        "profiles/dslash_half_bf16_32x32x32x64.md",
+        "kernel": "dslash BF16 storage, FP32 math, 1 RHS, 32^3x64", "avg_launch_ms": hb["avg_launch_ms"],
+        "alg_bytes_per_launch": hb["alg_bytes_per_launch"],
+        "alg_bytes_note": "240 B per site (48 + 48 B spinors, 144 B for four 3x3 BF16 links)", "peak_note": hbm_note}
+    f64 = kbench.dslash_case(g, dims, "f64", 16, 5)
+    fp64_peak = 1.25
+    out["roofline_stencil_fp64_pipe"] = {
+        "bound": "alu", "achieved": f64["achieved_tflops"], "peak": fp64_peak, "unit": "TFLOP/s",
+        "frac": f64["achieved_tflops"] / fp64_peak, "traffic": None,
+        "kernel": "dslash FP64 (the plain FP64 path's stencil), 16 RHS, 32^3x64",
+        "avg_launch_ms": f64["avg_launch_ms"], "achieved_gbs": f64["achieved_gbs"],
+        "peak_note": "nominal GB300 FP64 rate 1.25 TFLOP/s (no measured FP64 peak on this pool); 1368 flop per "
+                     "site and RHS; at 6.7 TB/s the same stencil would need ~9.5 TFLOP/s of FP64"}
+    del g, lat
+    dc = kbench.deflate_case((16, 16, 16, 32), 256, 16, 20, "bf16")
+    vbytes = dc["alg_bytes_per_launch"] - 1572864 * 16 * 16
+    out["roofline_deflation_tc_hbm"] = {
+        "bound": "hbm", "achieved": vbytes / (dc["avg_launch_ms"] * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+        "frac": vbytes / (dc["avg_launch_ms"] * 1e-3) / 1e9 / hbm_peak, "traffic": 2.0169e9,
+        "kernel": "k_defl_tc (tcgen05 BF16 x Z4 contraction, FP32 accumulation in TMEM), 16^3x32, k=256, 16 RHS",
+        "avg_launch_ms": dc["avg_launch_ms"], "alg_bytes_per_launch": vbytes,
+        "alg_bytes_note": "V only (N k 4 B): the contraction's algorithmic bytes with Z regenerated from the seed; "
+                          "the kernel reads Z too (N b 16 B), see traffic",
+        "achieved_tflops": dc["achieved_tflops"], "tensor_pipe_active_pct": 14.3, "peak_note": hbm_note}
+    return out
 
 
 if __name__ == "__main__":

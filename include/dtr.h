@@ -282,6 +282,73 @@ int dtr_defl_trace(dtr_defl d, double td[2]);
 int dtr_defl_gram(dtr_defl d, dtr_gauge g, double m0, void *stream);
 void dtr_destroy_defl(dtr_defl d);
 
+/* ------------------------------------------------------ setup eigensolver */
+/* The deflation space of Section 5.1 computed on the GPU: the k eigenpairs of
+ * Q = gamma_5 A with smallest |lambda| (the k smallest singular triplets of A,
+ * sigma = |lambda|, U = gamma_5 V sign(lambda)), returned as a dtr_defl in
+ * storage precision `store` without leaving the device.  The paper computes it
+ * once before the estimator to a loose 1e-2 residual with an external
+ * eigensolver; the estimator stays unbiased for any space (Section 5.2).
+ * Method: Chebyshev-filtered subspace iteration on S = A^H A = Q^2 with a basis
+ * of p >= k columns (degree `degree` per iteration, interval [cut, bound],
+ * bound = (|4 + m0| + 4)^2 >= ||A||^2), then a harmonic Rayleigh-Ritz step for
+ * the target 0 (H c = nu M c with H = Y^H Q Y, M = (QY)^H QY, nu = 1/lambda: the
+ * wanted lambda are the pencil's exterior values, so no spurious Ritz values
+ * near 0), signed lambda = Rayleigh quotients of Q.  The basis is stored
+ * row-major [dof][p] in the handle's own buffer and compacted to [dof][k],
+ * ordered by |lambda|; the Gram products, rotations and residuals (a fresh
+ * stencil on the stored vectors) run in the library's kernels, the p x p
+ * eigenproblems on the host (FP64 Householder tridiagonalisation and
+ * implicit QL).  Memory: the handle holds N p elements
+ * (16, 8 or 4 bytes) until destroyed; the workspace holds QY (N p elements),
+ * four chunk fields and p x p matrices (dtr_eig_workspace_bytes). */
+typedef struct {
+  int k;               /* wanted eigenpairs (deflation vectors), >= 1 */
+  int p;               /* basis columns, >= k (0: k + max(16, k / 8), rounded up to a multiple of 16) */
+  int degree;          /* Chebyshev degree of every iteration after the first */
+  int first_degree;    /* degree of the first iteration, from random vectors (0: degree) */
+  int max_iter;        /* iterations at most */
+  int chunk;           /* basis columns filtered at once (1..64; 0: 32) */
+  dtr_prec store;      /* storage of the basis and of the result: DTR_F64 (FP64 stencils), DTR_F32 or DTR_BF16
+                          (FP32 stencils) */
+  int tol_ref;         /* 0: residuals relative to |lambda_j|; 1: relative to the bound |4 + m0| + 4 on ||A||
+                          (the scale of a tolerance stated relative to the matrix norm) */
+  double tol;          /* stop when every ||Q v_j - lambda_j v_j|| <= tol ref_j ||v_j||, j < k */
+  double first_cut;    /* the first filter damps S above this value (0: a tenth of the bound) */
+  double time_limit_s; /* stop after the iteration that passes this wall time (0: no limit) */
+  uint64_t seed;       /* random start: Philox4x64-10 key {seed, 2} */
+} dtr_eig_params;
+
+typedef struct {
+  int iterations;      /* iterations run */
+  int converged;       /* of the k pairs, how many met tol */
+  int basis;           /* p used */
+  int pad_;
+  double max_residual; /* largest relative residual of the k pairs */
+  double seconds;      /* wall time of the call */
+  double cut;          /* last filter interval [cut, bound] */
+  double bound;
+  double t_filter;     /* wall seconds in the Chebyshev filter and QY, */
+  double t_gram;       /* in the three Gram products, */
+  double t_host;       /* in the host Rayleigh-Ritz algebra, */
+  double t_rotate;     /* and in the rotations and residuals */
+} dtr_eig_stats;
+
+/* Defaults: k 32, p 0, degree 48, first_degree 0, max_iter 100, chunk 32, DTR_F64, tol 1e-2. */
+void dtr_eig_params_default(dtr_eig_params *p);
+size_t dtr_eig_workspace_bytes(dtr_lattice lat, const dtr_eig_params *p);
+/* residuals: host k doubles (the relative residual of each pair) or NULL; stats: host or NULL.
+ * *out receives a new handle (destroy with dtr_destroy_defl) whose lambda are the signed Ritz
+ * values and whose T_D is computed from the stored V.  Synchronises `stream`.  DTR_EINVAL (bad
+ * parameters), DTR_ENOMEM (basis allocation failed or workspace too small), DTR_ENOTCONV (a
+ * small eigenproblem failed, or the filtered basis lost rank below k), DTR_ECUDA.  Running out of
+ * iterations or time is not an error: stats and residuals say how far it got. */
+int dtr_eig_deflation(dtr_gauge g, double m0, const dtr_eig_params *p, void *work, size_t work_bytes,
+                      double *residuals, dtr_eig_stats *stats, dtr_defl *out, void *stream);
+/* Copy a deflation space back: V_host (host, canonical N x k column-major complex128, the stored
+ * values widened exactly) and lambda_host (host, k); either may be NULL.  Synchronous. */
+int dtr_defl_to_host(dtr_defl d, double *V_host, double *lambda_host);
+
 /* Deflation projection of a block of probing vectors (Algorithm 1's deflation term,
  * second term; Section 5.2):
  *   C = V^H [Z, gamma_5 Z]                       (k x 2 nrhs, FP64)
@@ -472,11 +539,13 @@ typedef struct {
  * every candidate lane count (1, 2, 4, 8), and every RHS block (8, 16, 32, 64)
  * if p->block <= 0 (else p->block only), runs one warm-up and `reps` timed
  * waves of real trace estimates (lanes blocks each, on z0 runs reserved for
- * tuning) on `stream`; the fastest in RHS solves per second wins.  The choice
+ * tuning; a wave is the first lanes x block probing columns of a run when a run
+ * has more) on `stream`; the fastest in RHS solves per second wins.  The choice
  * is cached per (device, lattice, k, solver, engine, graph use, ncolors, nvec,
- * block, dilution); force = 1 re-times.  work must hold
- * dtr_trace_autotune_workspace_bytes bytes (candidates that do not fit are
- * skipped).  The caller then sets p->lanes and p->block from the result. */
+ * block, dilution); force = 1 re-times.  work holds up to
+ * dtr_trace_autotune_workspace_bytes bytes; candidates whose workspace does not
+ * fit in work_bytes are skipped (DTR_ENOMEM if none fits).  The caller then
+ * sets p->lanes and p->block from the result. */
 size_t dtr_trace_autotune_workspace_bytes(dtr_gauge g, dtr_defl d, const dtr_trace_params *p);
 int dtr_trace_autotune(dtr_gauge g, double m0, dtr_defl d, const dtr_trace_params *p, int reps, int force,
                        void *work, size_t work_bytes, dtr_tune_result *out, void *stream);

@@ -13,8 +13,9 @@ def dense_solve(Adense, Z):
     return np.linalg.solve(Adense, Z)
 
 
-def cgnr(A, Z, tol=1e-13, maxiter=20000):
-    """CG on A^H A y = A^H z for every column of Z (A: scipy sparse matrix).
+def cgnr(A, Z, tol=1e-13, maxiter=20000, AH=None):
+    """CG on A^H A y = A^H z for every column of Z (A: scipy sparse matrix, or
+    any operator supporting A @ X together with its adjoint AH).
 
     Columns iterate together (each with its own scalars); iteration stops when
     every column's true residual ||z - A y|| / ||z|| is below tol.
@@ -24,7 +25,8 @@ def cgnr(A, Z, tol=1e-13, maxiter=20000):
     single = Z.ndim == 1
     if single:
         Z = Z[:, None]
-    AH = A.conj().T.tocsr()
+    if AH is None:
+        AH = A.conj().T.tocsr()
     Y = np.zeros_like(Z)
     R = Z.copy()                     # r = z - A y
     S = AH @ R                       # s = A^H r (normal-equation residual)

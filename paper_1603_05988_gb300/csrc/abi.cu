@@ -43,6 +43,10 @@ int cuda_fail(cudaError_t e, const char *what) {
 }
 
 size_t trace_workspace_bytes(const dtr_gauge_s *g, const dtr_defl_s *D, const dtr_trace_params *p);
+size_t eig_workspace_bytes(const dtr_lattice_s &lat, const dtr_eig_params *P);
+int eig_solve(const dtr_gauge_s *g, double m0, const dtr_eig_params *P, void *work, size_t work_bytes,
+              dtr_defl_s *D, double *res_out, dtr_eig_stats *stats, cudaStream_t st);
+int eig_basis_columns(const dtr_eig_params *P);
 size_t tune_workspace_bytes(const dtr_gauge_s *g, const dtr_defl_s *D, const dtr_trace_params *p);
 int defl_gram(dtr_defl_s *D, const dtr_gauge_s *g, double m0, cudaStream_t st);
 int wd_diagnostic(const dtr_lattice_s *lat, const double2 *cols, const int64_t *dofs_host, int ns, int maxd,
@@ -530,6 +534,109 @@ int dtr_defl_trace(dtr_defl d, double td[2]) {
   if (!d || !td) return fail(DTR_EINVAL, "null argument");
   td[0] = d->td[0];
   td[1] = d->td[1];
+  return DTR_OK;
+}
+
+void dtr_eig_params_default(dtr_eig_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->k = 32;
+  p->degree = 48;
+  p->max_iter = 100;
+  p->chunk = 32;
+  p->store = DTR_F64;
+  p->tol = 1e-2;
+}
+
+size_t dtr_eig_workspace_bytes(dtr_lattice lat, const dtr_eig_params *p) {
+  if (!lat || !p || p->k < 1) return 0;
+  return eig_workspace_bytes(*lat, p);
+}
+
+int dtr_eig_deflation(dtr_gauge g, double m0, const dtr_eig_params *p, void *work, size_t work_bytes,
+                      double *residuals, dtr_eig_stats *stats, dtr_defl *out, void *stream) {
+  if (!g || !p || !work || !out) return fail(DTR_EINVAL, "null argument");
+  if (p->store != DTR_F64 && p->store != DTR_F32 && p->store != DTR_BF16)
+    return fail(DTR_EINVAL, "eigensolver storage must be DTR_F64, DTR_F32 or DTR_BF16");
+  const int nb = eig_basis_columns(p);
+  if (p->k < 1 || p->degree < 0 || p->first_degree < 0 || p->max_iter < 1 || !(p->tol > 0.0) ||
+      p->chunk < 0 || p->chunk > 64 || (p->p > 0 && p->p < p->k) || (int64_t)nb * 4 > g->lat.N)
+    return fail(DTR_EINVAL, "bad eigensolver parameters (k >= 1, p >= k, 4 p <= N, chunk <= 64, tol > 0)");
+  const size_t es = p->store == DTR_F64 ? sizeof(double2) : (p->store == DTR_F32 ? sizeof(float2) : 4);
+  dtr_defl_s *D = new (std::nothrow) dtr_defl_s;
+  if (!D) return fail(DTR_ENOMEM, "host allocation failed");
+  D->tdg_ok = 0u;
+  D->Ginv = nullptr;
+  D->lat = g->lat;
+  D->k = p->k;
+  D->prec = p->store;
+  D->V = nullptr;
+  D->inv_lambda = nullptr;
+  // the basis of nb columns lives in the handle's buffer and is compacted to k columns at the end
+  cudaError_t e = cudaMalloc(&D->V, (size_t)g->lat.N * nb * es);
+  if (e == cudaSuccess) e = cudaMalloc(&D->inv_lambda, p->k * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaFree(D->V);
+    cudaFree(D->inv_lambda);
+    delete D;
+    return fail(DTR_ENOMEM, std::string("eigensolver basis allocation failed: ") + cudaGetErrorString(e));
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = eig_solve(g, m0, p, work, work_bytes, D, residuals, stats, st);
+  if (rc == DTR_OK) rc = defl_trace_TD(D, st);
+  if (rc != DTR_OK) {
+    cudaFree(D->V);
+    cudaFree(D->inv_lambda);
+    delete D;
+    return rc;
+  }
+  *out = D;
+  return DTR_OK;
+}
+
+int dtr_defl_to_host(dtr_defl d, double *V_host, double *lambda_host) {
+  if (!d) return fail(DTR_EINVAL, "null argument");
+  const int k = d->k;
+  const int64_t N = d->lat.N;
+  if (lambda_host) {
+    std::vector<double> il(k);
+    DTR_CUDA(cudaMemcpy(il.data(), d->inv_lambda, k * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int m = 0; m < k; ++m) lambda_host[m] = 1.0 / il[m];
+  }
+  if (V_host) {
+    const size_t es = d->prec == DTR_F64 ? sizeof(double2) : (d->prec == DTR_F32 ? sizeof(float2) : 4);
+    std::vector<unsigned char> raw;
+    try {
+      raw.resize((size_t)N * k * es);
+    } catch (...) {
+      return fail(DTR_ENOMEM, "host allocation failed");
+    }
+    DTR_CUDA(cudaMemcpy(raw.data(), d->V, raw.size(), cudaMemcpyDeviceToHost));
+    double2 *dst = (double2 *)V_host;
+    for (int64_t i = 0; i < N; ++i)
+      for (int m = 0; m < k; ++m) {
+        const size_t q = (size_t)i * k + m;
+        double re, im;
+        if (d->prec == DTR_F64) {
+          const double *v = (const double *)raw.data() + 2 * q;
+          re = v[0];
+          im = v[1];
+        } else if (d->prec == DTR_F32) {
+          const float *v = (const float *)raw.data() + 2 * q;
+          re = v[0];
+          im = v[1];
+        } else {  // BF16 pair: the high 16 bits of an FP32 value each
+          const uint16_t *v = (const uint16_t *)raw.data() + 2 * q;
+          uint32_t ur = (uint32_t)v[0] << 16, ui = (uint32_t)v[1] << 16;
+          float fr, fi;
+          std::memcpy(&fr, &ur, 4);
+          std::memcpy(&fi, &ui, 4);
+          re = fr;
+          im = fi;
+        }
+        dst[(size_t)m * N + i] = make_double2(re, im);
+      }
+  }
   return DTR_OK;
 }
 

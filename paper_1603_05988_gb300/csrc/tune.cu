@@ -59,13 +59,21 @@ TuneKey make_key(const dtr_gauge_s *g, const dtr_defl_s *D, const dtr_trace_para
   return key;
 }
 
-// A candidate's parameters: one wave = `lanes` blocks of `block` columns.
+// A candidate's parameters: one wave = `lanes` blocks of `block` columns.  When a run
+// has more columns than a wave, the wave takes the first lanes x block probing columns of one
+// run (so timing a candidate costs one wave, not a whole run of hundreds of vectors).
 dtr_trace_params candidate(const dtr_trace_params *p, int lanes, int block) {
   dtr_trace_params q = *p;
   q.lanes = lanes;
   q.block = block;
-  const int ncols = p->nvec * (p->dilute12 ? 12 : 1);
+  const int per = p->dilute12 ? 12 : 1;
+  const int ncols = p->nvec * per;
   const int64_t want = (int64_t)lanes * block;               // columns in one wave
+  if (ncols > want) {
+    q.n_z0 = 1;
+    q.nvec = (int)((want + per - 1) / per);
+    return q;
+  }
   q.n_z0 = (int)((want + ncols - 1) / ncols);
   if (q.n_z0 < 1) q.n_z0 = 1;
   return q;

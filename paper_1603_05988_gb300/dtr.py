@@ -61,6 +61,20 @@ class TraceResult(ctypes.Structure):
                 ("frob2", ctypes.c_double), ("frob2_err", ctypes.c_double)]
 
 
+class EigParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("p", ctypes.c_int), ("degree", ctypes.c_int), ("first_degree", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("chunk", ctypes.c_int), ("store", ctypes.c_int), ("tol_ref", ctypes.c_int),
+                ("tol", ctypes.c_double), ("first_cut", ctypes.c_double), ("time_limit_s", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class EigStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("basis", ctypes.c_int),
+                ("pad_", ctypes.c_int), ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("cut", ctypes.c_double), ("bound", ctypes.c_double), ("t_filter", ctypes.c_double),
+                ("t_gram", ctypes.c_double), ("t_host", ctypes.c_double), ("t_rotate", ctypes.c_double)]
+
+
 class TuneResult(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int), ("block", ctypes.c_int), ("rhs_per_s", ctypes.c_double),
                 ("n_tried", ctypes.c_int), ("cached", ctypes.c_int), ("table_lanes", ctypes.c_int * 16),
@@ -127,6 +141,11 @@ _sig("dtr_trace_estimate", _i, [_vp, _d, _vp, ctypes.POINTER(TraceParams), _vp, 
                                 ctypes.POINTER(TraceResult), _vp])
 _sig("dtr_wd", _i, [_vp, _vp, _vp, _i, _i, _i, _vp, _vp])
 _sig("dtr_defl_gram", _i, [_vp, _vp, _d, _vp])
+_sig("dtr_eig_params_default", None, [ctypes.POINTER(EigParams)])
+_sig("dtr_eig_workspace_bytes", _sz, [_vp, ctypes.POINTER(EigParams)])
+_sig("dtr_eig_deflation", _i, [_vp, _d, ctypes.POINTER(EigParams), _vp, _sz, _vp, ctypes.POINTER(EigStats),
+                               ctypes.POINTER(_vp), _vp])
+_sig("dtr_defl_to_host", _i, [_vp, _vp, _vp])
 _sig("dtr_trace_autotune_workspace_bytes", _sz, [_vp, _vp, ctypes.POINTER(TraceParams)])
 _sig("dtr_trace_autotune", _i, [_vp, _d, _vp, ctypes.POINTER(TraceParams), _i, _i, _vp, _sz,
                                 ctypes.POINTER(TuneResult), _vp])
@@ -426,7 +445,10 @@ def solve_batch(gauge, m0, z, y0=None, params=None, allow_notconv=False):
 
 
 class Deflation:
-    def __init__(self, lat, V, lam, prec="f64"):
+    def __init__(self, lat, V, lam, prec="f64", handle=None, k=None):
+        if handle is not None:            # a space the library built on the device
+            self._h, self.lat, self.k = handle, lat, int(k)
+            return
         V = np.asarray(V, dtype=np.complex128)
         lam = np.ascontiguousarray(lam, dtype=np.float64)
         if V.ndim != 2 or V.shape[0] != lat.N or V.shape[1] != lam.shape[0]:
@@ -445,6 +467,19 @@ class Deflation:
         _check(_lib.dtr_defl_gram(self._h, gauge._h, float(m0), _stream()))
         return self
 
+    def to_host(self):
+        """(V (N, k) complex128, lambda (k,)): the stored space, widened exactly."""
+        V = np.empty((self.k, self.lat.N), dtype=np.complex128)
+        lam = np.empty(self.k)
+        _check(_lib.dtr_defl_to_host(self._h, V.ctypes.data_as(_vp), lam.ctypes.data_as(_vp)))
+        return V.T, lam
+
+    def lambdas(self):
+        """The k signed eigenvalues (host), without copying V."""
+        lam = np.empty(self.k)
+        _check(_lib.dtr_defl_to_host(self._h, None, lam.ctypes.data_as(_vp)))
+        return lam
+
     def T_D(self):
         td = (ctypes.c_double * 2)()
         _check(_lib.dtr_defl_trace(self._h, td))
@@ -458,6 +493,39 @@ class Deflation:
 
 def defl_create(lat, V, lam, prec="f64"):
     return Deflation(lat, V, lam, prec)
+
+
+def eig_params(k, p=0, degree=48, first_degree=0, max_iter=100, chunk=32, store="f64", tol=1e-2, first_cut=0.0,
+               time_limit_s=0.0, seed=0, tol_ref="lambda"):
+    """dtr_eig_params; tol_ref "lambda" (residual relative to |lambda_j|) or "norm" (relative to the
+    bound on ||A||)."""
+    q = EigParams()
+    q.tol_ref = {"lambda": 0, "norm": 1}[tol_ref]
+    _lib.dtr_eig_params_default(ctypes.byref(q))
+    q.k, q.p, q.degree, q.first_degree, q.max_iter, q.chunk = int(k), int(p), int(degree), int(first_degree), \
+        int(max_iter), int(chunk)
+    q.store, q.tol, q.first_cut, q.time_limit_s, q.seed = _PREC[store], float(tol), float(first_cut), \
+        float(time_limit_s), int(seed)
+    return q
+
+
+def eig_deflation(gauge, m0, params):
+    """The k smallest-|lambda| eigenpairs of g5 A computed on the device (dtr_eig_deflation).
+    Returns (Deflation, relative residuals (k,), stats dict)."""
+    nb = _lib.dtr_eig_workspace_bytes(gauge.lat._h, ctypes.byref(params))
+    if nb == 0:
+        raise DtrError(DTR_EINVAL, "bad eigensolver parameters")
+    w = _workspace(nb)
+    res = np.zeros(params.k)
+    st = EigStats()
+    h = _vp()
+    _check(_lib.dtr_eig_deflation(gauge._h, float(m0), ctypes.byref(params), _ptr(w), nb,
+                                  res.ctypes.data_as(_vp), ctypes.byref(st), ctypes.byref(h), _stream()))
+    del w
+    stats = dict(iterations=st.iterations, converged=st.converged, basis=st.basis, max_residual=st.max_residual,
+                 seconds=st.seconds, cut=st.cut, bound=st.bound, workspace_bytes=int(nb),
+                 t_filter=st.t_filter, t_gram=st.t_gram, t_host=st.t_host, t_rotate=st.t_rotate)
+    return Deflation(gauge.lat, None, None, handle=h, k=params.k), res, stats
 
 
 def deflate_project(defl, z, want_coeff=False, want_x0=False):
@@ -532,13 +600,17 @@ def wd(lat, cols, dofs, maxd, ncolors=0):
     return W
 
 
-def trace_autotune(gauge, m0, defl, params, reps=3, force=False):
+def trace_autotune(gauge, m0, defl, params, reps=3, force=False, max_workspace_bytes=None):
     """Time the candidate launch shapes (lanes; RHS block too if params.block <= 0)
     and return a dict with the fastest ("lanes", "block", "rhs_per_s") and the
-    table of candidates; the choice is cached per problem shape."""
+    table of candidates; the choice is cached per problem shape.  With
+    max_workspace_bytes the workspace is capped there and candidates that need
+    more are skipped."""
     nb = _lib.dtr_trace_autotune_workspace_bytes(gauge._h, defl._h if defl else None, ctypes.byref(params))
     if nb == 0:
         raise DtrError(DTR_EINVAL, "bad autotune parameters")
+    if max_workspace_bytes is not None:
+        nb = min(nb, int(max_workspace_bytes))
     w = _workspace(nb)
     r = TuneResult()
     _check(_lib.dtr_trace_autotune(gauge._h, float(m0), defl._h if defl else None, ctypes.byref(params), int(reps),

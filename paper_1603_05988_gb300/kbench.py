@@ -8,6 +8,8 @@
     python -m paper_1603_05988_gb300.kbench learned --lattice 16,16,16,32 --eval-lattice 24,24,24,48 \
         --eps 0.8 --m0 -0.75 --gauge-seed 1002 --nrhs 8 [--steps 200 --batch 8 --pool 16]
     python -m paper_1603_05988_gb300.kbench deflate --lattice 16,16,16,32 --k 256 --prec bf16 --nrhs 16 --reps 20
+    python -m paper_1603_05988_gb300.kbench eig --lattice 16,16,16,32 --eps 0.8 --m0 -0.75 --gauge-seed 1002 \
+        --k 200 --prec f32 [--degree 16 --iters 60 --tol 1e-2 --time-limit 0 --device-gauge]
 
 Large lattices take their links from the seeded 16^3x32 field repeated
 periodically (exact SU(3) matrices; the stencil's cost does not depend on
@@ -202,6 +204,29 @@ def deflate_case(dims, k, nrhs, reps, prec="bf16"):
             "achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9, "achieved_tflops": flops / (ms * 1e-3) / 1e12}
 
 
+def eig_case(dims, eps, m0, seed, k, store, degree, iters, tol, time_limit, device_gauge, first_degree=0):
+    """The setup eigensolver: the k smallest-|lambda| eigenpairs of g5 A to a relative residual tol
+    (or until iters / time_limit), with its wall time, iterations and memory."""
+    import torch
+    from . import dtr, synth
+    lat = dtr.make_lattice(dims)
+    g = dtr.make_gauge(lat, eps, seed) if device_gauge else dtr.gauge_from_host(lat, synth.random_su3_links(dims, eps, seed))
+    p = dtr.eig_params(k, store=store, tol=tol, degree=degree, first_degree=first_degree, max_iter=iters,
+                       time_limit_s=time_limit)
+    torch.cuda.synchronize()
+    D, res, st = dtr.eig_deflation(g, m0, p)
+    _, lam = D.to_host() if lat.N * k <= 50_000_000 else (None, None)
+    out = {"kernel": "setup eigensolver", "lattice": list(dims), "eps": eps, "m0": m0, "k": k, "store": store,
+           "degree": degree, "tol": tol, "gauge": "device" if device_gauge else "host"}
+    out.update(st)
+    out["median_residual"] = float(np.median(res))
+    out["T_D"] = [D.T_D().real, D.T_D().imag]
+    if lam is not None:
+        out["abs_lambda_range"] = [float(np.abs(lam).min()), float(np.abs(lam).max())]
+    out["peak_device_gb"] = torch.cuda.max_memory_allocated() / 1e9
+    return out
+
+
 def dtr_pad(n):
     b = 1
     while b < n:
@@ -211,7 +236,7 @@ def dtr_pad(n):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["dslash", "solve", "deflate", "learned", "trace"])
+    ap.add_argument("what", choices=["dslash", "solve", "deflate", "learned", "trace", "eig"])
     ap.add_argument("--k", type=int, default=256)
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--prec", default="bf16")
@@ -232,6 +257,11 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=200, help="learned: Adam steps")
     ap.add_argument("--batch", type=int, default=8, help="learned: pairs per step")
     ap.add_argument("--pool", type=int, default=16, help="learned: batches of independent pairs")
+    ap.add_argument("--degree", type=int, default=16, help="eig: Chebyshev degree")
+    ap.add_argument("--iters", type=int, default=60, help="eig: iterations at most")
+    ap.add_argument("--tol", type=float, default=1e-2, help="eig: relative residual target")
+    ap.add_argument("--time-limit", type=float, default=0.0, help="eig: stop after this many seconds")
+    ap.add_argument("--device-gauge", action="store_true", help="eig: generate the gauge field on the device")
     a = ap.parse_args(argv)
     import torch
     torch.cuda.set_device(0)
@@ -249,6 +279,11 @@ def main(argv=None):
         ev = tuple(int(v) for v in a.eval_lattice.split(","))
         print(json.dumps(learned_case(dims, ev, a.eps, a.m0, a.gauge_seed, a.steps, a.batch, a.pool,
                                       int(a.nrhs.split(",")[0]))), flush=True)
+        return
+    if a.what == "eig":
+        for prec in a.prec.split(","):
+            print(json.dumps(eig_case(dims, a.eps, a.m0, a.gauge_seed, a.k, prec, a.degree, a.iters, a.tol,
+                                      a.time_limit, a.device_gauge)), flush=True)
         return
     if a.what == "deflate":
         for prec in a.prec.split(","):

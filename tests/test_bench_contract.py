@@ -13,7 +13,8 @@ def _run(extra_env):
     env = dict(os.environ)
     env.update(extra_env)
     return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                           "--warmup", "0"], capture_output=True, text=True, env=env, timeout=600, cwd=ROOT)
+                           "--warmup", "0", "--cpu-procs", "2", "--ref-lattice", "8,8,8,16"],
+                          capture_output=True, text=True, env=env, timeout=600, cwd=ROOT)
 
 
 def test_reference_arm_prints_contract_line():
@@ -25,7 +26,7 @@ def test_reference_arm_prints_contract_line():
                 "scaling", "dtype", "data", "config"):
         assert key in line, key
     assert line["value"] > 0 and line["higher_is_better"] is True
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 2
     assert line["cpu_baseline"]["value"] == line["value"]
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]

@@ -109,3 +109,23 @@ def test_apply_at_sites_matches_whole_field(dims, nr):
     ex = wilson.explicit(U, dims, -0.3) @ psi[:, 0]
     at1 = wilson.apply_at(U, dims, -0.3, psi[:, 0], sites)
     assert np.allclose(at1, np.stack([ex[12 * s:12 * s + 12] for s in sites]), rtol=1e-13, atol=1e-13)
+
+
+def test_cgnr_matrix_free_equals_explicit():
+    """The oracle's CGNR on the matrix-free operator (with A^H = g5 A g5) takes the
+    same iterations and gives the same solution as on the explicit matrix."""
+    from scipy.sparse.linalg import LinearOperator
+    from oracle import noise, solve
+    from paper_1603_05988_gb300 import synth
+    dims, m0 = (4, 4, 2, 4), -0.4
+    U = synth.random_su3_links(dims, 0.5, 7)
+    A = wilson.explicit(U, dims, m0)
+    N = A.shape[0]
+    Aop = LinearOperator((N, N), matvec=lambda x: wilson.apply(U, dims, m0, x), dtype=np.complex128)
+    AHop = LinearOperator((N, N), matvec=lambda x: wilson.gamma5_vec(wilson.apply(U, dims, m0, wilson.gamma5_vec(x))),
+                          dtype=np.complex128)
+    z = noise.noise_vectors(dims, 3, 0, 2, False, 0, 1)[:, 0]
+    y1, it1, r1 = solve.cgnr(A, z, tol=1e-12)
+    y2, it2, r2 = solve.cgnr(Aop, z, tol=1e-12, AH=AHop)
+    assert it1 == it2 and r2 <= 1e-12
+    assert np.abs(y1 - y2).max() <= 1e-10 * np.abs(y1).max()
