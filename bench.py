@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--eig-time", type=float, default=100.0,
+    ap.add_argument("--eig-time", type=float, default=45.0,
                     help="wall-time cap (s) of the 32^3x64 setup eigensolver (untimed setup)")
     ap.add_argument("--eig-iters", type=int, default=40, help="iteration cap of the setup eigensolvers")
     ap.add_argument("--f64-steps", type=int, default=2, help="steps of the plain FP64 path timed for comparison")
@@ -82,6 +82,12 @@ def measured_peaks():
         return v, "hbm_gbs of MEASURED_PEAKS.json (of measured)"
     except (OSError, KeyError, ValueError):
         return 6800.0, "6.8 TB/s fallback (MEASURED_PEAKS.json absent; of fallback)"
+
+
+def log(what, **kw):
+    """Progress record on stderr (the result line goes to stdout at the end)."""
+    sys.stderr.write(json.dumps(dict(stage=what, **kw)) + "\n")
+    sys.stderr.flush()
 
 
 def dist_env():
@@ -384,6 +390,8 @@ def main():
                         time_limit_s=args.eig_time, seed=rank)
     defl, eres, est = dtr.eig_deflation(gauge, w.m0, ep)
     torch.cuda.empty_cache()
+    log("32^3x64 setup", **{k_: est[k_] for k_ in ("iterations", "converged", "seconds", "max_residual", "t_filter",
+                                                   "t_gram", "t_host", "t_rotate")})
     bound = (abs(4.0 + w.m0) + 4.0)
     lam = defl.lambdas()
     rn = eres * np.abs(lam) / bound                    # the same residuals relative to the bound on ||A||
@@ -412,19 +420,21 @@ def main():
         tune = dtr.trace_autotune(gauge, w.m0, defl, tp, reps=1, max_workspace_bytes=free - (6 << 30))
         torch.cuda.empty_cache()
     L, B = tune["lanes"], tune["block"]
+    log("32^3x64 autotune", lanes=L, block=B, table=tune.get("table"))
     W = L * B                                          # probing vectors per step
     steps_per_run = ncol // W
-    ws = dtr.TraceWorkspace(gauge, defl, params("mixed_f32", L, B, 0, 0, W))
+    wsh = {"ws": dtr.TraceWorkspace(gauge, defl, params("mixed_f32", L, B, 0, 0, W))}   # current workspace
     base = 1 + rank * 100003
 
-    def step(solver, i, wsp=ws, g=gauge, graph=True):
+    def step(solver, i, g=None, graph=True):
         run = base + i // steps_per_run
         v0 = (i % steps_per_run) * W
-        return dtr.trace_estimate(g, w.m0, defl, params(solver, L, B, run, v0, W, graph), workspace=wsp)
+        return dtr.trace_estimate(g or gauge, w.m0, defl, params(solver, L, B, run, v0, W, graph),
+                                  workspace=wsh["ws"])
 
     # warm-up on runs of their own
     for i in range(args.warmup):
-        dtr.trace_estimate(gauge, w.m0, defl, params("mixed_f32", L, B, 500000 + i, 0, W), workspace=ws)
+        dtr.trace_estimate(gauge, w.m0, defl, params("mixed_f32", L, B, 500000 + i, 0, W), workspace=wsh["ws"])
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
@@ -466,9 +476,14 @@ def main():
     tr_mean = complex(np.mean(traces))
     var_T = float(np.sum(np.abs(np.array(traces) - tr_mean) ** 2) / max(len(traces) - 1, 1))
 
-    # plain FP64 path on the same seeds (the first steps of the timed sequence)
+    log("32^3x64 mixed", value=value, ms_per_step=total_ms / args.steps, lanes=L, block=B,
+        iterations_per_rhs=iters / (args.steps * W), var_T=var_T, trace=[tr_mean.real, tr_mean.imag])
+    # plain FP64 path on the same seeds (the first steps of the timed sequence), in its own workspace
+    wsh["ws"] = None
+    torch.cuda.empty_cache()
+    wsh["ws"] = dtr.TraceWorkspace(gauge, defl, params("f64", L, B, 0, 0, W))
     ms64, diff = [], 0.0
-    step("f64", 0)                                    # warm-up (graph-free FP64 solver)
+    step("f64", 0)                                     # warm-up
     for i in range(args.f64_steps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -479,6 +494,10 @@ def main():
         ms64.append(e0.elapsed_time(e1))
         diff = max(diff, float(np.abs(o64["samples"][0] - samples[i]).max() / np.abs(samples[i]).max()))
     value64 = W * args.f64_steps / (sum(ms64) / 1e3)
+    log("32^3x64 fp64", value=value64, max_rel_sample_diff=diff)
+    wsh["ws"] = None
+    torch.cuda.empty_cache()
+    wsh["ws"] = dtr.TraceWorkspace(gauge, defl, params("mixed_f32", L, B, 0, 0, W))
     t_run = ncol / value * world
     t_run64 = ncol / value64
     ttr = t_run * var_T / (1e-3 * abs(tr_mean)) ** 2
@@ -500,6 +519,7 @@ def main():
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_value = W * args.steps * world / e2e_s
+    log("32^3x64 e2e", value=e2e_value)
     up_bytes = U_np.nbytes
     del gauge_e, U_pin, U_np
 
@@ -525,7 +545,7 @@ def main():
                         "deflation space (setup output, %.1f GB) stays resident" % (up_bytes, args.steps,
                                                                                     lat.N * w.k * 4 / 1e9)},
     }
-    del ws
+    wsh["ws"] = None
     torch.cuda.empty_cache()
 
     # ------------------------------------------------------ the 8^4 workload
@@ -534,9 +554,12 @@ def main():
         del defl, gauge
         torch.cuda.empty_cache()
         small = measure_small(args, dtr, synth, torch, barrier, max_over_ranks, sms, hbm_peak, hbm_note, rank, world)
+        log("8^4", value=small["value"], speedup_vs_fp64_path=small["speedup_vs_fp64_path"],
+            setup=small["setup"])
 
     # ------------------------------------------- standalone kernel rooflines
     kern = {} if args.skip_kernels else kernel_rooflines(dtr, hbm_peak, hbm_note)
+    log("kernels", **{k_: round(v["frac"], 4) for k_, v in kern.items()})
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:

@@ -294,7 +294,8 @@ void dtr_destroy_defl(dtr_defl d);
  * bound = (|4 + m0| + 4)^2 >= ||A||^2), then a harmonic Rayleigh-Ritz step for
  * the target 0 (H c = nu M c with H = Y^H Q Y, M = (QY)^H QY, nu = 1/lambda: the
  * wanted lambda are the pencil's exterior values, so no spurious Ritz values
- * near 0), signed lambda = Rayleigh quotients of Q.  The basis is stored
+ * near 0), signed lambda = the harmonic Ritz values 1/nu (equal to the Rayleigh quotients for
+ * converged pairs; for unconverged ones |1/lambda| <= 1/sigma_min stays bounded).  The basis is stored
  * row-major [dof][p] in the handle's own buffer and compacted to [dof][k],
  * ordered by |lambda|; the Gram products, rotations and residuals (a fresh
  * stencil on the stored vectors) run in the library's kernels, the p x p

@@ -837,7 +837,7 @@ size_t dtr_time_deflate_workspace_bytes(dtr_defl d, int nrhs) {
   if (!d || nrhs < 1 || nrhs > 64) return 0;
   const int b = pad_rhs(nrhs);
   return (((size_t)d->lat.V * 12 * b * sizeof(double2) + 255) / 256) * 256 + 64 * sizeof(double2) + 256 +
-         defl_scratch_bytes(d->lat.V, d->k, b, device_sms()) + 256;
+         defl_scratch_bytes(d->lat.V, d->k, b, device_sms()) + 256 + (((size_t)d->lat.V * 12 * b + 255) / 256) * 256;
 }
 
 int dtr_time_deflate(dtr_defl d, int nrhs, int reps, void *work, size_t work_bytes, double *avg_ms, void *stream) {
@@ -853,15 +853,16 @@ int dtr_time_deflate(dtr_defl d, int nrhs, int reps, void *work, size_t work_byt
   double2 *dd = (double2 *)w;
   w += 64 * sizeof(double2) + 256;
   const size_t sb = defl_scratch_bytes(d->lat.V, d->k, b, device_sms());
-  launch_noise(Z, geo, 0x5EED, 0, 1, 0, 0, 1, nrhs, b, st);  // one Z4 vector per column
-  int rc = defl_project_internal(d, Z, b, dd, nullptr, nullptr, nullptr, w, sb, device_sms(), st, 1);  // warm
+  unsigned char *Zc = (unsigned char *)(w + ((sb + 255) / 256) * 256);  // the block as one-byte codes
+  launch_noise(Z, geo, 0x5EED, 0, 1, 0, 0, 1, nrhs, b, st, 0, Zc);  // one Z4 vector per column
+  int rc = defl_project_internal(d, Z, b, dd, nullptr, nullptr, nullptr, w, sb, device_sms(), st, 1, Zc);  // warm
   if (rc) return rc;
   cudaEvent_t e0, e1;
   DTR_CUDA(cudaEventCreate(&e0));
   DTR_CUDA(cudaEventCreate(&e1));
   DTR_CUDA(cudaEventRecord(e0, st));
   for (int r = 0; r < reps && rc == DTR_OK; ++r)
-    rc = defl_project_internal(d, Z, b, dd, nullptr, nullptr, nullptr, w, sb, device_sms(), st, 1);
+    rc = defl_project_internal(d, Z, b, dd, nullptr, nullptr, nullptr, w, sb, device_sms(), st, 1, Zc);
   DTR_CUDA(cudaEventRecord(e1, st));
   DTR_CUDA(cudaEventSynchronize(e1));
   float ms = 0.f;

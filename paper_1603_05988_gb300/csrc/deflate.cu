@@ -345,7 +345,7 @@ int *defl_error_word(void *work) { return (int *)(((uintptr_t)work + 255) & ~(ui
 
 int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 *d_dev, double2 *terms_dev,
                           double2 *x0_internal, double2 **C_out, void *work, size_t work_bytes, int sms,
-                          cudaStream_t st, int z4) {
+                          cudaStream_t st, int z4, const unsigned char *Zc) {
   const int64_t V = D->lat.V;
   const int k = D->k;
   if (work_bytes < defl_scratch_bytes(V, k, b, sms)) return fail(DTR_ENOMEM, "deflation workspace too small");
@@ -368,7 +368,7 @@ int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 
   const int64_t nkb = (int64_t)k * b;
   if (z4 && defl_tc_enabled(D, b)) {
     DTR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-    int rc = defl_contract_tc(D, Z, b, C, partial, partbytes, err, sms, st);
+    int rc = defl_contract_tc(D, Z, b, C, partial, partbytes, err, sms, st, Zc);
     if (rc) return rc;
   } else {
   if (D->prec == DTR_F64)

@@ -26,15 +26,17 @@ size_t defl_scratch_bytes(int64_t V, int k, int b, int sms);  // includes k x b 
 // z4: the caller guarantees Z's entries are 0, +-1 or +-i (probing noise); with
 // a BF16-stored V the contraction then runs on the tensor cores (deflate_tc.cu),
 // and a stalled tensor-core stage raises *defl_error_word(work).
+// Zc (or NULL): Z's entries as one-byte codes (launch_noise), read by the tensor-core path
+// instead of the FP64 values.
 int defl_project_internal(const dtr_defl_s *D, const double2 *Z, int b, double2 *d_dev, double2 *terms_dev,
                           double2 *x0_internal, double2 **C_out, void *work, size_t work_bytes, int sms,
-                          cudaStream_t st, int z4 = 0);
+                          cudaStream_t st, int z4 = 0, const unsigned char *Zc = nullptr);
 int *defl_error_word(void *work);
 // tensor-core contraction C = V^H [Z, g5 Z] for BF16 V and Z4-valued Z (deflate_tc.cu)
 bool defl_tc_enabled(const dtr_defl_s *D, int b);
 size_t defl_tc_scratch_bytes(int64_t V, int k, int b, int sms);
 int defl_contract_tc(const dtr_defl_s *D, const double2 *Z, int b, double2 *C, void *scratch, size_t scratch_bytes,
-                     int *err_dev, int sms, cudaStream_t st);
+                     int *err_dev, int sms, cudaStream_t st, const unsigned char *Zc = nullptr);
 unsigned long long defl_tc_calls();
 
 // d_j (and per-m terms, or NULL) from C (column-major k x 2b): with the

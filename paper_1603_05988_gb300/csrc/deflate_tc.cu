@@ -8,7 +8,9 @@
 //     A[2m + c, i] = c-th part (Re, Im) of V[i][m]   -- V's stored row, as it lies
 //     B[4j + q, i] = Re z, Im z, g5 Re z, g5 Im z  (q = 0..3),  z = Z[i][j]
 // so that V^H z_j = (D[2m, 4j] + D[2m+1, 4j+1]) + i (D[2m, 4j+1] - D[2m+1, 4j])
-// and the same with columns 4j+2, 4j+3 for g5 z_j.
+// and the same with columns 4j+2, 4j+3 for g5 z_j.  The block comes either as
+// its FP64 values or, when the noise generator wrote them, as one-byte codes
+// (z = i^c or 0), so that the kernel reads V plus one byte per entry of Z.
 //
 // A is MN-major in memory (r contiguous in a row of V), so the tensor memory
 // accelerator (TMA) moves it untouched: per stage of 64 dofs, four 64 x 64 boxes
@@ -50,6 +52,8 @@ constexpr size_t kTcMaxSmem = 232448;                  // opt-in shared memory p
 
 struct TcArgs {
   const double2 *Z;    // internal [site][12][b] (dof-major, b columns)
+  const unsigned char *Zc;  // or NULL: the same block as one byte per entry (bits 0-1: z = i^c, bit 2: zero),
+                            // 16x fewer bytes than the FP64 values
   int k, b, logb, N;   // N = MMA N = 4b rounded up to 16; logb = log2 b when b is a power of two, else -1
   int ndof;            // dof indices fit 32 bits (checked on the host)
   int chunk_dofs;      // multiple of kTcStageDofs
@@ -274,10 +278,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
 #pragma unroll
         for (int g = 0; g < 8; ++g) {
           const int i = d0 + 8 * o + g;
-          zv[u][g] = make_uint2(0u, 0u);
+          zv[u][g] = make_uint2(0u, a.Zc ? 4u : 0u);
           if (st < nst && idx < 8 * a.b && i < c1) {
-            const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(a.Z + (int64_t)i * a.b + j));
-            zv[u][g] = make_uint2(w.y, w.w);
+            if (a.Zc) {
+              zv[u][g] = make_uint2(0u, (uint32_t)__ldcs(a.Zc + (int64_t)i * a.b + j));
+            } else {
+              const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(a.Z + (int64_t)i * a.b + j));
+              zv[u][g] = make_uint2(w.y, w.w);
+            }
           }
         }
       }
@@ -297,8 +305,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
         uint32_t re[8], im[8], g5[8];
 #pragma unroll
         for (int g = 0; g < 8; ++g) {
-          re[g] = bf16_of_exact_f64(zv[u][g].x);
-          im[g] = bf16_of_exact_f64(zv[u][g].y);
+          if (a.Zc) {  // code c: z = i^c (bit 0: imaginary, bit 1: negative), bit 2: zero
+            const uint32_t c = zv[u][g].y;
+            const uint32_t v = ((c & 4u) ? 0u : 0x3F80u) | ((c & 2u) ? 0x8000u : 0u);
+            re[g] = (c & 1u) ? 0u : v;
+            im[g] = (c & 1u) ? v : 0u;
+          } else {
+            re[g] = bf16_of_exact_f64(zv[u][g].x);
+            im[g] = bf16_of_exact_f64(zv[u][g].y);
+          }
           g5[g] = (r12 + 8 * o + g) % 12 >= 6 ? 0x8000u : 0u;  // g5 = -1 on spins 2, 3
         }
 #pragma unroll
@@ -455,7 +470,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 }
 
 int defl_contract_tc(const dtr_defl_s *D, const double2 *Z, int b, double2 *C, void *scratch, size_t scratch_bytes,
-                     int *err_dev, int sms, cudaStream_t st) {
+                     int *err_dev, int sms, cudaStream_t st, const unsigned char *Zc) {
   const int k = D->k;
   const int64_t ndof = D->lat.N;
   int N, rt, nc, cd;
@@ -476,6 +491,7 @@ int defl_contract_tc(const dtr_defl_s *D, const double2 *Z, int b, double2 *C, v
     return fail(DTR_ECUDA, "cuTensorMapEncodeTiled failed");
   TcArgs a;
   a.Z = Z;
+  a.Zc = Zc;
   a.k = k;
   a.b = b;
   a.logb = 0;

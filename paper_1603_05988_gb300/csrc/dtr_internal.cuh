@@ -221,9 +221,10 @@ void launch_dslash_half_raw(const void *Uh, void *work, const Geom &g, int b, do
 // noise into internal FP64 layout of width b: block column k is global column
 // g0 + k of the run-major sequence (ncols probing columns per run, runs from
 // run0), probing column qoff + (g0 + k) % ncols of its run; columns nrhs..b-1
-// are zero padding
+// are zero padding.  codes (or NULL): the same entries as one byte each, same
+// layout: bits 0-1 the power c of i (z = i^c), bit 2 set for a zero.
 void launch_noise(double2 *out, const Geom &g, uint64_t seed, int64_t run0, int ncolors, int dilute12, int64_t g0,
-                  int64_t ncols, int nrhs, int b, cudaStream_t st, int64_t qoff = 0);
+                  int64_t ncols, int nrhs, int b, cudaStream_t st, int64_t qoff = 0, unsigned char *codes = nullptr);
 // noise into canonical layout
 void launch_noise_canon(double2 *out, const Geom &g, uint64_t seed, int64_t z0_index, int ncolors,
                         int dilute12, int64_t q0, int nrhs, cudaStream_t st);

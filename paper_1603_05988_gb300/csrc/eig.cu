@@ -21,7 +21,8 @@
 //      H c = nu M c, nu = 1/theta, on an M-orthonormal basis from canonical
 //      orthogonalisation of M (directions with tiny eigenvalues dropped); the
 //      wanted theta near 0 are the exterior |nu|, so no spurious small Ritz
-//      values; eigenvalue estimate = Rayleigh quotient of Q, sorted by |nu|;
+//      values; eigenvalue = the harmonic Ritz value 1/nu (|1/lambda| stays
+//      below 1/sigma_min even for unconverged vectors), sorted by |nu|;
 //   5. Y <- Y C in place (row blocks through a per-CTA buffer), columns
 //      normalised by a norms pass (which also gives the Ritz values of S for
 //      the next filter interval); dropped columns are refilled with random
@@ -676,8 +677,11 @@ static int eig_solve_t(const dtr_gauge_s *gauge, double m0, const dtr_eig_params
     int nch = 4 * device_sms();
     if (nch > N) nch = (int)N;
     // ||y_q||^2 of the rotated columns; then mu_q = ||Q y_q||^2 / ||y_q||^2 = 1 / ||y_q||^2 (the Ritz
-    // value of S), the Rayleigh quotient theta_q = y^H Q y / y^H y = nu_q / ||y_q||^2, and the
-    // columns are scaled to unit length
+    // value of S) and the columns are scaled to unit length.  The eigenvalue kept for a pair is the
+    // harmonic Ritz value theta_q = 1 / nu_q: the same as the Rayleigh quotient y^H Q y / y^H y =
+    // nu_q / ||y_q||^2 once a pair has converged, but for a vector that is not yet an eigenvector
+    // the Rayleigh quotient of the indefinite Q can lie near 0, while |nu_q| = |y^H Q y| / ||Q y||^2
+    // <= 1 / ||Q y|| <= 1 / sigma_min keeps 1 / theta bounded in the deflation
     k_eig_colnorm<T><<<dim3(nch, (r + 127) / 128), 128, 0, st>>>(Y, N, p, r, nch, rpart);
     count_launches(1);
     DTR_LAUNCH_CHECK("eigensolver rotation");
@@ -690,7 +694,7 @@ static int eig_solve_t(const dtr_gauge_s *gauge, double m0, const dtr_eig_params
     double mu_lo = INFINITY, mu_hi = 0.0;
     for (int q = 0; q < r; ++q) {
       mu[q] = 1.0 / y2[q];
-      thq[q] = nu[ord[q]] / y2[q];
+      thq[q] = 1.0 / nu[ord[q]];
       sc[q] = 1.0 / std::sqrt(y2[q]);
       mu_lo = std::min(mu_lo, mu[q]);
       mu_hi = std::max(mu_hi, mu[q]);

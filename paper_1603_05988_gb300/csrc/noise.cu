@@ -14,16 +14,23 @@ namespace dtr {
 // Internal layout [site][12][b]; one thread per (site, column).  Column k of
 // the block is global column G = g0 + k of the run-major sequence
 // (run = run0 + G / ncols, probing index q = qoff + G % ncols).
+// With `codes` non-NULL every entry is also written as one byte in the same layout:
+// bits 0-1 the power c of i (z = i^c), bit 2 set for a zero (dilution, padding).
 __global__ void noise_internal_kernel(double2 *out, Geom g, uint64_t seed, int64_t run0, int ncolors, int dilute12,
-                                      int64_t g0, int64_t ncols, int64_t qoff, int nrhs, int b) {
+                                      int64_t g0, int64_t ncols, int64_t qoff, int nrhs, int b,
+                                      unsigned char *codes) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (int64_t)g.V * b) return;
   const int j = (int)(tid % b);
   const int s = (int)(tid / b);
   double2 *o = out + (int64_t)s * 12 * b + j;
+  unsigned char *oc = codes ? codes + (int64_t)s * 12 * b + j : nullptr;
   if (j >= nrhs) {
 #pragma unroll
-    for (int c = 0; c < 12; ++c) o[c * b] = make_double2(0.0, 0.0);
+    for (int c = 0; c < 12; ++c) {
+      o[c * b] = make_double2(0.0, 0.0);
+      if (oc) oc[c * b] = 4;
+    }
     return;
   }
   int xc[4];
@@ -47,8 +54,10 @@ __global__ void noise_internal_kernel(double2 *out, Geom g, uint64_t seed, int64
     const uint64_t *w = ((i >> 7) == (i0 >> 7)) ? w0 : w1;
     const int code = (int)((w[(i >> 5) & 3] >> (2 * (i & 31))) & 3ull);
     double2 z = z4_value<double2>(code, sign);
-    if (keep >= 0 && c != keep) z = make_double2(0.0, 0.0);
+    const bool zero = keep >= 0 && c != keep;
+    if (zero) z = make_double2(0.0, 0.0);
     o[c * b] = z;
+    if (oc) oc[c * b] = (unsigned char)(zero ? 4 : ((code + (sign < 0 ? 2 : 0)) & 3));
   }
 }
 
@@ -73,11 +82,11 @@ __global__ void noise_canon_kernel(double2 *out, Geom g, uint64_t seed, int64_t 
 }
 
 void launch_noise(double2 *out, const Geom &g, uint64_t seed, int64_t run0, int ncolors, int dilute12, int64_t g0,
-                  int64_t ncols, int nrhs, int b, cudaStream_t st, int64_t qoff) {
+                  int64_t ncols, int nrhs, int b, cudaStream_t st, int64_t qoff, unsigned char *codes) {
   const int64_t n = (int64_t)g.V * b;
   const int T = 256;
   noise_internal_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(out, g, seed, run0, ncolors, dilute12, g0, ncols,
-                                                                    qoff, nrhs, b); count_launches(1);
+                                                                    qoff, nrhs, b, codes); count_launches(1);
 }
 
 void launch_noise_canon(double2 *out, const Geom &g, uint64_t seed, int64_t z0_index, int ncolors, int dilute12,

@@ -176,7 +176,7 @@ constexpr int kMaxLanes = 8;
 
 struct TraceLayout {
   int b, lanes;
-  size_t vec, zdot_red, solver, defl, hp, sites, small, gam, lane, total;
+  size_t vec, zdot_red, solver, defl, hp, sites, small, gam, codes, lane, total;
 };
 
 // Lanes actually used: concurrency needs a solver that can run without
@@ -204,7 +204,9 @@ static TraceLayout trace_layout(const dtr_gauge_s *g, const dtr_defl_s *D, const
   L.lanes = trace_lanes(p);
   // Gamma insertion: copy of the block's C (k x 2b), Gamma^H Z (generic projection), dG and tG (16 x 64)
   L.gam = p->n_gamma > 0 ? al((size_t)k * 2 * 64 * sizeof(double2)) + L.vec + 2 * al(16 * 64 * sizeof(double2)) : 0;
-  L.lane = 2 * L.vec + L.zdot_red + L.solver + L.defl + L.hp + L.small + L.gam;
+  // the block's entries as one-byte codes, read by the tensor-core contraction instead of the FP64 values
+  L.codes = (D && defl_tc_enabled(D, L.b)) ? al((size_t)V * 12 * L.b) : 0;
+  L.lane = 2 * L.vec + L.zdot_red + L.solver + L.defl + L.hp + L.small + L.gam + L.codes;
   L.total = 256 + L.sites + L.lanes * L.lane;
   return L;
 }
@@ -221,6 +223,7 @@ struct Lane {
   void *solver_work = nullptr, *defl_work = nullptr, *hp_work = nullptr;
   double2 *d_dev = nullptr, *t_dev = nullptr, *yn_dev = nullptr, *terms_dev = nullptr;
   double2 *Cmain = nullptr, *GZ = nullptr, *dg = nullptr, *tg = nullptr;  // Gamma insertion
+  unsigned char *Zc = nullptr;                  // Z as one-byte codes (tensor-core contraction)
   double2 *t_h = nullptr, *terms_h = nullptr, *tg_h = nullptr;  // pinned
   Scal *sc_h = nullptr;                         // pinned
   int *err_h = nullptr;                         // pinned
@@ -292,8 +295,9 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
       ln.Cmain = (double2 *)q;  q += al((size_t)k * 2 * 64 * sizeof(double2));
       ln.GZ = (double2 *)q;     q += L.vec;
       ln.dg = (double2 *)q;     q += al(16 * 64 * sizeof(double2));
-      ln.tg = (double2 *)q;
+      ln.tg = (double2 *)q;     q += al(16 * 64 * sizeof(double2));
     }
+    if (L.codes) ln.Zc = (unsigned char *)q;
     int rc = lane_host_buffers(l, k);
     if (rc) return rc;
     ln.t_h = t_pool.t_h[l];
@@ -386,7 +390,7 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
     ln.nb = nb;
     const int64_t q0 = G0 % ncols;
     const bool one_run = q0 + nb <= ncols;
-    launch_noise(ln.Z, g, p->seed, p->z0_first, p->ncolors, p->dilute12, G0, ncols, nb, b, s, qoff);
+    launch_noise(ln.Z, g, p->seed, p->z0_first, p->ncolors, p->dilute12, G0, ncols, nb, b, s, qoff, ln.Zc);
     DTR_LAUNCH_CHECK("noise");
     if (D) {
       int rc;
@@ -403,7 +407,7 @@ int trace_estimate(const dtr_gauge_s *gauge, double m0, const dtr_defl_s *D, con
         ln.hp_run = run;
       } else
         rc = defl_project_internal(D, ln.Z, b, ln.d_dev, res->replay ? ln.terms_dev : nullptr,
-                                   p->use_x0 ? ln.X : nullptr, &Cm, ln.defl_work, L.defl, sms, s, 1);
+                                   p->use_x0 ? ln.X : nullptr, &Cm, ln.defl_work, L.defl, sms, s, 1, ln.Zc);
       if (rc) return rc;
       if (ng) {
         // d^G_j = (V^H Gamma^H z_j)^H Lambda^-1 (V^H g5 z_j): the g5 half of this block's C is kept

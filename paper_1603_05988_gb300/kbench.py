@@ -261,7 +261,7 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=60, help="eig: iterations at most")
     ap.add_argument("--tol", type=float, default=1e-2, help="eig: relative residual target")
     ap.add_argument("--time-limit", type=float, default=0.0, help="eig: stop after this many seconds")
-    ap.add_argument("--device-gauge", action="store_true", help="eig: generate the gauge field on the device")
+    ap.add_argument("--device-gauge", action="store_true", help="eig, solve: generate the gauge field on the device")
     a = ap.parse_args(argv)
     import torch
     torch.cuda.set_device(0)
@@ -293,7 +293,8 @@ def main(argv=None):
     lat = dtr.make_lattice(dims)
     if a.what == "solve":
         from . import synth
-        g = dtr.gauge_from_host(lat, synth.random_su3_links(dims, a.eps, a.gauge_seed))
+        g = dtr.make_gauge(lat, a.eps, a.gauge_seed) if a.device_gauge else \
+            dtr.gauge_from_host(lat, synth.random_su3_links(dims, a.eps, a.gauge_seed))
         for solver in a.solver.split(","):
             for n in a.nrhs.split(","):
                 print(json.dumps(solve_case(g, dims, int(n), a.reps, a.m0, graph=not a.no_graph, solver=solver,
