@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--eig-time", type=float, default=45.0,
                     help="wall-time cap (s) of the 32^3x64 setup eigensolver (untimed setup)")
     ap.add_argument("--eig-iters", type=int, default=40, help="iteration cap of the setup eigensolvers")
+    ap.add_argument("--eig-degree", type=int, default=48, help="Chebyshev degree of the setup eigensolvers")
     ap.add_argument("--f64-steps", type=int, default=2, help="steps of the plain FP64 path timed for comparison")
     ap.add_argument("--var-runs", type=int, default=2, help="complete z0 runs of 512 vectors for Var_T")
     ap.add_argument("--small-steps", type=int, default=48, help="timed steps of the 8^4 workload (extra)")
@@ -63,6 +64,8 @@ def parse():
     ap.add_argument("--skip-kernels", action="store_true", help="skip the standalone kernel roofline lines")
     ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-autotune", action="store_true", help="use --block/--lanes instead of the autotuner")
+    ap.add_argument("--solver", default="auto", choices=["auto", "mixed_f32", "mixed_f16"],
+                    help="inner-solve storage of the mixed solver (auto: the faster on one timed wave)")
     ap.add_argument("--block", type=int, default=32)
     ap.add_argument("--lanes", type=int, default=1)
     ap.add_argument("--cpu-procs", type=int, default=0, help="CPU oracle processes (0: cores, memory permitting)")
@@ -318,12 +321,13 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- GPU path
-def persistent_roofline(prof, sms, lanes, wall_ms, block, hbm_peak, hbm_note, workload):
-    """Roofline of the persistent FP32 BiCGStab kernel from its device-timed launches.
+def persistent_roofline(prof, sms, lanes, wall_ms, block, hbm_peak, hbm_note, workload, vec_bytes=96):
+    """Roofline of the persistent BiCGStab kernel from its device-timed launches.
     Algorithmic bytes per site, RHS and iteration: the fused minimum of one BiCGStab
-    iteration in FP32 storage, two stencils (96 B in + 96 B out + 288 / b B links each)
-    and six vector passes of 96 B; flops 2 x 1368 + 12 x 104."""
-    bytes_unit = 2 * (96 + 96 + 288.0 / block) + 6 * 96
+    iteration, two stencils (a vector in + a vector out + 288 / b B of FP32 links each)
+    and six vector passes, a vector being 96 B per site and RHS in FP32 storage and 48 B
+    in FP16; flops 2 x 1368 + 12 x 104."""
+    bytes_unit = 2 * (2 * vec_bytes + 288.0 / block) + 6 * vec_bytes
     flop_unit = 2 * 1368.0 + 12 * 104.0
     n = max(prof["launches"], 1)
     pms = prof["ms"] / n
@@ -334,11 +338,12 @@ def persistent_roofline(prof, sms, lanes, wall_ms, block, hbm_peak, hbm_note, wo
     share = grid / sms
     fp32_peak = sms * 128 * 2 * 2.07e9 / 1e12
     return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak * share, "unit": "GB/s", "frac": gbs / (hbm_peak * share),
-            "traffic": None, "kernel": "k_bicgstab_persistent (FP32 inner BiCGStab, %d RHS, %s)" % (block, workload),
+            "traffic": None, "kernel": "k_bicgstab_persistent (%s-stored inner BiCGStab, %d RHS, %s)"
+                                       % ("FP32" if vec_bytes == 96 else "FP16", block, workload),
             "avg_launch_ms": pms, "launches": prof["launches"], "alg_bytes_per_launch": units * bytes_unit,
-            "alg_bytes_note": "%.0f B per site, RHS and iteration (two FP32 stencils 2 x (96 + 96 + 288/%d) + six "
-                              "96 B vector passes: the fused minimum) x site-RHS-iterations of the launch"
-                              % (bytes_unit, block),
+            "alg_bytes_note": "%.0f B per site, RHS and iteration (two stencils 2 x (%d + %d + 288/%d) + six "
+                              "%d B vector passes: the fused minimum) x site-RHS-iterations of the launch"
+                              % (bytes_unit, vec_bytes, vec_bytes, block, vec_bytes),
             "peak_note": hbm_note + "; times the launch's SM share %d/%d" % (grid, sms),
             "fp32": {"achieved_tflops": tfl, "peak_tflops": fp32_peak * share, "frac": tfl / (fp32_peak * share),
                      "note": "3984 flop per site, RHS and iteration; FP32 peak = SMs x 128 x 2 x 2.07 GHz (nominal)"},
@@ -386,7 +391,7 @@ def main():
     t0 = time.perf_counter()
     gauge = dtr.make_gauge(lat, w.eps, w.gauge_seed)
     t_gauge = time.perf_counter() - t0
-    ep = dtr.eig_params(w.k, store=w.defl_prec, tol=1e-2, degree=48, max_iter=args.eig_iters,
+    ep = dtr.eig_params(w.k, store=w.defl_prec, tol=1e-2, degree=args.eig_degree, max_iter=args.eig_iters,
                         time_limit_s=args.eig_time, seed=rank)
     defl, eres, est = dtr.eig_deflation(gauge, w.m0, ep)
     torch.cuda.empty_cache()
@@ -432,14 +437,27 @@ def main():
         return dtr.trace_estimate(g or gauge, w.m0, defl, params(solver, L, B, run, v0, W, graph),
                                   workspace=wsh["ws"])
 
+    # inner-solve storage: FP32 or FP16 Krylov vectors, the faster on one timed wave at this shape
+    cands = ["mixed_f32", "mixed_f16"] if args.solver == "auto" else [args.solver]
+    solver_t = {}
+    for c_ in cands:
+        for rep in range(2 if len(cands) > 1 else 0):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dtr.trace_estimate(gauge, w.m0, defl, params(c_, L, B, 400000 + rep, 0, W), workspace=wsh["ws"])
+            torch.cuda.synchronize()
+            solver_t[c_] = W / (time.perf_counter() - t0)
+    SOLVER = max(solver_t, key=solver_t.get) if solver_t else cands[0]
+    log("32^3x64 solver", choice=SOLVER, rhs_per_s=solver_t)
     # warm-up on runs of their own
     for i in range(args.warmup):
-        dtr.trace_estimate(gauge, w.m0, defl, params("mixed_f32", L, B, 500000 + i, 0, W), workspace=wsh["ws"])
+        dtr.trace_estimate(gauge, w.m0, defl, params(SOLVER, L, B, 500000 + i, 0, W), workspace=wsh["ws"])
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = dtr.kernel_launches()
     dtr.profile_persistent(1)
+    torch.cuda.nvtx.range_push("timed")               # the timed region, for profilers' launch lists
     samples = {}
     ms = []
     iters = 0
@@ -448,7 +466,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        out = step("mixed_f32", i)
+        out = step(SOLVER, i)
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
@@ -457,6 +475,7 @@ def main():
         maxres = max(maxres, out["max_true_residual"])
         if not out["all_converged"] or out["max_true_residual"] > w.tol:
             raise RuntimeError("step did not converge: %r" % (out["max_true_residual"],))
+    torch.cuda.nvtx.range_pop()
     prof = dtr.profile_persistent(0)
     launches = dtr.kernel_launches() - launches0
     barrier()
@@ -467,7 +486,7 @@ def main():
     # complete z0 runs (untimed steps beyond the timed ones) for the run-to-run variance
     nvar = max(args.var_runs, 1) * steps_per_run
     for i in range(args.steps, nvar):
-        samples[i] = step("mixed_f32", i)["samples"][0]
+        samples[i] = step(SOLVER, i)["samples"][0]
     td = defl.T_D()
     traces = []
     for r in range(max(args.var_runs, 1)):
@@ -476,7 +495,7 @@ def main():
     tr_mean = complex(np.mean(traces))
     var_T = float(np.sum(np.abs(np.array(traces) - tr_mean) ** 2) / max(len(traces) - 1, 1))
 
-    log("32^3x64 mixed", value=value, ms_per_step=total_ms / args.steps, lanes=L, block=B,
+    log("32^3x64 mixed", solver=SOLVER, value=value, ms_per_step=total_ms / args.steps, lanes=L, block=B,
         iterations_per_rhs=iters / (args.steps * W), var_T=var_T, trace=[tr_mean.real, tr_mean.imag])
     # plain FP64 path on the same seeds (the first steps of the timed sequence), in its own workspace
     wsh["ws"] = None
@@ -514,7 +533,7 @@ def main():
     t0 = time.perf_counter()
     gauge_e = dtr.gauge_from_host(lat, U_np)
     for i in range(args.steps):
-        o = step("mixed_f32", i, g=gauge_e)
+        o = step(SOLVER, i, g=gauge_e)
         _ = o["samples"].sum()
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
@@ -523,7 +542,8 @@ def main():
     up_bytes = U_np.nbytes
     del gauge_e, U_pin, U_np
 
-    roof = persistent_roofline(prof, sms, L, total_ms, B, hbm_peak, hbm_note, "32^3x64")
+    roof = persistent_roofline(prof, sms, L, total_ms, B, hbm_peak, hbm_note, "32^3x64",
+                               vec_bytes=48 if SOLVER == "mixed_f16" else 96)
     head = {
         "value": value, "ms_per_step": total_ms / args.steps, "rhs_per_step": W, "lanes": L, "block": B,
         "iterations_per_rhs": iters / (args.steps * W), "max_true_residual": maxres, "launches": launches,
@@ -534,7 +554,7 @@ def main():
                       "max_rel_sample_diff_vs_mixed": diff},
         "variance_x_time": {"trace": [tr_mean.real, tr_mean.imag], "var_T": var_T, "runs": len(traces),
                             "time_to_1e-3_s": ttr, "time_to_1e-3_s_fp64_path": ttr64,
-                            "speedup_vs_fp64_path": ttr64 / ttr,
+                            "speedup_vs_fp64_path": ttr64 / ttr if ttr > 0 else t_run64 / t_run,
                             "note": "Var_T over %d complete runs of 512 vectors (complex form); both paths give the "
                                     "same samples (max relative difference above), so they share Var_T" % len(traces)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": up_bytes / args.steps,
@@ -571,12 +591,14 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64 (FP32 inner BiCGStab, FP64 defect correction; BF16 deflation space with FP64 "
-                     "accumulation; FP64 reductions)",
+            "dtype": ("f16" if SOLVER == "mixed_f16" else "f32") + "+f64 (%s-stored inner BiCGStab with FP32 "
+                     "arithmetic, FP64 defect correction; BF16 deflation space with FP64 accumulation; FP64 "
+                     "reductions)" % ("FP16" if SOLVER == "mixed_f16" else "FP32"),
             "data": "synthetic (random SU(3) links generated on the device, seeded)",
             "config": {"workload": WORKLOAD, "lattice": list(w.dims), "eps": w.eps, "m0": w.m0, "k": w.k,
                        "defl_prec": w.defl_prec, "ncolors": ncol, "rhs_per_step": W, "block": B, "lanes": L,
-                       "tol": w.tol, "solver": "mixed_f32", "graph": not args.no_graph,
+                       "tol": w.tol, "solver": SOLVER, "solver_wave_rhs_per_s": solver_t,
+                       "graph": not args.no_graph,
                        "l2": "inputs far larger than L2 (V 100.7 GB, one 32-RHS FP64 field 12.9 GB)",
                        "step": "one wave of %d probing vectors of a z0 run (%d steps per run of 512)"
                                % (W, steps_per_run)},

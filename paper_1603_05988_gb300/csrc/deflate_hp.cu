@@ -24,6 +24,8 @@
 // additions per term instead of one FP64 addition, 64x cheaper on GB300) and is
 // bound by the V stream; FP64 V keeps plain FP64 additions.  W of a run is
 // computed once and reused by every block of that run (reuse_w).
+#include <cstring>
+
 #include "deflate.cuh"
 #include "philox.cuh"
 
@@ -35,10 +37,12 @@ constexpr int kHPEpt = 4;    // row elements (dof type a, vector m) per thread a
 
 // Every site's deflation rows are one contiguous run of 12 k values
 // (V[12x + a][m], row-major), so a block streams whole site runs: thread t
-// keeps the elements e = e0 + t + j T (j < kHPEpt, T = blockDim.x) of the run,
-// each with a fixed dof type a = e / k, and accumulates conj(V) z0 over the
-// block's sites of one colour (two sites in flight).  blockIdx.y picks the
-// chunk e0 of the run when 12 k > T kHPEpt.  partial[(split*nc + c) * 12k + e].
+// keeps the kHPEpt consecutive elements e = e0 + kHPEpt t + j of the run (one
+// 16-byte load for BF16 values, two for FP32; 12 k is a multiple of 4, so they
+// never pass the end of the run), each with a fixed dof type a = e / k, and
+// accumulates conj(V) z0 over the block's sites of one colour (four sites in
+// flight).  blockIdx.y picks the chunk e0 of the run when 12 k > T kHPEpt.
+// partial[(split*nc + c) * 12k + e].
 // Tile accumulator: FP32 TwoSum pairs for FP32 / BF16 V, plain FP64 for FP64 V.
 struct HPAccF {
   float2 s, c;  // running sum and the sum of the rounding errors
@@ -77,6 +81,27 @@ __device__ __forceinline__ float2 hp_widen(const float2 &v) { return v; }
 __device__ __forceinline__ float2 hp_widen(const bfc2 &v) { return __bfloat1622float2(v); }
 __device__ __forceinline__ double2 hp_widen(const double2 &v) { return v; }
 
+// four consecutive stored values (16-byte aligned: 12 k and the element offset are multiples of 4)
+struct Four16 { uint4 w[1]; };
+struct Four32 { uint4 w[2]; };
+struct Four64 { uint4 w[4]; };
+template <typename VC> struct FourOf;
+template <> struct FourOf<bfc2> { typedef Four16 type; };
+template <> struct FourOf<float2> { typedef Four32 type; };
+template <> struct FourOf<double2> { typedef Four64 type; };
+template <typename VC> __device__ __forceinline__ typename FourOf<VC>::type hp_load4(const VC *p) {
+  typename FourOf<VC>::type f;
+  const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+  for (int u = 0; u < (int)(sizeof(f) / 16); ++u) f.w[u] = __ldcs(q + u);
+  return f;
+}
+template <typename VC> __device__ __forceinline__ VC hp_elem(const typename FourOf<VC>::type &f, int j) {
+  VC v;
+  memcpy(&v, reinterpret_cast<const char *>(f.w) + j * sizeof(VC), sizeof(VC));
+  return v;
+}
+
 template <typename VC>
 __global__ void __launch_bounds__(kHPMaxThreads)
     k_hp_partial(const VC *__restrict__ Vd, const int *__restrict__ sites, int per_colour, int nc, int nsplit, int k,
@@ -87,7 +112,7 @@ __global__ void __launch_bounds__(kHPMaxThreads)
   const int c = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
   const int L = 12 * k;
   const int T = blockDim.x;
-  const int e0 = blockIdx.y * T * kHPEpt + threadIdx.x;
+  const int e0 = blockIdx.y * T * kHPEpt + kHPEpt * threadIdx.x;  // this thread's first element
   const int s0 = (int)(((int64_t)per_colour * split) / nsplit);
   const int s1 = (int)(((int64_t)per_colour * (split + 1)) / nsplit);
   const int *list = sites + (int64_t)c * per_colour;
@@ -95,10 +120,11 @@ __global__ void __launch_bounds__(kHPMaxThreads)
   double2 acc[kHPEpt];
 #pragma unroll
   for (int j = 0; j < kHPEpt; ++j) {
-    const int e = e0 + j * T;
+    const int e = e0 + j;
     aj[j] = e < L ? e / k : -1;
     acc[j] = make_double2(0.0, 0.0);
   }
+  const bool live = e0 < L;  // all kHPEpt elements lie in the run when the first does
   for (int t0 = s0; t0 < s1; t0 += kHPTile) {
     const int nt = (s1 - t0) < kHPTile ? (s1 - t0) : kHPTile;
     __syncthreads();
@@ -138,31 +164,24 @@ __global__ void __launch_bounds__(kHPMaxThreads)
       }
       tacc[j].add(re, im);
     };
+    constexpr int SF = 4;  // sites in flight
+    typedef typename FourOf<VC>::type F4;
     int u = 0;
-    for (; u + 1 < nt; u += 2) {
-      const VC *r0 = Vd + (int64_t)tile_sites[u] * L;
-      const VC *r1 = Vd + (int64_t)tile_sites[u + 1] * L;
-      VC v0[kHPEpt], v1[kHPEpt];
+    if (live) {
+      for (; u + SF - 1 < nt; u += SF) {
+        F4 f[SF];
 #pragma unroll
-      for (int j = 0; j < kHPEpt; ++j) {
-        if (aj[j] >= 0) {
-          v0[j] = __ldcs(r0 + e0 + j * T);
-          v1[j] = __ldcs(r1 + e0 + j * T);
-        }
+        for (int q = 0; q < SF; ++q) f[q] = hp_load4<VC>(Vd + (int64_t)tile_sites[u + q] * L + e0);
+#pragma unroll
+        for (int q = 0; q < SF; ++q)
+#pragma unroll
+          for (int j = 0; j < kHPEpt; ++j) add(j, hp_elem<VC>(f[q], j), codes[(u + q) * 12 + aj[j]]);
       }
+      for (; u < nt; ++u) {
+        const F4 f = hp_load4<VC>(Vd + (int64_t)tile_sites[u] * L + e0);
 #pragma unroll
-      for (int j = 0; j < kHPEpt; ++j) {
-        if (aj[j] >= 0) {
-          add(j, v0[j], codes[u * 12 + aj[j]]);
-          add(j, v1[j], codes[(u + 1) * 12 + aj[j]]);
-        }
+        for (int j = 0; j < kHPEpt; ++j) add(j, hp_elem<VC>(f, j), codes[u * 12 + aj[j]]);
       }
-    }
-    if (u < nt) {
-      const VC *r0 = Vd + (int64_t)tile_sites[u] * L;
-#pragma unroll
-      for (int j = 0; j < kHPEpt; ++j)
-        if (aj[j] >= 0) add(j, __ldcs(r0 + e0 + j * T), codes[u * 12 + aj[j]]);
     }
 #pragma unroll
     for (int j = 0; j < kHPEpt; ++j) tacc[j].flush(acc[j]);
@@ -170,7 +189,7 @@ __global__ void __launch_bounds__(kHPMaxThreads)
   double2 *out = partial + ((int64_t)split * nc + c) * L;
 #pragma unroll
   for (int j = 0; j < kHPEpt; ++j)
-    if (aj[j] >= 0) out[e0 + j * T] = acc[j];
+    if (aj[j] >= 0) out[e0 + j] = acc[j];
 }
 
 // Sum over splits (fixed order) and over the dof types of a group.  With

@@ -6,9 +6,11 @@
 //   P1  v = A p                      partial  rhat^H v                 -> alpha
 //   P2  t = A s, s = r - alpha v     partials t^H s, t^H t, rhat^H s,
 //       (s formed on the fly at       rhat^H t, s^H s                  -> omega, and
-//        neighbours, stored at own    rho' = rhat^H s - omega rhat^H t, |r'|^2 =
-//        site)                        s^H s - |t^H s|^2 / t^H t -> beta, convergence
-//   P3  x += alpha p + omega s, r = s - omega t, p = r + beta (p - omega v)
+//        neighbours and at the own    rho' = rhat^H s - omega rhat^H t, |r'|^2 =
+//        site, never stored)          s^H s - |t^H s|^2 / t^H t -> beta, convergence
+//   P3  s = r - alpha v again, x += alpha p + omega s, r = s - omega t,
+//       p = r + beta (p - omega v)   (recomputing s from r and v, which P3 reads
+//       anyway, saves the write and read of a stored s: one vector pass in 16)
 // so the r-reduction of textbook BiCGStab folds into the omega reduction.
 //
 // Reductions are all-reduce barriers: each block reduces its per-thread sums
@@ -328,7 +330,6 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R, S> a) {
 #pragma unroll
           for (int c = 0; c < 12; ++c) {
             SS::st(a.t, base + c * b, o[c]);
-            SS::st(a.s, base + c * b, self[c]);
             const C rh = SS::ld(a.rhat, base + c * b);
             vx[0] += o[c].x * self[c].x + o[c].y * self[c].y;  // t^H s
             vy[0] += o[c].x * self[c].y - o[c].y * self[c].x;
@@ -351,12 +352,14 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R, S> a) {
         n_active = __syncthreads_count(threadIdx.x < b && ss.active[threadIdx.x]);
         if (threadIdx.x == 0) ss.n_active = n_active;
       }
-      {  // P3: x += alpha p + omega s ; r = s - omega t ; p = r + beta (p - omega v)
+      {  // P3: s = r - alpha v ; x += alpha p + omega s ; r = s - omega t ; p = r + beta (p - omega v)
+        // (v is needed wherever alpha != 0, also by a column that converged in this iteration)
         const C al = mkc<C>(ss.alpha[j]);
         const C om = mkc<C>(ss.omega[j]);
         const C be = mkc<C>(ss.beta[j]);
-        const C mom = cneg(om);
+        const C mom = cneg(om), mal = cneg(al);
         const bool act = ss.active[j] != 0;
+        const bool nv = act || ss.alpha[j].x != 0.0 || ss.alpha[j].y != 0.0;
         constexpr int U = 4;  // independent elements (or FP32 pairs) in flight per thread
         int64_t e = t0;
         if constexpr (sizeof(R) == 4 && std::is_same<S, float2>::value) {
@@ -367,11 +370,15 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R, S> a) {
           const C al0 = mkc<C>(ss.alpha[j0]), om0 = mkc<C>(ss.omega[j0]);
           const C be0 = mkc<C>(ss.beta[j0]), mom0 = cneg(om0);
           const bool act0 = ss.active[j0] != 0, act1 = ss.active[j0 + 1] != 0;
+          const bool nv2 = act0 || act1 || ss.alpha[j0].x != 0.0 || ss.alpha[j0].y != 0.0 ||
+                           ss.alpha[j0 + 1].x != 0.0 || ss.alpha[j0 + 1].y != 0.0;
+          const C mal0 = cneg(al0), mal1 = cneg(al1);
           const int64_t n2 = nel >> 1;
           float4 *X = (float4 *)a.x, *Rr = (float4 *)a.r, *Pp = (float4 *)a.p;
-          const float4 *Ss = (const float4 *)a.s, *Tt = (const float4 *)a.t, *Vv = (const float4 *)a.v;
-          auto upd = [&](float4 sv, float4 pv, float4 xv, float4 tv, float4 vv, int64_t q) {
-            const C s0 = mk<C>(sv.x, sv.y), s1 = mk<C>(sv.z, sv.w);
+          const float4 *Tt = (const float4 *)a.t, *Vv = (const float4 *)a.v;
+          auto upd = [&](float4 rv, float4 pv, float4 xv, float4 tv, float4 vv, int64_t q) {
+            const C s0 = caxpy(mal0, mk<C>(vv.x, vv.y), mk<C>(rv.x, rv.y));
+            const C s1 = caxpy(mal1, mk<C>(vv.z, vv.w), mk<C>(rv.z, rv.w));
             const C p0 = mk<C>(pv.x, pv.y), p1 = mk<C>(pv.z, pv.w);
             const C x0 = caxpy(om0, s0, caxpy(al0, p0, mk<C>(xv.x, xv.y)));
             const C x1 = caxpy(om1, s1, caxpy(al1, p1, mk<C>(xv.z, xv.w)));
@@ -387,51 +394,54 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R, S> a) {
           };
           int64_t f = t0;
           for (; f + (U - 1) * stride < n2; f += U * stride) {
-            float4 sv[U], pv[U], xv[U], tv[U], vv[U];
+            float4 rv[U], pv[U], xv[U], tv[U], vv[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
               const int64_t q = f + u * stride;
-              sv[u] = Ss[q];
+              rv[u] = Rr[q];
               pv[u] = Pp[q];
               xv[u] = X[q];
               tv[u] = Tt[q];
-              vv[u] = (act0 || act1) ? Vv[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+              vv[u] = nv2 ? Vv[q] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) upd(sv[u], pv[u], xv[u], tv[u], vv[u], f + u * stride);
+            for (int u = 0; u < U; ++u) upd(rv[u], pv[u], xv[u], tv[u], vv[u], f + u * stride);
           }
           for (; f < n2; f += stride)
-            upd(Ss[f], Pp[f], X[f], Tt[f], (act0 || act1) ? Vv[f] : make_float4(0.f, 0.f, 0.f, 0.f), f);
+            upd(Rr[f], Pp[f], X[f], Tt[f], nv2 ? Vv[f] : make_float4(0.f, 0.f, 0.f, 0.f), f);
           e = nel;  // done
           }
         }
         if constexpr (!std::is_same<S, C>::value) {
           if (b >= 4) {  // half storage: four adjacent columns per 16-byte access; x in FP32
             const int j0 = (4 * threadIdx.x) & (b - 1);
-            C al4[4], om4[4], be4[4], mom4[4];
-            bool act4[4], any = false;
+            C al4[4], om4[4], be4[4], mom4[4], mal4[4];
+            bool act4[4], any = false, anyv = false;
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
               al4[w] = mkc<C>(ss.alpha[j0 + w]);
               om4[w] = mkc<C>(ss.omega[j0 + w]);
               be4[w] = mkc<C>(ss.beta[j0 + w]);
               mom4[w] = cneg(om4[w]);
+              mal4[w] = cneg(al4[w]);
               act4[w] = ss.active[j0 + w] != 0;
               any = any || act4[w];
+              anyv = anyv || act4[w] || ss.alpha[j0 + w].x != 0.0 || ss.alpha[j0 + w].y != 0.0;
             }
             const int64_t n4 = nel >> 2;
             float4 *X = (float4 *)a.x;
             uint4 *Rr = (uint4 *)a.r, *Pp = (uint4 *)a.p;
-            const uint4 *Ss = (const uint4 *)a.s, *Tt = (const uint4 *)a.t, *Vv = (const uint4 *)a.v;
-            auto upd = [&](uint4 sw, uint4 pw, float4 xa, float4 xb, uint4 tw, uint4 vw, int64_t q) {
+            const uint4 *Tt = (const uint4 *)a.t, *Vv = (const uint4 *)a.v;
+            auto upd = [&](uint4 rw, uint4 pw, float4 xa, float4 xb, uint4 tw, uint4 vw, int64_t q) {
               C sv[4], pv[4], tv[4], vv[4], rn[4], pn[4];
-              unpack4<S>(sw, sv);
+              unpack4<S>(rw, sv);
               unpack4<S>(pw, pv);
               unpack4<S>(tw, tv);
               unpack4<S>(vw, vv);
               C xv[4] = {mk<C>(xa.x, xa.y), mk<C>(xa.z, xa.w), mk<C>(xb.x, xb.y), mk<C>(xb.z, xb.w)};
 #pragma unroll
               for (int w = 0; w < 4; ++w) {
+                sv[w] = caxpy(mal4[w], vv[w], sv[w]);  // s = r - alpha v
                 xv[w] = caxpy(om4[w], sv[w], caxpy(al4[w], pv[w], xv[w]));
                 rn[w] = caxpy(mom4[w], tv[w], sv[w]);
                 pn[w] = act4[w] ? caxpy(be4[w], caxpy(mom4[w], vv[w], pv[w]), rn[w]) : pv[w];
@@ -444,22 +454,22 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R, S> a) {
             const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
             int64_t f = t0;
             for (; f + stride < n4; f += 2 * stride) {
-              uint4 sw[2], pw[2], tw[2], vw[2];
+              uint4 rw[2], pw[2], tw[2], vw[2];
               float4 xa[2], xb[2];
 #pragma unroll
               for (int u = 0; u < 2; ++u) {
                 const int64_t q = f + u * stride;
-                sw[u] = Ss[q];
+                rw[u] = Rr[q];
                 pw[u] = Pp[q];
                 xa[u] = X[2 * q];
                 xb[u] = X[2 * q + 1];
                 tw[u] = Tt[q];
-                vw[u] = any ? Vv[q] : zero4;
+                vw[u] = anyv ? Vv[q] : zero4;
               }
 #pragma unroll
-              for (int u = 0; u < 2; ++u) upd(sw[u], pw[u], xa[u], xb[u], tw[u], vw[u], f + u * stride);
+              for (int u = 0; u < 2; ++u) upd(rw[u], pw[u], xa[u], xb[u], tw[u], vw[u], f + u * stride);
             }
-            for (; f < n4; f += stride) upd(Ss[f], Pp[f], X[2 * f], X[2 * f + 1], Tt[f], any ? Vv[f] : zero4, f);
+            for (; f < n4; f += stride) upd(Rr[f], Pp[f], X[2 * f], X[2 * f + 1], Tt[f], anyv ? Vv[f] : zero4, f);
             e = nel;  // done
           }
         }
@@ -468,15 +478,16 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R, S> a) {
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int64_t q = e + u * stride;
-            sv[u] = SS::ld(a.s, q);
+            sv[u] = SS::ld(a.r, q);
             pv[u] = SS::ld(a.p, q);
             xv[u] = a.x[q];
             tv[u] = SS::ld(a.t, q);
-            if (act) vv[u] = SS::ld(a.v, q);
+            vv[u] = nv ? SS::ld(a.v, q) : mk<C>(0.0, 0.0);
           }
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int64_t q = e + u * stride;
+            sv[u] = caxpy(mal, vv[u], sv[u]);  // s = r - alpha v
             a.x[q] = caxpy(om, sv[u], caxpy(al, pv[u], xv[u]));
             const C rn = caxpy(mom, tv[u], sv[u]);
             SS::st(a.r, q, rn);
@@ -484,12 +495,13 @@ __global__ void __launch_bounds__(T, 1) k_bicgstab_persistent(PArgs<R, S> a) {
           }
         }
         for (; e < nel; e += stride) {
-          const C sv = SS::ld(a.s, e);
+          const C vv = nv ? SS::ld(a.v, e) : mk<C>(0.0, 0.0);
+          const C sv = caxpy(mal, vv, SS::ld(a.r, e));
           const C pv = SS::ld(a.p, e);
           a.x[e] = caxpy(om, sv, caxpy(al, pv, a.x[e]));
           const C rn = caxpy(mom, SS::ld(a.t, e), sv);
           SS::st(a.r, e, rn);
-          if (act) SS::st(a.p, e, caxpy(be, caxpy(mom, SS::ld(a.v, e), pv), rn));
+          if (act) SS::st(a.p, e, caxpy(be, caxpy(mom, vv, pv), rn));
         }
         const bool stop = n_active == 0;
         if (stop && !WITH_RESID) break;  // kernel exit orders these writes for the host
