@@ -431,27 +431,36 @@ def main():
     wsh = {"ws": dtr.TraceWorkspace(gauge, defl, params("mixed_f32", L, B, 0, 0, W))}   # current workspace
     base = 1 + rank * 100003
 
-    def step(solver, i, g=None, graph=True):
+    def step(solver, i, g=None):
         run = base + i // steps_per_run
         v0 = (i % steps_per_run) * W
-        return dtr.trace_estimate(g or gauge, w.m0, defl, params(solver, L, B, run, v0, W, graph),
+        return dtr.trace_estimate(g or gauge, w.m0, defl, params(solver, L, B, run, v0, W, GRAPH),
                                   workspace=wsh["ws"])
 
-    # inner-solve storage: FP32 or FP16 Krylov vectors, the faster on one timed wave at this shape
+    # inner-solve storage (FP32 or FP16 Krylov vectors) and cycle driver (one CUDA graph per solve
+    # with device-side loop control, or host-driven launches of the same kernels): the fastest on a
+    # timed wave at this shape (the second of two, the first capturing the graph)
     cands = ["mixed_f32", "mixed_f16"] if args.solver == "auto" else [args.solver]
+    graphs = [False] if args.no_graph else [True, False]
     solver_t = {}
-    for c_ in cands:
-        for rep in range(2 if len(cands) > 1 else 0):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            dtr.trace_estimate(gauge, w.m0, defl, params(c_, L, B, 400000 + rep, 0, W), workspace=wsh["ws"])
-            torch.cuda.synchronize()
-            solver_t[c_] = W / (time.perf_counter() - t0)
-    SOLVER = max(solver_t, key=solver_t.get) if solver_t else cands[0]
-    log("32^3x64 solver", choice=SOLVER, rhs_per_s=solver_t)
+    if len(cands) * len(graphs) > 1:
+        for c_ in cands:
+            for g_ in graphs:
+                for rep in range(2):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    dtr.trace_estimate(gauge, w.m0, defl, params(c_, L, B, 400000 + rep, 0, W, g_),
+                                       workspace=wsh["ws"])
+                    torch.cuda.synchronize()
+                    solver_t["%s/%s" % (c_, "graph" if g_ else "host")] = W / (time.perf_counter() - t0)
+        best = max(solver_t, key=solver_t.get)
+        SOLVER, GRAPH = best.split("/")[0], best.endswith("graph")
+    else:
+        SOLVER, GRAPH = cands[0], graphs[0]
+    log("32^3x64 solver", choice=SOLVER, graph=GRAPH, rhs_per_s=solver_t)
     # warm-up on runs of their own
     for i in range(args.warmup):
-        dtr.trace_estimate(gauge, w.m0, defl, params(SOLVER, L, B, 500000 + i, 0, W), workspace=wsh["ws"])
+        dtr.trace_estimate(gauge, w.m0, defl, params(SOLVER, L, B, 500000 + i, 0, W, GRAPH), workspace=wsh["ws"])
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
@@ -598,7 +607,7 @@ def main():
             "config": {"workload": WORKLOAD, "lattice": list(w.dims), "eps": w.eps, "m0": w.m0, "k": w.k,
                        "defl_prec": w.defl_prec, "ncolors": ncol, "rhs_per_step": W, "block": B, "lanes": L,
                        "tol": w.tol, "solver": SOLVER, "solver_wave_rhs_per_s": solver_t,
-                       "graph": not args.no_graph,
+                       "graph": GRAPH,
                        "l2": "inputs far larger than L2 (V 100.7 GB, one 32-RHS FP64 field 12.9 GB)",
                        "step": "one wave of %d probing vectors of a z0 run (%d steps per run of 512)"
                                % (W, steps_per_run)},
