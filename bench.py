@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--var-runs", type=int, default=2, help="complete z0 runs of 512 vectors for Var_T")
     ap.add_argument("--small-steps", type=int, default=48, help="timed steps of the 8^4 workload (extra)")
     ap.add_argument("--skip-small", action="store_true", help="skip the 8^4 workload")
+    ap.add_argument("--skip-learned", action="store_true", help="skip the learned-preconditioner line (16^3x32)")
+    ap.add_argument("--learned-pairs", type=int, default=1024,
+                    help="distinct (residual, error) pairs the network trains on in the bench (kbench learned "
+                         "--stream-pairs 20000 trains at the workload's full count)")
     ap.add_argument("--skip-kernels", action="store_true", help="skip the standalone kernel roofline lines")
     ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-autotune", action="store_true", help="use --block/--lanes instead of the autotuner")
@@ -337,8 +341,17 @@ def persistent_roofline(prof, sms, lanes, wall_ms, block, hbm_peak, hbm_note, wo
     grid = sms // lanes if lanes > 1 else sms
     share = grid / sms
     fp32_peak = sms * 128 * 2 * 2.07e9 / 1e12
+    # DRAM bytes per site, RHS and iteration of the same kernel under ncu (16^3x32, 16 RHS, FP16
+    # storage: profiles/persistent_bicgstab_f16_16x16x16x32_b16.md), scaled to this launch's units;
+    # the FP32-storage counters predate the current kernel, so none is given for it
+    traffic, traffic_note = None, "no capture of the current FP32-storage kernel"
+    if vec_bytes == 48 and block == 16:
+        traffic = 848.0 * units
+        traffic_note = ("848 B per site, RHS and iteration (ncu DRAM read + write at 16^3x32, 16 RHS, FP16 storage) "
+                        "x this launch's site-RHS-iterations")
     return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak * share, "unit": "GB/s", "frac": gbs / (hbm_peak * share),
-            "traffic": None, "kernel": "k_bicgstab_persistent (%s-stored inner BiCGStab, %d RHS, %s)"
+            "traffic": traffic, "traffic_note": traffic_note,
+            "kernel": "k_bicgstab_persistent (%s-stored inner BiCGStab, %d RHS, %s)"
                                        % ("FP32" if vec_bytes == 96 else "FP16", block, workload),
             "avg_launch_ms": pms, "launches": prof["launches"], "alg_bytes_per_launch": units * bytes_unit,
             "alg_bytes_note": "%.0f B per site, RHS and iteration (two stencils 2 x (%d + %d + 288/%d) + six "
@@ -586,6 +599,12 @@ def main():
         log("8^4", value=small["value"], speedup_vs_fp64_path=small["speedup_vs_fp64_path"],
             setup=small["setup"])
 
+    learned_line = None
+    if not args.skip_learned:
+        torch.cuda.empty_cache()
+        learned_line = measure_learned(args, dtr, synth, torch)
+        log("learned", **{k_: v for k_, v in learned_line.items() if k_ in ("rhs_per_s", "speedup_vs_fp64_path")})
+
     # ------------------------------------------- standalone kernel rooflines
     kern = {} if args.skip_kernels else kernel_rooflines(dtr, hbm_peak, hbm_note)
     log("kernels", **{k_: round(v["frac"], 4) for k_, v in kern.items()})
@@ -622,7 +641,7 @@ def main():
             "fp64_path": head["fp64_path"],
             "variance_x_time": head["variance_x_time"],
             "speedup_vs_fp64_path": value / value64,
-            "extra": {"wilson8x8x8x8_hp16x256_k100": small, **kern},
+            "extra": {"wilson8x8x8x8_hp16x256_k100": small, "learned_16x16x16x32": learned_line, **kern},
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -713,6 +732,59 @@ def measure_small(args, dtr, synth, torch, barrier, max_over_ranks, sms, hbm_pea
                          "kernel": "k_bicgstab_persistent (FP32 inner solve, 16 RHS, 8^4, L2-resident)",
                          "avg_launch_ms": pms, "launches": prof["launches"], "ctas_per_launch": grid},
             "l2": "flushed (256 MiB write) before every timed step"}
+
+
+def measure_learned(args, dtr, synth, torch):
+    """The learned preconditioner on the 16^3x32 workload (eps 0.8, m0 -0.75, k = 200 FP32
+    deflation vectors from the setup eigensolver, 512-colour HP runs, 32-RHS blocks): the
+    network is trained on the GPU on `learned_pairs` distinct (residual, error) pairs drawn from
+    the library's own solves, then one run's first blocks are solved by FGMRES(16) with the
+    network, FGMRES(16) without it, the mixed FP32 BiCGStab and the plain FP64 BiCGStab on the
+    same seeds.  All four give the same samples, so variance x time compares as time per RHS."""
+    from paper_1603_05988_gb300 import learned
+    w = synth.WORKLOADS["wilson16x16x16x32_hp512x4_k200"]
+    lat = dtr.make_lattice(w.dims)
+    g = dtr.gauge_from_host(lat, synth.random_su3_links(w.dims, w.eps, w.gauge_seed))
+    defl, _, est = dtr.eig_deflation(g, w.m0, dtr.eig_params(w.k, store=w.defl_prec, tol=1e-2, degree=48,
+                                                             max_iter=60))
+    net = dtr.Net(lat, act=0, init_scale=1.0 / (4.0 + w.m0), noise=1e-3, seed=1)
+    hist, t_solve, t_train = learned.train_stream(net, g, w.m0, pairs=args.learned_pairs, batch=16)
+    solvers = {"fgmres_learned": dtr.solve_params(tol=w.tol, solver="fgmres_net", net=net, gmres_m=16),
+               "fgmres_plain": dtr.solve_params(tol=w.tol, solver="fgmres_net", net=None, gmres_m=16),
+               "mixed_f32": dtr.solve_params(tol=w.tol, solver="mixed_f32"),
+               "f64": dtr.solve_params(tol=w.tol, solver="f64")}
+    B = w.block
+    out = {"workload": w.name, "pairs": args.learned_pairs, "train_steps": len(hist), "train_solve_s": t_solve,
+           "train_step_s": t_train, "loss_first": float(np.mean(hist[:4])), "loss_last": float(np.mean(hist[-4:])),
+           "eigensolver": {k_: est[k_] for k_ in ("iterations", "converged", "max_residual", "seconds")},
+           "rhs_per_s": {}, "iterations_per_rhs": {}, "steps": 2}
+    samples = {}
+    for name, sp in solvers.items():
+        p = dtr.trace_params(seed=w.noise_seed, z0_first=1, n_z0=1, ncolors=w.ncolors, nvec=B, block=B, solve=sp)
+        ws = dtr.TraceWorkspace(g, defl, p)
+        dtr.trace_estimate(g, w.m0, defl, p, workspace=ws, allow_notconv=True)          # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, smp = 0, []
+        for i in range(2):
+            p.vec_first = i * B
+            o = dtr.trace_estimate(g, w.m0, defl, p, workspace=ws)
+            its += o["iterations"]
+            smp.append(o["samples"][0])
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out["rhs_per_s"][name] = 2 * B / dt
+        out["iterations_per_rhs"][name] = its / (2 * B)
+        samples[name] = np.concatenate(smp)
+        del ws
+    ref = samples["f64"]
+    out["max_rel_sample_diff_vs_fp64"] = {n: float(np.abs(v - ref).max() / np.abs(ref).max())
+                                           for n, v in samples.items() if n != "f64"}
+    out["variance_x_time_speedup_vs_fp64_path"] = {n: out["rhs_per_s"][n] / out["rhs_per_s"]["f64"]
+                                                   for n in solvers if n != "f64"}
+    out["note"] = ("variance x time ratio = RHS/s ratio (identical samples); the network sees no links, so at this "
+                   "disorder it learns little (the weak-disorder gains kbench learned measures do not carry over)")
+    return out
 
 
 def kernel_rooflines(dtr, hbm_peak, hbm_note):

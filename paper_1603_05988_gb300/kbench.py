@@ -6,7 +6,7 @@
     python -m paper_1603_05988_gb300.kbench trace --lattice 16,16,16,32 --eps 0.8 --m0 -0.75 --gauge-seed 1002 \
         --k 200 --prec f32 --ncolors 512 --nvec 512 --block 32 --solver f64,mixed_f32,mixed_f16,mixed_bf16
     python -m paper_1603_05988_gb300.kbench learned --lattice 16,16,16,32 --eval-lattice 24,24,24,48 \
-        --eps 0.8 --m0 -0.75 --gauge-seed 1002 --nrhs 8 [--steps 200 --batch 8 --pool 16]
+        --eps 0.8 --m0 -0.75 --gauge-seed 1002 --nrhs 8 [--steps 200 --batch 8 --pool 16 | --stream-pairs 20000]
     python -m paper_1603_05988_gb300.kbench deflate --lattice 16,16,16,32 --k 256 --prec bf16 --nrhs 16 --reps 20
     python -m paper_1603_05988_gb300.kbench eig --lattice 16,16,16,32 --eps 0.8 --m0 -0.75 --gauge-seed 1002 \
         --k 200 --prec f32 [--degree 16 --iters 60 --tol 1e-2 --time-limit 0 --device-gauge]
@@ -100,7 +100,8 @@ def solve_case(gauge, dims, nrhs, reps, m0, graph=True, grid=0, solver="mixed_f3
             "max_true_residual": float(max(s["true_residual"] for s in st)),
             "all_converged": bool(all(s["converged"] for s in st)),
             "persistent_launches": prof["launches"],
-            "persistent_ms_per_launch": prof["ms"] / max(prof["launches"], 1)}
+            "persistent_ms_per_launch": prof["ms"] / max(prof["launches"], 1),
+            "site_rhs_iterations_per_solve": prof["site_rhs_iterations"] / reps}
 
 
 def trace_case(dims, eps, m0, seed, k, defl_prec, ncolors, nvec, block, solvers):
@@ -136,7 +137,7 @@ def trace_case(dims, eps, m0, seed, k, defl_prec, ncolors, nvec, block, solvers)
     return rows
 
 
-def learned_case(train_dims, eval_dims, eps, m0, seed, steps, batch, pool, nrhs, gmres_m=16):
+def learned_case(train_dims, eval_dims, eps, m0, seed, steps, batch, pool, nrhs, gmres_m=16, stream_pairs=0):
     """The learned preconditioner at the sizes of its workload: the network is
     trained at train_dims on pool x batch (residual, error) pairs from the
     library's own solves (residual loss, Adam, all on the GPU), then FGMRES(m)
@@ -155,11 +156,18 @@ def learned_case(train_dims, eval_dims, eps, m0, seed, steps, batch, pool, nrhs,
     net = dtr.Net(g.lat, act=0, init_scale=1.0 / (4.0 + m0), noise=1e-3, seed=1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hist = learned.train(net, g, m0, steps=steps, batch=batch, lr=3e-4, pool=pool)
+    if stream_pairs:
+        hist, ts, tt = learned.train_stream(net, g, m0, pairs=stream_pairs, batch=batch, lr=3e-4)
+        npairs, nsteps = stream_pairs, len(hist)
+    else:
+        hist = learned.train(net, g, m0, steps=steps, batch=batch, lr=3e-4, pool=pool)
+        npairs, nsteps, ts, tt = pool * batch, steps, None, None
     torch.cuda.synchronize()
     out = {"kernel": "learned preconditioner", "train_lattice": list(train_dims), "eps": eps, "m0": m0,
-           "pairs": pool * batch, "steps": steps, "train_s": time.perf_counter() - t0,
-           "loss_first": float(np.mean(hist[:5])), "loss_last": float(np.mean(hist[-10:])), "eval": []}
+           "pairs": npairs, "steps": nsteps, "train_s": time.perf_counter() - t0, "solve_s": ts, "step_s": tt,
+           "loss_first": float(np.mean(hist[:5])), "loss_last": float(np.mean(hist[-10:])),
+           "loss_curve": [float(np.mean(hist[i:i + max(1, len(hist) // 10)]))
+                          for i in range(0, len(hist), max(1, len(hist) // 10))], "eval": []}
     W = net.weights()
     for dims in (train_dims, eval_dims):
         if tuple(dims) == tuple(train_dims):
@@ -257,6 +265,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=200, help="learned: Adam steps")
     ap.add_argument("--batch", type=int, default=8, help="learned: pairs per step")
     ap.add_argument("--pool", type=int, default=16, help="learned: batches of independent pairs")
+    ap.add_argument("--stream-pairs", type=int, default=0,
+                    help="learned: train on this many distinct pairs, a fresh batch from new solves every step")
     ap.add_argument("--degree", type=int, default=16, help="eig: Chebyshev degree")
     ap.add_argument("--iters", type=int, default=60, help="eig: iterations at most")
     ap.add_argument("--tol", type=float, default=1e-2, help="eig: relative residual target")
@@ -278,7 +288,7 @@ def main(argv=None):
     if a.what == "learned":
         ev = tuple(int(v) for v in a.eval_lattice.split(","))
         print(json.dumps(learned_case(dims, ev, a.eps, a.m0, a.gauge_seed, a.steps, a.batch, a.pool,
-                                      int(a.nrhs.split(",")[0]))), flush=True)
+                                      int(a.nrhs.split(",")[0]), stream_pairs=a.stream_pairs)), flush=True)
         return
     if a.what == "eig":
         for prec in a.prec.split(","):

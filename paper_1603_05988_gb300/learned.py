@@ -15,6 +15,11 @@ The network is a translation-invariant stencil that does not see the gauge
 links, so it can only learn the disorder-averaged propagator: it gains where
 the links are close to unit (weak disorder) and the mass is small, and gains
 nothing at strong disorder.
+
+train() cycles a fixed pool of pairs; train_stream() draws a fresh batch of
+pairs from new solves at every step, so the number of distinct pairs (20k for
+the 16^3x32 workload) is limited by time, not by memory (one pair of 16^3x32
+fields is 50 MB).
 """
 import numpy as np
 
@@ -44,3 +49,25 @@ def train(net, gauge, m0, steps=100, batch=8, lr=3e-4, seed=12345, pool=8, resid
         if log_every and s % log_every == 0:
             print("step %d loss %.4e" % (s, loss))
     return np.array(hist)
+
+
+def train_stream(net, gauge, m0, pairs=20000, batch=16, lr=3e-4, seed=54321, residual_loss=True, solve_tol=1e-6):
+    """Train on `pairs` distinct (residual, error) pairs, `batch` new ones per Adam
+    step from the library's own solves (runs seed-indexed, never reused).
+    Returns (loss history, seconds in solves, seconds in training steps)."""
+    import time
+
+    import torch
+    hist, t_solve, t_train = [], 0.0, 0.0
+    steps = (pairs + batch - 1) // batch
+    for s in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        z, e = make_pairs(gauge, m0, batch, seed, s * batch, tol=solve_tol)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        hist.append(net.train_step(z, e, lr=lr, step=True, gauge=gauge if residual_loss else None, m0=m0) / batch)
+        torch.cuda.synchronize()
+        t_solve += t1 - t0
+        t_train += time.perf_counter() - t1
+    return np.array(hist), t_solve, t_train
