@@ -749,6 +749,24 @@ def measure_learned(args, dtr, synth, torch):
                                                              max_iter=60))
     net = dtr.Net(lat, act=0, init_scale=1.0 / (4.0 + w.m0), noise=1e-3, seed=1)
     hist, t_solve, t_train = learned.train_stream(net, g, w.m0, pairs=args.learned_pairs, batch=16)
+    # one network application to 16 right-hand sides with each kernel set (CUDA events)
+    xa = torch.cat([dtr.gen_noise(lat, 4242, k, 1, False, 0, 1) for k in range(16)])
+    napply = {}
+    for prec in ("bf16", "f32"):
+        net.set_precision(prec)
+        net.apply(xa)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            net.apply(xa)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        napply[prec] = {"ms": ms, "useful_tflops": 4 * 93312.0 * lat.V * 16 / (ms * 1e-3) / 1e12}
+    net.set_precision("bf16")
+    napply["note"] = ("4 layers x 93,312 flop per site and RHS (81 offsets x 24 x 24 x 2); bf16 = tensor-core "
+                      "convolutions with BF16 layer inputs (M = 128 sites, N = 32 of which 24 real, K = 24 + 8 of "
+                      "zero weights per offset: 1.78x the useful flops issued), f32 = CUDA-core FP32")
     solvers = {"fgmres_learned": dtr.solve_params(tol=w.tol, solver="fgmres_net", net=net, gmres_m=16),
                "fgmres_plain": dtr.solve_params(tol=w.tol, solver="fgmres_net", net=None, gmres_m=16),
                "mixed_f32": dtr.solve_params(tol=w.tol, solver="mixed_f32"),
@@ -757,6 +775,7 @@ def measure_learned(args, dtr, synth, torch):
     out = {"workload": w.name, "pairs": args.learned_pairs, "train_steps": len(hist), "train_solve_s": t_solve,
            "train_step_s": t_train, "loss_first": float(np.mean(hist[:4])), "loss_last": float(np.mean(hist[-4:])),
            "eigensolver": {k_: est[k_] for k_ in ("iterations", "converged", "max_residual", "seconds")},
+           "network_apply_16rhs": napply,
            "rhs_per_s": {}, "iterations_per_rhs": {}, "steps": 2}
     samples = {}
     for name, sp in solvers.items():

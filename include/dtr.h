@@ -409,6 +409,12 @@ void dtr_destroy_net(dtr_net net);
 /* Copy the weights to host: master FP32 (bf16_rounded = 0) or the BF16 values
  * the kernels use (1). */
 int dtr_net_get_weights(dtr_net net, int bf16_rounded, float *weights_host);
+/* Arithmetic of the network's kernels.  DTR_BF16 (the default): the layers'
+ * inputs and the back-propagated gradients are stored in BF16 and every
+ * convolution runs on the tensor cores (tcgen05, FP32 accumulation), the weight
+ * gradient on the CUDA cores from the BF16 fields; DTR_F32: FP32 fields and
+ * CUDA-core convolutions.  Returns DTR_EINVAL for any other value. */
+int dtr_net_set_precision(dtr_net net, dtr_prec prec);
 size_t dtr_net_workspace_bytes(dtr_net net, int nrhs);
 /* out = M in for nrhs fields (device, canonical N x nrhs complex128). */
 int dtr_net_apply(dtr_net net, const double *in, double *out, int nrhs, void *work, size_t work_bytes,

@@ -722,10 +722,17 @@ int dtr_net_create(dtr_lattice lat, int act, const float *weights_host, double i
   n->L = L;
   n->act = act;
   n->step = 0;
+  n->tc = 1;
   n->w = n->m = n->v = n->grad = n->wf = n->wb = nullptr;
+  n->wtc_f = n->wtc_b = nullptr;
+  n->err = nullptr;
   float **bufs[6] = {&n->w, &n->m, &n->v, &n->grad, &n->wf, &n->wb};
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaMalloc((void **)bufs[i], nw * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&n->wtc_f, net_tc_weight_bytes(L));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&n->wtc_b, net_tc_weight_bytes(L));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&n->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(n->err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(n->w, w.data(), nw * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(n->m, 0, nw * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(n->v, 0, nw * sizeof(float));
@@ -736,6 +743,9 @@ int dtr_net_create(dtr_lattice lat, int act, const float *weights_host, double i
   }
   if (e != cudaSuccess) {
     for (int i = 0; i < 6; ++i) cudaFree(*bufs[i]);
+    cudaFree(n->wtc_f);
+    cudaFree(n->wtc_b);
+    cudaFree(n->err);
     delete n;
     return cuda_fail(e, "network create");
   }
@@ -751,7 +761,17 @@ void dtr_destroy_net(dtr_net n) {
   cudaFree(n->grad);
   cudaFree(n->wf);
   cudaFree(n->wb);
+  cudaFree(n->wtc_f);
+  cudaFree(n->wtc_b);
+  cudaFree(n->err);
   delete n;
+}
+
+int dtr_net_set_precision(dtr_net n, dtr_prec prec) {
+  if (!n) return fail(DTR_EINVAL, "null argument");
+  if (prec != DTR_BF16 && prec != DTR_F32) return fail(DTR_EINVAL, "network precision must be DTR_BF16 or DTR_F32");
+  n->tc = prec == DTR_BF16;
+  return DTR_OK;
 }
 
 int dtr_net_get_weights(dtr_net n, int bf16_rounded, float *host) {
@@ -780,7 +800,7 @@ int dtr_net_apply(dtr_net n, const double *in, double *out, int nrhs, void *work
   net_apply(n, x, y, b, t0, t1, st);
   launch_unpack<float>(y, (double2 *)out, n->lat.V, nrhs, b, st);
   DTR_LAUNCH_CHECK("network apply");
-  return DTR_OK;
+  return n->tc ? net_check_err(n, st) : DTR_OK;
 }
 
 int dtr_net_train_step(dtr_net n, dtr_gauge g, double m0, const double *in, const double *target, int nrhs, double lr,

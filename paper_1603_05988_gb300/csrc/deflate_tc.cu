@@ -21,9 +21,10 @@
 // (128 complex m: two M = 128 MMAs per K step, two accumulators in tensor
 // memory) and one chunk of dofs (split K), one CTA per SM, with warp roles: a
 // lane of warp 0 streams A through a 5-6 stage ring, a lane of warp 1 issues the
-// MMAs, warps 2-9 build B into two buffers from probing values loaded two
-// stages ahead; full/empty mbarriers order them (tcgen05.commit arrives on a
-// stage's empty barrier once its MMAs have read their operands).  The epilogue
+// MMAs, warps 2-9 build B into two buffers (four for blocks of at most 16
+// columns) from probing values loaded two stages ahead; full/empty mbarriers
+// order them (tcgen05.commit arrives on a stage's empty barrier once its MMAs
+// have read their operands).  The epilogue
 // reads tensor memory with tcgen05.ld into FP32 partials, which a warp per
 // output combines into C and sums over chunks in FP64 in a fixed order
 // (deterministic).
@@ -39,6 +40,7 @@
 #include <mutex>
 
 #include "deflate.cuh"
+#include "tc.cuh"
 
 namespace dtr {
 
@@ -47,7 +49,6 @@ constexpr int kTcStageDofs = 64;  // dofs per pipeline stage (four K steps of 16
 constexpr int kTcRows = 256;      // rows r = 2m + c per CTA (two MMAs of M = 128)
 constexpr int kTcBox = 64;        // TMA box: 64 BF16 (128 bytes, the swizzle span) x 64 dofs
 constexpr int kTcABytes = kTcRows * kTcStageDofs * 2;  // 32 KB per stage
-constexpr long long kTcBudget = 2000000000LL;          // ~1 s at 2 GHz
 constexpr size_t kTcMaxSmem = 232448;                  // opt-in shared memory per block
 
 struct TcArgs {
@@ -62,16 +63,9 @@ struct TcArgs {
   int *err;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
 // K-major operand without swizzle: core matrices of 8 rows x 16 bytes, the two core
 // matrices of a K step 128 bytes apart (leading), 8-row groups 256 bytes apart (stride)
-__device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(256u >> 4) << 32) |
-         (1ull << 46);
-}
+__device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr) { return desc_noswz(saddr, 128u, 256u); }
 
 // MN-major operand with the 128-byte swizzle: atoms of 64 BF16 (MN) x 8 rows (K) of
 // 1 KB; the next 64 MN elements one TMA box (8 KB) further (leading), the next 8 K
@@ -79,20 +73,6 @@ __device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr) {
 __device__ __forceinline__ uint64_t desc_mn_sw128(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(8192u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
          (1ull << 46) | (2ull << 61);
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, long long budget) {
-  const long long t0 = clock64();
-  while (true) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > budget) return false;
-  }
 }
 
 // BF16 bits of an FP64 value that BF16 holds exactly (zero, or a normal number with at
@@ -105,33 +85,16 @@ __device__ __forceinline__ uint32_t bf16_of_exact_f64(uint32_t hi) {
   return mag == 0u ? sign : bits;
 }
 
-// bounded wait that also gives up as soon as another role has given up (*abort)
-__device__ __forceinline__ bool mbar_wait_ab(uint32_t addr, uint32_t parity, volatile int *abort) {
-  const long long t0 = clock64();
-  while (true) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (*abort) return false;
-    if (clock64() - t0 > kTcBudget) {
-      *abort = 1;
-      return false;
-    }
-  }
-}
-
 constexpr int kTcBuilders = kTcThreads - 64;  // warps 2 .. 9 build B
 
 // Warp roles: lane 0 of warp 0 issues the TMA copies of A into an S-stage ring, lane 0
 // of warp 1 issues the MMAs, warps 2-9 build B (two buffers) from the probing values
 // they load into registers two stages ahead; full/empty mbarriers order the three, so
 // no block-wide barrier sits inside the stage loop.  Warps 0-7 run the epilogue.
-// UNITS = (dof octet, column) pairs of B per builder thread = ceil(8 b / 256).
-template <int S, int UNITS>
+// UNITS = (dof octet, column) pairs of B per builder thread = ceil(8 b / 256).  NB = B buffers: with
+// two, the builders of stage s + 2 wait for the MMAs of stage s to complete, which throttles the ring
+// when the B tile is small; narrow blocks (N <= 64) take four.
+template <int S, int UNITS, int NB>
 __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   // the 128-byte swizzle repeats every 1 KB: operand buffers start on a 1 KB boundary
@@ -140,11 +103,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
   const uint32_t bbytes = (uint32_t)N * kTcStageDofs * 2;
   unsigned char *Abuf = smem;
   unsigned char *Bbuf = smem + S * kTcABytes;
-  uint64_t *afull = reinterpret_cast<uint64_t *>(Bbuf + 2 * bbytes);  // A of a stage has landed
+  uint64_t *afull = reinterpret_cast<uint64_t *>(Bbuf + NB * bbytes);  // A of a stage has landed
   uint64_t *aempty = afull + S;                                        // MMAs have read an A buffer
   uint64_t *bfull = aempty + S;                                        // B of a stage is built
-  uint64_t *bempty = bfull + 2;                                        // MMAs have read a B buffer
-  uint64_t *accf = bempty + 2;                                         // every MMA has completed
+  uint64_t *bempty = bfull + NB;                                       // MMAs have read a B buffer
+  uint64_t *accf = bempty + NB;                                        // every MMA has completed
   uint32_t *tslot = reinterpret_cast<uint32_t *>(accf + 1);
   volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
   int *consumed = reinterpret_cast<int *>(tslot + 2);  // A stages the MMA lane saw land
@@ -160,7 +123,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&aempty[q])) : "memory");
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < NB; ++q) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bfull[q])), "r"(kTcBuilders) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bempty[q])) : "memory");
     }
@@ -170,9 +133,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (4 * a.b < N) {  // rows 4b .. N-1 of B are padding: zero once in both buffers
+  if (4 * a.b < N) {  // rows 4b .. N-1 of B are padding: zero once in every buffer
     const int pad = N - 4 * a.b;
-    for (int idx = tid; idx < 2 * 8 * pad; idx += kTcThreads) {
+    for (int idx = tid; idx < NB * 8 * pad; idx += kTcThreads) {
       const int bf = idx / (8 * pad), r = idx - bf * 8 * pad;
       const int o = r / pad, n = 4 * a.b + r % pad;
       *reinterpret_cast<uint4 *>(Bbuf + bf * bbytes + (o >> 1) * (N * 32) + (o & 1) * 128 + (n >> 3) * 256 +
@@ -229,9 +192,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
       for (int s = 0; s < nst; ++s) {
         if (!mbar_wait_ab(smem_u32(&afull[s % S]), (uint32_t)((s / S) & 1), abort)) break;
         *consumed = s + 1;
-        if (!mbar_wait_ab(smem_u32(&bfull[s & 1]), (uint32_t)((s >> 1) & 1), abort)) break;
+        if (!mbar_wait_ab(smem_u32(&bfull[s % NB]), (uint32_t)((s / NB) & 1), abort)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sa = smem_u32(Abuf + (s % S) * kTcABytes), sb = smem_u32(Bbuf + (s & 1) * bbytes);
+        const uint32_t sa = smem_u32(Abuf + (s % S) * kTcABytes), sb = smem_u32(Bbuf + (s % NB) * bbytes);
 #pragma unroll
         for (int ks = 0; ks < kTcStageDofs / 16; ++ks) {
 #pragma unroll
@@ -251,7 +214,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
                          smem_u32(&aempty[s % S]))
                      : "memory");
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&bempty[s & 1]))
+                         smem_u32(&bempty[s % NB]))
                      : "memory");
         mma_issued = s + 1;
       }
@@ -292,10 +255,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
     };
     // build B of stage s from zv, then reuse zv for the loads of stage s + 2
     auto step = [&](int s, uint2 (&zv)[UNITS][8]) -> bool {
-      if (s >= 2 && !mbar_wait_ab(smem_u32(&bempty[s & 1]), (uint32_t)(((s >> 1) - 1) & 1), abort)) return false;
+      if (s >= NB && !mbar_wait_ab(smem_u32(&bempty[s % NB]), (uint32_t)(((s / NB) - 1) & 1), abort)) return false;
       const int d0 = cbeg + s * kTcStageDofs;
       const int r12 = d0 % 12;
-      unsigned char *B = Bbuf + (s & 1) * bbytes;
+      unsigned char *B = Bbuf + (s % NB) * bbytes;
 #pragma unroll
       for (int u = 0; u < UNITS; ++u) {
         const int idx = tb + u * kTcBuilders;
@@ -329,7 +292,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant
       }
       load_Z(s + 2, zv);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bfull[s & 1])) : "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bfull[s % NB])) : "memory");
       return true;
     };
     load_Z(0, za);
@@ -425,9 +388,11 @@ static void tc_shape(int64_t ndof, int k, int b, int sms, int *N, int *rtiles, i
   *nchunks = (int)((ndof + cd - 1) / cd);
 }
 
-// stages of A that fit beside the two B buffers, the barriers and the 1 KB alignment slack
+// B buffers for an MMA width N, and the stages of A that fit beside them, the barriers and the
+// 1 KB alignment slack
+static int tc_bbufs(int N) { return N <= 64 ? 4 : 2; }
 static int tc_stages(int N, size_t *smem) {
-  const size_t fixed = 2 * (size_t)N * kTcStageDofs * 2 + 1024 + 256;
+  const size_t fixed = (size_t)tc_bbufs(N) * N * kTcStageDofs * 2 + 1024 + 256;
   int S = (int)((kTcMaxSmem - fixed) / kTcABytes);
   if (S > 6) S = 6;
   *smem = (size_t)S * kTcABytes + fixed;
@@ -507,12 +472,13 @@ int defl_contract_tc(const dtr_defl_s *D, const double2 *Z, int b, double2 *C, v
   const int S = tc_stages(N, &smem);
   const int units = (8 * b + kTcBuilders - 1) / kTcBuilders;
   const dim3 grid(rt, nc);
-#define DTR_TC_LAUNCH(SS, UU)                                                                                  \
-  if (S == SS && units == UU) {                                                                                \
-    DTR_CUDA(cudaFuncSetAttribute(k_defl_tc<SS, UU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    k_defl_tc<SS, UU><<<grid, kTcThreads, smem, st>>>(tmap, a);                                                \
+  const int nbb = tc_bbufs(N);
+#define DTR_TC_LAUNCH(SS, UU, NN)                                                                                  \
+  if (S == SS && units == UU && nbb == NN) {                                                                       \
+    DTR_CUDA(cudaFuncSetAttribute(k_defl_tc<SS, UU, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    k_defl_tc<SS, UU, NN><<<grid, kTcThreads, smem, st>>>(tmap, a);                                                \
   } else
-  DTR_TC_LAUNCH(6, 1) DTR_TC_LAUNCH(5, 2) {
+  DTR_TC_LAUNCH(6, 1, 4) DTR_TC_LAUNCH(6, 1, 2) DTR_TC_LAUNCH(5, 2, 2) {
     return fail(DTR_EINVAL, "tensor-core contraction: no pipeline for this block width");
   }
 #undef DTR_TC_LAUNCH

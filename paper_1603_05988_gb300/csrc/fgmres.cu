@@ -297,6 +297,10 @@ int fgmres_solve(const dtr_gauge_s *gauge, double m0, const dtr_net_s *net, cons
     k_combine<<<gv, 256, 0, st>>>(Zb, vstride, x, n, b, k, ydev);
     count_launches(1);
     DTR_LAUNCH_CHECK("fgmres cycle");
+    if (net && net->tc) {
+      const int rc3 = net_check_err(net, st);
+      if (rc3) return rc3;
+    }
   }
   return DTR_OK;
 }

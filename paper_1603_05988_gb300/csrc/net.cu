@@ -17,6 +17,7 @@
 // per-chunk partial sums reduced in a fixed order), loss and its gradient, Adam.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -248,7 +249,8 @@ constexpr int kWChunks = 64;
 
 size_t net_workspace_bytes(const dtr_net_s *net, int b) {
   const size_t vec = ((size_t)net->lat.V * 12 * b * sizeof(float2) + 255) / 256 * 256;
-  const size_t wpart = (size_t)kWChunks * kOffs * kCh * kCh * sizeof(float);
+  size_t wpart = (size_t)kWChunks * kOffs * kCh * kCh * sizeof(float);
+  if (net_wgrad_tc_scratch_bytes() > wpart) wpart = net_wgrad_tc_scratch_bytes();
   // x, h1..h3, y, target, g_a, g_b, (grad scratch) + loss partials
   const size_t lparts = (2 * 2048 * 64 + 256) * sizeof(double);  // loss partials [block][2][b] + per-column sums
   return 10 * vec + wpart + lparts + 4096;
@@ -257,10 +259,35 @@ size_t net_workspace_bytes(const dtr_net_s *net, int b) {
 void net_refresh(dtr_net_s *net, cudaStream_t st) {
   k_refresh<<<gs1((int64_t)net->L * kOffs * kCh * kCh), 256, 0, st>>>(net->w, net->wf, net->wb, net->L);
   count_launches(1);
+  net_refresh_tc(net, st);
 }
+
+int net_check_err(const dtr_net_s *net, cudaStream_t st) {
+  int e = 0;
+  DTR_CUDA(cudaMemcpyAsync(&e, net->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DTR_CUDA(cudaStreamSynchronize(st));
+  if (e) {
+    DTR_CUDA(cudaMemsetAsync(net->err, 0, sizeof(int), st));
+    return fail(DTR_ETIMEOUT, "tensor-core convolution: a bounded wait ran out");
+  }
+  return DTR_OK;
+}
+
+// planar BF16 field of width b: 3 chunks x 16 bytes per site and column (half a float2 field)
+static size_t planar_bytes(int64_t V, int b) { return ((size_t)V * 3 * b * 16 + 255) / 256 * 256; }
 
 // y = M x on float2 internal fields of width b (x, y distinct); scratch: 2 vectors
 void net_apply(const dtr_net_s *net, const float2 *x, float2 *y, int b, float2 *t0, float2 *t1, cudaStream_t st) {
+  if (net->tc) {  // two planar BF16 fields fit in t0
+    uint4 *pl[2] = {(uint4 *)t0, (uint4 *)((char *)t0 + planar_bytes(net->lat.V, b))};
+    net_to_planar(x, pl[0], net->lat.V, b, st);
+    for (int l = 0; l < net->L; ++l) {
+      const bool last = l == net->L - 1;
+      net_conv_tc(net, l, false, pl[l & 1], last ? nullptr : pl[(l + 1) & 1], last ? y : nullptr, nullptr, net->act,
+                  b, st);
+    }
+    return;
+  }
   const Geom g = geom_of(net->lat);
   const int n = (int)(net->lat.V * b);
   const int per = kOffs * kCh * kCh;
@@ -295,12 +322,24 @@ int net_train(dtr_net_s *net, const dtr_gauge_s *gauge, double m0, const float2 
   }
   float2 *ga = (float2 *)w; w += vec;
   float2 *gb = (float2 *)w; w += vec;
-  float *wpart = (float *)w; w += (size_t)kWChunks * per * sizeof(float);
+  float *wpart = (float *)w;
+  w += std::max((size_t)kWChunks * per * sizeof(float), net_wgrad_tc_scratch_bytes());
   double *lpart = (double *)w;
   double *lcol = lpart + 2 * 2048 * 64;
   h[0] = const_cast<float2 *>(x);
+  // tensor-core path: planar BF16 inputs of the layers a[0..L-1] (a[l] = phi(h[l]), a[0] = x) in h[1], h[2];
+  // planar gradients in h[3]; the FP32 output y in h[L]
+  const size_t pb = planar_bytes(net->lat.V, b);
+  uint4 *pa[4] = {(uint4 *)h[1], (uint4 *)((char *)h[1] + pb), (uint4 *)h[2], (uint4 *)((char *)h[2] + pb)};
+  uint4 *pg[2] = {(uint4 *)h[3], (uint4 *)((char *)h[3] + pb)};
+  if (net->tc) {
+    net_to_planar(x, pa[0], net->lat.V, b, st);
+    for (int l = 0; l < L; ++l)
+      net_conv_tc(net, l, false, pa[l], l < L - 1 ? pa[l + 1] : nullptr, l == L - 1 ? h[L] : nullptr, nullptr,
+                  net->act, b, st);
+  }
   // forward
-  for (int l = 0; l < L; ++l) {
+  for (int l = 0; l < (net->tc ? 0 : L); ++l) {
     k_conv<<<(n + kConvThreads - 1) / kConvThreads, kConvThreads, 0, st>>>(h[l], h[l + 1], net->wf + (int64_t)l * per,
                                                                          g, b, lg(b), +1, l > 0 ? net->act : 0,
                                                                          nullptr, 0);
@@ -324,8 +363,19 @@ int net_train(dtr_net_s *net, const dtr_gauge_s *gauge, double m0, const float2 
     count_launches(3);
   }
   // backward
+  if (net->tc) {
+    net_to_planar(ga, pg[0], net->lat.V, b, st);
+    int cur = 0;
+    for (int l = L - 1; l >= 0; --l) {
+      net_wgrad_tc(net, pa[l], pg[cur], b, wpart, net->grad + (int64_t)l * per, st);
+      if (l > 0) {
+        net_conv_tc(net, l, true, pg[cur], pg[cur ^ 1], nullptr, pa[l], 0, b, st);
+        cur ^= 1;
+      }
+    }
+  }
   float2 *gcur = ga, *gnext = gb;
-  for (int l = L - 1; l >= 0; --l) {
+  for (int l = L - 1; l >= (net->tc ? L : 0); --l) {
     // weight gradient of layer l: input phi(h[l]) (identity for l = 0), output grad gcur
     k_conv_wgrad<<<dim3(kOffs, kWChunks), 288, 0, st>>>(h[l], gcur, g, b, lg(b), l > 0 ? net->act : 0, kWChunks,
                                                         wpart);
@@ -357,7 +407,7 @@ int net_train(dtr_net_s *net, const dtr_gauge_s *gauge, double m0, const float2 
   double tot = 0.0;
   for (int j = 0; j < nrhs; ++j) tot += col[2 * j];
   *loss_out = tot;
-  return DTR_OK;
+  return net->tc ? net_check_err(net, st) : DTR_OK;
 }
 
 }  // namespace dtr

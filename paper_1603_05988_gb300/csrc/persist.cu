@@ -56,15 +56,21 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Counting grid barrier: arrive, then wait until `target` arrivals in total
 // (the barrier's sequence number times the grid size).  Returns false if the
 // wait exceeded `budget` clock cycles or another block reported an error.
+// Ordering without full fences: thread 0 arrives with a release reduction and
+// polls with acquire loads; the block barriers before and after extend that to
+// the whole block (the writes of the block's threads happen before the
+// release, and the acquire happens before their later reads).
 __device__ __forceinline__ bool grid_arrive_wait(GridSync *gs, unsigned int target, long long budget) {
   __shared__ int s_err;
   __syncthreads();
   if (threadIdx.x == 0) {
     s_err = 0;
-    __threadfence();
-    atomicAdd(&gs->count, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&gs->count) : "memory");
     const long long t0 = clock64();
-    while (*(volatile unsigned int *)&gs->count < target) {
+    while (true) {
+      unsigned int c;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(&gs->count) : "memory");
+      if (c >= target) break;
       if (*(volatile int *)&gs->error) {
         s_err = 1;
         break;
@@ -74,9 +80,7 @@ __device__ __forceinline__ bool grid_arrive_wait(GridSync *gs, unsigned int targ
         s_err = 1;
         break;
       }
-      __nanosleep(32);
     }
-    __threadfence();
   }
   __syncthreads();
   return !s_err;

@@ -132,6 +132,7 @@ _sig("dtr_deflate_project_static", _i, [_vp, _vp, _i, _vp, _vp, _vp])
 _sig("dtr_net_create", _i, [_vp, _i, _vp, _d, _d, _u64, ctypes.POINTER(_vp)])
 _sig("dtr_destroy_net", None, [_vp])
 _sig("dtr_net_get_weights", _i, [_vp, _i, _vp])
+_sig("dtr_net_set_precision", _i, [_vp, _i])
 _sig("dtr_net_workspace_bytes", _sz, [_vp, _i])
 _sig("dtr_net_apply", _i, [_vp, _vp, _vp, _i, _vp, _sz, _vp])
 _sig("dtr_net_train_step", _i, [_vp, _vp, _d, _vp, _vp, _i, _d, _i, ctypes.POINTER(ctypes.c_double), _vp, _vp, _sz,
@@ -374,9 +375,11 @@ NET_WEIGHTS = 4 * 81 * 24 * 24
 
 
 class Net:
-    """Learned preconditioner network (4 layers, 3^4 stencil, 24 real channels)."""
+    """Learned preconditioner network (4 layers, 3^4 stencil, 24 real channels).
+    precision "bf16": BF16 layer inputs and gradients, tensor-core convolutions;
+    "f32": FP32 fields, CUDA-core convolutions."""
 
-    def __init__(self, lat, act=0, weights=None, init_scale=1.0, noise=0.0, seed=0):
+    def __init__(self, lat, act=0, weights=None, init_scale=1.0, noise=0.0, seed=0, precision="bf16"):
         h = _vp()
         wp = None
         if weights is not None:
@@ -389,6 +392,11 @@ class Net:
         self._h = h
         self.lat = lat
         self.act = act
+        self.set_precision(precision)
+
+    def set_precision(self, precision):
+        _check(_lib.dtr_net_set_precision(self._h, _PREC[precision]))
+        self.precision = precision
 
     def weights(self, bf16_rounded=False):
         out = np.empty(NET_WEIGHTS, dtype=np.float32)

@@ -7,7 +7,8 @@
         --k 200 --prec f32 --ncolors 512 --nvec 512 --block 32 --solver f64,mixed_f32,mixed_f16,mixed_bf16
     python -m paper_1603_05988_gb300.kbench learned --lattice 16,16,16,32 --eval-lattice 24,24,24,48 \
         --eps 0.8 --m0 -0.75 --gauge-seed 1002 --nrhs 8 [--steps 200 --batch 8 --pool 16 | --stream-pairs 20000]
-    python -m paper_1603_05988_gb300.kbench deflate --lattice 16,16,16,32 --k 256 --prec bf16 --nrhs 16 --reps 20
+    python -m paper_1603_05988_gb300.kbench deflate --lattice 16,16,16,32 --k 256[,1000] --prec bf16 --nrhs 16 --reps 20
+    python -m paper_1603_05988_gb300.kbench net --lattice 16,16,16,32 --nrhs 8 --reps 5
     python -m paper_1603_05988_gb300.kbench eig --lattice 16,16,16,32 --eps 0.8 --m0 -0.75 --gauge-seed 1002 \
         --k 200 --prec f32 [--degree 16 --iters 60 --tol 1e-2 --time-limit 0 --device-gauge]
 
@@ -137,13 +138,17 @@ def trace_case(dims, eps, m0, seed, k, defl_prec, ncolors, nvec, block, solvers)
     return rows
 
 
-def learned_case(train_dims, eval_dims, eps, m0, seed, steps, batch, pool, nrhs, gmres_m=16, stream_pairs=0):
+def learned_case(train_dims, eval_dims, eps, m0, seed, steps, batch, pool, nrhs, gmres_m=16, stream_pairs=0,
+                 precision="bf16"):
     """The learned preconditioner at the sizes of its workload: the network is
     trained at train_dims on pool x batch (residual, error) pairs from the
     library's own solves (residual loss, Adam, all on the GPU), then FGMRES(m)
     with the trained network, FGMRES(m) without it and the mixed FP32 BiCGStab
     solve held-out Z4 right-hand sides to 1e-10 at train_dims and at eval_dims
-    (the same weights: the network is a translation-invariant stencil)."""
+    (the same weights: the network is a translation-invariant stencil).  Training
+    uses the network's `precision` kernels; the evaluation runs FGMRES with both
+    kernel sets and times one network application (4 layers x 93,312 flop per site
+    and RHS) with each."""
     import time
     import torch
     from . import dtr, learned, synth
@@ -153,7 +158,7 @@ def learned_case(train_dims, eval_dims, eps, m0, seed, steps, batch, pool, nrhs,
         return dtr.gauge_from_host(lat, synth.random_su3_links(dims, eps, gseed))
 
     g = gauge_at(train_dims, seed)
-    net = dtr.Net(g.lat, act=0, init_scale=1.0 / (4.0 + m0), noise=1e-3, seed=1)
+    net = dtr.Net(g.lat, act=0, init_scale=1.0 / (4.0 + m0), noise=1e-3, seed=1, precision=precision)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     if stream_pairs:
@@ -164,6 +169,7 @@ def learned_case(train_dims, eval_dims, eps, m0, seed, steps, batch, pool, nrhs,
         npairs, nsteps, ts, tt = pool * batch, steps, None, None
     torch.cuda.synchronize()
     out = {"kernel": "learned preconditioner", "train_lattice": list(train_dims), "eps": eps, "m0": m0,
+           "train_precision": precision,
            "pairs": npairs, "steps": nsteps, "train_s": time.perf_counter() - t0, "solve_s": ts, "step_s": tt,
            "loss_first": float(np.mean(hist[:5])), "loss_last": float(np.mean(hist[-10:])),
            "loss_curve": [float(np.mean(hist[i:i + max(1, len(hist) // 10)]))
@@ -176,10 +182,25 @@ def learned_case(train_dims, eval_dims, eps, m0, seed, steps, batch, pool, nrhs,
             gg = gauge_at(dims, seed + 1)
             nn = dtr.Net(gg.lat, act=0, weights=W)
         z = torch.cat([dtr.gen_noise(gg.lat, 4242, k, 1, False, 0, 1) for k in range(nrhs)])
-        row = {"lattice": list(dims)}
-        for name, p in (("fgmres_plain", dtr.solve_params(tol=1e-10, solver="fgmres_net", net=None, gmres_m=gmres_m)),
-                        ("fgmres_learned", dtr.solve_params(tol=1e-10, solver="fgmres_net", net=nn, gmres_m=gmres_m)),
-                        ("bicgstab_mixed_f32", dtr.solve_params(tol=1e-10, solver="mixed_f32"))):
+        row = {"lattice": list(dims), "apply": {}}
+        for prec in ("bf16", "f32"):
+            nn.set_precision(prec)
+            nn.apply(z)
+            torch.cuda.synchronize()
+            reps = 5
+            t1 = time.perf_counter()
+            for _ in range(reps):
+                nn.apply(z)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t1) * 1e3 / reps
+            row["apply"][prec] = {"ms": ms, "tflops": 4 * 93312.0 * gg.lat.N / 12 * nrhs / (ms * 1e-3) / 1e12}
+        runs = [("fgmres_plain", "bf16", dtr.solve_params(tol=1e-10, solver="fgmres_net", net=None, gmres_m=gmres_m))]
+        for prec in ("bf16", "f32"):
+            runs.append(("fgmres_learned_" + prec, prec,
+                         dtr.solve_params(tol=1e-10, solver="fgmres_net", net=nn, gmres_m=gmres_m)))
+        runs.append(("bicgstab_mixed_f32", "bf16", dtr.solve_params(tol=1e-10, solver="mixed_f32")))
+        for name, prec, p in runs:
+            nn.set_precision(prec)
             dtr.solve_batch(gg, m0, z, params=p, allow_notconv=True)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
@@ -190,6 +211,31 @@ def learned_case(train_dims, eval_dims, eps, m0, seed, steps, batch, pool, nrhs,
                          "converged": bool(all(s["converged"] for s in st)),
                          "max_true_residual": float(max(s["true_residual"] for s in st))}
         out["eval"].append(row)
+    return out
+
+
+def net_case(dims, nrhs, reps, act=1, seed=3):
+    """One application of the learned preconditioner's network (4 layers) to nrhs fields,
+    with the tensor-core kernels (BF16 layer inputs) and the FP32 CUDA-core kernels; CUDA
+    events around `reps` applications.  Useful work: 4 x 93,312 flop per site and RHS."""
+    import torch
+    from . import dtr
+    lat = dtr.make_lattice(dims)
+    net = dtr.Net(lat, act=act, init_scale=0.5, noise=0.05, seed=seed)
+    x = torch.cat([dtr.gen_noise(lat, 4242, k, 1, False, 0, 1) for k in range(nrhs)])
+    out = {"kernel": "network apply", "lattice": list(dims), "nrhs": nrhs, "act": act}
+    for prec in ("bf16", "f32"):
+        net.set_precision(prec)
+        net.apply(x)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            net.apply(x)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[prec] = {"ms": ms, "useful_tflops": 4 * 93312.0 * lat.V * nrhs / (ms * 1e-3) / 1e12}
     return out
 
 
@@ -244,8 +290,8 @@ def dtr_pad(n):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["dslash", "solve", "deflate", "learned", "trace", "eig"])
-    ap.add_argument("--k", type=int, default=256)
+    ap.add_argument("what", choices=["dslash", "solve", "deflate", "learned", "trace", "eig", "net"])
+    ap.add_argument("--k", default="256", help="deflation vectors (comma list for deflate)")
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--prec", default="bf16")
     ap.add_argument("--nrhs", default="1")
@@ -265,6 +311,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=200, help="learned: Adam steps")
     ap.add_argument("--batch", type=int, default=8, help="learned: pairs per step")
     ap.add_argument("--pool", type=int, default=16, help="learned: batches of independent pairs")
+    ap.add_argument("--net-precision", default="bf16", choices=["bf16", "f32"],
+                    help="learned: kernels used for training (bf16: tensor cores)")
     ap.add_argument("--stream-pairs", type=int, default=0,
                     help="learned: train on this many distinct pairs, a fresh batch from new solves every step")
     ap.add_argument("--degree", type=int, default=16, help="eig: Chebyshev degree")
@@ -281,24 +329,30 @@ def main(argv=None):
     from . import dtr
     dims = tuple(int(x) for x in a.lattice.split(","))
     if a.what == "trace":
-        for row in trace_case(dims, a.eps, a.m0, a.gauge_seed, a.k, a.prec, a.ncolors, a.nvec, a.block,
+        for row in trace_case(dims, a.eps, a.m0, a.gauge_seed, int(a.k), a.prec, a.ncolors, a.nvec, a.block,
                               a.solver.split(",")):
             print(json.dumps(row), flush=True)
         return
     if a.what == "learned":
         ev = tuple(int(v) for v in a.eval_lattice.split(","))
         print(json.dumps(learned_case(dims, ev, a.eps, a.m0, a.gauge_seed, a.steps, a.batch, a.pool,
-                                      int(a.nrhs.split(",")[0]), stream_pairs=a.stream_pairs)), flush=True)
+                                      int(a.nrhs.split(",")[0]), stream_pairs=a.stream_pairs,
+                                      precision=a.net_precision)), flush=True)
         return
     if a.what == "eig":
         for prec in a.prec.split(","):
-            print(json.dumps(eig_case(dims, a.eps, a.m0, a.gauge_seed, a.k, prec, a.degree, a.iters, a.tol,
+            print(json.dumps(eig_case(dims, a.eps, a.m0, a.gauge_seed, int(a.k), prec, a.degree, a.iters, a.tol,
                                       a.time_limit, a.device_gauge)), flush=True)
         return
     if a.what == "deflate":
         for prec in a.prec.split(","):
-            for n in a.nrhs.split(","):
-                print(json.dumps(deflate_case(dims, a.k, int(n), a.reps, prec)), flush=True)
+            for kk in a.k.split(","):
+                for n in a.nrhs.split(","):
+                    print(json.dumps(deflate_case(dims, int(kk), int(n), a.reps, prec)), flush=True)
+        return
+    if a.what == "net":
+        for n in a.nrhs.split(","):
+            print(json.dumps(net_case(dims, int(n), a.reps)), flush=True)
         return
     lat = dtr.make_lattice(dims)
     if a.what == "solve":
