@@ -62,9 +62,9 @@ def parse():
     ap.add_argument("--small-steps", type=int, default=48, help="timed steps of the 8^4 workload (extra)")
     ap.add_argument("--skip-small", action="store_true", help="skip the 8^4 workload")
     ap.add_argument("--skip-learned", action="store_true", help="skip the learned-preconditioner line (16^3x32)")
-    ap.add_argument("--learned-pairs", type=int, default=1024,
-                    help="distinct (residual, error) pairs the network trains on in the bench (kbench learned "
-                         "--stream-pairs 20000 trains at the workload's full count)")
+    ap.add_argument("--learned-pairs", type=int, default=20000,
+                    help="distinct (residual, error) pairs the network trains on in the bench (streamed: a fresh "
+                         "batch of 16 from new solves every Adam step)")
     ap.add_argument("--skip-kernels", action="store_true", help="skip the standalone kernel roofline lines")
     ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-autotune", action="store_true", help="use --block/--lanes instead of the autotuner")
@@ -765,8 +765,8 @@ def measure_learned(args, dtr, synth, torch):
         napply[prec] = {"ms": ms, "useful_tflops": 4 * 93312.0 * lat.V * 16 / (ms * 1e-3) / 1e12}
     net.set_precision("bf16")
     napply["note"] = ("4 layers x 93,312 flop per site and RHS (81 offsets x 24 x 24 x 2); bf16 = tensor-core "
-                      "convolutions with BF16 layer inputs (M = 128 sites, N = 32 of which 24 real, K = 24 + 8 of "
-                      "zero weights per offset: 1.78x the useful flops issued), f32 = CUDA-core FP32")
+                      "convolutions with BF16 layer inputs (M = 128 sites, N = 32 of which 24 real, five K = 16 MMAs "
+                      "per 3 offsets: 1.48x the useful flops issued), f32 = CUDA-core FP32")
     solvers = {"fgmres_learned": dtr.solve_params(tol=w.tol, solver="fgmres_net", net=net, gmres_m=16),
                "fgmres_plain": dtr.solve_params(tol=w.tol, solver="fgmres_net", net=None, gmres_m=16),
                "mixed_f32": dtr.solve_params(tol=w.tol, solver="mixed_f32"),

@@ -21,8 +21,8 @@
 // (128 complex m: two M = 128 MMAs per K step, two accumulators in tensor
 // memory) and one chunk of dofs (split K), one CTA per SM, with warp roles: a
 // lane of warp 0 streams A through a 5-6 stage ring, a lane of warp 1 issues the
-// MMAs, warps 2-9 build B into two buffers (four for blocks of at most 16
-// columns) from probing values loaded two stages ahead; full/empty mbarriers
+// MMAs, warps 2-9 build B into two buffers from probing values loaded two
+// stages ahead; full/empty mbarriers
 // order them (tcgen05.commit arrives on a stage's empty barrier once its MMAs
 // have read their operands).  The epilogue
 // reads tensor memory with tcgen05.ld into FP32 partials, which a warp per
@@ -91,9 +91,8 @@ constexpr int kTcBuilders = kTcThreads - 64;  // warps 2 .. 9 build B
 // of warp 1 issues the MMAs, warps 2-9 build B (two buffers) from the probing values
 // they load into registers two stages ahead; full/empty mbarriers order the three, so
 // no block-wide barrier sits inside the stage loop.  Warps 0-7 run the epilogue.
-// UNITS = (dof octet, column) pairs of B per builder thread = ceil(8 b / 256).  NB = B buffers: with
-// two, the builders of stage s + 2 wait for the MMAs of stage s to complete, which throttles the ring
-// when the B tile is small; narrow blocks (N <= 64) take four.
+// UNITS = (dof octet, column) pairs of B per builder thread = ceil(8 b / 256).  NB = B buffers (two:
+// four buffers for narrow blocks measured no faster, k = 256 and 1000 at b = 16).
 template <int S, int UNITS, int NB>
 __global__ void __launch_bounds__(kTcThreads, 1) k_defl_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
@@ -390,7 +389,7 @@ static void tc_shape(int64_t ndof, int k, int b, int sms, int *N, int *rtiles, i
 
 // B buffers for an MMA width N, and the stages of A that fit beside them, the barriers and the
 // 1 KB alignment slack
-static int tc_bbufs(int N) { return N <= 64 ? 4 : 2; }
+static int tc_bbufs(int /*N*/) { return 2; }
 static int tc_stages(int N, size_t *smem) {
   const size_t fixed = (size_t)tc_bbufs(N) * N * kTcStageDofs * 2 + 1024 + 256;
   int S = (int)((kTcMaxSmem - fixed) / kTcABytes);
@@ -478,7 +477,7 @@ int defl_contract_tc(const dtr_defl_s *D, const double2 *Z, int b, double2 *C, v
     DTR_CUDA(cudaFuncSetAttribute(k_defl_tc<SS, UU, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
     k_defl_tc<SS, UU, NN><<<grid, kTcThreads, smem, st>>>(tmap, a);                                                \
   } else
-  DTR_TC_LAUNCH(6, 1, 4) DTR_TC_LAUNCH(6, 1, 2) DTR_TC_LAUNCH(5, 2, 2) {
+  DTR_TC_LAUNCH(6, 1, 2) DTR_TC_LAUNCH(5, 2, 2) {
     return fail(DTR_EINVAL, "tensor-core contraction: no pipeline for this block width");
   }
 #undef DTR_TC_LAUNCH

@@ -13,14 +13,16 @@
 // displacement (dx, dy, dz) the 128 tile sites shifted by it form a K-major
 // operand without swizzle: 8 consecutive x rows are a core matrix, the next y row
 // is 160 bytes further (stride), the next chunk one plane further (leading).
-// Every offset o of the stencil is therefore two MMAs (M = 128 sites, N = 32
-// output channels, K = 16 input channels) whose A descriptor just starts at the
-// shifted address: no im2col copy.  The 24 input channels are 1.5 K steps: the
-// planes are stored in the order (chunk 2, chunk 0, chunk 1), the first MMA takes
-// chunks 0 and 1, the second chunk 2 and the chunk 0 behind it against a zero
-// block of weights.  The weights of all 81 offsets (B, K-major: 8 output-channel
-// rows x 16 bytes per core matrix, 24 real rows of 32) stay in shared memory for
-// the whole launch.
+// Every offset o of the stencil is therefore a K-major A operand (M = 128 sites,
+// N = 32 output channels, K = 16 input channels per MMA) whose descriptor just
+// starts at the shifted address: no im2col copy.  The 3 x-displacements x 3
+// chunks of a (dt, dz, dy) group are 9 K slices; a leading offset of 16 bytes
+// makes the second K slice of an MMA the same plane shifted by one site in x, so
+// the slices pair into five MMAs per group (135 per tile instead of 162 with one
+// offset per pair of MMAs); the planes are stored in the order (chunk 2, chunk 0,
+// chunk 1) and the odd slice is paired with a zero block of weights.  The
+// weights of all 81 offsets (B, K-major: 8 output-channel rows x 16 bytes per
+// core matrix, 24 real rows of 32) stay in shared memory for the whole launch.
 //
 // Warp roles: warps 0-3 read the accumulators (tcgen05.ld, thread = TMEM lane =
 // tile site) and write the output, lane 0 of warp 4 copies the weights (bulk
@@ -49,8 +51,9 @@ constexpr int kCvPlane = 3 * kCvHY * kCvHX * 16;         // 8640 B: one chunk of
 constexpr int kCvSlab = 3 * kCvPlane;                    // 25920 B
 constexpr int kCvSlots = 4;                              // slab ring
 constexpr int kCvSlabItems = 3 * 3 * kCvHY * kCvHX;      // 16-byte rows per slab (1620)
-constexpr int kCvWOff = 3 * 32 * 16;                     // B bytes per offset (3 chunks x 32 rows)
-constexpr int kCvWBytes = 81 * kCvWOff + 512;            // + a zero core column
+constexpr int kCvWBlk = 32 * 16;                         // B block: 32 output rows x 8 summed channels
+constexpr int kCvWGrp = 9 * kCvWBlk;                     // B bytes per (dt, dz, dy) group of 3 offsets
+constexpr int kCvWBytes = 27 * kCvWGrp + 512;            // + a zero block
 constexpr int kCvSeg = 8;                                // tiles per work item (along t)
 constexpr int kCvThreads = 320;
 constexpr int kCvLoaders = 160;                          // warps 5-9
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(kCvThreads, 1) k_conv_tc(ConvTcArgs a) {
       // D = FP32, A = B = BF16, both K-major; N = 32, M = 128
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(32 >> 3) << 17) |
                              ((uint32_t)(128 >> 4) << 24);
-      const uint32_t sW = smem_u32(W), sZero = sW + 81 * kCvWOff, sSlots = smem_u32(slots);
+      const uint32_t sW = smem_u32(W), sZero = sW + 27 * kCvWGrp, sSlots = smem_u32(slots);
       bool ok = mbar_wait_ab(wf, 0u, abort);
       int waited = 0;  // slabs (counted over the CTA's items) whose arrival was awaited
       int nb = 0;      // first slab of the current item
@@ -179,27 +182,38 @@ __global__ void __launch_bounds__(kCvThreads, 1) k_conv_tc(ConvTcArgs a) {
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t d = tmem + (uint32_t)(buf * 32);
-#pragma unroll 3
-          for (int o = 0; o < 81; ++o) {
-            const int dx = o % 3, dy = (o / 3) % 3, dz = (o / 9) % 3, dt = o / 27;
-            const uint32_t sb = sSlots + (uint32_t)(((nb + k + dt) % kCvSlots) * kCvSlab) +
-                                (uint32_t)(((dz * kCvHY + dy) * kCvHX + dx) * 16);
-            const uint32_t w1 = sW + (uint32_t)(o * kCvWOff), w2 = w1 + 1024u;
-            const uint64_t a1 = desc_noswz(sb + kCvPlane, kCvPlane, kCvHX * 16);
-            const uint64_t a2 = desc_noswz(sb, kCvPlane, kCvHX * 16);
-            const uint64_t b1 = desc_noswz(w1, 512u, 128u);
-            const uint64_t b2 = desc_noswz(w2, sZero - w2, 128u);
-            const uint32_t acc = o > 0 ? 1u : 0u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                "l"(a1), "l"(b1), "r"(idesc), "r"(acc)
-                : "memory");
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                "l"(a2), "l"(b2), "r"(idesc), "r"(1u)
-                : "memory");
+          // Per (dt, dz, dy) group the 3 x-displacements x 3 chunks are 9 K slices of 8 channels, done
+          // in five MMAs: with the leading offset at 16 B the second K slice is the first one's plane
+          // shifted by one site in x, so slices (chunk, dx 0) and (chunk, dx 1) pair up for each chunk;
+          // (chunk 0, dx 2) pairs with (chunk 1, dx 2) one plane further, and (chunk 2, dx 2) with a
+          // zero block of weights.  Descriptors are constant steps from per-tile bases, added to the
+          // start-address field (address >> 4 in the low 14 bits: shared addresses stay below 256 KB,
+          // so no carry leaves it).
+          uint64_t ap[3], aq[3];
+#pragma unroll
+          for (int dt = 0; dt < 3; ++dt) {
+            const uint32_t sa = sSlots + (uint32_t)(((nb + k + dt) % kCvSlots) * kCvSlab);
+            ap[dt] = desc_noswz(sa, 16u, kCvHX * 16);
+            aq[dt] = desc_noswz(sa, kCvPlane, kCvHX * 16);
+          }
+          const uint64_t bp = desc_noswz(sW, 512u, 128u);
+          const uint64_t bz = desc_noswz(sW + 4096u, sZero - (sW + 4096u), 128u);
+          constexpr uint64_t PL = kCvPlane >> 4, GW = kCvWGrp >> 4;
+#pragma unroll
+          for (int gi = 0; gi < 27; ++gi) {
+            const int dy = gi % 3, dz = (gi / 3) % 3, dt = gi / 9;
+            const uint64_t ro = (uint64_t)((dz * kCvHY + dy) * kCvHX);  // the group's (dz, dy) row, dx = 0
+            const uint64_t wg = (uint64_t)gi * GW;
+            const uint64_t adesc[5] = {ap[dt] + ro, ap[dt] + ro + PL, ap[dt] + ro + 2 * PL, aq[dt] + ro + 2 + PL,
+                                       aq[dt] + ro + 2};
+            const uint64_t bdesc[5] = {bp + wg, bp + wg + 64, bp + wg + 128, bp + wg + 192, bz + wg - (wg << 16)};
+#pragma unroll
+            for (int q = 0; q < 5; ++q)
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                  "l"(adesc[q]), "l"(bdesc[q]), "r"(idesc), "r"((gi > 0 || q > 0) ? 1u : 0u)
+                  : "memory");
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            smem_u32(&accfull[buf]))
@@ -225,8 +239,28 @@ __global__ void __launch_bounds__(kCvThreads, 1) k_conv_tc(ConvTcArgs a) {
     const int lt = tid - 5 * 32;
     int n = 0;
     bool ok = true;
+    // this thread's rows of a slab: shared-memory offset (fixed) and, per item, the input
+    // index of the row's site at t = 0 (the slab of t adds t x the 3D volume)
+    int soff[kCvLoadIters], gofs[kCvLoadIters];
+#pragma unroll
+    for (int q = 0; q < kCvLoadIters; ++q) {
+      const int idx = lt + q * kCvLoaders;
+      const int c = idx / (kCvSlabItems / 3), rem = idx - c * (kCvSlabItems / 3);
+      soff[q] = idx < kCvSlabItems ? (c == 2 ? 0 : c + 1) * kCvPlane + rem * 16 : -1;  // planes (chunk 2, 0, 1)
+    }
+    const int vol3 = g.L[0] * g.L[1] * g.L[2];
     for (int i = blockIdx.x; ok && i < a.items; i += gridDim.x) {
       const CvItem it = cv_item(a, i);
+#pragma unroll
+      for (int q = 0; q < kCvLoadIters; ++q) {
+        const int idx = lt + q * kCvLoaders;
+        const int c = idx / (kCvSlabItems / 3), rem = idx - c * (kCvSlabItems / 3);
+        const int iz = rem / (kCvHY * kCvHX), rem2 = rem - iz * (kCvHY * kCvHX);
+        const int iy = rem2 / kCvHX, ix = rem2 - iy * kCvHX;
+        const int xs = wrapc(it.x0 - 1 + ix, g.L[0]), ys = wrapc(it.y0 - 1 + iy, g.L[1]);
+        const int zs = wrapc(it.z - 1 + iz, g.L[2]);
+        gofs[q] = (it.j * 3 + c) * g.V + xs + g.L[0] * (ys + g.L[1] * zs);
+      }
       for (int u = 0; u < it.ts + 2; ++u, ++n) {
         const int slot = n % kCvSlots;
         if (n >= kCvSlots &&
@@ -234,31 +268,15 @@ __global__ void __launch_bounds__(kCvThreads, 1) k_conv_tc(ConvTcArgs a) {
           ok = false;
           break;
         }
-        const int tt = wrapc(it.t0 - 1 + u, g.L[3]);
+        const int tofs = wrapc(it.t0 - 1 + u, g.L[3]) * vol3;
         unsigned char *base = slots + slot * kCvSlab;
         uint4 v[kCvLoadIters];
 #pragma unroll
-        for (int q = 0; q < kCvLoadIters; ++q) {
-          const int idx = lt + q * kCvLoaders;
-          if (idx < kCvSlabItems) {
-            const int c = idx / (kCvSlabItems / 3), rem = idx - c * (kCvSlabItems / 3);
-            const int iz = rem / (kCvHY * kCvHX), rem2 = rem - iz * (kCvHY * kCvHX);
-            const int iy = rem2 / kCvHX, ix = rem2 - iy * kCvHX;
-            const int xs = wrapc(it.x0 - 1 + ix, g.L[0]), ys = wrapc(it.y0 - 1 + iy, g.L[1]);
-            const int zs = wrapc(it.z - 1 + iz, g.L[2]);
-            const int site = xs + g.L[0] * (ys + g.L[1] * (zs + g.L[2] * tt));
-            v[q] = __ldg(a.in + ((int64_t)(it.j * 3 + c)) * g.V + site);
-          }
-        }
+        for (int q = 0; q < kCvLoadIters; ++q)
+          if (soff[q] >= 0) v[q] = __ldg(a.in + (int64_t)gofs[q] + tofs);
 #pragma unroll
-        for (int q = 0; q < kCvLoadIters; ++q) {
-          const int idx = lt + q * kCvLoaders;
-          if (idx < kCvSlabItems) {
-            const int c = idx / (kCvSlabItems / 3), rem = idx - c * (kCvSlabItems / 3);
-            const int pos = c == 2 ? 0 : c + 1;  // planes ordered (chunk 2, chunk 0, chunk 1)
-            *reinterpret_cast<uint4 *>(base + pos * kCvPlane + rem * 16) = v[q];
-          }
-        }
+        for (int q = 0; q < kCvLoadIters; ++q)
+          if (soff[q] >= 0) *reinterpret_cast<uint4 *>(base + soff[q]) = v[q];
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[slot])) : "memory");
       }
@@ -466,14 +484,18 @@ __global__ void __launch_bounds__(kCvThreads, 1) k_wgrad_tc(WgradTcArgs a) {
           // the triple of slabs starts at ring position (nb + k) % 4 and is contiguous (mirrors)
           const uint32_t tri = sSlots + (uint32_t)(((nb + k) % kCvSlots) * kCvSlab);
           const uint32_t gt = sG + (uint32_t)(gb * kWgGBytes);
+          // descriptors at displacement 0 and K step 0; the others differ by constant address steps
+          // added to the start-address field (shared addresses stay below 256 KB: no carry)
+          const uint64_t a00 = desc_noswz(tri, kCvHX * 16, kCvPlane);
+          const uint64_t b00 = desc_noswz(gt, kCvX * 16, kWgGPlane);
           for (int dd = 0; dd < nd; ++dd) {
             const int dsp = d0 + dd;
             const int dx = dsp % 3, dy = (dsp / 3) % 3, dz = dsp / 9;
-            const uint32_t abase = tri + (uint32_t)(((dz * kCvHY + dy) * kCvHX + dx) * 16);
+            const uint64_t a0 = a00 + (uint64_t)((dz * kCvHY + dy) * kCvHX + dx);
 #pragma unroll
             for (int ks = 0; ks < kCvY / 2; ++ks) {
-              const uint64_t ad = desc_noswz(abase + (uint32_t)(ks * 2 * kCvHX * 16), kCvHX * 16, kCvPlane);
-              const uint64_t bd = desc_noswz(gt + (uint32_t)(ks * 2 * kCvX * 16), kCvX * 16, kWgGPlane);
+              const uint64_t ad = a0 + (uint64_t)(ks * 2 * kCvHX);  // two y rows of 160 B per K step
+              const uint64_t bd = b00 + (uint64_t)(ks * 2 * kCvX);  // two rows of 8 sites x 16 B
               const uint32_t acc = (mma_tiles > 0 || ks > 0) ? 1u : 0u;
               asm volatile(
                   "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -504,33 +526,42 @@ __global__ void __launch_bounds__(kCvThreads, 1) k_wgrad_tc(WgradTcArgs a) {
     const int lt = tid - 5 * 32;
     int n = 0, tiles = 0;
     bool ok = true;
+    // this thread's rows of a slab: shared-memory offset (fixed) and, per item, the input index
+    // of the row's site at t = 0 (as in k_conv_tc)
+    int soff[kCvLoadIters], gofs[kCvLoadIters];
+#pragma unroll
+    for (int q = 0; q < kCvLoadIters; ++q) {
+      const int idx = lt + q * kCvLoaders;
+      const int c = idx / (kCvSlabItems / 3), rem = idx - c * (kCvSlabItems / 3);
+      soff[q] = idx < kCvSlabItems ? (c == 2 ? 0 : c + 1) * kCvPlane + rem * 16 : -1;
+    }
+    const int vol3 = g.L[0] * g.L[1] * g.L[2];
+    auto item_rows = [&](const CvItem &it) {
+#pragma unroll
+      for (int q = 0; q < kCvLoadIters; ++q) {
+        const int idx = lt + q * kCvLoaders;
+        const int c = idx / (kCvSlabItems / 3), rem = idx - c * (kCvSlabItems / 3);
+        const int iz = rem / (kCvHY * kCvHX), rem2 = rem - iz * (kCvHY * kCvHX);
+        const int iy = rem2 / kCvHX, ix = rem2 - iy * kCvHX;
+        const int xs = wrapc(it.x0 - 1 + ix, g.L[0]), ys = wrapc(it.y0 - 1 + iy, g.L[1]);
+        const int zs = wrapc(it.z - 1 + iz, g.L[2]);
+        gofs[q] = (it.j * 3 + c) * g.V + xs + g.L[0] * (ys + g.L[1] * zs);
+      }
+    };
     auto load_slab = [&](const CvItem &it, int u) -> bool {
       const int slot = n % kCvSlots;
       if (n >= kCvSlots && !mbar_wait_ab(smem_u32(&empty[slot]), (uint32_t)(((n / kCvSlots) - 1) & 1), abort))
         return false;
-      const int tt = wrapc(it.t0 - 1 + u, g.L[3]);
+      const int tofs = wrapc(it.t0 - 1 + u, g.L[3]) * vol3;
       uint4 v[kCvLoadIters];
 #pragma unroll
-      for (int q = 0; q < kCvLoadIters; ++q) {
-        const int idx = lt + q * kCvLoaders;
-        if (idx < kCvSlabItems) {
-          const int c = idx / (kCvSlabItems / 3), rem = idx - c * (kCvSlabItems / 3);
-          const int iz = rem / (kCvHY * kCvHX), rem2 = rem - iz * (kCvHY * kCvHX);
-          const int iy = rem2 / kCvHX, ix = rem2 - iy * kCvHX;
-          const int xs = wrapc(it.x0 - 1 + ix, g.L[0]), ys = wrapc(it.y0 - 1 + iy, g.L[1]);
-          const int zs = wrapc(it.z - 1 + iz, g.L[2]);
-          v[q] = __ldg(a.a + ((int64_t)(it.j * 3 + c)) * g.V + (xs + g.L[0] * (ys + g.L[1] * (zs + g.L[2] * tt))));
-        }
-      }
+      for (int q = 0; q < kCvLoadIters; ++q)
+        if (soff[q] >= 0) v[q] = __ldg(a.a + (int64_t)gofs[q] + tofs);
 #pragma unroll
       for (int q = 0; q < kCvLoadIters; ++q) {
-        const int idx = lt + q * kCvLoaders;
-        if (idx < kCvSlabItems) {
-          const int c = idx / (kCvSlabItems / 3), rem = idx - c * (kCvSlabItems / 3);
-          const int pos = c == 2 ? 0 : c + 1;
-          const int off = pos * kCvPlane + rem * 16;
-          *reinterpret_cast<uint4 *>(slots + slot * kCvSlab + off) = v[q];
-          if (slot < 2) *reinterpret_cast<uint4 *>(slots + (slot + kCvSlots) * kCvSlab + off) = v[q];
+        if (soff[q] >= 0) {
+          *reinterpret_cast<uint4 *>(slots + slot * kCvSlab + soff[q]) = v[q];
+          if (slot < 2) *reinterpret_cast<uint4 *>(slots + (slot + kCvSlots) * kCvSlab + soff[q]) = v[q];
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -560,6 +591,7 @@ __global__ void __launch_bounds__(kCvThreads, 1) k_wgrad_tc(WgradTcArgs a) {
     };
     for (int i = cta; ok && i < a.items; i += ncta) {
       const CvItem it = wg_item(a, i);
+      item_rows(it);
       ok = load_slab(it, 0) && load_slab(it, 1);
       for (int k = 0; ok && k < it.ts; ++k) ok = load_slab(it, k + 2) && load_g(it, k);
     }
@@ -638,19 +670,22 @@ __global__ void k_to_planar(const float2 *__restrict__ x, uint4 *__restrict__ p,
 }
 
 // master weights [L][o][co][ci] (FP32) -> B operands of the tensor-core convolution, per layer
-// kCvWBytes: forward [o][chunk of ci][co row (32)][8 ci]; backward [o'][chunk of co][ci row][8 co]
-// with o' the reflected offset 80 - o; rows 24-31 and the trailing core column are zero
+// kCvWBytes: per (dt, dz, dy) group gi (offsets o = 3 gi + dx), nine blocks of [32 output rows][8 summed
+// channels] in the order the MMAs pair them: (dx, chunk) = (0,2) (1,2) (0,0) (1,0) (0,1) (1,1) (2,0)
+// (2,1) (2,2); forward: row = co, summed = ci of W[o][co][ci]; backward data: offset reflected
+// (o -> 80 - o) and transposed, row = ci, summed = co; rows 24-31 and the trailing block are zero
 __global__ void k_refresh_tc(const float *__restrict__ w, unsigned short *__restrict__ wf,
                              unsigned short *__restrict__ wb, int L) {
   const int per = kCvWBytes / 2;  // BF16 elements per layer
+  const int bdx[9] = {0, 1, 0, 1, 0, 1, 2, 2, 2}, bch[9] = {2, 2, 0, 0, 1, 1, 0, 1, 2};
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < L * per; e += gridDim.x * blockDim.x) {
     const int l = e / per, r = e % per;
     unsigned short vf = 0, vb = 0;
-    if (r < 81 * (kCvWOff / 2)) {
-      const int o = r / (kCvWOff / 2), rr = r % (kCvWOff / 2);
-      const int c = rr / 256, n = (rr / 8) % 32, q = rr % 8;  // chunk, row, element
+    if (r < 27 * (kCvWGrp / 2)) {
+      const int gi = r / (kCvWGrp / 2), rr = r % (kCvWGrp / 2);
+      const int blk = rr / (kCvWBlk / 2), n = (rr / 8) % 32, q = rr % 8;  // block, row, element
       if (n < 24) {
-        const int k = 8 * c + q;
+        const int o = 3 * gi + bdx[blk], k = 8 * bch[blk] + q;
         const float *wl = w + (int64_t)l * 81 * 576;
         const __nv_bfloat16 f = __float2bfloat16_rn(wl[(o * 24 + n) * 24 + k]);          // W[o][co=n][ci=k]
         const __nv_bfloat16 bk = __float2bfloat16_rn(wl[((80 - o) * 24 + k) * 24 + n]);  // W[80-o][co=k][ci=n]

@@ -116,10 +116,13 @@ def trace_case(dims, eps, m0, seed, k, defl_prec, ncolors, nvec, block, solvers)
     from . import dtr, synth
     lat = dtr.make_lattice(dims)
     g = dtr.gauge_from_host(lat, synth.random_su3_links(dims, eps, seed))
-    V = synth.disjoint_orthonormal(lat.N, k, 4)
-    lam = np.where(np.arange(k) % 2 == 0, 1.0, -1.0) * np.linspace(0.8, 1.5, k)
-    D = dtr.defl_create(lat, V, lam, prec=defl_prec)
-    del V
+    if k * 256 <= lat.N and lat.N * k <= (1 << 29):
+        V = synth.disjoint_orthonormal(lat.N, k, 4)
+        lam = np.where(np.arange(k) % 2 == 0, 1.0, -1.0) * np.linspace(0.8, 1.5, k)
+        D = dtr.defl_create(lat, V, lam, prec=defl_prec)
+        del V
+    else:  # too large to build on the host: one filter iteration of the device eigensolver
+        D, _, _ = dtr.eig_deflation(g, m0, dtr.eig_params(k, store=defl_prec, degree=4, max_iter=1, tol=1e-2))
     rows = []
     for solver in solvers:
         sp = dtr.solve_params(tol=1e-10, solver=solver)
