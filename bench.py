@@ -837,12 +837,14 @@ def kernel_rooflines(dtr, hbm_peak, hbm_note):
     vbytes = dc["alg_bytes_per_launch"] - 1572864 * 16 * 16
     out["roofline_deflation_tc_hbm"] = {
         "bound": "hbm", "achieved": vbytes / (dc["avg_launch_ms"] * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-        "frac": vbytes / (dc["avg_launch_ms"] * 1e-3) / 1e9 / hbm_peak, "traffic": 2.0169e9,
+        "frac": vbytes / (dc["avg_launch_ms"] * 1e-3) / 1e9 / hbm_peak, "traffic": 1.6427e9,
+        "traffic_note": "DRAM read + write of one launch under ncu (1639.6 + 3.1 MB, 1.02x the V bytes): "
+                        "profiles/defl_tc_bf16_16x16x16x32_k256_b16.md",
         "kernel": "k_defl_tc (tcgen05 BF16 x Z4 contraction, FP32 accumulation in TMEM), 16^3x32, k=256, 16 RHS",
         "avg_launch_ms": dc["avg_launch_ms"], "alg_bytes_per_launch": vbytes,
         "alg_bytes_note": "V only (N k 4 B): the contraction's algorithmic bytes with Z regenerated from the seed; "
-                          "the kernel reads Z too (N b 16 B), see traffic",
-        "achieved_tflops": dc["achieved_tflops"], "tensor_pipe_active_pct": 14.3, "peak_note": hbm_note}
+                          "the kernel reads Z as one-byte codes (N b B, 1.6% of V here)",
+        "achieved_tflops": dc["achieved_tflops"], "peak_note": hbm_note}
     return out
 
 
