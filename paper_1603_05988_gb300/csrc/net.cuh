@@ -29,6 +29,8 @@ int net_train(dtr_net_s *net, const dtr_gauge_s *gauge, double m0, const float2 
               double lr, int do_step, float *grad_host, double *loss_out, void *work, size_t work_bytes,
               cudaStream_t st);
 
+int device_sms();
+
 // tensor-core convolution (net_tc.cu)
 size_t net_tc_weight_bytes(int L);
 void net_refresh_tc(dtr_net_s *net, cudaStream_t st);

@@ -720,13 +720,9 @@ void net_to_planar(const float2 *x, uint4 *p, int64_t V, int b, cudaStream_t st)
 
 void net_conv_tc(const dtr_net_s *net, int layer, bool backward, const uint4 *in, uint4 *out_planar, float2 *out_f2,
                  const uint4 *mask, int act_out, int b, cudaStream_t st) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCvSmem);
-  }
+  const int sms = device_sms();
+  // per call: the attribute belongs to the current device's context
+  cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCvSmem);
   ConvTcArgs a;
   a.in = in;
   a.wtc = reinterpret_cast<const uint4 *>((backward ? net->wtc_b : net->wtc_f) + (size_t)layer * kCvWBytes);
@@ -747,22 +743,12 @@ void net_conv_tc(const dtr_net_s *net, int layer, bool backward, const uint4 *in
   count_launches(1);
 }
 
-size_t net_wgrad_tc_scratch_bytes() {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return (size_t)sms * kWgDisp0 * 128 * 32 * sizeof(float);
-}
+size_t net_wgrad_tc_scratch_bytes() { return (size_t)device_sms() * kWgDisp0 * 128 * 32 * sizeof(float); }
 
 void net_wgrad_tc(const dtr_net_s *net, const uint4 *a, const uint4 *gp, int b, float *part, float *dW,
                   cudaStream_t st) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
-  }
+  const int sms = device_sms();
+  cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
   WgradTcArgs w;
   w.a = a;
   w.gp = gp;
