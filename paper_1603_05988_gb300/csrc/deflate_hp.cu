@@ -25,6 +25,7 @@
 // bound by the V stream; FP64 V keeps plain FP64 additions.  W of a run is
 // computed once and reused by every block of that run (reuse_w).
 #include <cstring>
+#include <type_traits>
 
 #include "deflate.cuh"
 #include "philox.cuh"
@@ -103,7 +104,7 @@ template <typename VC> __device__ __forceinline__ VC hp_elem(const typename Four
 }
 
 template <typename VC>
-__global__ void __launch_bounds__(kHPMaxThreads)
+__global__ void __launch_bounds__(kHPMaxThreads, 2)
     k_hp_partial(const VC *__restrict__ Vd, const int *__restrict__ sites, int per_colour, int nc, int nsplit, int k,
                  uint64_t seed, int64_t run, CodeXform xf, double2 *__restrict__ partial) {
   typedef typename HPAcc<VC>::type AC;
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(kHPMaxThreads)
     acc[j] = make_double2(0.0, 0.0);
   }
   const bool live = e0 < L;  // all kHPEpt elements lie in the run when the first does
+  const bool uni = live && aj[0] == aj[kHPEpt - 1];
   for (int t0 = s0; t0 < s1; t0 += kHPTile) {
     const int nt = (s1 - t0) < kHPTile ? (s1 - t0) : kHPTile;
     __syncthreads();
@@ -166,6 +168,18 @@ __global__ void __launch_bounds__(kHPMaxThreads)
     };
     constexpr int SF = 4;  // sites in flight
     typedef typename FourOf<VC>::type F4;
+    // the kHPEpt elements of a thread share one dof type unless they straddle a multiple of k
+    // (never when k is a multiple of 4): then one code per site serves all of them
+    auto site = [&](const F4 &f, const unsigned char *cs) {
+      if (!std::is_same<VC, double2>::value && uni) {  // (FP64 V keeps one path: its registers are full)
+        const int c0 = cs[aj[0]];
+#pragma unroll
+        for (int j = 0; j < kHPEpt; ++j) add(j, hp_elem<VC>(f, j), c0);
+      } else {
+#pragma unroll
+        for (int j = 0; j < kHPEpt; ++j) add(j, hp_elem<VC>(f, j), cs[aj[j]]);
+      }
+    };
     int u = 0;
     if (live) {
       for (; u + SF - 1 < nt; u += SF) {
@@ -173,15 +187,9 @@ __global__ void __launch_bounds__(kHPMaxThreads)
 #pragma unroll
         for (int q = 0; q < SF; ++q) f[q] = hp_load4<VC>(Vd + (int64_t)tile_sites[u + q] * L + e0);
 #pragma unroll
-        for (int q = 0; q < SF; ++q)
-#pragma unroll
-          for (int j = 0; j < kHPEpt; ++j) add(j, hp_elem<VC>(f[q], j), codes[(u + q) * 12 + aj[j]]);
+        for (int q = 0; q < SF; ++q) site(f[q], codes + (u + q) * 12);
       }
-      for (; u < nt; ++u) {
-        const F4 f = hp_load4<VC>(Vd + (int64_t)tile_sites[u] * L + e0);
-#pragma unroll
-        for (int j = 0; j < kHPEpt; ++j) add(j, hp_elem<VC>(f, j), codes[u * 12 + aj[j]]);
-      }
+      for (; u < nt; ++u) site(hp_load4<VC>(Vd + (int64_t)tile_sites[u] * L + e0), codes + u * 12);
     }
 #pragma unroll
     for (int j = 0; j < kHPEpt; ++j) tacc[j].flush(acc[j]);
