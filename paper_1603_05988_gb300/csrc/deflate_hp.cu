@@ -20,10 +20,12 @@
 // transformation (Knuth's TwoSum: s + t = fl(s + t) + e exactly), the error
 // words summed apart, so the tile's sum is carried as a pair (s, c) accurate
 // to about 64 * 2^-48 relative; each tile's pair is added into FP64
-// accumulators in a fixed order.  The pass stays on the FP32 pipe (six FP32
-// additions per term instead of one FP64 addition, 64x cheaper on GB300) and is
-// bound by the V stream; FP64 V keeps plain FP64 additions.  W of a run is
-// computed once and reused by every block of that run (reuse_w).
+// accumulators in a fixed order.  The pass stays on the FP32 pipe (seven FP32
+// additions per term instead of one FP64 addition, 64x cheaper on GB300; the
+// real and imaginary parts go through one packed FP32x2 TwoSum, and a thread's
+// four elements share one probing code per site); FP64 V keeps plain FP64
+// additions.  W of a run is computed once and reused by every block of that
+// run (reuse_w).
 #include <cstring>
 #include <type_traits>
 
@@ -55,9 +57,15 @@ struct HPAccF {
     s = t;
     c = __fadd_rn(c, e);
   }
+  // both parts at once with packed FP32x2 additions (each lane rounds as __fadd_rn does)
+  __device__ __forceinline__ static float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
   __device__ __forceinline__ void add(float re, float im) {
-    two_sum(s.x, c.x, re);
-    two_sum(s.y, c.y, im);
+    const float2 x = make_float2(re, im);
+    const float2 t = __fadd2_rn(s, x);
+    const float2 bp = __fadd2_rn(t, neg2(s));
+    const float2 e = __fadd2_rn(__fadd2_rn(s, neg2(__fadd2_rn(t, neg2(bp)))), __fadd2_rn(x, neg2(bp)));
+    s = t;
+    c = __fadd2_rn(c, e);
   }
   __device__ __forceinline__ void flush(double2 &acc) const {
     acc.x += (double)s.x + (double)c.x;
