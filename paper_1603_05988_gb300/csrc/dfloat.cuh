@@ -110,6 +110,16 @@ __device__ __forceinline__ cdf cjmul(cdf a, cdf b) {
 // a + s*b
 __device__ __forceinline__ cdf caxpy(cdf s, cdf b, cdf a) { return cadd(a, cmul(s, b)); }
 
+// FP64 field value held as double-float hi + lo arrays (written by k_split_df)
+struct DfPairLoad {
+  const float2 *__restrict__ hi;
+  const float2 *__restrict__ lo;
+  __device__ __forceinline__ cdf operator()(int64_t idx) const {
+    const float2 h = hi[idx], l = lo[idx];
+    return mkc2(dff(h.x, l.x), dff(h.y, l.y));
+  }
+};
+
 // FP32 field value as a df complex (exact)
 struct F32AsDf {
   const float2 *__restrict__ f;

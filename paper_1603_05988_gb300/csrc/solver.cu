@@ -164,11 +164,79 @@ __global__ void __launch_bounds__(kBlock) k_resid_update(const cdf *__restrict__
   }
 }
 
-// Whether cycles may end with the double-float residual update (costing about half an
-// FP64 residual): k_mixed_accum then takes it for cycles predicted to stay well above
-// tol and the FP64 residual for the cycle predicted to converge, which also certifies
-// the result, so a solve of c cycles runs c - 1 updates and one FP64 residual.  On
-// unless DTR_RESID_UPDATE=0 (every cycle ends with the FP64 residual).
+// x (FP64) as double-float hi + lo for the true residual below: hi = x rounded to FP32, lo = the
+// remainder rounded to FP32 (hi + lo equals x to ~2^-48 relative)
+__global__ void __launch_bounds__(kBlock) k_split_df(const double2 *__restrict__ x, float2 *__restrict__ hi,
+                                                     float2 *__restrict__ lo, int64_t n, const int *run_flag,
+                                                     int run_if) {
+  if (run_flag && *(volatile const int *)run_flag != run_if) return;  // not selected (uniform over the grid)
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = x[e];
+    const float hx = __double2float_rn(v.x), hy = __double2float_rn(v.y);
+    hi[e] = make_float2(hx, hy);
+    lo[e] = make_float2(__double2float_rn(v.x - (double)hx), __double2float_rn(v.y - (double)hy));
+  }
+}
+
+// True residual r = z - A x of the mixed solvers, with A x in double-float arithmetic on the
+// split x (links split into FP32 hi + lo): each component carries an error of ~2^-46 |A| |x|,
+// i.e. ~1e-14 kappa |z|, far below the 1e-10 tolerances it certifies, on the FP32 pipe instead
+// of the FP64 one (about a third of k_resid's time on this part).  tot = (||r||^2, ||z||^2).
+__global__ void __launch_bounds__(kBlock) k_resid_df(const cdf *__restrict__ Udf, const float2 *__restrict__ xhi,
+                                                     const float2 *__restrict__ xlo, const double2 *__restrict__ z,
+                                                     double2 *__restrict__ r, Geom g, int b, int logb, dff diag,
+                                                     Scal *sc, Reduce red, int restart, const int *run_flag,
+                                                     int run_if, int *mark) {
+  __shared__ double2 tot[64];
+  if (run_flag && *(volatile const int *)run_flag != run_if) return;  // not selected (uniform over the grid)
+  double2 acc[1] = {make_double2(0.0, 0.0)};
+  const int64_t n = (int64_t)g.V << logb;
+  const int j = threadIdx.x & (b - 1);
+  const DfPairLoad ld{xhi, xlo};
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n; it += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(it >> logb);
+    const int64_t base = (int64_t)s * 12 * b + j;
+    cdf o[12], self[12];
+    dslash_site_ld<1, dff>(Udf, ld, g, b, s, j, diag, o, self);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      const double2 zz = z[base + c * b];
+      const double2 rr = make_double2(zz.x - ((double)o[c].x.hi + (double)o[c].x.lo),
+                                      zz.y - ((double)o[c].y.hi + (double)o[c].y.lo));
+      r[base + c * b] = rr;
+      acc[0].x += rr.x * rr.x + rr.y * rr.y;
+      acc[0].y += zz.x * zz.x + zz.y * zz.y;
+    }
+  }
+  if (block_reduce<1>(acc, b, red.partial, red.counter, tot)) {
+    if (threadIdx.x < b) fin_resid(sc, threadIdx.x, tot[threadIdx.x], restart);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      count_active(sc, b);
+      if (mark) *mark = 0;
+    }
+  }
+}
+
+// The mixed solvers' true residual: split x into (xhi, xlo) (two n-element FP32 scratch fields,
+// idle between inner solves), then r = z - A x in double-float arithmetic; gated like k_resid.
+static void launch_true_resid_df(const dtr_gauge_s *gauge, const double2 *x, const double2 *z, double2 *r64,
+                                 float2 *xhi, float2 *xlo, const Geom &g, int b, int logb, double m0, Scal *sc,
+                                 const Reduce &red, int restart, const int *run_flag, int run_if, int *mark,
+                                 unsigned gd, unsigned gv, cudaStream_t st) {
+  const int64_t n = (int64_t)g.V * 12 * b;
+  k_split_df<<<gv, kBlock, 0, st>>>(x, xhi, xlo, n, run_flag, run_if);
+  const float dh = (float)(4.0 + m0);
+  k_resid_df<<<gd, kBlock, 0, st>>>((const cdf *)gauge->Udf, xhi, xlo, z, r64, g, b, logb,
+                                    dff(dh, (float)((4.0 + m0) - (double)dh)), sc, red, restart, run_flag, run_if,
+                                    mark);
+}
+
+// Whether cycles may end with the double-float residual update (r -= A e, cheaper than a
+// true residual of x): k_mixed_accum then takes it for cycles predicted to stay well above
+// tol and the true residual (k_resid_df) for the cycle predicted to converge, which also
+// certifies the result, so a solve of c cycles runs c - 1 updates and one true residual.
+// On unless DTR_RESID_UPDATE=0 (every cycle ends with the true residual).
 static bool resid_update_enabled(int /*store*/) {
   static int v = -1;
   if (v < 0) {
@@ -527,9 +595,9 @@ static int read_gs_error(const GridSync *gs, cudaStream_t st) {
 
 // ------------------------------------------------ graph-driven mixed solve
 // The whole defect-correction loop of the mixed solver as ONE CUDA graph: the
-// first FP64 residual, then a conditional WHILE node whose body is one cycle
-// (FP32 inner init, persistent inner BiCGStab, FP64 accumulate, FP64 true
-// residual) and ends with k_loop_cond, which sets the loop condition from the
+// first true residual, then a conditional WHILE node whose body is one cycle
+// (FP32 inner init, persistent inner BiCGStab, FP64 accumulate, double-float
+// update or true residual) and ends with k_loop_cond, which sets the loop condition from the
 // number of columns still active.  No host round trip between cycles.
 
 __global__ void k_loop_cond(cudaGraphConditionalHandle h, const Scal *__restrict__ outer, GridSync *gs,
@@ -569,7 +637,7 @@ struct MixedState {
   int maxiter, grid;
   int store;  // inner Krylov vectors: 0 FP32, 1 FP16, 2 BF16
   double hs;  // inner right-hand-side scale (see k_mixed_init)
-  int upd;    // cycles end with the double-float residual update (then one FP64 verification)
+  int upd;    // cycles end with the double-float residual update (then one true-residual verification)
 };
 
 // inner iterations of one defect-correction cycle on the caller-initialised state
@@ -697,8 +765,8 @@ int capture_mixed_graph(const MixedState &S, int x_is_zero, double tol2, int max
   if (x_is_zero)
     k_resid_zero<<<S.gv, kBlock, 0, cs>>>(S.z, S.r64, n, S.b, S.outer, S.red);
   else
-    k_resid<double, 0><<<S.gd, kBlock, 0, cs>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
-                                                4.0 + S.m0, S.outer, S.red, 1, nullptr, 0, &S.gs->last_upd);
+    launch_true_resid_df(S.gauge, S.x, S.z, S.r64, S.K.v, S.K.t, S.g, S.b, S.logb, S.m0, S.outer, S.red, 1, nullptr,
+                         0, &S.gs->last_upd, S.gd, S.gv, cs);
   unsigned long long *devcnt = device_launch_counter();
   k_loop_cond<<<1, 32, 0, cs>>>(h, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 1, devcnt, 0);
   CAP_CHECK(cudaGetLastError());
@@ -725,22 +793,20 @@ int capture_mixed_graph(const MixedState &S, int x_is_zero, double tol2, int max
     k_resid_update<<<S.gd, kBlock, 0, cs2>>>((const cdf *)S.gauge->Udf, S.K.x, S.r64, S.g, S.b, S.logb,
                                              split_df(4.0 + S.m0), S.hs, S.outer, S.red, &S.gs->sel, 1,
                                              &S.gs->last_upd);
-  k_resid<double, 0><<<S.gd, kBlock, 0, cs2>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
-                                               4.0 + S.m0, S.outer, S.red, 1, S.upd ? &S.gs->sel : nullptr, 0,
-                                               &S.gs->last_upd);
+  launch_true_resid_df(S.gauge, S.x, S.z, S.r64, S.K.v, S.K.t, S.g, S.b, S.logb, S.m0, S.outer, S.red, 1,
+                       S.upd ? &S.gs->sel : nullptr, 0, &S.gs->last_upd, S.gd, S.gv, cs2);
   k_loop_cond<<<1, 32, 0, cs2>>>(h, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 0, devcnt,
-                                 (unsigned)(kin + (S.upd ? 4 : 3)));
+                                 (unsigned)(kin + (S.upd ? 5 : 4)));
   CAP_CHECK(cudaGetLastError());
   cudaGraph_t tmp = nullptr;
   CAP_CHECK(cudaStreamEndCapture(cs2, &tmp));
   open = 1;
   if (S.upd) {
-    // verification (when the loop ended on a double-float update): the FP64 residual
+    // verification (when the loop ended on a double-float update): the true residual
     // of x decides; columns it finds short of tol continue in a second loop whose
-    // cycles end with the FP64 residual
-    k_resid<double, 0><<<S.gd, kBlock, 0, cs>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
-                                                4.0 + S.m0, S.outer, S.red, 1, &S.gs->last_upd, 1,
-                                                &S.gs->last_upd);
+    // cycles end with the true residual
+    launch_true_resid_df(S.gauge, S.x, S.z, S.r64, S.K.v, S.K.t, S.g, S.b, S.logb, S.m0, S.outer, S.red, 1,
+                         &S.gs->last_upd, 1, &S.gs->last_upd, S.gd, S.gv, cs);
     cudaGraphConditionalHandle h2;
     CAP_CHECK(cudaGraphConditionalHandleCreate(&h2, graph, 0, 0));
     k_loop_cond<<<1, 32, 0, cs>>>(h2, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 2, devcnt, 0);
@@ -759,9 +825,9 @@ int capture_mixed_graph(const MixedState &S, int x_is_zero, double tol2, int max
     rc = enqueue_inner(S, cs2, &kin);
     if (rc) return bail(rc);
     k_mixed_accum<<<S.gv, kBlock, 0, cs2>>>(S.x, S.K.x, n, S.b, S.outer, S.inner, S.hs, nullptr, 0);
-    k_resid<double, 0><<<S.gd, kBlock, 0, cs2>>>(S.gauge->U64, S.x, S.z, S.r64, nullptr, nullptr, S.g, S.b, S.logb,
-                                                 4.0 + S.m0, S.outer, S.red, 1, nullptr, 0, &S.gs->last_upd);
-    k_loop_cond<<<1, 32, 0, cs2>>>(h2, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 0, devcnt, (unsigned)(kin + 3));
+    launch_true_resid_df(S.gauge, S.x, S.z, S.r64, S.K.v, S.K.t, S.g, S.b, S.logb, S.m0, S.outer, S.red, 1, nullptr,
+                         0, &S.gs->last_upd, S.gd, S.gv, cs2);
+    k_loop_cond<<<1, 32, 0, cs2>>>(h2, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 0, devcnt, (unsigned)(kin + 4));
     CAP_CHECK(cudaGetLastError());
     CAP_CHECK(cudaStreamEndCapture(cs2, &tmp));
     open = 1;
@@ -841,9 +907,10 @@ static int solve_mixed_graph(const MixedState &S, int x_is_zero, double tol2, in
   }
   hit->last_use = ++g_graph_tick;
   DTR_CUDA(cudaGraphLaunch(hit->exec, st));
-  // k_scal_init, first residual, k_loop_cond (+ FP64 verification and its k_loop_cond);
-  // the loop bodies count themselves on the device
-  count_launches(S.upd ? 5 : 3);
+  // k_scal_init, first residual (one kernel for x = 0, else split + residual), k_loop_cond
+  // (+ verification: split + residual, and its k_loop_cond); the loop bodies count
+  // themselves on the device
+  count_launches(3 + (x_is_zero ? 0 : 1) + (S.upd ? 3 : 0));
   ++g_graph_launches;
   return DTR_OK;
 }
@@ -972,9 +1039,9 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
     bool fgmres = p->solver == DTR_SOLVER_FGMRES_NET;
     std::vector<double> prev_rel(64, -1.0);
     // phase 1: each cycle ends with the residual k_mixed_accum chose (the double-float
-    // update or the FP64 residual; the other kernel exits at entry); when no column is
-    // left active, an FP64 residual verifies unless the last one already was FP64;
-    // phase 2: any further cycles end with the FP64 residual (the same kernel
+    // update or the true residual; the other kernel exits at entry); when no column is
+    // left active, a true residual verifies unless the last one already was one;
+    // phase 2: any further cycles end with the true residual (the same kernel
     // sequence as the graph-driven loop)
     bool upd_phase = resid_update_enabled(store);
     for (int cycle = 0; cycle <= kMaxRestarts; ++cycle) {
@@ -985,23 +1052,23 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
       } else if (cycle > 0 && upd_phase) {
         k_resid_update<<<gd, kBlock, 0, st>>>((const cdf *)gauge->Udf, K.x, r64, g, b, logb, split_df(4.0 + m0), hs,
                                               outer, red, &gs->sel, 1, &gs->last_upd);
-        k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0,
-                                                   outer, red, restart, &gs->sel, 0, &gs->last_upd);
-        count_launches(2);
+        launch_true_resid_df(gauge, x, z, r64, K.v, K.t, g, b, logb, m0, outer, red, restart, &gs->sel, 0,
+                             &gs->last_upd, gd, gv, st);
+        count_launches(3);
       } else {
-        k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0,
-                                                   outer, red, restart, nullptr, 0, &gs->last_upd);
-        count_launches(1);
+        launch_true_resid_df(gauge, x, z, r64, K.v, K.t, g, b, logb, m0, outer, red, restart, nullptr, 0,
+                             &gs->last_upd, gd, gv, st);
+        count_launches(2);
       }
       DTR_LAUNCH_CHECK("outer residual");
       int n_active = 0;
       int rc = read_n_active(outer, st, &n_active);
       if (rc) return rc;
-      if (n_active == 0 && cycle > 0 && upd_phase) {  // verify in FP64 if the last residual was the update
-        k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0,
-                                                   outer, red, restart, &gs->last_upd, 1, &gs->last_upd);
-        count_launches(1);
-        DTR_LAUNCH_CHECK("FP64 verification residual");
+      if (n_active == 0 && cycle > 0 && upd_phase) {  // verify if the last residual was the update
+        launch_true_resid_df(gauge, x, z, r64, K.v, K.t, g, b, logb, m0, outer, red, restart, &gs->last_upd, 1,
+                             &gs->last_upd, gd, gv, st);
+        count_launches(2);
+        DTR_LAUNCH_CHECK("verification residual");
         upd_phase = false;
         rc = read_n_active(outer, st, &n_active);
         if (rc) return rc;
