@@ -119,8 +119,8 @@ __global__ void __launch_bounds__(kBlock) k_resid_zero(const double2 *__restrict
 // e / (hs * scale) to x (k_mixed_accum), so r -= A e / (hs * scale), with A e
 // evaluated in double-float arithmetic (links split into FP32 hi + lo, e exact in
 // FP32): relative error ~2^-46 of |A| |e|, so r stays the true residual of x to
-// ~1e-14 kappa |z| over all cycles.  tot = (||r||^2, ||z||^2 as stored).  An FP64
-// residual (k_resid) confirms convergence before the solve reports it.
+// ~1e-14 kappa |z| over all cycles.  tot = (||r||^2, ||z||^2 as stored).  A true
+// residual (k_resid_df) confirms convergence before the solve reports it.
 // (Two blocks per SM: the register cap spills ~500 B per thread to L1, yet the solve runs ~2% faster
 // than with one block of 255-register threads.)
 __global__ void __launch_bounds__(kBlock, 2) k_resid_update(const cdf *__restrict__ Udf, const float2 *__restrict__ e,
