@@ -214,7 +214,7 @@ int dtr_gen_noise(dtr_lattice lat, uint64_t seed, int64_t z0_index, int ncolors,
 typedef struct {
   double tol;          /* stop when ||z - A y|| / ||z|| <= tol (true residual: FP64 for the FP64
                           solver; for the mixed solvers z - A y with A y in double-float arithmetic,
-                          error ~2^-46 |A| |y| per component, far below any tol >= 1e-12) */
+                          relative error ~1e-13 ||y|| / ||z||) */
   int maxiter;         /* cap on inner iterations per RHS (summed over restarts) */
   int solver;          /* dtr_solver */
   int check_every;     /* iterations between host convergence checks (>= 1) */

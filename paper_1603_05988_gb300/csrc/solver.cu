@@ -181,8 +181,9 @@ __global__ void __launch_bounds__(kBlock) k_split_df(const double2 *__restrict__
 }
 
 // True residual r = z - A x of the mixed solvers, with A x in double-float arithmetic on the
-// split x (links split into FP32 hi + lo): each component carries an error of ~2^-46 |A| |x|,
-// i.e. ~1e-14 kappa |z|, far below the 1e-10 tolerances it certifies, on the FP32 pipe instead
+// split x (links split into FP32 hi + lo): each component carries an error of about 2^-46 times
+// the sum of the stencil terms' magnitudes (~9 |x|), i.e. ~1e-13 ||x|| / ||z|| relative to z,
+// a hundredth of a 1e-10 tolerance while ||x|| / ||z|| stays below ~10, on the FP32 pipe instead
 // of the FP64 one (about a third of k_resid's time on this part).  tot = (||r||^2, ||z||^2).
 __global__ void __launch_bounds__(kBlock, 2) k_resid_df(const cdf *__restrict__ Udf, const float2 *__restrict__ xhi,
                                                      const float2 *__restrict__ xlo, const double2 *__restrict__ z,
