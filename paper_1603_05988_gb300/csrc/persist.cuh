@@ -20,6 +20,7 @@ struct GridSync {
   unsigned int cycles;      // defect-correction cycles run by the graph-driven loop
   int sel;                  // mixed solver: the next residual is the double-float update (1) or FP64 (0)
   int last_upd;             // mixed solver: the last residual computed was the double-float update
+  int fp64_cert;            // mixed solver: ||x|| / ||z|| too large for the double-float true residual
 };
 constexpr size_t kGridSyncLaunchBytes = offsetof(GridSync, error);
 

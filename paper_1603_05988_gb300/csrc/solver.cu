@@ -61,10 +61,12 @@ __global__ void __launch_bounds__(kBlock) k_resid(const typename cplx_t<R>::type
                                                   typename cplx_t<R>::type *__restrict__ rhat,
                                                   typename cplx_t<R>::type *__restrict__ p, Geom g, int b, int logb,
                                                   R diag, Scal *sc, Reduce red, int restart,
-                                                  const int *run_flag, int run_if, int *mark) {
+                                                  const int *run_flag, int run_if, int *mark,
+                                                  const int *run_if_set = nullptr) {
   typedef typename cplx_t<R>::type C;
   __shared__ double2 tot[64];
   if (run_flag && *(volatile const int *)run_flag != run_if) return;  // not selected (uniform over the grid)
+  if (run_if_set && *(volatile const int *)run_if_set == 0) return;    // (second condition, likewise)
   double2 acc[1] = {make_double2(0.0, 0.0)};
   const int64_t n = (int64_t)g.V << logb;
   const int j = threadIdx.x & (b - 1);
@@ -168,15 +170,33 @@ __global__ void __launch_bounds__(kBlock, 2) k_resid_update(const cdf *__restric
 
 // x (FP64) as double-float hi + lo for the true residual below: hi = x rounded to FP32, lo = the
 // remainder rounded to FP32 (hi + lo equals x to ~2^-48 relative)
+// It also measures ||x|| per column: where ||x|| / ||z|| exceeds kDfCertRatio (||z|| from the
+// previous residual) the double-float residual's error (~1e-13 ||x|| / ||z||) would no longer be
+// negligible next to a 1e-10 tolerance, and *fp64_cert selects the FP64 residual instead.
+constexpr double kDfCertRatio = 30.0;
 __global__ void __launch_bounds__(kBlock) k_split_df(const double2 *__restrict__ x, float2 *__restrict__ hi,
-                                                     float2 *__restrict__ lo, int64_t n, const int *run_flag,
-                                                     int run_if) {
+                                                     float2 *__restrict__ lo, int64_t n, int b, const Scal *sc,
+                                                     Reduce red, int *fp64_cert, const int *run_flag, int run_if) {
+  __shared__ double2 tot[64];
+  __shared__ int any;
   if (run_flag && *(volatile const int *)run_flag != run_if) return;  // not selected (uniform over the grid)
+  double2 acc[1] = {make_double2(0.0, 0.0)};
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const double2 v = x[e];
     const float hx = __double2float_rn(v.x), hy = __double2float_rn(v.y);
     hi[e] = make_float2(hx, hy);
     lo[e] = make_float2(__double2float_rn(v.x - (double)hx), __double2float_rn(v.y - (double)hy));
+    acc[0].x += v.x * v.x + v.y * v.y;  // the grid stride is a multiple of b: one column per thread
+  }
+  if (block_reduce<1>(acc, b, red.partial, red.counter, tot)) {
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    if (threadIdx.x < b) {
+      const double z2 = sc->bnorm2[threadIdx.x];
+      if (z2 > 0.0 && tot[threadIdx.x].x > kDfCertRatio * kDfCertRatio * z2) atomicOr(&any, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *fp64_cert = any;
   }
 }
 
@@ -189,9 +209,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_resid_df(const cdf *__restrict__ 
                                                      const float2 *__restrict__ xlo, const double2 *__restrict__ z,
                                                      double2 *__restrict__ r, Geom g, int b, int logb, dff diag,
                                                      Scal *sc, Reduce red, int restart, const int *run_flag,
-                                                     int run_if, int *mark) {
+                                                     int run_if, int *mark, const int *fp64_cert) {
   __shared__ double2 tot[64];
   if (run_flag && *(volatile const int *)run_flag != run_if) return;  // not selected (uniform over the grid)
+  if (*(volatile const int *)fp64_cert) return;                        // the FP64 residual runs instead
   double2 acc[1] = {make_double2(0.0, 0.0)};
   const int64_t n = (int64_t)g.V << logb;
   const int j = threadIdx.x & (b - 1);
@@ -222,17 +243,20 @@ __global__ void __launch_bounds__(kBlock, 2) k_resid_df(const cdf *__restrict__ 
 }
 
 // The mixed solvers' true residual: split x into (xhi, xlo) (two n-element FP32 scratch fields,
-// idle between inner solves), then r = z - A x in double-float arithmetic; gated like k_resid.
+// idle between inner solves) and measure ||x||, then r = z - A x in double-float arithmetic, or in
+// FP64 where ||x|| / ||z|| is large (three launches, two of which run; gated like k_resid).
 static void launch_true_resid_df(const dtr_gauge_s *gauge, const double2 *x, const double2 *z, double2 *r64,
                                  float2 *xhi, float2 *xlo, const Geom &g, int b, int logb, double m0, Scal *sc,
                                  const Reduce &red, int restart, const int *run_flag, int run_if, int *mark,
-                                 unsigned gd, unsigned gv, cudaStream_t st) {
+                                 int *fp64_cert, unsigned gd, unsigned gv, cudaStream_t st) {
   const int64_t n = (int64_t)g.V * 12 * b;
-  k_split_df<<<gv, kBlock, 0, st>>>(x, xhi, xlo, n, run_flag, run_if);
+  k_split_df<<<gv, kBlock, 0, st>>>(x, xhi, xlo, n, b, sc, red, fp64_cert, run_flag, run_if);
   const float dh = (float)(4.0 + m0);
   k_resid_df<<<gd, kBlock, 0, st>>>((const cdf *)gauge->Udf, xhi, xlo, z, r64, g, b, logb,
                                     dff(dh, (float)((4.0 + m0) - (double)dh)), sc, red, restart, run_flag, run_if,
-                                    mark);
+                                    mark, fp64_cert);
+  k_resid<double, 0><<<gd, kBlock, 0, st>>>(gauge->U64, x, z, r64, nullptr, nullptr, g, b, logb, 4.0 + m0, sc, red,
+                                            restart, run_flag, run_if, mark, fp64_cert);
 }
 
 // Whether cycles may end with the double-float residual update (r -= A e, cheaper than a
@@ -769,7 +793,7 @@ int capture_mixed_graph(const MixedState &S, int x_is_zero, double tol2, int max
     k_resid_zero<<<S.gv, kBlock, 0, cs>>>(S.z, S.r64, n, S.b, S.outer, S.red);
   else
     launch_true_resid_df(S.gauge, S.x, S.z, S.r64, S.K.v, S.K.t, S.g, S.b, S.logb, S.m0, S.outer, S.red, 1, nullptr,
-                         0, &S.gs->last_upd, S.gd, S.gv, cs);
+                         0, &S.gs->last_upd, &S.gs->fp64_cert, S.gd, S.gv, cs);
   unsigned long long *devcnt = device_launch_counter();
   k_loop_cond<<<1, 32, 0, cs>>>(h, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 1, devcnt, 0);
   CAP_CHECK(cudaGetLastError());
@@ -797,9 +821,9 @@ int capture_mixed_graph(const MixedState &S, int x_is_zero, double tol2, int max
                                              split_df(4.0 + S.m0), S.hs, S.outer, S.red, &S.gs->sel, 1,
                                              &S.gs->last_upd);
   launch_true_resid_df(S.gauge, S.x, S.z, S.r64, S.K.v, S.K.t, S.g, S.b, S.logb, S.m0, S.outer, S.red, 1,
-                       S.upd ? &S.gs->sel : nullptr, 0, &S.gs->last_upd, S.gd, S.gv, cs2);
+                       S.upd ? &S.gs->sel : nullptr, 0, &S.gs->last_upd, &S.gs->fp64_cert, S.gd, S.gv, cs2);
   k_loop_cond<<<1, 32, 0, cs2>>>(h, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 0, devcnt,
-                                 (unsigned)(kin + (S.upd ? 5 : 4)));
+                                 (unsigned)(kin + (S.upd ? 6 : 5)));
   CAP_CHECK(cudaGetLastError());
   cudaGraph_t tmp = nullptr;
   CAP_CHECK(cudaStreamEndCapture(cs2, &tmp));
@@ -809,7 +833,7 @@ int capture_mixed_graph(const MixedState &S, int x_is_zero, double tol2, int max
     // of x decides; columns it finds short of tol continue in a second loop whose
     // cycles end with the true residual
     launch_true_resid_df(S.gauge, S.x, S.z, S.r64, S.K.v, S.K.t, S.g, S.b, S.logb, S.m0, S.outer, S.red, 1,
-                         &S.gs->last_upd, 1, &S.gs->last_upd, S.gd, S.gv, cs);
+                         &S.gs->last_upd, 1, &S.gs->last_upd, &S.gs->fp64_cert, S.gd, S.gv, cs);
     cudaGraphConditionalHandle h2;
     CAP_CHECK(cudaGraphConditionalHandleCreate(&h2, graph, 0, 0));
     k_loop_cond<<<1, 32, 0, cs>>>(h2, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 2, devcnt, 0);
@@ -829,8 +853,8 @@ int capture_mixed_graph(const MixedState &S, int x_is_zero, double tol2, int max
     if (rc) return bail(rc);
     k_mixed_accum<<<S.gv, kBlock, 0, cs2>>>(S.x, S.K.x, n, S.b, S.outer, S.inner, S.hs, nullptr, 0);
     launch_true_resid_df(S.gauge, S.x, S.z, S.r64, S.K.v, S.K.t, S.g, S.b, S.logb, S.m0, S.outer, S.red, 1, nullptr,
-                         0, &S.gs->last_upd, S.gd, S.gv, cs2);
-    k_loop_cond<<<1, 32, 0, cs2>>>(h2, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 0, devcnt, (unsigned)(kin + 4));
+                         0, &S.gs->last_upd, &S.gs->fp64_cert, S.gd, S.gv, cs2);
+    k_loop_cond<<<1, 32, 0, cs2>>>(h2, S.outer, S.gs, (unsigned)kMaxRestarts + 1, 0, devcnt, (unsigned)(kin + 5));
     CAP_CHECK(cudaGetLastError());
     CAP_CHECK(cudaStreamEndCapture(cs2, &tmp));
     open = 1;
@@ -910,10 +934,10 @@ static int solve_mixed_graph(const MixedState &S, int x_is_zero, double tol2, in
   }
   hit->last_use = ++g_graph_tick;
   DTR_CUDA(cudaGraphLaunch(hit->exec, st));
-  // k_scal_init, first residual (one kernel for x = 0, else split + residual), k_loop_cond
-  // (+ verification: split + residual, and its k_loop_cond); the loop bodies count
-  // themselves on the device
-  count_launches(3 + (x_is_zero ? 0 : 1) + (S.upd ? 3 : 0));
+  // k_scal_init, first residual (one kernel for x = 0, else split + two residual kernels),
+  // k_loop_cond (+ verification: split + two residual kernels, and its k_loop_cond); the
+  // loop bodies count themselves on the device
+  count_launches(3 + (x_is_zero ? 0 : 2) + (S.upd ? 4 : 0));
   ++g_graph_launches;
   return DTR_OK;
 }
@@ -1056,12 +1080,12 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
         k_resid_update<<<gd, kBlock, 0, st>>>((const cdf *)gauge->Udf, K.x, r64, g, b, logb, split_df(4.0 + m0), hs,
                                               outer, red, &gs->sel, 1, &gs->last_upd);
         launch_true_resid_df(gauge, x, z, r64, K.v, K.t, g, b, logb, m0, outer, red, restart, &gs->sel, 0,
-                             &gs->last_upd, gd, gv, st);
-        count_launches(3);
+                             &gs->last_upd, &gs->fp64_cert, gd, gv, st);
+        count_launches(4);
       } else {
         launch_true_resid_df(gauge, x, z, r64, K.v, K.t, g, b, logb, m0, outer, red, restart, nullptr, 0,
-                             &gs->last_upd, gd, gv, st);
-        count_launches(2);
+                             &gs->last_upd, &gs->fp64_cert, gd, gv, st);
+        count_launches(3);
       }
       DTR_LAUNCH_CHECK("outer residual");
       int n_active = 0;
@@ -1069,8 +1093,8 @@ int solve_internal(const dtr_gauge_s *gauge, double m0, double2 *x, const double
       if (rc) return rc;
       if (n_active == 0 && cycle > 0 && upd_phase) {  // verify if the last residual was the update
         launch_true_resid_df(gauge, x, z, r64, K.v, K.t, g, b, logb, m0, outer, red, restart, &gs->last_upd, 1,
-                             &gs->last_upd, gd, gv, st);
-        count_launches(2);
+                             &gs->last_upd, &gs->fp64_cert, gd, gv, st);
+        count_launches(3);
         DTR_LAUNCH_CHECK("verification residual");
         upd_phase = false;
         rc = read_n_active(outer, st, &n_active);
