@@ -88,8 +88,8 @@ typedef enum {
   DTR_SOLVER_MIXED_F16 = 3,      /* as DTR_SOLVER_MIXED_F32, with the inner Krylov vectors (r, r^, p, v,
                                     s, t) stored in FP16 and the inner right-hand side scaled to entries of
                                     RMS 1; FP32 arithmetic and FP32 inner iterate; the stencil reads its
-                                    input in FP16.  Persistent engine only.  inner_tol below 3e-4 is
-                                    raised to 3e-4 (deeper inner solves of an FP16-stored recursion cost
+                                    input in FP16.  Persistent engine only.  inner_tol below 2e-4 is
+                                    raised to 2e-4 (deeper inner solves of an FP16-stored recursion cost
                                     more iterations than the cycles they save) */
   DTR_SOLVER_MIXED_BF16 = 4      /* the same with BF16 storage; inner_tol floor 1e-2 */
 } dtr_solver;

@@ -450,7 +450,7 @@ __global__ void k_mixed_scal_init(const Scal *__restrict__ outer, Scal *inner, i
   if (j < b) {
     const int act = outer->active[j];
     inner->active[j] = act;
-    inner->rho[j] = make_double2(1.0, 0.0);
+    inner->rho[j] = make_double2(hs2, 0.0);  // rhat^H r0 = ||r32||^2 (rhat = r0 = r32)
     inner->bnorm2[j] = hs2;  // ||r32||^2 of a unit column scaled by hs
     inner->rnorm2[j] = hs2;
     inner->iters[j] = 0;
@@ -586,9 +586,10 @@ static int inner_store(int solver) {
   return solver == DTR_SOLVER_MIXED_F16 ? 1 : solver == DTR_SOLVER_MIXED_BF16 ? 2 : 0;
 }
 // Relative residual reduction asked of one inner solve.  A recursion whose vectors are
-// rounded to 11 (FP16) or 8 (BF16) significant bits stops paying beyond ~3e-4 or ~1e-2
+// rounded to 11 (FP16) or 8 (BF16) significant bits stops paying beyond ~2e-4 or ~1e-2
 // of reduction (measured: deeper requests cost more iterations than the defect-correction
-// cycles they save), so smaller requests are raised to that floor (the FP64 outer loop
+// cycles they save; at 32^3x64 2e-4 is the loosest FP16 request that still reaches 1e-10
+// in three cycles), so smaller requests are raised to that floor (the FP64 outer loop
 // reaches the outer tolerance either way).
 static double inner_tol_for(const dtr_solve_params *p) {
   double t = p->inner_tol > 0 ? p->inner_tol : 1e-5;

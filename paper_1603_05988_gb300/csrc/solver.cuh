@@ -8,7 +8,7 @@ namespace dtr {
 constexpr int kFlagNaN = 1;
 constexpr int kFlagBreakdown = 2;
 constexpr int kMaxRestarts = 32;  // true-residual restarts / defect-correction cycles per column
-constexpr double kInnerTolFloorF16 = 3e-4;   // least inner reduction asked of FP16-stored inner vectors
+constexpr double kInnerTolFloorF16 = 2e-4;   // least inner reduction asked of FP16-stored inner vectors
 constexpr double kInnerTolFloorBF16 = 1e-2;  // and of BF16-stored ones
 
 // Per-column Krylov scalars, resident in device memory (b <= 64 columns).

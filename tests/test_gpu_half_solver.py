@@ -116,3 +116,28 @@ def test_dslash_double_float_matches_oracle(dtr):
     err_32 = np.abs(dtr.dslash(g, m0, x, prec="f32").cpu().numpy() - ref).max() / scale
     assert err_df <= 1e-13, err_df
     assert err_32 >= 1e-9, err_32
+
+
+def test_half_inner_iterations_follow_fp32_storage(dtr):
+    """At the same inner tolerance the FP16-stored inner BiCGStab takes the steps of
+    the FP32-stored one: the same number of defect-correction cycles per column and
+    iteration counts within rounding noise.  Its right-hand side is scaled to
+    ||r32||^2 = 12 V, so the first step needs rho = rhat^H r0 = 12 V; a solver that
+    started from rho = 1 (the FP32 scale) would take a near-zero first step in
+    every cycle, about one wasted iteration per cycle and column (+10% here)."""
+    import torch
+    dims, m0 = (8, 8, 8, 8), -0.6
+    U, lat, g = _setup(dtr, dims, 0.8, m0, 5)
+    rng = np.random.default_rng(3)
+    Z = rng.standard_normal((8, lat.N)) + 1j * rng.standard_normal((8, lat.N))
+    z = torch.from_numpy(Z).cuda()
+    its, cyc = {}, {}
+    for solver in ("mixed_f32", "mixed_f16"):
+        p = dtr.solve_params(tol=1e-10, solver=solver, graph=False, inner_tol=3e-4)
+        y, st = dtr.solve_batch(g, m0, z, params=p)
+        assert all(s["converged"] for s in st)
+        its[solver] = np.array([s["iterations"] for s in st])
+        cyc[solver] = [s["restarts"] for s in st]
+    assert cyc["mixed_f16"] == cyc["mixed_f32"], cyc
+    assert np.abs(its["mixed_f16"] - its["mixed_f32"]).max() <= 3, its
+    assert its["mixed_f16"].sum() <= 1.05 * its["mixed_f32"].sum(), its
