@@ -72,9 +72,10 @@ def test_free_field_closed_forms(dims, m0):
     assert np.allclose(np.sort(sv), exact.free_field_singular_values(dims, m0), atol=1e-12)
 
 
-def test_free_field_published_4x4x4x4_value():
-    # value fixed by the closed form and dense LU together (both in test above);
-    # here the 4^4, m0 = -0.4 numbers are pinned to 11 digits
+def test_free_field_4x4x4x4_regression_values():
+    # derived values, not published ones: the closed forms, checked against dense
+    # LU in the test above, evaluated at 4^4, m0 = -0.4 and kept to 11 digits so a
+    # later change of the closed-form code shows up here
     assert abs(exact.free_field_z4_variance((4, 4, 4, 4), -0.4) - 219.02256161327) < 1e-9
     assert abs(exact.free_field_trace((4, 4, 4, 4), -0.4) - 747.17054921780) < 1e-9
 
